@@ -1,0 +1,156 @@
+"""Seeded synthetic workloads shared by the CUDA path's tests, the bench and the oracle.
+
+This module only draws random inputs: per-cell density fields (in lexicographic
+order, x fastest), zero-mean right-hand sides and seeded network weights.  It
+holds none of the method's arithmetic (no ordering, no assembly, no
+preconditioner), so importing it on either side couples nothing but the data.
+
+Workload shapes follow the multiphase Poisson benchmark of Supp. D (density
+contrast between a light phase rho=1 and heavy inclusions, b ~ N(0, I) projected
+to zero mean), instantiated with discs (2D) and spheres (3D) instead of the
+paper's rectangular barriers.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+__all__ = [
+    "grid_centres", "density_discs", "density_spheres", "rhs", "frame",
+    "FRAMES", "batch_mixed_dims", "network_weights",
+]
+
+
+def grid_centres(dims):
+    """Cell-centre coordinates (x, y[, z]) for a lexicographic grid, x fastest."""
+    axes = [np.arange(n, dtype=np.float64) + 0.5 for n in dims]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    # meshgrid with indexing='ij' gives shape (nx, ny[, nz]); lexicographic with x
+    # fastest is Fortran order of that array.
+    return [m.ravel(order="F") for m in mesh]
+
+
+def density_discs(seed, dims=(32, 32), n_discs=1, r=(8.0, 8.0), rho_heavy=10.0,
+                  centre_margin=True):
+    """2D density: 1 outside, ``rho_heavy`` inside the union of ``n_discs`` discs.
+
+    Radii are uniform in [r[0], r[1]] (a single value when equal); centres are
+    uniform in [r, W - r] x [r, H - r] when ``centre_margin`` else in the box.
+    A cell is heavy iff its centre lies within distance r of a disc centre
+    (comparison in float64).
+    """
+    rng = np.random.default_rng(seed)
+    cx, cy = grid_centres(dims)
+    heavy = np.zeros(cx.shape, dtype=bool)
+    for _ in range(n_discs):
+        rad = float(rng.uniform(r[0], r[1])) if r[1] > r[0] else float(r[0])
+        lo = rad if centre_margin else 0.0
+        px = rng.uniform(lo, dims[0] - lo)
+        py = rng.uniform(lo, dims[1] - lo)
+        heavy |= (cx - px) ** 2 + (cy - py) ** 2 <= rad * rad
+    rho = np.ones(cx.shape, dtype=np.float64)
+    rho[heavy] = rho_heavy
+    return rho
+
+
+def density_spheres(seed, dims=(32, 16, 16), n_range=(5, 12), r=(2.0, 6.0),
+                    rho_heavy=100.0):
+    """3D density: 1 outside, ``rho_heavy`` inside the union of n spheres.
+
+    n is uniform in {n_range[0], ..., n_range[1]}; radii uniform in [r0, r1];
+    centres uniform in the box.  ``rho_heavy`` may be the string "loguniform"
+    to draw the contrast log-uniformly in [1, 100] for this frame.
+    """
+    rng = np.random.default_rng(seed)
+    if isinstance(rho_heavy, str):
+        rho_heavy = float(math.exp(rng.uniform(0.0, math.log(100.0))))
+    c = grid_centres(dims)
+    heavy = np.zeros(c[0].shape, dtype=bool)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    for _ in range(n):
+        rad = float(rng.uniform(r[0], r[1]))
+        ctr = [rng.uniform(0.0, d) for d in dims]
+        d2 = sum((c[a] - ctr[a]) ** 2 for a in range(len(dims)))
+        heavy |= d2 <= rad * rad
+    rho = np.ones(c[0].shape, dtype=np.float64)
+    rho[heavy] = rho_heavy
+    return rho
+
+
+def rhs(seed, n):
+    """b ~ N(0, I) of length n, projected onto the complement of the constant
+    vector (Supp. D, right-hand side).  Drawn directly in solver order."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xB]))
+    b = rng.standard_normal(n)
+    return b - b.mean()
+
+
+# Named frame families.  Each maps a seed to (dims, rho, b, hyper-parameters).
+FRAMES = {
+    # one disc of contrast 10 in a 32x32 square: the plain SVD-H workload
+    "disc2d_1024": dict(dims=(32, 32), leaf=64, rank=16,
+                        gen=lambda s: density_discs(s, (32, 32), 1, (8.0, 8.0), 10.0)),
+    # 5-12 spheres of contrast 100 in a 32x16x16 box: the learned-inference workload
+    "spheres3d_8192": dict(dims=(32, 16, 16), leaf=64, rank=16,
+                           gen=lambda s: density_spheres(s, (32, 16, 16))),
+    # training systems: 16^3 boxes, contrast log-uniform in [1, 100]
+    "spheres3d_4096_lu": dict(dims=(16, 16, 16), leaf=64, rank=16,
+                              gen=lambda s: density_spheres(s, (16, 16, 16),
+                                                            rho_heavy="loguniform")),
+    # 20 discs of contrast 100 in a 128x128 square: the precision sweep
+    "discs2d_16384": dict(dims=(128, 128), leaf=64, rank=32,
+                          gen=lambda s: density_discs(s, (128, 128), 20, (2.0, 8.0),
+                                                      100.0, centre_margin=False)),
+}
+
+
+def frame(family, seed):
+    """Return dict(dims, rho, b, leaf, rank) for one seeded frame of ``family``."""
+    f = FRAMES[family]
+    rho = f["gen"](seed)
+    n = int(np.prod(f["dims"]))
+    return dict(dims=tuple(f["dims"]), rho=rho, b=rhs(seed, n),
+                leaf=f["leaf"], rank=f["rank"])
+
+
+_MIXED_2D = {1024: (32, 32), 2048: (64, 32), 4096: (64, 64), 8192: (128, 64),
+             16384: (128, 128)}
+_MIXED_3D = {1024: (16, 8, 8), 2048: (16, 16, 8), 4096: (16, 16, 16),
+             8192: (32, 16, 16), 16384: (32, 32, 16)}
+
+
+def batch_mixed_dims(seed, count=64):
+    """Grid shapes of a ragged batch: N uniform over {1024, ..., 16384},
+    2D and 3D alternating by system index."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA7C]))
+    sizes = rng.choice(sorted(_MIXED_2D), size=count)
+    return [(_MIXED_2D if i % 2 == 0 else _MIXED_3D)[int(n)] for i, n in enumerate(sizes)]
+
+
+def density_for_dims(seed, dims, rho_heavy=100.0):
+    """1:rho_heavy density for an arbitrary grid: spheres (3D) or discs (2D)."""
+    if len(dims) == 3:
+        return density_spheres(seed, dims, rho_heavy=rho_heavy)
+    n = max(1, (dims[0] * dims[1]) // 800)
+    return density_discs(seed, dims, n, (2.0, 8.0), rho_heavy, centre_margin=False)
+
+
+def network_weights(seed, shapes, init):
+    """Seeded parameter draw for a flat weight blob.
+
+    ``shapes`` is an ordered list of (name, shape); ``init`` maps a name to one of
+    ("normal", std), ("const", value).  Normal draws are truncated at 2 std.
+    Returns a float32 vector with the parameters concatenated in order.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x3E7]))
+    parts = []
+    for name, shape in shapes:
+        kind, val = init(name)
+        size = int(np.prod(shape))
+        if kind == "normal":
+            x = rng.standard_normal(size)
+            x = np.clip(x, -2.0, 2.0) * val
+        else:
+            x = np.full(size, val, dtype=np.float64)
+        parts.append(x.astype(np.float32))
+    return np.concatenate(parts) if parts else np.zeros(0, np.float32)
