@@ -1,0 +1,189 @@
+/*
+ * hmpcg -- per-frame PCG with a hierarchical (weak-admissibility H-matrix)
+ * preconditioner whose factors a hierarchical transformer infers from A.
+ *
+ * C ABI.  Every pointer argument is a plain device pointer unless marked
+ * "host".  Streams are passed as `void*` holding a cudaStream_t (NULL = the
+ * legacy default stream).  All calls are asynchronous on that stream except
+ * where a host output is written, which synchronises the stream first.
+ *
+ * Return value: an hmpcg_status.  0 = OK; >0 = result written but flagged;
+ * <0 = error, outputs unspecified.  Errors never abort the process.
+ *
+ * Ownership: the caller owns every vector, system and factor buffer.  An
+ * hmpcg_ctx owns network weights, optimiser state, and the scratch buffers of
+ * the solver and the network, all allocated by hmpcg_create for the maximum
+ * sizes it is given.  hmpcg_apply and hmpcg_solve never allocate.
+ *
+ * Threading: one context per stream at a time.
+ */
+#ifndef HMPCG_H
+#define HMPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMPCG_OK = 0,
+  HMPCG_NOT_CONVERGED = 1,   /* max_iter reached; x and info written            */
+  HMPCG_E_INVALID = -1,      /* NULL pointer or bad enum / option               */
+  HMPCG_E_SHAPE = -2,        /* extents not powers of two, N % leaf, sizes > max */
+  HMPCG_E_CUDA = -3,         /* a CUDA call failed                              */
+  HMPCG_E_BREAKDOWN = -4,    /* p.Ap <= 0 or r.z <= 0: M or A not SPD in practice */
+  HMPCG_E_NAN = -5,          /* a NaN / Inf reached the PCG scalars             */
+  HMPCG_E_TIMEOUT = -6,      /* a bounded device-side wait gave up              */
+  HMPCG_E_NOMEM = -7         /* hmpcg_create could not allocate                 */
+} hmpcg_status;
+
+typedef enum { HMPCG_F32 = 0, HMPCG_BF16 = 1, HMPCG_FP8E4M3 = 2 } hmpcg_dtype;
+
+typedef enum {
+  HMPCG_PRE_NONE = 0,     /* plain CG                                         */
+  HMPCG_PRE_JACOBI = 1,   /* M = diag(A)^-1                                   */
+  HMPCG_PRE_SVDH = 2,     /* packed "svdh" layout (dense leaves, per-level bridges) */
+  HMPCG_PRE_LEARNED = 3   /* packed "learned" layout (F F^T leaves, U~ B V~^T tiles, gate) */
+} hmpcg_precond;
+
+typedef enum { HMPCG_BC_DIRICHLET = 0, HMPCG_BC_NEUMANN = 1 } hmpcg_bc;
+typedef enum { HMPCG_FACE_INV_RHO = 0, HMPCG_FACE_RHO = 1 } hmpcg_face;
+
+/* Sizes a context is built for, and the network's hyper-parameters. */
+typedef struct {
+  int64_t max_n;       /* largest system (unknowns) any call will see            */
+  int32_t max_batch;   /* largest number of systems in one train/infer batch      */
+  int32_t max_nrhs;    /* largest nrhs for hmpcg_apply                            */
+  int32_t leaf;        /* L, leaf size (power of two)                             */
+  int32_t rank;        /* r = L_s, coarse tokens per tile (L % r == 0)            */
+  int32_t d_model;     /* d (multiple of 64)                                      */
+  int32_t n_layers;    /* n_l                                                     */
+  int32_t n_heads;     /* h; d / h must be 32                                     */
+  int32_t d_mlp;       /* FFN hidden width (multiple of 64)                       */
+} hmpcg_config;
+
+/*
+ * An assembled system in Morton order (Supp. D "Grid and ordering"; Sec. 7.1).
+ * Every array is caller-owned device memory of n elements; hmpcg_system_layout
+ * carves them out of one buffer of hmpcg_system_bytes bytes.
+ * A_ii = diag[i];  A_ij = -wplus[a][i] for the +a face neighbour j of cell i.
+ */
+typedef struct {
+  int32_t ndim;        /* 2 or 3                                    */
+  int32_t dims[3];     /* extents, x fastest; powers of two          */
+  int64_t n;           /* dims product                               */
+  double* diag;        /* FP64 canonical operator                    */
+  double* wplus[3];
+  float* diag32;       /* FP32 mirror used inside the PCG iteration  */
+  float* wplus32[3];
+  double* rho;         /* density, Morton order                      */
+  int32_t* perm;       /* perm[m] = lexicographic index of Morton cell m */
+} hmpcg_system;
+
+/* Packed preconditioner factors (Sec. 4.4; Supp. B "Apply-path tensor layout").
+ * learned: [F (K L L)][B (M_H r r)][U~ (N r)][V~ (N r)][g (N)], g_i = lambda_i/diag(A)_i
+ * svdh:    [G (K L L)][Sigma (M_H r r)][W (levels N r)]
+ * Row-major blocks; K = N/L, M_H = K-1, tiles in heap order.  For FP8 each
+ * block has one FP32 scale (value = stored * scale), laid out
+ * [K leaf][M_H core][nslot K bridge][K gate], nslot = 2 (learned) or levels. */
+typedef struct {
+  int32_t kind;        /* hmpcg_precond                         */
+  int32_t dtype;       /* hmpcg_dtype of `packed`               */
+  int32_t leaf;
+  int32_t rank;
+  int64_t n;
+  const void* packed;
+  const float* scales; /* FP8 only, else NULL                   */
+} hmpcg_factors;
+
+typedef struct {
+  double rtol;            /* stop when ||r_k|| / ||r_0|| <= rtol (Supp. A)     */
+  int32_t max_iter;       /* <= 0: 10 N                                       */
+  int32_t recompute_every;/* true-residual replacement period, 0 = never       */
+} hmpcg_solve_opts;
+
+typedef struct {
+  int32_t iters;          /* number of A p products                           */
+  int32_t status;         /* hmpcg_status of the solve                        */
+  double rel_res_true;    /* ||b - A x||_2 / ||b||_2, FP64, at exit           */
+  float ms_solve;         /* device time of the solve (CUDA events)           */
+} hmpcg_solve_info;
+
+/* ------------------------------------------------------------------ context */
+/* Create a context.  `weights` (host, may be NULL for a context that only
+ * solves) holds hmpcg_weight_count(cfg) floats in the documented order.
+ * Allocates every scratch buffer for cfg's maxima. */
+int hmpcg_create(void** ctx_out, const hmpcg_config* cfg, const float* weights,
+                 int64_t n_weights, void* stream);
+int hmpcg_destroy(void* ctx);
+int64_t hmpcg_weight_count(const hmpcg_config* cfg);
+const char* hmpcg_status_string(int status);
+
+/* ------------------------------------------------------------------ systems */
+/* Bytes of one system buffer for the given grid (ndim 2 or 3). */
+int64_t hmpcg_system_bytes(int32_t ndim, const int32_t* dims);
+/* Fill `sys` with pointers into `base` (device, >= hmpcg_system_bytes bytes,
+ * 256-byte aligned). */
+int hmpcg_system_layout(int32_t ndim, const int32_t* dims, void* base, hmpcg_system* sys);
+
+/* Assemble A from a density field (Supp. D "Operator assembly"; Sec. 7.1):
+ * rho_lex: device FP64, lexicographic (x fastest).  Writes every array of
+ * `sys` (Morton order).  w_ij = 2/(rho_i+rho_j) (HMPCG_FACE_INV_RHO) or
+ * 2 rho_i rho_j/(rho_i+rho_j) (HMPCG_FACE_RHO); Dirichlet ghost faces add
+ * 1/rho_i.  Integer outputs and FP64 arrays are exact (IEEE operations in a
+ * fixed order). */
+int hmpcg_assemble(const double* rho_lex, const hmpcg_system* sys, int32_t bc,
+                   int32_t face, void* stream);
+
+/* y = A x with the FP32 mirror (the inner-loop SpMV, Sec. 5 (iii)). */
+int hmpcg_spmv(const hmpcg_system* sys, const float* x, float* y, void* stream);
+
+/* ------------------------------------------------------------------ apply / solve */
+/* z = M r (Sec. 5 stages (i)-(ii); Supp. B explicit equations).  r and z are
+ * FP32, node-major [n][nrhs].  Uses ctx scratch; no allocation. */
+int hmpcg_apply(void* ctx, const hmpcg_factors* f, const float* r, float* z,
+                int32_t nrhs, void* stream);
+
+/* PCG (Sec. 5 "Single-graph capture"; Sec. 6.3; Supp. G) on `sys` with
+ * preconditioner `f` (NULL or kind NONE/JACOBI need no factors).  b, x: FP64
+ * device vectors (x is written; the start is x0 = 0).  Vectors r, z, p, q
+ * are FP32; every dot product, alpha, beta, the stop test and the periodic
+ * true-residual replacement are FP64.  The whole loop runs in one persistent
+ * cooperative kernel with a device-side stop test.  If `info` (host) is
+ * non-NULL the stream is synchronised and info written; the return value is
+ * then info->status.  No allocation. */
+int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f,
+                const double* b, double* x, const hmpcg_solve_opts* opts,
+                hmpcg_solve_info* info, void* stream);
+
+/* ------------------------------------------------------------------ network */
+/* Infer the learned factors of `nsys` systems (Sec. 4; Supp. B): encoder ->
+ * diagonal and off-diagonal attention stacks with highways -> decoder heads ->
+ * packed tensor.  `packed` holds nsys consecutive packed vectors of width
+ * hmpcg_packed_width(n, leaf, rank, HMPCG_PRE_LEARNED), element type `dtype`;
+ * all systems have the same grid. */
+int hmpcg_infer_factors(void* ctx, const hmpcg_system* systems, int32_t nsys,
+                        void* packed, int32_t dtype, float* scales, void* stream);
+
+int64_t hmpcg_packed_width(int64_t n, int32_t leaf, int32_t rank, int32_t kind);
+
+/* One optimiser step of the cosine-Hutchinson objective (Sec. 6.1 Eq. 7;
+ * Supp. C): n_probes Rademacher probes per system drawn from SplitMix64 keyed
+ * by (step_seed, system); W = A Z; Y = M W; loss = mean over systems of
+ * 1 - <Z, Y>_F / (||Z||_F ||Y||_F); backward through the apply and the
+ * network; global-norm clip to 1; AdamW (beta 0.9/0.999, eps 1e-8, wd 1e-4).
+ * If loss_out (host) is non-NULL the stream is synchronised and the mean loss
+ * written. */
+int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys,
+                     int32_t n_probes, float lr, uint64_t step_seed,
+                     float* loss_out, void* stream);
+
+/* Copy the context's FP32 master weights to `weights` (host, count floats). */
+int hmpcg_get_weights(void* ctx, float* weights, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMPCG_H */

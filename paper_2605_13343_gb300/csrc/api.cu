@@ -1,0 +1,232 @@
+// The C ABI of libhmpcg (include/hmpcg.h): context, systems, apply, solve.
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include "ctx.cuh"
+
+namespace hm {
+int solve_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* b,
+                   double* x, const hmpcg_solve_opts* o, cudaStream_t st, int chunk_override);
+int apply_dispatch(Ctx* c, const hmpcg_factors* f, const float* r, float* z, cudaStream_t st);
+int assemble_launch(const double* rho, const hmpcg_system* sys, int bc, int face, cudaStream_t st);
+int spmv_launch(const hmpcg_system* sys, const float* x, float* y, cudaStream_t st);
+int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st);
+void net_destroy(Ctx* c);
+int64_t net_weight_count(const hmpcg_config* cfg);
+int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int dtype, float* scales,
+              cudaStream_t st);
+int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int n_probes, float lr,
+                   uint64_t seed, float* loss_out, cudaStream_t st);
+int net_get_weights(Ctx* c, float* w, int64_t count);
+}  // namespace hm
+
+using namespace hm;
+
+static bool valid_grid(int32_t ndim, const int32_t* dims) {
+  if (ndim < 1 || ndim > 3 || !dims) return false;
+  int64_t n = 1;
+  for (int a = 0; a < ndim; ++a) {
+    if (dims[a] < 1 || (dims[a] & (dims[a] - 1))) return false;
+    n *= dims[a];
+  }
+  return n <= (int64_t(1) << 30);
+}
+
+static int chunk_from_env() {
+  const char* e = getenv("HMPCG_PCG_CHUNK");
+  return e ? atoi(e) : 0;
+}
+
+extern "C" {
+
+const char* hmpcg_status_string(int s) {
+  switch (s) {
+    case HMPCG_OK: return "ok";
+    case HMPCG_NOT_CONVERGED: return "not converged (max_iter reached)";
+    case HMPCG_E_INVALID: return "invalid argument";
+    case HMPCG_E_SHAPE: return "unsupported shape";
+    case HMPCG_E_CUDA: return "CUDA error";
+    case HMPCG_E_BREAKDOWN: return "PCG breakdown (p.Ap <= 0 or r.z <= 0)";
+    case HMPCG_E_NAN: return "NaN in PCG scalars";
+    case HMPCG_E_TIMEOUT: return "device-side wait timed out";
+    case HMPCG_E_NOMEM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+int64_t hmpcg_packed_width(int64_t n, int32_t leaf, int32_t rank, int32_t kind) {
+  if (leaf <= 0 || rank <= 0 || n % leaf) return -1;
+  const int64_t k = n / leaf;
+  const int64_t base = k * leaf * leaf + (k - 1) * rank * rank;
+  if (kind == HMPCG_PRE_LEARNED) return base + 2 * n * rank + n;
+  if (kind == HMPCG_PRE_SVDH) return base + (int64_t)levels_of(k) * n * rank;
+  return -1;
+}
+
+int64_t hmpcg_weight_count(const hmpcg_config* cfg) { return cfg ? net_weight_count(cfg) : -1; }
+
+int64_t hmpcg_system_bytes(int32_t ndim, const int32_t* dims) {
+  if (!valid_grid(ndim, dims)) return -1;
+  int64_t n = 1;
+  for (int a = 0; a < ndim; ++a) n *= dims[a];
+  auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+  return 4 * al(8 * n) + 4 * al(4 * n) + al(8 * n) + al(4 * n);
+}
+
+int hmpcg_system_layout(int32_t ndim, const int32_t* dims, void* base, hmpcg_system* sys) {
+  if (!valid_grid(ndim, dims) || !base || !sys) return HMPCG_E_INVALID;
+  if (reinterpret_cast<uintptr_t>(base) % 256) return HMPCG_E_INVALID;
+  int64_t n = 1;
+  for (int a = 0; a < ndim; ++a) n *= dims[a];
+  auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+  char* p = static_cast<char*>(base);
+  memset(sys, 0, sizeof(*sys));
+  sys->ndim = ndim;
+  for (int a = 0; a < 3; ++a) sys->dims[a] = a < ndim ? dims[a] : 1;
+  sys->n = n;
+  sys->diag = reinterpret_cast<double*>(p); p += al(8 * n);
+  for (int a = 0; a < 3; ++a) { sys->wplus[a] = reinterpret_cast<double*>(p); p += al(8 * n); }
+  sys->diag32 = reinterpret_cast<float*>(p); p += al(4 * n);
+  for (int a = 0; a < 3; ++a) { sys->wplus32[a] = reinterpret_cast<float*>(p); p += al(4 * n); }
+  sys->rho = reinterpret_cast<double*>(p); p += al(8 * n);
+  sys->perm = reinterpret_cast<int32_t*>(p);
+  return HMPCG_OK;
+}
+
+int hmpcg_assemble(const double* rho_lex, const hmpcg_system* sys, int32_t bc, int32_t face,
+                   void* stream) {
+  if (!rho_lex || !sys || !sys->diag) return HMPCG_E_INVALID;
+  if (!valid_grid(sys->ndim, sys->dims)) return HMPCG_E_SHAPE;
+  if ((bc != HMPCG_BC_DIRICHLET && bc != HMPCG_BC_NEUMANN) ||
+      (face != HMPCG_FACE_INV_RHO && face != HMPCG_FACE_RHO))
+    return HMPCG_E_INVALID;
+  return assemble_launch(rho_lex, sys, bc, face, (cudaStream_t)stream);
+}
+
+int hmpcg_spmv(const hmpcg_system* sys, const float* x, float* y, void* stream) {
+  if (!sys || !x || !y) return HMPCG_E_INVALID;
+  return spmv_launch(sys, x, y, (cudaStream_t)stream);
+}
+
+int hmpcg_create(void** out, const hmpcg_config* cfg, const float* weights, int64_t n_weights,
+                 void* stream) {
+  if (!out || !cfg) return HMPCG_E_INVALID;
+  *out = nullptr;
+  if (cfg->max_n < 2 || cfg->leaf <= 0 || cfg->rank <= 0) return HMPCG_E_INVALID;
+  Ctx* c = new Ctx();
+  c->cfg = *cfg;
+  c->max_n = cfg->max_n;
+  c->max_nrhs = std::max(1, cfg->max_nrhs);
+  c->levels_max = std::max(1, levels_of(std::max<int64_t>(2, cfg->max_n / 8)));
+  c->net = nullptr;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 256)) != cudaSuccess) return nullptr;
+    c->allocs.push_back(p);
+    return p;
+  };
+  const size_t n = (size_t)cfg->max_n;
+  const size_t nr = n * c->max_nrhs;
+  Scratch& s = c->s;
+  s.r = (float*)alloc(4 * nr); s.z = (float*)alloc(4 * nr); s.q = (float*)alloc(4 * nr);
+  s.p0 = (float*)alloc(4 * nr); s.p1 = (float*)alloc(4 * nr); s.ydiag = (float*)alloc(4 * nr);
+  // bridge restrictions: nslot * K * r <= levels * N;  couplings: 2 (K-1) r <= 2 N
+  const int64_t widen = std::max(1, (cfg->rank + cfg->leaf - 1) / cfg->leaf);  // rank > leaf (svdh)
+  c->uhat_cap = (int64_t)nr * std::max(2, c->levels_max) * widen;
+  c->tcoup_cap = 2 * (int64_t)nr * widen;
+  s.uhat = (float*)alloc(4 * (size_t)c->uhat_cap);
+  s.tcoup = (float*)alloc(4 * (size_t)c->tcoup_cap);
+  s.x2 = (double*)alloc(8 * n);
+  s.part = (double*)alloc(8 * 4 * kMaxGrid);
+  s.counter = (unsigned*)alloc(256);
+  s.st = (DevStatus*)alloc(sizeof(DevStatus));
+  bool ok = s.r && s.z && s.q && s.p0 && s.p1 && s.ydiag && s.uhat && s.tcoup && s.x2 && s.part &&
+            s.counter && s.st;
+  ok = ok && cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+  if (!ok) { hmpcg_destroy(c); return HMPCG_E_NOMEM; }
+  if (weights || cfg->d_model > 0) {
+    int rc = net_create(c, weights, n_weights, (cudaStream_t)stream);
+    if (rc) { hmpcg_destroy(c); return rc; }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { hmpcg_destroy(c); return HMPCG_E_CUDA; }
+  *out = c;
+  return HMPCG_OK;
+}
+
+int hmpcg_destroy(void* ctx) {
+  if (!ctx) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  cudaDeviceSynchronize();
+  net_destroy(c);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+  return HMPCG_OK;
+}
+
+int hmpcg_apply(void* ctx, const hmpcg_factors* f, const float* r, float* z, int32_t nrhs,
+                void* stream) {
+  if (!ctx || !f || !r || !z || !f->packed) return HMPCG_E_INVALID;
+  if (nrhs != 1) return HMPCG_E_SHAPE;
+  if (f->kind != HMPCG_PRE_SVDH && f->kind != HMPCG_PRE_LEARNED) return HMPCG_E_INVALID;
+  return apply_dispatch(static_cast<Ctx*>(ctx), f, r, z, (cudaStream_t)stream);
+}
+
+int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f, const double* b,
+                double* x, const hmpcg_solve_opts* opts, hmpcg_solve_info* info, void* stream) {
+  if (!ctx || !sys || !b || !x) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (sys->n > c->max_n) return HMPCG_E_SHAPE;
+  if (opts && !(opts->rtol >= 0.0)) return HMPCG_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (info) HM_CUDA(cudaEventRecord(c->ev0, st));
+  int rc = solve_dispatch(c, sys, f, b, x, opts, st, chunk_from_env());
+  if (rc) return rc;
+  if (!info) return HMPCG_OK;
+  HM_CUDA(cudaEventRecord(c->ev1, st));
+  DevStatus ds;
+  HM_CUDA(cudaMemcpyAsync(&ds, c->s.st, sizeof(ds), cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  info->ms_solve = ms;
+  if (ds.err) {
+    info->iters = ds.iters;
+    info->status = ds.err;
+    info->rel_res_true = -1.0;
+    return ds.err;
+  }
+  info->iters = ds.iters;
+  info->status = ds.status;
+  info->rel_res_true = ds.rel_res;
+  return ds.status;
+}
+
+int hmpcg_infer_factors(void* ctx, const hmpcg_system* systems, int32_t nsys, void* packed,
+                        int32_t dtype, float* scales, void* stream) {
+  if (!ctx || !systems || nsys <= 0 || !packed) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net) return HMPCG_E_INVALID;
+  return net_infer(c, systems, nsys, packed, dtype, scales, (cudaStream_t)stream);
+}
+
+int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys, int32_t n_probes,
+                     float lr, uint64_t step_seed, float* loss_out, void* stream) {
+  if (!ctx || !systems || nsys <= 0 || n_probes <= 0) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net) return HMPCG_E_INVALID;
+  return net_train_step(c, systems, nsys, n_probes, lr, step_seed, loss_out, (cudaStream_t)stream);
+}
+
+int hmpcg_get_weights(void* ctx, float* w, int64_t count) {
+  if (!ctx || !w) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net) return HMPCG_E_INVALID;
+  return net_get_weights(c, w, count);
+}
+
+}  // extern "C"

@@ -131,3 +131,19 @@ def test_svdh_eckart_young_and_apply():
     x = np.random.default_rng(5).standard_normal(256)
     assert np.allclose(hmatrix.apply(f, x), m @ x, atol=1e-12)
     assert np.array_equal(m, m.T)
+
+
+def test_svdh_leaf_modes_definiteness_on_disc_frame():
+    # With exact block inverses (A_kk)^-1 as leaves and rank-16 tiles the assembled M of the
+    # 32x32 disc frame is indefinite; with (A^-1)_kk leaves it is SPD.  M-matrix theory gives
+    # (A^-1)_kk >= (A_kk)^-1 entrywise, which is what the first mode drops.
+    fr = inputs.frame("disc2d_1024", 0)
+    ref = grid.assemble(fr["rho"], fr["dims"])
+    ad = grid.dense_matrix(ref)
+    f1 = hmatrix.svdh_factors(ad, 64, 16, leaves="block_inverse")
+    f2 = hmatrix.svdh_factors(ad, 64, 16, leaves="inverse_block")
+    assert np.linalg.eigvalsh(hmatrix.dense_m(f1)).min() < 0
+    assert np.linalg.eigvalsh(hmatrix.dense_m(f2)).min() > 0
+    for b in range(16):
+        s = slice(b * 64, (b + 1) * 64)
+        assert (f2["leafblk"][b] - f1["leafblk"][b] >= -1e-12).all()
