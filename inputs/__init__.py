@@ -17,7 +17,7 @@ import numpy as np
 
 __all__ = [
     "grid_centres", "density_discs", "density_spheres", "rhs", "frame",
-    "FRAMES", "batch_mixed_dims", "network_weights",
+    "FRAMES", "batch_mixed_dims", "density_for_dims", "network_layout", "network_blob",
 ]
 
 
@@ -135,22 +135,68 @@ def density_for_dims(seed, dims, rho_heavy=100.0):
     return density_discs(seed, dims, n, (2.0, 8.0), rho_heavy, centre_margin=False)
 
 
-def network_weights(seed, shapes, init):
-    """Seeded parameter draw for a flat weight blob.
+# ---------------------------------------------------------------- network weight layout
+# The flat weight blob is an interface shared by both sides (like the packed
+# factor layout): an ordered list of named float32 tensors.  Linear layers are
+# stored as (out, in) followed by their bias.
+N_NODE_FEATURES = 8
+N_GLOBAL_FEATURES = 12
+EDGE_HIDDEN = 32
 
-    ``shapes`` is an ordered list of (name, shape); ``init`` maps a name to one of
-    ("normal", std), ("const", value).  Normal draws are truncated at 2 std.
-    Returns a float32 vector with the parameters concatenated in order.
-    """
+
+def network_layout(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16):
+    f_in = N_NODE_FEATURES + N_GLOBAL_FEATURES
+    out = [("enc1.w", (d, f_in)), ("enc1.b", (d,)), ("enc2.w", (d, d)), ("enc2.b", (d,))]
+    for g in range(2):
+        out += [(f"gcn{g}.w", (d, d)), (f"gcn{g}.b", (d,))]
+    out += [("pool.w", (d, 2 * d)), ("pool.b", (d,))]
+    for s in ("diag", "off"):
+        for l in range(n_layers):
+            p = f"{s}{l}."
+            out += [(p + "ln1.g", (d,)), (p + "ln1.b", (d,)),
+                    (p + "qkv.w", (3 * d, d)), (p + "qkv.b", (3 * d,)),
+                    (p + "out.w", (d, d)), (p + "out.b", (d,)),
+                    (p + "ln2.g", (d,)), (p + "ln2.b", (d,)),
+                    (p + "ffn1.w", (d_mlp, 4 * d)), (p + "ffn1.b", (d_mlp,)),
+                    (p + "ffn2.w", (d, d_mlp)), (p + "ffn2.b", (d,)),
+                    (p + "edge1.w", (EDGE_HIDDEN, 4)), (p + "edge1.b", (EDGE_HIDDEN,)),
+                    (p + "edge2.w", (n_heads, EDGE_HIDDEN)), (p + "edge2.b", (n_heads,))]
+        out += [(f"{s}.lnf.g", (d,)), (f"{s}.lnf.b", (d,))]
+    out += [("leaf1.w", (d, d)), ("leaf1.b", (d,)), ("leaf2.w", (leaf, d)), ("leaf2.b", (leaf,)),
+            ("node.w", (2 * rank + 1, d)), ("node.b", (2 * rank + 1,)),
+            ("off.w", (2 * rank, d)), ("off.b", (2 * rank,))]
+    return out
+
+
+def network_init_rule(name):
+    """Seeded init: truncated normal(0, 0.02) weights, zero biases, unit LayerNorm
+    gains; the factor heads start 100x smaller so that M starts near the Jacobi
+    gate; the gate bias starts at log(e - 1) so that softplus gives lambda = 1."""
+    if name.endswith(".g"):
+        return ("const", 1.0)
+    if name == "node.b":
+        return ("gate_bias", math.log(math.e - 1.0))
+    if name.endswith(".b"):
+        return ("const", 0.0)
+    if name in ("leaf2.w", "node.w", "off.w"):
+        return ("normal", 0.02 * 1e-2)
+    return ("normal", 0.02)
+
+
+def network_blob(seed, **cfg):
+    """Flat float32 weight vector for ``network_layout(**cfg)``."""
+    shapes = network_layout(**cfg)
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x3E7]))
     parts = []
     for name, shape in shapes:
-        kind, val = init(name)
+        kind, val = network_init_rule(name)
         size = int(np.prod(shape))
         if kind == "normal":
-            x = rng.standard_normal(size)
-            x = np.clip(x, -2.0, 2.0) * val
+            x = np.clip(rng.standard_normal(size), -2.0, 2.0) * val
+        elif kind == "gate_bias":
+            x = np.zeros(size)
+            x[-1] = val
         else:
-            x = np.full(size, val, dtype=np.float64)
+            x = np.full(size, val)
         parts.append(x.astype(np.float32))
-    return np.concatenate(parts) if parts else np.zeros(0, np.float32)
+    return np.concatenate(parts)
