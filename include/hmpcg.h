@@ -180,6 +180,13 @@ int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys,
                      int32_t n_probes, float lr, uint64_t step_seed,
                      float* loss_out, void* stream);
 
+/* The tensor-core GEMM the network runs on (tcgen05, TMA, TMEM accumulator):
+ * C[M x N] = A[M x K] B[N x K]^T (+ bias[N]) (GELU if act == 1), A and B
+ * row-major BF16 with K contiguous (K % 64 == 0, N % 16 == 0, 16-byte aligned
+ * rows), C row-major FP32.  Exposed for kernel-level tests and measurement. */
+int hmpcg_gemm_bf16(const void* a, const void* b, float* c, int32_t m, int32_t n, int32_t k,
+                    const float* bias, int32_t act, void* stream);
+
 /* Copy the context's FP32 master weights to `weights` (host, count floats). */
 int hmpcg_get_weights(void* ctx, float* weights, int64_t count);
 

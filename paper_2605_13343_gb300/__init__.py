@@ -74,6 +74,8 @@ EXPORTS = {
     "hmpcg_train_step": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_int32, C.c_float,
                                    C.c_uint64, C.POINTER(C.c_float), C.c_void_p]),
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmpcg_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                  C.c_void_p, C.c_int32, C.c_void_p]),
 }
 
 
@@ -284,3 +286,15 @@ def get_weights(ctx, count):
     w = np.empty(count, dtype=np.float32)
     _check(lib().hmpcg_get_weights(ctx.h, w.ctypes.data_as(C.c_void_p), count), "get_weights")
     return w
+
+
+def gemm_bf16(a, b, bias=None, act=0, out=None, stream=None):
+    """hmpcg_gemm_bf16: C = A B^T (+ bias, GELU) on the tcgen05 GEMM; A, B BF16."""
+    assert a.dtype == torch.bfloat16 and b.dtype == torch.bfloat16
+    m, k = a.shape
+    n = b.shape[0]
+    if out is None:
+        out = torch.empty(m, n, dtype=torch.float32, device=a.device)
+    _check(lib().hmpcg_gemm_bf16(_ptr(a), _ptr(b), _ptr(out), m, n, k, _ptr(bias), act, _stream(stream)),
+           "gemm_bf16")
+    return out

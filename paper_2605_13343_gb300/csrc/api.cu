@@ -3,6 +3,7 @@
 #include <cstring>
 #include <algorithm>
 #include "ctx.cuh"
+#include "net.cuh"
 
 namespace hm {
 int solve_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* b,
@@ -220,6 +221,18 @@ int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys, int32
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c->net) return HMPCG_E_INVALID;
   return net_train_step(c, systems, nsys, n_probes, lr, step_seed, loss_out, (cudaStream_t)stream);
+}
+
+int hmpcg_gemm_bf16(const void* a, const void* b, float* c, int32_t m, int32_t n, int32_t k,
+                    const float* bias, int32_t act, void* stream) {
+  if (!a || !b || !c || m < 0 || n < 0 || k < 0 || (act != 0 && act != 1)) return HMPCG_E_INVALID;
+  GemmArgs g;
+  g.A = static_cast<const bf16*>(a); g.lda = k;
+  g.B = static_cast<const bf16*>(b); g.ldb = k;
+  g.M = m; g.N = n; g.K = k;
+  g.ep.bias = bias; g.ep.act = act; g.ep.out32 = c; g.ep.ld32 = n;
+  int rc = gemm_bf16(g, (cudaStream_t)stream);
+  return rc;
 }
 
 int hmpcg_get_weights(void* ctx, float* w, int64_t count) {

@@ -1,0 +1,303 @@
+// BF16 GEMM on the 5th-generation tensor cores: C[M x N] = A[M x K] . B[N x K]^T.
+//
+// One CTA computes a 128 x BN tile.  A TMA producer thread streams 128x64 and
+// BNx64 K-major tiles (128-byte swizzle) into a 4-stage shared-memory ring; one
+// thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM);
+// tcgen05.commit frees ring slots through mbarriers.  Four warps then read the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows) and
+// run the fused epilogue: + bias, GELU, + residual, FP32 / BF16 / transposed BF16
+// stores.  Every mbarrier wait is bounded; a timeout sets an error flag, and the
+// CTA still waits for its MMAs and frees its TMEM before it returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cstdio>
+#include <mutex>
+#include "ctx.cuh"
+#include "net.cuh"
+
+namespace hm {
+
+namespace tc {
+
+HM_INLINE uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+HM_INLINE void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+HM_INLINE void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+HM_INLINE bool mbar_wait(uint32_t bar, uint32_t parity, long limit = (1l << 22)) {
+  for (long i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+HM_INLINE void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 B,
+// 8-row core groups 1024 B apart.
+HM_INLINE uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                          // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+HM_INLINE void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+HM_INLINE void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+HM_INLINE void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+HM_INLINE float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+}  // namespace tc
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const GemmEpi ep, int M, int N, int K) {
+  using namespace tc;
+  constexpr int BM = 128, BK = 64, STAGES = 4;
+  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_done;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int fail_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = K / BK;
+  uint8_t* sa = smem;
+  uint8_t* sb = smem + STAGES * A_BYTES;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    fail_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), ((kb / STAGES) - 1) & 1)) {
+        fail_s = 1;
+        break;
+      }
+      const uint32_t fb = smem_u32(&bar_full[s]);
+      mbar_expect_tx(fb, A_BYTES + B_BYTES);
+      tma_load_2d(smem_u32(sa + s * A_BYTES), &tmA, kb * BK, m0, fb);
+      tma_load_2d(smem_u32(sb + s * B_BYTES), &tmB, kb * BK, n0, fb);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(smem_u32(&bar_full[s]), (kb / STAGES) & 1)) {
+        fail_s = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t ad = sw128_desc(smem_u32(sa + s * A_BYTES));
+      const uint64_t bd = sw128_desc(smem_u32(sb + s * B_BYTES));
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k)
+        mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      mma_commit(smem_u32(&bar_empty[s]));
+    }
+    mma_commit(smem_u32(&bar_done));
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> global
+  const bool done = mbar_wait(smem_u32(&bar_done), 0, 1l << 24);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+  const bool ok = done && !fail_s;
+  for (int c = 0; c < BN; c += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+    const int col = n0 + c;
+    if (!ok || row >= M || col >= N) continue;
+    const int ncol = min(16, N - col);
+    if (ep.bias) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) if (j < ncol) v[j] += ep.bias[col + j];
+    }
+    if (ep.pre16) {
+      __nv_bfloat16* p = ep.pre16 + (size_t)row * ep.ldpre + col;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) if (j < ncol) p[j] = __float2bfloat16_rn(v[j]);
+    }
+    if (ep.act == 1) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = gelu_f(v[j]);
+    }
+    if (ep.resid) {
+      const float* rp = ep.resid + (size_t)row * ep.ldr + col;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) if (j < ncol) v[j] += rp[j];
+    }
+    if (ep.out32) {
+      float* o = ep.out32 + (size_t)row * ep.ld32 + col;
+      if (ncol == 16 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      } else {
+        for (int j = 0; j < ncol; ++j) o[j] = v[j];
+      }
+    }
+    if (ep.out16) {
+      __nv_bfloat16* o = ep.out16 + (size_t)row * ep.ld16 + col;
+      if (ncol == 16 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
+        uint4 pk[2];
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        reinterpret_cast<uint4*>(o)[0] = pk[0];
+        reinterpret_cast<uint4*>(o)[1] = pk[1];
+      } else {
+        for (int j = 0; j < ncol; ++j) o[j] = __float2bfloat16_rn(v[j]);
+      }
+    }
+    if (ep.out16T) {
+      for (int j = 0; j < ncol; ++j) ep.out16T[(size_t)(col + j) * ep.ldT + row] = __float2bfloat16_rn(v[j]);
+    }
+  }
+  if (!ok && threadIdx.x == 0 && ep.err) atomicExch(ep.err, (int)HMPCG_E_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static bool encode_fn() {
+  std::call_once(g_encode_once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  return g_encode != nullptr;
+}
+
+// Row-major BF16 matrix (rows x cols, leading dimension ld elements), box 64 x box_rows.
+static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+  if (!encode_fn()) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) {
+  constexpr int STAGES = 4;
+  const size_t smem = STAGES * (128 * 64 * 2 + BN * 64 * 2) + 1024;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return HMPCG_E_CUDA;
+    attr_set = true;
+  }
+  CUtensorMap mb;
+  if (!make_map(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
+  dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN);
+  gemm_bf16_tc_kernel<BN><<<grid, 128, smem, st>>>(ma, mb, g.ep, g.M, g.N, g.K);
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return HMPCG_OK;
+  if (g.K <= 0 || g.K % 64 || g.N % 16) return HMPCG_E_SHAPE;
+  CUtensorMap ma;
+  if (!make_map(&ma, g.A, g.M, g.K, g.lda, 128)) return HMPCG_E_INVALID;
+  int bn = g.bn;
+  if (bn == 0) bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
+  if (g.N < bn) bn = 64;
+  switch (bn) {
+    case 64: return launch_bn<64>(g, ma, st);
+    case 128: return launch_bn<128>(g, ma, st);
+    case 256: return launch_bn<256>(g, ma, st);
+  }
+  return HMPCG_E_SHAPE;
+}
+
+}  // namespace hm

@@ -1,11 +1,369 @@
-// Hierarchical transformer (Sec. 4; Supp. B): placeholder until the network lands.
-#include "ctx.cuh"
+// Hierarchical transformer forward pass (Sec. 4; Supp. B): encoder + GCN, the
+// diagonal and off-diagonal attention stacks with edge biases and highway
+// buffers, decoder heads and the pack into the learned factor layout.
+//
+// GEMMs run on tcgen05 (gemm_tc.cu); the window attention, LayerNorm, highway
+// scatter/gather, feature and pack kernels are CUDA-core kernels.  Every kernel
+// handles a batch of B systems of one grid; diagonal tokens are ordered
+// (system, node) and off-diagonal tokens (system, tile, coarse token).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include "net.cuh"
+#include "netk.cuh"
+
 namespace hm {
-struct Net {};
-int64_t net_weight_count(const hmpcg_config*) { return 0; }
-int net_create(Ctx* c, const float*, int64_t, cudaStream_t) { c->net = nullptr; return HMPCG_OK; }
-void net_destroy(Ctx* c) { c->net = nullptr; }
-int net_infer(Ctx*, const hmpcg_system*, int, void*, int, float*, cudaStream_t) { return HMPCG_E_INVALID; }
-int net_train_step(Ctx*, const hmpcg_system*, int, int, float, uint64_t, float*, cudaStream_t) { return HMPCG_E_INVALID; }
-int net_get_weights(Ctx*, float*, int64_t) { return HMPCG_E_INVALID; }
+
+// ============================================================================ weights
+WeightOff weight_offsets(const hmpcg_config& c) {
+  WeightOff o;
+  const int64_t d = c.d_model, dm = c.d_mlp, h = c.n_heads, L = c.leaf, r = c.rank;
+  int64_t p = 0, p16 = 0;
+  auto take = [&](int64_t n) {
+    int64_t q = p;
+    o.seg32.push_back(p);
+    o.seg16.push_back(p16);
+    o.segn.push_back(n);
+    p += n;
+    p16 += (n + 63) / 64 * 64;
+    return q;
+  };
+  o.enc1w = take(d * kFeat); o.enc1b = take(d);
+  o.enc2w = take(d * d); o.enc2b = take(d);
+  for (int g = 0; g < 2; ++g) { o.gcnw[g] = take(d * d); o.gcnb[g] = take(d); }
+  o.poolw = take(d * 2 * d); o.poolb = take(d);
+  for (int s = 0; s < 2; ++s) {
+    o.blk[s].resize(c.n_layers);
+    for (int l = 0; l < c.n_layers; ++l) {
+      BlockOff& b = o.blk[s][l];
+      b.ln1g = take(d); b.ln1b = take(d);
+      b.qkvw = take(3 * d * d); b.qkvb = take(3 * d);
+      b.outw = take(d * d); b.outb = take(d);
+      b.ln2g = take(d); b.ln2b = take(d);
+      b.f1w = take(dm * 4 * d); b.f1b = take(dm);
+      b.f2w = take(d * dm); b.f2b = take(d);
+      b.e1w = take(kEdgeHidden * 4); b.e1b = take(kEdgeHidden);
+      b.e2w = take(h * kEdgeHidden); b.e2b = take(h);
+    }
+    o.lnfg[s] = take(d); o.lnfb[s] = take(d);
+  }
+  o.leaf1w = take(d * d); o.leaf1b = take(d);
+  o.leaf2w = take(L * d); o.leaf2b = take(L);
+  o.nodew = take((2 * r + 1) * d); o.nodeb = take(2 * r + 1);
+  o.offw = take(2 * r * d); o.offb = take(2 * r);
+  o.total = p;
+  o.total16 = p16;
+  return o;
 }
+
+int64_t WeightOff::map16(int64_t off32) const {
+  auto it = std::lower_bound(seg32.begin(), seg32.end(), off32);
+  if (it == seg32.end() || *it != off32) return -1;
+  return seg16[it - seg32.begin()];
+}
+
+int64_t net_weight_count(const hmpcg_config* c) {
+  if (c->d_model <= 0) return 0;
+  return weight_offsets(*c).total;
+}
+
+static bool net_shape_ok(const hmpcg_config& c) {
+  return c.d_model % 64 == 0 && c.d_model >= 64 && c.n_heads > 0 && c.d_model / c.n_heads == 32 &&
+         c.d_mlp % 64 == 0 && c.n_layers >= 1 && c.leaf >= 16 && c.leaf <= 64 && (c.leaf & (c.leaf - 1)) == 0 &&
+         c.rank % 16 == 0 && c.leaf % c.rank == 0 && c.rank <= 32 && c.max_batch >= 1 && c.max_batch <= kMaxSys;
+}
+
+// One CTA per weight tensor: FP32 master (dense) -> BF16 copy (padded layout).
+__global__ void cast_bf16_kernel(const float* __restrict__ a, bf16* __restrict__ b, const int64_t* __restrict__ segs,
+                                 int nseg) {
+  const int s = blockIdx.x;
+  if (s >= nseg) return;
+  const int64_t o32 = segs[3 * s], o16 = segs[3 * s + 1], n = segs[3 * s + 2];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[o16 + i] = __float2bfloat16_rn(a[o32 + i]);
+}
+
+void net_refresh_bf16(Net* N, cudaStream_t st) {
+  const int nseg = (int)N->off.seg32.size();
+  cast_bf16_kernel<<<nseg, 256, 0, st>>>(N->w32, N->w16, N->segs, nseg);
+}
+
+void net_destroy(Ctx* c);
+
+int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
+  const hmpcg_config& cf = c->cfg;
+  if (!net_shape_ok(cf)) return HMPCG_E_SHAPE;
+  Net* N = new Net();
+  N->cfg = cf;
+  N->off = weight_offsets(cf);
+  N->nw = N->off.total;
+  if (weights && count != N->nw) { delete N; return HMPCG_E_INVALID; }
+  N->step = 0;
+  bool ok = true;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 256)) != cudaSuccess) { ok = false; return nullptr; }
+    cudaMemsetAsync(p, 0, std::max<size_t>(bytes, 256), st);
+    N->allocs.push_back(p);
+    return p;
+  };
+  const int64_t B = cf.max_batch, n = cf.max_n, d = cf.d_model, dm = cf.d_mlp, h = cf.n_heads;
+  const int64_t L = cf.leaf, r = cf.rank;
+  const int64_t K = n / L, MH = K - 1;
+  const int64_t Td = B * n, To = B * MH * r;
+  N->max_tok_d = (int)Td;
+  N->max_tok_o = (int)To;
+  N->w32 = (float*)alloc(4 * N->nw);
+  N->w16 = (bf16*)alloc(2 * N->off.total16);
+  N->segs = (int64_t*)alloc(8 * 3 * N->off.seg32.size());
+  N->grad = (float*)alloc(4 * N->nw);
+  N->m1 = (float*)alloc(4 * N->nw);
+  N->m2 = (float*)alloc(4 * N->nw);
+  N->feat = (float*)alloc(4 * Td * kFeat);
+  N->gstat = (double*)alloc(8 * B * 12);
+  N->h1 = (bf16*)alloc(2 * Td * d);
+  N->h1pre = (bf16*)alloc(2 * Td * d);
+  N->xenc = (float*)alloc(4 * Td * d);
+  for (int g = 0; g < 3; ++g) N->xg[g] = (float*)alloc(4 * Td * d);
+  for (int g = 0; g < 2; ++g) { N->pm[g] = (bf16*)alloc(2 * Td * d); N->gpre[g] = (bf16*)alloc(2 * Td * d); }
+  N->pooled = (bf16*)alloc(2 * To * 2 * d);
+  N->edesc_off = (float*)alloc(4 * B * MH * r * r * 4);
+  for (int s = 0; s < 2; ++s) {
+    const int64_t T = s == 0 ? Td : To;
+    const int64_t W = s == 0 ? L : r;
+    const int64_t nwin = T / W;
+    N->act[s].resize(cf.n_layers);
+    for (int l = 0; l < cf.n_layers; ++l) {
+      StackAct& a = N->act[s][l];
+      a.x_in = (float*)alloc(4 * T * d);
+      a.mu1 = (float*)alloc(4 * T); a.rs1 = (float*)alloc(4 * T);
+      a.y1 = (bf16*)alloc(2 * T * d);
+      a.qkv = (bf16*)alloc(2 * T * 3 * d);
+      a.o = (bf16*)alloc(2 * T * d);
+      a.lse = (float*)alloc(4 * T * h);
+      a.x_mid = (float*)alloc(4 * T * d);
+      a.mu2 = (float*)alloc(4 * T); a.rs2 = (float*)alloc(4 * T);
+      a.y2f = (float*)alloc(4 * T * d);
+      a.u = (bf16*)alloc(2 * T * 4 * d);
+      a.hpre = (bf16*)alloc(2 * T * dm);
+      a.hact = (bf16*)alloc(2 * T * dm);
+      a.bias = (float*)alloc(4 * nwin * h * W * W);
+    }
+    N->x_final[s] = (float*)alloc(4 * T * d);
+    N->muf[s] = (float*)alloc(4 * T); N->rsf[s] = (float*)alloc(4 * T);
+    N->yf[s] = (bf16*)alloc(2 * T * d);
+  }
+  N->leafh = (bf16*)alloc(2 * Td * d);
+  N->leafhpre = (bf16*)alloc(2 * Td * d);
+  N->frow = (float*)alloc(4 * Td * L);
+  N->nodeo = (float*)alloc(4 * Td * 2 * r);
+  N->gate_logit = (float*)alloc(4 * Td);
+  N->offo = (float*)alloc(4 * To * 2 * r);
+  N->rhw = (float*)alloc(4 * Td * d);
+  N->chw = (float*)alloc(4 * Td * d);
+  N->gmean = (float*)alloc(4 * B * d);
+  N->err = (int*)alloc(256);
+  if (!ok) { c->net = N; net_destroy(c); return HMPCG_E_NOMEM; }
+  if (weights) {
+    if (cudaMemcpyAsync(N->w32, weights, 4 * N->nw, cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
+  }
+  {
+    std::vector<int64_t> segs;
+    for (size_t q = 0; q < N->off.seg32.size(); ++q) {
+      segs.push_back(N->off.seg32[q]);
+      segs.push_back(N->off.seg16[q]);
+      segs.push_back(N->off.segn[q]);
+    }
+    if (cudaMemcpyAsync(N->segs, segs.data(), 8 * segs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
+    if (cudaStreamSynchronize(st) != cudaSuccess) ok = false;
+  }
+  net_refresh_bf16(N, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess || !ok) { c->net = N; net_destroy(c); return HMPCG_E_CUDA; }
+  c->net = N;
+  return HMPCG_OK;
+}
+
+void net_destroy(Ctx* c) {
+  if (!c->net) return;
+  for (void* p : c->net->allocs) cudaFree(p);
+  delete c->net;
+  c->net = nullptr;
+}
+
+int net_get_weights(Ctx* c, float* w, int64_t count) {
+  Net* N = c->net;
+  if (count != N->nw) return HMPCG_E_INVALID;
+  if (cudaMemcpy(w, N->w32, 4 * count, cudaMemcpyDeviceToHost) != cudaSuccess) return HMPCG_E_CUDA;
+  return HMPCG_OK;
+}
+
+// ============================================================================ batch description
+int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, SysBatch& sb) {
+  if (nsys < 1 || nsys > cf.max_batch || nsys > kMaxSys) return HMPCG_E_SHAPE;
+  const hmpcg_system& s0 = systems[0];
+  if (s0.n > cf.max_n || s0.n % cf.leaf) return HMPCG_E_SHAPE;
+  sb.B = nsys;
+  sb.n = (int)s0.n;
+  sb.ndim = s0.ndim;
+  for (int a = 0; a < 3; ++a) sb.dims[a] = s0.dims[a];
+  sb.L = cf.leaf;
+  sb.r = cf.rank;
+  sb.K = sb.n / sb.L;
+  if (sb.K < 2 || (sb.K & (sb.K - 1))) return HMPCG_E_SHAPE;
+  sb.MH = sb.K - 1;
+  sb.levels = levels_of(sb.K);
+  sb.mo = make_morton(s0.ndim, s0.dims);
+  sb.leaf_side = (float)std::round(std::pow((double)sb.L, 1.0 / s0.ndim));
+  for (int b = 0; b < nsys; ++b) {
+    const hmpcg_system& s = systems[b];
+    if (s.n != s0.n || s.ndim != s0.ndim) return HMPCG_E_SHAPE;
+    for (int a = 0; a < 3; ++a) if (s.dims[a] != s0.dims[a]) return HMPCG_E_SHAPE;
+    sb.diag[b] = s.diag;
+    sb.rho[b] = s.rho;
+    for (int a = 0; a < 3; ++a) sb.w[b][a] = s.wplus[a];
+  }
+  return HMPCG_OK;
+}
+
+// ============================================================================ forward
+static int gemm(const bf16* A, int lda, const bf16* Bw, int M, int Nn, int Kk, const GemmEpi& ep, cudaStream_t st) {
+  GemmArgs g;
+  g.A = A; g.lda = lda; g.B = Bw; g.ldb = Kk; g.M = M; g.N = Nn; g.K = Kk; g.ep = ep;
+  return gemm_bf16(g, st);
+}
+
+#define NET_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+
+int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
+  const hmpcg_config& cf = N->cfg;
+  const WeightOff& o = N->off;
+  const int B = sb.B, n = sb.n, d = cf.d_model, h = cf.n_heads, dm = cf.d_mlp;
+  const int L = sb.L, r = sb.r, MH = sb.MH;
+  const int Td = B * n, To = B * MH * r;
+  const float* W = N->w32;
+  const bf16* W16 = N->w16;
+  GemmEpi e;
+  e.err = N->err;
+
+  // ---- features and encoder
+  global_stats_kernel<<<B, 256, 0, st>>>(sb, N->gstat);
+  encoder1_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, N->gstat, W + o.enc1w, W + o.enc1b, d, N->feat, N->h1, N->h1pre);
+  {
+    GemmEpi ep = e; ep.bias = W + o.enc2b; ep.out32 = N->xg[0]; ep.ld32 = d;
+    NET_TRY(gemm(N->h1, d, W16 + o.map16(o.enc2w), Td, d, d, ep, st));
+  }
+  for (int g = 0; g < 2; ++g) {
+    prop_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, N->xg[g], d, N->pm[g]);
+    GemmEpi ep = e; ep.bias = W + o.gcnb[g]; ep.act = 1; ep.resid = N->xg[g]; ep.ldr = d;
+    ep.out32 = N->xg[g + 1]; ep.ld32 = d; ep.pre16 = N->gpre[g]; ep.ldpre = d;
+    NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
+  }
+  const float* xd0 = N->xg[2];
+  pool_kernel<<<(To + 7) / 8, 256, 0, st>>>(sb, xd0, d, N->pooled);
+  edge_desc_off_kernel<<<(B * MH * r * r + 127) / 128, 128, 0, st>>>(sb, N->edesc_off);
+  float* xcur[2];
+  {
+    GemmEpi ep = e; ep.bias = W + o.poolb; ep.out32 = N->act[1][0].x_in; ep.ld32 = d;
+    NET_TRY(gemm(N->pooled, 2 * d, W16 + o.map16(o.poolw), To, d, 2 * d, ep, st));
+  }
+  cudaMemcpyAsync(N->act[0][0].x_in, xd0, sizeof(float) * (size_t)Td * d, cudaMemcpyDeviceToDevice, st);
+
+  for (int l = 0; l < cf.n_layers; ++l) {
+    for (int s = 0; s < 2; ++s) {
+      StackAct& a = N->act[s][l];
+      const BlockOff& bo = o.blk[s][l];
+      const int T = s == 0 ? Td : To;
+      const int Wn = s == 0 ? L : r;
+      const int nwin = T / Wn;
+      if (s == 0)
+        edge_bias_diag_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, st>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
+                                                                            W + bo.e2b, h, a.bias);
+      else
+        edge_bias_off_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, st>>>(sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
+                                                                           W + bo.e2w, W + bo.e2b, h, a.bias);
+      layernorm_kernel<<<(T + 7) / 8, 256, 0, st>>>(a.x_in, W + bo.ln1g, W + bo.ln1b, T, d, a.y1, nullptr, a.mu1, a.rs1);
+      {
+        GemmEpi ep = e; ep.bias = W + bo.qkvb; ep.out16 = a.qkv; ep.ld16 = 3 * d;
+        NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, st));
+      }
+      if (s == 0)
+        attention_kernel<64><<<dim3((T + 127) / 128, h), 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+      else
+        attention_kernel<16><<<dim3((T + 127) / 128, h), 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+      {
+        GemmEpi ep = e; ep.bias = W + bo.outb; ep.resid = a.x_in; ep.ldr = d; ep.out32 = a.x_mid; ep.ld32 = d;
+        NET_TRY(gemm(a.o, d, W16 + o.map16(bo.outw), T, d, d, ep, st));
+      }
+      layernorm_kernel<<<(T + 7) / 8, 256, 0, st>>>(a.x_mid, W + bo.ln2g, W + bo.ln2b, T, d, a.u, a.y2f, a.mu2, a.rs2,
+                                                   4 * d);
+    }
+    // ---- highways (Sec. 4.3) from LN2 outputs of both stacks
+    StackAct& ad = N->act[0][l];
+    StackAct& ao = N->act[1][l];
+    highway_rc_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+    highway_g_kernel<<<dim3(B, d / 32), 256, 0, st>>>(sb, ad.y2f, ao.y2f, d, N->gmean);
+    concat_g_kernel<<<(Td + 7) / 8, 256, 0, st>>>(N->gmean, n, Td, d, ad.u);
+    highway_off_kernel<<<(To + 7) / 8, 256, 0, st>>>(sb, N->rhw, N->chw, N->gmean, d, ao.u);
+    for (int s = 0; s < 2; ++s) {
+      StackAct& a = N->act[s][l];
+      const BlockOff& bo = o.blk[s][l];
+      const int T = s == 0 ? Td : To;
+      float* xout = (l + 1 < cf.n_layers) ? N->act[s][l + 1].x_in : N->x_final[s];
+      {
+        GemmEpi ep = e; ep.bias = W + bo.f1b; ep.act = 1; ep.out16 = a.hact; ep.ld16 = dm; ep.pre16 = a.hpre; ep.ldpre = dm;
+        NET_TRY(gemm(a.u, 4 * d, W16 + o.map16(bo.f1w), T, dm, 4 * d, ep, st));
+      }
+      {
+        GemmEpi ep = e; ep.bias = W + bo.f2b; ep.resid = a.x_mid; ep.ldr = d; ep.out32 = xout; ep.ld32 = d;
+        NET_TRY(gemm(a.hact, dm, W16 + o.map16(bo.f2w), T, d, dm, ep, st));
+      }
+    }
+  }
+  (void)xcur;
+  // ---- final norms and heads
+  for (int s = 0; s < 2; ++s) {
+    const int T = s == 0 ? Td : To;
+    layernorm_kernel<<<(T + 7) / 8, 256, 0, st>>>(N->x_final[s], W + o.lnfg[s], W + o.lnfb[s], T, d, N->yf[s], nullptr,
+                                                 N->muf[s], N->rsf[s]);
+  }
+  {
+    GemmEpi ep = e; ep.bias = W + o.leaf1b; ep.act = 1; ep.out16 = N->leafh; ep.ld16 = d; ep.pre16 = N->leafhpre; ep.ldpre = d;
+    NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.leaf1w), Td, d, d, ep, st));
+  }
+  {
+    GemmEpi ep = e; ep.bias = W + o.leaf2b; ep.out32 = N->frow; ep.ld32 = L;
+    NET_TRY(gemm(N->leafh, d, W16 + o.map16(o.leaf2w), Td, L, d, ep, st));
+  }
+  {
+    GemmEpi ep = e; ep.bias = W + o.nodeb; ep.out32 = N->nodeo; ep.ld32 = 2 * r;
+    NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.nodew), Td, 2 * r, d, ep, st));
+  }
+  gate_logit_kernel<<<(Td + 7) / 8, 256, 0, st>>>(N->yf[0], W + o.nodew + (int64_t)2 * r * d, W + o.nodeb + 2 * r, Td, d,
+                                                 N->gate_logit);
+  {
+    GemmEpi ep = e; ep.bias = W + o.offb; ep.out32 = N->offo; ep.ld32 = 2 * r;
+    NET_TRY(gemm(N->yf[1], d, W16 + o.map16(o.offw), To, 2 * r, d, ep, st));
+  }
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int dtype, float* scales, cudaStream_t st) {
+  Net* N = c->net;
+  SysBatch sb;
+  NET_TRY(make_batch(N->cfg, systems, nsys, sb));
+  if (dtype != HMPCG_F32 && dtype != HMPCG_BF16) return HMPCG_E_INVALID;
+  (void)scales;
+  NET_TRY(net_forward(N, sb, st));
+  const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
+  const int Td = sb.B * sb.n;
+  const int Tt = sb.B * sb.MH;
+  if (dtype == HMPCG_F32) {
+    pack_nodes_kernel<float><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, (float*)packed, P);
+    pack_tiles_kernel<float><<<Tt, 256, 0, st>>>(sb, N->offo, (float*)packed, P);
+  } else {
+    pack_nodes_kernel<bf16><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, (bf16*)packed, P);
+    pack_tiles_kernel<bf16><<<Tt, 256, 0, st>>>(sb, N->offo, (bf16*)packed, P);
+  }
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+}  // namespace hm

@@ -1,0 +1,136 @@
+// Hierarchical transformer internals shared by net.cu (forward), net_bwd.cu
+// (backward, optimiser) and gemm_tc.cu.
+#pragma once
+#include <string>
+#include <vector>
+#include "ctx.cuh"
+
+namespace hm {
+
+typedef __nv_bfloat16 bf16;
+
+// Fused GEMM epilogue: v = acc + bias; pre16 <- v; v = act(v); v += resid; stores.
+struct GemmEpi {
+  const float* bias = nullptr;
+  int act = 0;                    // 0: none, 1: GELU (erf form)
+  const float* resid = nullptr;   // FP32 [M][ldr], may alias out32
+  int ldr = 0;
+  float* out32 = nullptr;
+  int ld32 = 0;
+  bf16* out16 = nullptr;
+  int ld16 = 0;
+  bf16* out16T = nullptr;         // transposed BF16 copy: out16T[col * ldT + row]
+  int ldT = 0;
+  bf16* pre16 = nullptr;          // pre-activation copy (BF16)
+  int ldpre = 0;
+  int* err = nullptr;
+};
+
+// C[M x N] = A[M x K] . B[N x K]^T, A and B row-major BF16 (K contiguous).
+struct GemmArgs {
+  const bf16* A = nullptr;
+  int lda = 0;
+  const bf16* B = nullptr;
+  int ldb = 0;
+  int M = 0, N = 0, K = 0;
+  int bn = 0;                     // tile width (64/128/256); 0 = choose
+  GemmEpi ep;
+};
+
+int gemm_bf16(const GemmArgs& g, cudaStream_t st);
+
+constexpr int kFeat = 20;         // 8 node features + 12 global statistics
+constexpr int kEdgeHidden = 32;
+
+// Offsets (in floats) of every tensor in the flat weight blob; same order as the
+// documented layout (encoder, GCN, pool, per-stack blocks, final norms, heads).
+struct BlockOff {
+  int64_t ln1g, ln1b, qkvw, qkvb, outw, outb, ln2g, ln2b, f1w, f1b, f2w, f2b, e1w, e1b, e2w, e2b;
+};
+struct WeightOff {
+  int64_t enc1w, enc1b, enc2w, enc2b, gcnw[2], gcnb[2], poolw, poolb;
+  std::vector<BlockOff> blk[2];   // [stack][layer]
+  int64_t lnfg[2], lnfb[2];
+  int64_t leaf1w, leaf1b, leaf2w, leaf2b, nodew, nodeb, offw, offb;
+  int64_t total;
+  // BF16 working copies live in a padded layout: every tensor starts on a
+  // 64-element (128-byte) boundary so that TMA can read any weight matrix.
+  std::vector<int64_t> seg32, seg16, segn;
+  int64_t total16;
+  int64_t map16(int64_t off32) const;
+};
+WeightOff weight_offsets(const hmpcg_config& c);
+
+// Per-layer activations of one stack (kept for the backward pass).
+struct StackAct {
+  float* x_in;      // residual stream entering the layer [T][d]
+  float* mu1; float* rs1;   // LN1 statistics
+  bf16* y1;         // LN1 output [T][d]
+  bf16* qkv;        // [T][3d]
+  bf16* o;          // attention output [T][d]
+  float* lse;       // softmax log-sum-exp [nwin][h][W]
+  float* x_mid;     // after attention residual [T][d]
+  float* mu2; float* rs2;
+  float* y2f;       // LN2 output FP32 [T][d]
+  bf16* u;          // FFN input [T][4d]
+  bf16* hpre;       // FFN hidden pre-activation [T][d_mlp]
+  bf16* hact;       // FFN hidden after GELU [T][d_mlp]
+  float* bias;      // edge bias [nwin][h][W][W]
+};
+
+struct Net {
+  hmpcg_config cfg;
+  WeightOff off;
+  int64_t nw;
+  float* w32;        // FP32 master weights
+  bf16* w16;         // BF16 copies (padded layout, see WeightOff::map16)
+  int64_t* segs;     // (off32, off16, count) per tensor, on the device
+  float* grad;       // gradients (FP32, same offsets)
+  float* m1; float* m2;   // AdamW moments
+  int64_t step;
+  int max_tok_d, max_tok_o;
+  // activations
+  float* feat;       // [Td][kFeat]
+  double* gstat;     // [B][12]
+  bf16* h1;          // encoder hidden [Td][d]
+  bf16* h1pre;
+  float* xenc;       // encoder output [Td][d]
+  float* xg[3];      // residual stream after encoder / gcn0 / gcn1
+  bf16* pm[2];       // P h (GCN input) BF16
+  bf16* gpre[2];     // GCN pre-activation
+  bf16* pooled;      // [To][2d]
+  float* edesc_off;  // [B*MH][r][r][4]
+  std::vector<StackAct> act[2];
+  float* x_final[2];
+  float* muf[2]; float* rsf[2];
+  bf16* yf[2];
+  bf16* leafh; bf16* leafhpre;   // leaf head hidden
+  float* frow;       // [Td][L]
+  float* nodeo;      // [Td][2r]
+  float* gate_logit; // [Td]
+  float* offo;       // [To][2r]
+  float* rhw; float* chw; float* gmean;   // highway buffers (FP32)
+  int* err;
+  // scratch for the backward pass and training
+  std::vector<void*> allocs;
+};
+
+}  // namespace hm
+
+namespace hm {
+constexpr int kMaxSys = 64;
+
+// A batch of B systems on one grid, passed by value to the network kernels.
+struct SysBatch {
+  int B, n, ndim, dims[3], L, r, K, MH, levels;
+  float leaf_side;   // round(L^(1/ndim)): leaf-window length unit of the edge descriptors
+  Morton mo;
+  const double* diag[kMaxSys];
+  const double* w[kMaxSys][3];
+  const double* rho[kMaxSys];
+};
+
+int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, SysBatch& sb);
+int net_forward(Net* N, const SysBatch& sb, cudaStream_t st);
+void net_refresh_bf16(Net* N, cudaStream_t st);
+}  // namespace hm

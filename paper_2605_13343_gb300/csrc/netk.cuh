@@ -1,0 +1,509 @@
+// Forward kernels of the hierarchical transformer (included by net.cu only).
+#pragma once
+#include "net.cuh"
+
+namespace hm {
+namespace {
+
+HM_INLINE float gelu_fwd(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+
+HM_INLINE unsigned compact(unsigned v, unsigned mask) {
+  unsigned out = 0, bit = 0;
+  while (mask) {
+    const unsigned low = mask & (0u - mask);
+    if (v & low) out |= 1u << bit;
+    ++bit;
+    mask &= mask - 1u;
+  }
+  return out;
+}
+
+// Tile m (heap order) -> level, S (leaves per side), first row / column node, chunk size.
+struct TileGeo { int lev, S, r0, c0, ch; };
+HM_INLINE TileGeo tile_geo(const SysBatch& sb, int m) {
+  TileGeo g;
+  g.lev = 32 - __clz(m + 1);
+  const int t = m + 1 - (1 << (g.lev - 1));
+  g.S = sb.K >> g.lev;
+  g.r0 = 2 * t * g.S * sb.L;
+  g.c0 = (2 * t + 1) * g.S * sb.L;
+  g.ch = g.S * sb.L / sb.r;
+  return g;
+}
+
+HM_INLINE double block_sum_d(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+HM_INLINE double block_max_d(double v, double* red, bool is_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, u) : fmin(v, u);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = red[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) s = is_max ? fmax(s, red[i]) : fmin(s, red[i]);
+  return s;
+}
+
+// d_glob = 12 per-system statistics (FP64, deterministic order).
+__global__ void global_stats_kernel(const SysBatch sb, double* __restrict__ gstat) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, n = sb.n;
+  const double* rho = sb.rho[b];
+  const double* dg = sb.diag[b];
+  double slr = 0, sld = 0, mxr = -1e300, mnr = 1e300, mxd = -1e300, mnd = 1e300, nbd = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double lr = log(rho[i]), ld = log(dg[i]);
+    slr += lr; sld += ld;
+    mxr = fmax(mxr, lr); mnr = fmin(mnr, lr); mxd = fmax(mxd, ld); mnd = fmin(mnd, ld);
+    bool bnd = false;
+    for (int a = 0; a < sb.ndim; ++a) {
+      const unsigned m = sb.mo.mask[a];
+      if ((i & m) == m || (i & m) == 0u) bnd = true;
+    }
+    nbd += bnd ? 1.0 : 0.0;
+  }
+  slr = block_sum_d(slr, red); sld = block_sum_d(sld, red);
+  mxr = block_max_d(mxr, red, true); mnr = block_max_d(mnr, red, false);
+  mxd = block_max_d(mxd, red, true); mnd = block_max_d(mnd, red, false);
+  nbd = block_sum_d(nbd, red);
+  const double mr = slr / n, md = sld / n, thr = 0.5 * (mxr + mnr);
+  double vr = 0, vd = 0, hv = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double lr = log(rho[i]), ld = log(dg[i]);
+    vr += (lr - mr) * (lr - mr);
+    vd += (ld - md) * (ld - md);
+    hv += lr > thr ? 1.0 : 0.0;
+  }
+  vr = block_sum_d(vr, red); vd = block_sum_d(vd, red); hv = block_sum_d(hv, red);
+  if (threadIdx.x == 0) {
+    double* g = gstat + 12 * b;
+    g[0] = log2((double)n) / 16.0;
+    g[1] = sb.ndim == 3 ? 1.0 : 0.0;
+    g[2] = mxr; g[3] = mnr; g[4] = mr; g[5] = sqrt(vr / n); g[6] = hv / n;
+    g[7] = md; g[8] = sqrt(vd / n); g[9] = mxd; g[10] = mnd; g[11] = nbd / n;
+  }
+}
+
+// Node features (8 + 12 global) and the first encoder layer Linear(20 -> d) + GELU.
+__global__ void encoder1_kernel(const SysBatch sb, const double* __restrict__ gstat, const float* __restrict__ w1,
+                                const float* __restrict__ b1, int d, float* __restrict__ feat, bf16* __restrict__ h1,
+                                bf16* __restrict__ h1pre) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const double* rho = sb.rho[b];
+  const double* dg = sb.diag[b];
+  const double* g = gstat + 12 * b;
+  const double ri = rho[i], di = dg[i];
+  double off = 0.0, nb = 0.0, iface = 0.0;
+  float f[kFeat];
+  for (int a = 0; a < sb.ndim; ++a) {
+    const int jp = sb.mo.plus(i, a);
+    if (jp >= 0) { off += sb.w[b][a][i]; if (rho[jp] != ri) iface = 1.0; } else nb += 1.0;
+    const int jm = sb.mo.minus(i, a);
+    if (jm >= 0) { off += sb.w[b][a][jm]; if (rho[jm] != ri) iface = 1.0; } else nb += 1.0;
+  }
+  f[0] = (float)(log(ri) - g[4]);
+  for (int a = 0; a < 3; ++a)
+    f[1 + a] = a < sb.ndim ? (float)(((double)compact(i, sb.mo.mask[a]) + 0.5) / sb.dims[a] - 0.5) : 0.f;
+  f[4] = (float)(nb / (2 * sb.ndim));
+  f[5] = (float)(log(di) - g[7]);
+  f[6] = (float)(off / di);
+  f[7] = (float)iface;
+  for (int q = 0; q < 12; ++q) f[8 + q] = (float)g[q];
+  if (lane < kFeat) feat[(size_t)t * kFeat + lane] = f[lane];
+  for (int j = lane; j < d; j += 32) {
+    float acc = b1[j];
+#pragma unroll
+    for (int q = 0; q < kFeat; ++q) acc = fmaf(w1[j * kFeat + q], f[q], acc);
+    h1pre[(size_t)t * d + j] = __float2bfloat16_rn(acc);
+    h1[(size_t)t * d + j] = __float2bfloat16_rn(gelu_fwd(acc));
+  }
+}
+
+// GCN message passing with P = D^-1 A: out_i = x_i - sum_j (w_ij / d_i) x_j.
+__global__ void prop_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const size_t base = (size_t)b * sb.n;
+  const double di = sb.diag[b][i];
+  int js[6];
+  float cs[6];
+  int nj = 0;
+  for (int a = 0; a < sb.ndim; ++a) {
+    const int jp = sb.mo.plus(i, a);
+    if (jp >= 0) { js[nj] = jp; cs[nj++] = (float)(sb.w[b][a][i] / di); }
+    const int jm = sb.mo.minus(i, a);
+    if (jm >= 0) { js[nj] = jm; cs[nj++] = (float)(sb.w[b][a][jm] / di); }
+  }
+  for (int c = lane; c < d; c += 32) {
+    float v = x[(base + i) * d + c];
+    for (int q = 0; q < nj; ++q) v = fmaf(-cs[q], x[(base + js[q]) * d + c], v);
+    out[(size_t)t * d + c] = __float2bfloat16_rn(v);
+  }
+}
+
+// Off-diagonal tokens: [mean over row chunk ; mean over column chunk] of the encoder output.
+__global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ pooled) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  const int To = sb.B * sb.MH * sb.r;
+  if (t >= To) return;
+  const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
+  const TileGeo g = tile_geo(sb, m);
+  const size_t base = (size_t)b * sb.n;
+  const float inv = 1.f / g.ch;
+  for (int c = lane; c < d; c += 32) {
+    float sr = 0.f, sc = 0.f;
+    for (int q = 0; q < g.ch; ++q) {
+      sr += x[(base + g.r0 + a * g.ch + q) * d + c];
+      sc += x[(base + g.c0 + a * g.ch + q) * d + c];
+    }
+    pooled[(size_t)t * 2 * d + c] = __float2bfloat16_rn(sr * inv);
+    pooled[(size_t)t * 2 * d + d + c] = __float2bfloat16_rn(sc * inv);
+  }
+}
+
+// Tile edge descriptors: chunk-centroid offset / tile side, mean normalised coupling.
+__global__ void edge_desc_off_kernel(const SysBatch sb, float* __restrict__ e) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = sb.r;
+  if (idx >= sb.B * sb.MH * r * r) return;
+  const int bb = idx % r, a = (idx / r) % r, m = (idx / (r * r)) % sb.MH, b = idx / (r * r * sb.MH);
+  const TileGeo g = tile_geo(sb, m);
+  const double side = pow((double)g.S * sb.L, 1.0 / sb.ndim);
+  const unsigned low = (unsigned)g.ch - 1u;
+  const unsigned fr = g.r0 + a * g.ch, fc = g.c0 + bb * g.ch;
+  float* out = e + (size_t)idx * 4;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (ax >= sb.ndim) { out[ax] = 0.f; continue; }
+    const double ext = (double)(1u << __popc(sb.mo.mask[ax] & low));
+    const double cr = compact(fr, sb.mo.mask[ax]) + 0.5 * (ext - 1.0);
+    const double cc = compact(fc, sb.mo.mask[ax]) + 0.5 * (ext - 1.0);
+    out[ax] = (float)((cc - cr) / side);
+  }
+  const double* dg = sb.diag[b];
+  double acc = 0.0;
+  for (unsigned i = fr; i < fr + g.ch; ++i)
+    for (int ax = 0; ax < sb.ndim; ++ax) {
+      const int j = sb.mo.plus(i, ax);
+      if (j >= (int)fc && j < (int)(fc + g.ch)) acc += -sb.w[b][ax][i] / sqrt(dg[i] * dg[j]);
+    }
+  out[3] = (float)(acc / ((double)g.ch * g.ch));
+}
+
+// Edge-bias MLP 4 -> 32 (GELU) -> h, weights staged in shared memory.
+struct EdgeMlp {
+  float w1[kEdgeHidden * 4], b1[kEdgeHidden], w2[8 * kEdgeHidden], b2[8];
+};
+HM_INLINE void load_edge_mlp(EdgeMlp& s, const float* w1, const float* b1, const float* w2, const float* b2, int h) {
+  for (int q = threadIdx.x; q < kEdgeHidden * 4; q += blockDim.x) s.w1[q] = w1[q];
+  for (int q = threadIdx.x; q < kEdgeHidden; q += blockDim.x) s.b1[q] = b1[q];
+  for (int q = threadIdx.x; q < h * kEdgeHidden; q += blockDim.x) s.w2[q] = w2[q];
+  for (int q = threadIdx.x; q < h; q += blockDim.x) s.b2[q] = b2[q];
+  __syncthreads();
+}
+HM_INLINE void edge_mlp(const EdgeMlp& s, const float* e, int h, float* out) {
+  float hid[kEdgeHidden];
+#pragma unroll
+  for (int k = 0; k < kEdgeHidden; ++k) {
+    float v = s.b1[k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v = fmaf(s.w1[k * 4 + q], e[q], v);
+    hid[k] = gelu_fwd(v);
+  }
+  for (int hh = 0; hh < h; ++hh) {
+    float v = s.b2[hh];
+#pragma unroll
+    for (int k = 0; k < kEdgeHidden; ++k) v = fmaf(s.w2[hh * kEdgeHidden + k], hid[k], v);
+    out[hh] = v;
+  }
+}
+
+// Leaf-window descriptor of pair (a, b) of leaf k of system bsys.
+HM_INLINE void leaf_desc(const SysBatch& sb, int bsys, int k, int a, int bb, float* e) {
+  const unsigned i = k * sb.L + a, j = k * sb.L + bb;
+  const float side = sb.leaf_side;
+  for (int ax = 0; ax < 3; ++ax)
+    e[ax] = ax < sb.ndim ? ((float)compact(j, sb.mo.mask[ax]) - (float)compact(i, sb.mo.mask[ax])) / side : 0.f;
+  float al = 0.f;
+  if (a == bb) {
+    al = 1.f;
+  } else {
+    const double* dg = sb.diag[bsys];
+    for (int ax = 0; ax < sb.ndim; ++ax) {
+      if (sb.mo.plus(i, ax) == (int)j) al = (float)(-sb.w[bsys][ax][i] / sqrt(dg[i] * dg[j]));
+      if (sb.mo.minus(i, ax) == (int)j) al = (float)(-sb.w[bsys][ax][j] / sqrt(dg[i] * dg[j]));
+    }
+  }
+  e[3] = al;
+}
+
+__global__ void edge_bias_diag_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
+                                      const float* b2, int h, float* __restrict__ bias) {
+  __shared__ EdgeMlp s;
+  load_edge_mlp(s, w1, b1, w2, b2, h);
+  const int L = sb.L;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= sb.B * sb.K * L * L) return;
+  const int bb = idx % L, a = (idx / L) % L, win = idx / (L * L);
+  const int k = win % sb.K, bsys = win / sb.K;
+  float e[4], out[8];
+  leaf_desc(sb, bsys, k, a, bb, e);
+  edge_mlp(s, e, h, out);
+  for (int hh = 0; hh < h; ++hh) bias[(((size_t)win * h + hh) * L + a) * L + bb] = out[hh];
+}
+
+__global__ void edge_bias_off_kernel(const SysBatch sb, const float* __restrict__ edesc, const float* w1, const float* b1,
+                                     const float* w2, const float* b2, int h, float* __restrict__ bias) {
+  __shared__ EdgeMlp s;
+  load_edge_mlp(s, w1, b1, w2, b2, h);
+  const int r = sb.r;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= sb.B * sb.MH * r * r) return;
+  const int bb = idx % r, a = (idx / r) % r, win = idx / (r * r);
+  float out[8];
+  edge_mlp(s, edesc + (size_t)idx * 4, h, out);
+  for (int hh = 0; hh < h; ++hh) bias[(((size_t)win * h + hh) * r + a) * r + bb] = out[hh];
+}
+
+// LayerNorm over d (warp per token), eps = 1e-5.  Writes BF16 (leading dim ld16) and/or FP32.
+__global__ void layernorm_kernel(const float* __restrict__ x, const float* __restrict__ gam,
+                                 const float* __restrict__ bet, int T, int d, bf16* __restrict__ out16,
+                                 float* __restrict__ out32, float* __restrict__ mu, float* __restrict__ rs,
+                                 int ld16 = 0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  if (ld16 == 0) ld16 = d;
+  float v[8];
+  const int per = d / 32;
+  float s = 0.f;
+  for (int q = 0; q < per; ++q) { v[q] = x[(size_t)t * d + lane + 32 * q]; s += v[q]; }
+  s = warp_sum(s);
+  const float mean = s / d;
+  float ss = 0.f;
+  for (int q = 0; q < per; ++q) { const float u = v[q] - mean; ss += u * u; }
+  ss = warp_sum(ss);
+  const float rstd = rsqrtf(ss / d + 1e-5f);
+  for (int q = 0; q < per; ++q) {
+    const int c = lane + 32 * q;
+    const float y = (v[q] - mean) * rstd * gam[c] + bet[c];
+    if (out16) out16[(size_t)t * ld16 + c] = __float2bfloat16_rn(y);
+    if (out32) out32[(size_t)t * d + c] = y;
+  }
+  if (lane == 0) { mu[t] = mean; rs[t] = rstd; }
+}
+
+// Window attention with additive per-head bias; one thread per (query token, head),
+// a 128-token block of whole windows per CTA.  Head dim 32.
+template <int W>
+__global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__ qkv, const float* __restrict__ bias,
+                                                        int T, int d, int h, bf16* __restrict__ out,
+                                                        float* __restrict__ lse) {
+  __shared__ float ks[128][33];
+  __shared__ float vs[128][33];
+  const int head = blockIdx.y;
+  const int t0 = blockIdx.x * 128;
+  const int t = t0 + threadIdx.x;
+  const int ld = 3 * d;
+  if (t < T) {
+    const bf16* kp = qkv + (size_t)t * ld + d + head * 32;
+    const bf16* vp = qkv + (size_t)t * ld + 2 * d + head * 32;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { ks[threadIdx.x][c] = __bfloat162float(kp[c]); vs[threadIdx.x][c] = __bfloat162float(vp[c]); }
+  }
+  __syncthreads();
+  if (t >= T) return;
+  float q[32];
+  const bf16* qp = qkv + (size_t)t * ld + head * 32;
+  const float scale = 0.17677669529663688f;  // 1 / sqrt(32)
+#pragma unroll
+  for (int c = 0; c < 32; ++c) q[c] = __bfloat162float(qp[c]) * scale;
+  const int win = t / W, a = t % W;
+  const int ws = win * W - t0;
+  const float* bp = bias + (((size_t)win * h + head) * W + a) * W;
+  float s[W];
+  float mx = -1e30f;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    float v = bp[j];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v = fmaf(q[c], ks[ws + j][c], v);
+    s[j] = v;
+    mx = fmaxf(mx, v);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int j = 0; j < W; ++j) { s[j] = __expf(s[j] - mx); sum += s[j]; }
+  const float inv = 1.f / sum;
+  float o[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) o[c] = 0.f;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    const float p = s[j] * inv;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) o[c] = fmaf(p, vs[ws + j][c], o[c]);
+  }
+  bf16* op = out + (size_t)t * d + head * 32;
+#pragma unroll
+  for (int c = 0; c < 32; c += 2) *reinterpret_cast<__nv_bfloat162*>(op + c) = __floats2bfloat162_rn(o[c], o[c + 1]);
+  lse[(size_t)t * h + head] = mx + logf(sum);
+}
+
+// Axial highway buffers for the diagonal tokens (mean over the tokens covering each
+// row / column) and their BF16 copies into the FFN input (columns d..3d).
+__global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo, int d,
+                                  float* __restrict__ rhw, float* __restrict__ chw, bf16* __restrict__ ud) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const int k = i / sb.L;
+  int toks[32];
+  int sides = 0, nl = 0;
+  for (int lev = 1; lev <= sb.levels; ++lev) {
+    const int S = sb.K >> lev;
+    const int cl = k / S;
+    const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+    const int ch = S * sb.L / sb.r;
+    const int a = (i - cl * S * sb.L) / ch;
+    toks[nl] = (b * sb.MH + m) * sb.r + a;
+    if (cl & 1) sides |= 1 << nl;
+    ++nl;
+  }
+  const int nr = 1 + (nl - __popc(sides)), nc = 1 + __popc(sides);
+  for (int c = lane; c < d; c += 32) {
+    const float y = yd[(size_t)t * d + c];
+    float rs = y, cs = y;
+    for (int q = 0; q < nl; ++q) {
+      const float v = yo[(size_t)toks[q] * d + c];
+      if ((sides >> q) & 1) cs += v; else rs += v;
+    }
+    rs /= (float)nr;
+    cs /= (float)nc;
+    rhw[(size_t)t * d + c] = rs;
+    chw[(size_t)t * d + c] = cs;
+    ud[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(rs);
+    ud[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(cs);
+  }
+}
+
+// Global summary token: mean of y over all tokens of both stacks (per system).
+__global__ void highway_g_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo, int d,
+                                 float* __restrict__ g) {
+  __shared__ double part[8][33];
+  const int b = blockIdx.x, c = blockIdx.y * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
+  double s = 0.0;
+  for (int i = w; i < sb.n; i += 8) s += yd[((size_t)b * sb.n + i) * d + c];
+  const int no = sb.MH * sb.r;
+  for (int i = w; i < no; i += 8) s += yo[((size_t)b * no + i) * d + c];
+  part[w][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (w == 0) {
+    double tot = 0.0;
+    for (int q = 0; q < 8; ++q) tot += part[q][threadIdx.x & 31];
+    g[(size_t)b * d + c] = (float)(tot / (sb.n + no));
+  }
+}
+
+__global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d, bf16* __restrict__ u) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  const int b = t / n;
+  for (int c = lane; c < d; c += 32) u[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
+}
+
+// Off-diagonal token gathers: mean of r_hw over its row chunk, of c_hw over its column chunk, g.
+__global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ rhw, const float* __restrict__ chw,
+                                   const float* __restrict__ g, int d, bf16* __restrict__ uo) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.MH * sb.r) return;
+  const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
+  const TileGeo gg = tile_geo(sb, m);
+  const size_t base = (size_t)b * sb.n;
+  const float inv = 1.f / gg.ch;
+  for (int c = lane; c < d; c += 32) {
+    float sr = 0.f, sc = 0.f;
+    for (int q = 0; q < gg.ch; ++q) {
+      sr += rhw[(base + gg.r0 + a * gg.ch + q) * d + c];
+      sc += chw[(base + gg.c0 + a * gg.ch + q) * d + c];
+    }
+    uo[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(sr * inv);
+    uo[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(sc * inv);
+    uo[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
+  }
+}
+
+__global__ void gate_logit_kernel(const bf16* __restrict__ y, const float* __restrict__ wg, const float* __restrict__ bg,
+                                  int T, int d, float* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  float s = 0.f;
+  for (int c = lane; c < d; c += 32) s = fmaf(__bfloat162float(y[(size_t)t * d + c]), wg[c], s);
+  s = warp_sum(s);
+  if (lane == 0) out[t] = s + bg[0];
+}
+
+template <class T> HM_INLINE T from_f(float v);
+template <> HM_INLINE float from_f<float>(float v) { return v; }
+template <> HM_INLINE bf16 from_f<bf16>(float v) { return __float2bfloat16_rn(v); }
+
+HM_INLINE float softplus_f(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+
+// Node rows of the packed factors: F rows, U~, V~ scaled by diag^-1/2; gate lambda / diag.
+template <class T>
+__global__ void pack_nodes_kernel(const SysBatch sb, const float* __restrict__ frow, const float* __restrict__ nodeo,
+                                  const float* __restrict__ glog, T* __restrict__ packed, int64_t P) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const int L = sb.L, r = sb.r, n = sb.n;
+  const double di = sb.diag[b][i];
+  const float s = (float)(1.0 / sqrt(di));
+  T* base = packed + (size_t)b * P;
+  const int k = i / L, a = i % L;
+  const int64_t offU = (int64_t)sb.K * L * L + (int64_t)sb.MH * r * r, offV = offU + (int64_t)n * r, offG = offV + (int64_t)n * r;
+  for (int c = lane; c < L; c += 32) base[(int64_t)k * L * L + a * L + c] = from_f<T>(frow[(size_t)t * L + c] * s);
+  for (int c = lane; c < r; c += 32) {
+    base[offU + (int64_t)i * r + c] = from_f<T>(nodeo[(size_t)t * 2 * r + c] * s);
+    base[offV + (int64_t)i * r + c] = from_f<T>(nodeo[(size_t)t * 2 * r + r + c] * s);
+  }
+  if (lane == 0) base[offG + i] = from_f<T>((float)(softplus_f(glog[t]) / di));
+}
+
+// Tile cores B_m = U_m V_m^T from the off-diagonal head (one CTA per tile).
+template <class T>
+__global__ void pack_tiles_kernel(const SysBatch sb, const float* __restrict__ offo, T* __restrict__ packed, int64_t P) {
+  const int r = sb.r;
+  const int tile = blockIdx.x;
+  const int b = tile / sb.MH, m = tile % sb.MH;
+  const float* base = offo + (size_t)tile * r * 2 * r;
+  T* out = packed + (size_t)b * P + (int64_t)sb.K * sb.L * sb.L + (int64_t)m * r * r;
+  for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
+    const int a = q / r, c = q % r;
+    float v = 0.f;
+    for (int e = 0; e < r; ++e) v = fmaf(base[a * 2 * r + e], base[c * 2 * r + r + e], v);
+    out[q] = from_f<T>(v);
+  }
+}
+
+}  // namespace
+}  // namespace hm

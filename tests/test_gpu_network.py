@@ -1,0 +1,130 @@
+"""GPU parity of the tcgen05 GEMM and of the hierarchical-transformer inference.
+
+The GEMM is checked against a plain PyTorch FP32 matmul of the same BF16
+operands (TF32 off).  The network forward runs BF16 GEMM operands with FP32
+accumulation through ~30 dependent layers; its factors are checked against the
+FP64 oracle forward on the same seeded weights at 3e-2 relative Frobenius
+error per factor block (BF16 unit roundoff 3.9e-3 times the depth of the
+residual stream, with margin).
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import grid, hmatrix, network, pcg
+
+pytestmark = pytest.mark.gpu
+h = pytest.importorskip("paper_2605_13343_gb300")
+
+CFG = dict(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16)
+
+
+@pytest.mark.parametrize("m,n,k,bias,act", [(8192, 384, 128, True, 0), (2032, 128, 512, True, 1),
+                                            (100, 64, 64, False, 0), (300, 32, 128, True, 1),
+                                            (4096, 256, 256, False, 1), (128, 512, 512, True, 0)])
+def test_gemm_tc_matches_torch(m, n, k, bias, act):
+    torch.backends.cuda.matmul.allow_tf32 = False
+    g = torch.Generator(device="cuda").manual_seed(m + n + k)
+    a = torch.randn(m, k, device="cuda", generator=g).to(torch.bfloat16)
+    b = torch.randn(n, k, device="cuda", generator=g).to(torch.bfloat16)
+    bb = torch.randn(n, device="cuda", generator=g) if bias else None
+    c = h.gemm_bf16(a, b, bias=bb, act=act)
+    ref = a.float() @ b.float().T
+    if bias:
+        ref = ref + bb
+    if act:
+        ref = torch.nn.functional.gelu(ref)
+    torch.cuda.synchronize()
+    err = (c - ref).abs().max().item()
+    assert err <= 1e-4 * max(1.0, ref.abs().max().item()), err
+
+
+def _blob(seed, scale_heads=100.0):
+    lay = inputs.network_layout(**CFG)
+    w = inputs.network_blob(seed, **CFG)
+    off = 0
+    for name, shp in lay:
+        n = int(np.prod(shp))
+        if name in ("leaf2.w", "node.w", "off.w"):
+            w[off:off + n] *= scale_heads
+        off += n
+    return w, lay
+
+
+def _ctx(max_n, weights, batch=1):
+    return h.Context(max_n=max_n, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
+                     max_batch=batch, weights=weights)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def _gpu_system(fr):
+    s = h.System(fr["dims"])
+    h.assemble(torch.from_numpy(fr["rho"]).cuda(), s)
+    return s
+
+
+def test_weight_count_matches_layout():
+    w, lay = _blob(0)
+    c = h.Config(max_n=4096, max_batch=1, max_nrhs=1, leaf=64, rank=16, d_model=128, n_layers=4,
+                 n_heads=4, d_mlp=512)
+    import ctypes
+    assert h.lib().hmpcg_weight_count(ctypes.byref(c)) == w.size
+
+
+@pytest.mark.parametrize("family,seeds", [("spheres3d_4096_lu", [0]), ("spheres3d_4096_lu", [1, 2]),
+                                          ("spheres3d_8192", [0])])
+def test_inference_parity(family, seeds):
+    w, lay = _blob(7)
+    frs = [inputs.frame(family, s) for s in seeds]
+    n = int(np.prod(frs[0]["dims"]))
+    ctx = _ctx(n, w, batch=len(seeds))
+    systems = [_gpu_system(fr) for fr in frs]
+    P = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+    packed = torch.empty(len(seeds) * P, dtype=torch.float32, device="cuda")
+    h.infer_factors(ctx, systems, packed)
+    torch.cuda.synchronize()
+    got_all = packed.cpu().numpy().astype(np.float64)
+    p = network.unflatten(w, lay)
+    for b, fr in enumerate(frs):
+        ref = grid.assemble(fr["rho"], fr["dims"])
+        with torch.no_grad():
+            f = network.to_numpy_factors(network.forward(p, ref, CFG))
+        got = hmatrix.unpack(got_all[b * P:(b + 1) * P], n, 64, 16, "learned")
+        for key in ("leafblk", "U", "V", "core"):
+            assert _rel(got[key], f[key]) <= 3e-2, (key, _rel(got[key], f[key]))
+        assert _rel(got["g"], f["g"]) <= 1e-2
+        # the assembled preconditioners agree as operators too
+        x = np.random.default_rng(b).standard_normal(n)
+        assert _rel(hmatrix.apply(got, x), hmatrix.apply(f, x)) <= 3e-2
+    ctx.close()
+
+
+def test_learned_pcg_end_to_end():
+    w, lay = _blob(3, scale_heads=10.0)
+    fr = inputs.frame("spheres3d_8192", 4)
+    n = 8192
+    ctx = _ctx(n, w)
+    s = _gpu_system(fr)
+    P = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+    packed = torch.empty(P, dtype=torch.bfloat16, device="cuda")
+    h.infer_factors(ctx, [s], packed)
+    b = torch.from_numpy(fr["b"]).cuda()
+    x = torch.empty_like(b)
+    info = h.solve(ctx, s, h.factors(h.PRE_LEARNED, packed, n, 64, 16), b, x, rtol=1e-6)
+    assert info.status == h.OK
+    ref = grid.assemble(fr["rho"], fr["dims"])
+    a = grid.sparse_matrix(ref)
+    rel = np.linalg.norm(fr["b"] - a @ x.cpu().numpy()) / np.linalg.norm(fr["b"])
+    assert rel <= 1e-6
+    # iteration count against the oracle PCG on the oracle's FP64 factors
+    p = network.unflatten(w, lay)
+    with torch.no_grad():
+        f = network.to_numpy_factors(network.forward(p, ref, CFG))
+    out = pcg.pcg(lambda v: a @ v, lambda v: hmatrix.apply(f, v), fr["b"], rtol=1e-6)
+    assert out["status"] == pcg.OK
+    assert abs(info.iters - out["iters"]) <= max(3, 0.05 * out["iters"])
+    ctx.close()
