@@ -180,6 +180,27 @@ int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys,
                      int32_t n_probes, float lr, uint64_t step_seed,
                      float* loss_out, void* stream);
 
+/* z = M r exactly as hmpcg_apply with nrhs = 1, but without a context and
+ * without allocating anything.  The paper has no counterpart: this is for
+ * callers that cannot call cudaMalloc, such as code inside a custom device
+ * allocator's own callbacks, a real-time loop whose device-memory budget is
+ * fixed after start-up, or a plug-in whose host application owns every device
+ * allocation.  The caller still passes the factors and the r and z vectors.
+ *
+ * Scratch is one file-scope device array of 4 Mi floats (16 MiB) that every
+ * GPU loading this library holds until the process exits.  Factors needing
+ * more than that (n + nslot K r + 2 (K-1) r floats, nslot = 2 learned or
+ * levels svdh) are rejected with HMPCG_E_SHAPE before anything runs; at
+ * leaf 64 / rank 16 the learned layout fits up to n = 2^21.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array, which keeps the last
+ * call's values (every stage writes its scratch before reading it, so nothing
+ * needs clearing): calls that overlap on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller. */
+int hmpcg_apply_noalloc(const hmpcg_factors* f, const float* r, float* z, void* stream);
+
 /* The tensor-core GEMM the network runs on (tcgen05, TMA, TMEM accumulator):
  * C[M x N] = A[M x K] B[N x K]^T (+ bias[N]) (GELU if act == 1), A and B
  * row-major BF16 with K contiguous (K % 64 == 0, N % 16 == 0, 16-byte aligned

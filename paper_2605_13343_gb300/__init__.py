@@ -74,6 +74,7 @@ EXPORTS = {
     "hmpcg_train_step": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_int32, C.c_float,
                                    C.c_uint64, C.POINTER(C.c_float), C.c_void_p]),
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmpcg_apply_noalloc": (C.c_int, [C.POINTER(Factors), C.c_void_p, C.c_void_p, C.c_void_p]),
     "hmpcg_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                   C.c_void_p, C.c_int32, C.c_void_p]),
 }
@@ -249,6 +250,14 @@ def apply(ctx, f, r, z, nrhs=1, stream=None):
     """hmpcg_apply: z = M r (FP32, node-major)."""
     assert r.dtype == torch.float32 and z.dtype == torch.float32
     _check(lib().hmpcg_apply(ctx.h, C.byref(f), _ptr(r), _ptr(z), nrhs, _stream(stream)), "apply")
+    return z
+
+
+def apply_noalloc(f, r, z, stream=None):
+    """hmpcg_apply_noalloc: z = M r with the library's fixed scratch array (no context,
+    no allocation); for callers that cannot allocate device memory."""
+    assert r.dtype == torch.float32 and z.dtype == torch.float32
+    _check(lib().hmpcg_apply_noalloc(C.byref(f), _ptr(r), _ptr(z), _stream(stream)), "apply_noalloc")
     return z
 
 

@@ -640,6 +640,46 @@ int apply_dispatch(Ctx* c, const hmpcg_factors* f, const float* r, float* z, cud
   return HMPCG_E_INVALID;
 }
 
+// The same three apply kernels with caller-provided scratch (used by the allocation-free
+// entry point); capacities are checked by the caller.
+template <class T>
+static int launch_apply_scratch(const FactorView<T>& f, const float* r, float* z, float* ydiag, float* uhat,
+                                float* tcoup, int num_sms, cudaStream_t st) {
+  const size_t smem = apply_smem_bytes(f.L, f.r, f.nslot);
+  const int g1 = std::min(f.K, num_sms * 8);
+  apply_restrict_kernel<T><<<g1, kThreads, smem, st>>>(f, r, ydiag, uhat);
+  apply_tile_kernel<T><<<std::max(1, std::min(f.K - 1, num_sms * 8)), kThreads, smem, st>>>(f, uhat, tcoup);
+  apply_prolong_kernel<T><<<g1, kThreads, smem, st>>>(f, tcoup, ydiag, z);
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+// Scratch floats the apply needs for these factors: ydiag (n), restrictions (nslot K r),
+// couplings (2 (K-1) r); -1 if the factor shape is invalid.
+int64_t apply_scratch_floats(const hmpcg_factors* f) {
+  FactorView<float> v;
+  hmpcg_factors g = *f;
+  g.dtype = HMPCG_F32;
+  if (make_factor_view(&g, v)) return -1;
+  return (int64_t)v.n + (int64_t)v.nslot * v.K * v.r + 2LL * (v.K - 1) * v.r;
+}
+
+int apply_with_scratch(const hmpcg_factors* f, const float* r, float* z, float* scratch, int num_sms,
+                       cudaStream_t st) {
+  int rc;
+  auto run = [&](auto v) -> int {
+    float* ydiag = scratch;
+    float* uhat = ydiag + v.n;
+    float* tcoup = uhat + (size_t)v.nslot * v.K * v.r;
+    return launch_apply_scratch(v, r, z, ydiag, uhat, tcoup, num_sms, st);
+  };
+  switch (f->dtype) {
+    case HMPCG_F32: { FactorView<float> v; if ((rc = make_factor_view(f, v))) return rc; return run(v); }
+    case HMPCG_BF16: { FactorView<__nv_bfloat16> v; if ((rc = make_factor_view(f, v))) return rc; return run(v); }
+    case HMPCG_FP8E4M3: { FactorView<__nv_fp8_e4m3> v; if ((rc = make_factor_view(f, v))) return rc; return run(v); }
+  }
+  return HMPCG_E_INVALID;
+}
+
 int assemble_launch(const double* rho, const hmpcg_system* sys, int bc, int face, cudaStream_t st) {
   AsmOut o;
   o.diag = sys->diag; o.diag32 = sys->diag32; o.rho = sys->rho; o.perm = sys->perm;
