@@ -208,6 +208,10 @@ int hmpcg_apply_noalloc(const hmpcg_factors* f, const float* r, float* z, void* 
 int hmpcg_gemm_bf16(const void* a, const void* b, float* c, int32_t m, int32_t n, int32_t k,
                     const float* bias, int32_t act, void* stream);
 
+/* Copy the gradient of the last hmpcg_train_step (after the global-norm clip,
+ * FP32, weight-blob order) to `grads` (host, count floats). */
+int hmpcg_get_grads(void* ctx, float* grads, int64_t count);
+
 /* Copy the context's FP32 master weights to `weights` (host, count floats). */
 int hmpcg_get_weights(void* ctx, float* weights, int64_t count);
 

@@ -74,6 +74,7 @@ EXPORTS = {
     "hmpcg_train_step": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_int32, C.c_float,
                                    C.c_uint64, C.POINTER(C.c_float), C.c_void_p]),
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "hmpcg_get_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "hmpcg_apply_noalloc": (C.c_int, [C.POINTER(Factors), C.c_void_p, C.c_void_p, C.c_void_p]),
     "hmpcg_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                   C.c_void_p, C.c_int32, C.c_void_p]),
@@ -288,6 +289,13 @@ def train_step(ctx, systems, n_probes, lr, step_seed, want_loss=True, stream=Non
     _check(lib().hmpcg_train_step(ctx.h, arr, len(systems), n_probes, lr, step_seed,
                                   C.byref(loss) if want_loss else None, _stream(stream)), "train_step")
     return loss.value if want_loss else None
+
+
+def get_grads(ctx, count):
+    import numpy as np
+    g = np.empty(count, dtype=np.float32)
+    _check(lib().hmpcg_get_grads(ctx.h, g.ctypes.data_as(C.c_void_p), count), "get_grads")
+    return g
 
 
 def get_weights(ctx, count):

@@ -19,6 +19,7 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
 int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int n_probes, float lr,
                    uint64_t seed, float* loss_out, cudaStream_t st);
 int net_get_weights(Ctx* c, float* w, int64_t count);
+int net_get_grads(Ctx* c, float* g, int64_t count);
 }  // namespace hm
 
 using namespace hm;
@@ -233,6 +234,13 @@ int hmpcg_gemm_bf16(const void* a, const void* b, float* c, int32_t m, int32_t n
   g.ep.bias = bias; g.ep.act = act; g.ep.out32 = c; g.ep.ld32 = n;
   int rc = gemm_bf16(g, (cudaStream_t)stream);
   return rc;
+}
+
+int hmpcg_get_grads(void* ctx, float* g, int64_t count) {
+  if (!ctx || !g) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net) return HMPCG_E_INVALID;
+  return net_get_grads(c, g, count);
 }
 
 int hmpcg_get_weights(void* ctx, float* w, int64_t count) {

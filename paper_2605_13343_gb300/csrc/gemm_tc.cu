@@ -1,11 +1,12 @@
 // BF16 GEMM on the 5th-generation tensor cores: C[M x N] = A[M x K] . B[N x K]^T.
 //
 // One CTA computes a 128 x BN tile.  A TMA producer thread streams 128x64 and
-// BNx64 K-major tiles (128-byte swizzle) into a 4-stage shared-memory ring; one
+// BNx64 K-major tiles (128-byte swizzle) into a 3-stage shared-memory ring; one
 // thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM);
 // tcgen05.commit frees ring slots through mbarriers.  Four warps then read the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows) and
-// run the fused epilogue: + bias, GELU, + residual, FP32 / BF16 / transposed BF16
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows),
+// transpose 32x32 blocks through the freed ring memory so that global accesses are
+// coalesced along rows, and run the fused epilogue: + bias, GELU, + residual, FP32 / BF16 / transposed BF16
 // stores.  Every mbarrier wait is bounded; a timeout sets an error flag, and the
 // CTA still waits for its MMAs and frees its TMEM before it returns.
 #include <cuda.h>
@@ -101,11 +102,11 @@ HM_INLINE float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.7071067811
 }  // namespace tc
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const GemmEpi ep, int M, int N, int K) {
   using namespace tc;
-  constexpr int BM = 128, BK = 64, STAGES = 4;
+  constexpr int BM = 128, BK = 64, STAGES = 3;
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
   extern __shared__ uint8_t smem_raw[];
@@ -115,7 +116,12 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ int fail_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nk = K / BK;
+  // split-K: CTA z reduces k-blocks [kb0, kb1) and writes its own FP32 partial tile
+  const int nk_all = (K + BK - 1) / BK;
+  const int kps = (nk_all + gridDim.z - 1) / gridDim.z;
+  const int kb0 = blockIdx.z * kps;
+  const int kb1 = min(nk_all, kb0 + kps);
+  const int nk = max(0, kb1 - kb0);
   uint8_t* sa = smem;
   uint8_t* sb = smem + STAGES * A_BYTES;
 
@@ -150,8 +156,8 @@ __global__ void __launch_bounds__(128, 1)
       }
       const uint32_t fb = smem_u32(&bar_full[s]);
       mbar_expect_tx(fb, A_BYTES + B_BYTES);
-      tma_load_2d(smem_u32(sa + s * A_BYTES), &tmA, kb * BK, m0, fb);
-      tma_load_2d(smem_u32(sb + s * B_BYTES), &tmB, kb * BK, n0, fb);
+      tma_load_2d(smem_u32(sa + s * A_BYTES), &tmA, (kb0 + kb) * BK, m0, fb);
+      tma_load_2d(smem_u32(sb + s * B_BYTES), &tmB, (kb0 + kb) * BK, n0, fb);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -173,61 +179,52 @@ __global__ void __launch_bounds__(128, 1)
     mma_commit(smem_u32(&bar_done));
   }
   __syncwarp();
+  const bool empty_k = (nk == 0);
 
-  // ---------------- epilogue: TMEM -> registers -> global
+  // ---------------- epilogue: TMEM -> registers -> shared (transpose) -> coalesced global
   const bool done = mbar_wait(smem_u32(&bar_done), 0, 1l << 24);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + warp * 32 + lane;
   const bool ok = done && !fail_s;
-  for (int c = 0; c < BN; c += 16) {
-    float v[16];
+  // The ring buffers are free once every MMA has completed: each warp stages a
+  // 32 x 32 FP32 block there so that lanes walk columns when touching global memory.
+  float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+  const int rbase = m0 + warp * 32;
+  for (int c = 0; c < BN; c += 32) {
+    float v[32];
     tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-    const int col = n0 + c;
-    if (!ok || row >= M || col >= N) continue;
-    const int ncol = min(16, N - col);
-    if (ep.bias) {
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c + 16), v + 16);
+    if (empty_k) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) if (j < ncol) v[j] += ep.bias[col + j];
+      for (int j = 0; j < 32; ++j) v[j] = 0.f;
     }
-    if (ep.pre16) {
-      __nv_bfloat16* p = ep.pre16 + (size_t)row * ep.ldpre + col;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) if (j < ncol) p[j] = __float2bfloat16_rn(v[j]);
-    }
-    if (ep.act == 1) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = gelu_f(v[j]);
-    }
-    if (ep.resid) {
-      const float* rp = ep.resid + (size_t)row * ep.ldr + col;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) if (j < ncol) v[j] += rp[j];
-    }
-    if (ep.out32) {
-      float* o = ep.out32 + (size_t)row * ep.ld32 + col;
-      if (ncol == 16 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
-#pragma unroll
-        for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-      } else {
-        for (int j = 0; j < ncol; ++j) o[j] = v[j];
+    if (!ok || n0 + c >= N) continue;
+    if (ep.out16T && rbase + lane < M) {
+      // transposed copy: lanes are consecutive rows, so each column store is contiguous
+      const float* bb = ep.bias;
+      for (int j = 0; j < 32 && n0 + c + j < N; ++j) {
+        float y = v[j] + (bb ? bb[n0 + c + j] : 0.f);
+        if (ep.act == 1) y = gelu_f(y);
+        ep.out16T[(size_t)(n0 + c + j) * ep.ldT + rbase + lane] = __float2bfloat16_rn(y);
       }
     }
-    if (ep.out16) {
-      __nv_bfloat16* o = ep.out16 + (size_t)row * ep.ld16 + col;
-      if (ncol == 16 && ((reinterpret_cast<uintptr_t>(o) & 15) == 0)) {
-        uint4 pk[2];
-        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(pk);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) h[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-        reinterpret_cast<uint4*>(o)[0] = pk[0];
-        reinterpret_cast<uint4*>(o)[1] = pk[1];
-      } else {
-        for (int j = 0; j < ncol; ++j) o[j] = __float2bfloat16_rn(v[j]);
+    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+    __syncwarp();
+    const int col = n0 + c + lane;
+    if (col < N) {
+      const float bias = ep.bias ? ep.bias[col] : 0.f;
+      for (int rr = 0; rr < 32; ++rr) {
+        const int row = rbase + rr;
+        if (row >= M) break;
+        float y = stage[rr * 33 + lane] + bias;
+        if (ep.pre16) ep.pre16[(size_t)row * ep.ldpre + col] = __float2bfloat16_rn(y);
+        if (ep.act == 1) y = gelu_f(y);
+        if (ep.resid) y += ep.resid[(size_t)row * ep.ldr + col];
+        if (ep.out32) ep.out32[(size_t)blockIdx.z * ep.zstride + (size_t)row * ep.ld32 + col] = y;
+        if (ep.out16) ep.out16[(size_t)row * ep.ld16 + col] = __float2bfloat16_rn(y);
       }
     }
-    if (ep.out16T) {
-      for (int j = 0; j < ncol; ++j) ep.out16T[(size_t)(col + j) * ep.ldT + row] = __float2bfloat16_rn(v[j]);
-    }
+    __syncwarp();
   }
   if (!ok && threadIdx.x == 0 && ep.err) atomicExch(ep.err, (int)HMPCG_E_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -268,7 +265,7 @@ static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int
 
 template <int BN>
 static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) {
-  constexpr int STAGES = 4;
+  constexpr int STAGES = 3;
   const size_t smem = STAGES * (128 * 64 * 2 + BN * 64 * 2) + 1024;
   static bool attr_set = false;
   if (!attr_set) {
@@ -279,14 +276,16 @@ static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) 
   }
   CUtensorMap mb;
   if (!make_map(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
-  dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN);
+  dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, std::max(1, g.ksplit));
   gemm_bf16_tc_kernel<BN><<<grid, 128, smem, st>>>(ma, mb, g.ep, g.M, g.N, g.K);
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
 int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return HMPCG_OK;
-  if (g.K <= 0 || g.K % 64 || g.N % 16) return HMPCG_E_SHAPE;
+  if (g.K <= 0 || g.N % 16) return HMPCG_E_SHAPE;
+  if (g.ksplit > 1 && (g.ep.out16 || g.ep.out16T || g.ep.pre16 || g.ep.resid || g.ep.bias || g.ep.act))
+    return HMPCG_E_INVALID;   // split-K writes raw FP32 partials only
   CUtensorMap ma;
   if (!make_map(&ma, g.A, g.M, g.K, g.lda, 128)) return HMPCG_E_INVALID;
   int bn = g.bn;

@@ -19,38 +19,42 @@ WeightOff weight_offsets(const hmpcg_config& c) {
   WeightOff o;
   const int64_t d = c.d_model, dm = c.d_mlp, h = c.n_heads, L = c.leaf, r = c.rank;
   int64_t p = 0, p16 = 0;
+  int64_t rows_next = 1;
   auto take = [&](int64_t n) {
     int64_t q = p;
     o.seg32.push_back(p);
     o.seg16.push_back(p16);
     o.segn.push_back(n);
+    o.segr.push_back(rows_next);
+    o.segc.push_back(n / rows_next);
+    rows_next = 1;
     p += n;
     p16 += (n + 63) / 64 * 64;
     return q;
   };
-  o.enc1w = take(d * kFeat); o.enc1b = take(d);
-  o.enc2w = take(d * d); o.enc2b = take(d);
-  for (int g = 0; g < 2; ++g) { o.gcnw[g] = take(d * d); o.gcnb[g] = take(d); }
-  o.poolw = take(d * 2 * d); o.poolb = take(d);
+  rows_next = d; o.enc1w = take(d * kFeat); o.enc1b = take(d);
+  rows_next = d; o.enc2w = take(d * d); o.enc2b = take(d);
+  for (int g = 0; g < 2; ++g) { rows_next = d; o.gcnw[g] = take(d * d); o.gcnb[g] = take(d); }
+  rows_next = d; o.poolw = take(d * 2 * d); o.poolb = take(d);
   for (int s = 0; s < 2; ++s) {
     o.blk[s].resize(c.n_layers);
     for (int l = 0; l < c.n_layers; ++l) {
       BlockOff& b = o.blk[s][l];
       b.ln1g = take(d); b.ln1b = take(d);
-      b.qkvw = take(3 * d * d); b.qkvb = take(3 * d);
-      b.outw = take(d * d); b.outb = take(d);
+      rows_next = 3 * d; b.qkvw = take(3 * d * d); b.qkvb = take(3 * d);
+      rows_next = d; b.outw = take(d * d); b.outb = take(d);
       b.ln2g = take(d); b.ln2b = take(d);
-      b.f1w = take(dm * 4 * d); b.f1b = take(dm);
-      b.f2w = take(d * dm); b.f2b = take(d);
-      b.e1w = take(kEdgeHidden * 4); b.e1b = take(kEdgeHidden);
-      b.e2w = take(h * kEdgeHidden); b.e2b = take(h);
+      rows_next = dm; b.f1w = take(dm * 4 * d); b.f1b = take(dm);
+      rows_next = d; b.f2w = take(d * dm); b.f2b = take(d);
+      rows_next = kEdgeHidden; b.e1w = take(kEdgeHidden * 4); b.e1b = take(kEdgeHidden);
+      rows_next = h; b.e2w = take(h * kEdgeHidden); b.e2b = take(h);
     }
     o.lnfg[s] = take(d); o.lnfb[s] = take(d);
   }
-  o.leaf1w = take(d * d); o.leaf1b = take(d);
-  o.leaf2w = take(L * d); o.leaf2b = take(L);
-  o.nodew = take((2 * r + 1) * d); o.nodeb = take(2 * r + 1);
-  o.offw = take(2 * r * d); o.offb = take(2 * r);
+  rows_next = d; o.leaf1w = take(d * d); o.leaf1b = take(d);
+  rows_next = L; o.leaf2w = take(L * d); o.leaf2b = take(L);
+  rows_next = 2 * r + 1; o.nodew = take((2 * r + 1) * d); o.nodeb = take(2 * r + 1);
+  rows_next = 2 * r; o.offw = take(2 * r * d); o.offb = take(2 * r);
   o.total = p;
   o.total16 = p16;
   return o;
@@ -82,9 +86,23 @@ __global__ void cast_bf16_kernel(const float* __restrict__ a, bf16* __restrict__
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[o16 + i] = __float2bfloat16_rn(a[o32 + i]);
 }
 
+// One CTA per weight matrix: BF16 transposed copy (rows x cols -> cols x rows).
+__global__ void transpose_w_kernel(const float* __restrict__ a, bf16* __restrict__ b, const int64_t* __restrict__ segs,
+                                   int nseg) {
+  const int s = blockIdx.x;
+  if (s >= nseg) return;
+  const int64_t o32 = segs[5 * s], o16 = segs[5 * s + 1], n = segs[5 * s + 2], rows = segs[5 * s + 3],
+                cols = segs[5 * s + 4];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t rr = i / cols, cc = i % cols;
+    b[o16 + cc * rows + rr] = __float2bfloat16_rn(a[o32 + i]);
+  }
+}
+
 void net_refresh_bf16(Net* N, cudaStream_t st) {
   const int nseg = (int)N->off.seg32.size();
   cast_bf16_kernel<<<nseg, 256, 0, st>>>(N->w32, N->w16, N->segs, nseg);
+  if (N->w16t) transpose_w_kernel<<<nseg, 256, 0, st>>>(N->w32, N->w16t, N->segs5, nseg);
 }
 
 void net_destroy(Ctx* c);
@@ -114,6 +132,9 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
   N->max_tok_o = (int)To;
   N->w32 = (float*)alloc(4 * N->nw);
   N->w16 = (bf16*)alloc(2 * N->off.total16);
+  N->w16t = (bf16*)alloc(2 * N->off.total16);
+  N->segs5 = (int64_t*)alloc(8 * 5 * N->off.seg32.size());
+  N->tr = nullptr;
   N->segs = (int64_t*)alloc(8 * 3 * N->off.seg32.size());
   N->grad = (float*)alloc(4 * N->nw);
   N->m1 = (float*)alloc(4 * N->nw);
@@ -161,6 +182,8 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
   N->rhw = (float*)alloc(4 * Td * d);
   N->chw = (float*)alloc(4 * Td * d);
   N->gmean = (float*)alloc(4 * B * d);
+  N->gpart = (double*)alloc(8 * B * ((n + 63) / 64 + (MH * r + 63) / 64) * d);
+  N->etable = (float*)alloc(4 * h * L * L);
   N->err = (int*)alloc(256);
   if (!ok) { c->net = N; net_destroy(c); return HMPCG_E_NOMEM; }
   if (weights) {
@@ -174,6 +197,12 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
       segs.push_back(N->off.segn[q]);
     }
     if (cudaMemcpyAsync(N->segs, segs.data(), 8 * segs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
+    std::vector<int64_t> s5;
+    for (size_t q = 0; q < N->off.seg32.size(); ++q) {
+      s5.push_back(N->off.seg32[q]); s5.push_back(N->off.seg16[q]); s5.push_back(N->off.segn[q]);
+      s5.push_back(N->off.segr[q]); s5.push_back(N->off.segc[q]);
+    }
+    if (cudaMemcpyAsync(N->segs5, s5.data(), 8 * s5.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
     if (cudaStreamSynchronize(st) != cudaSuccess) ok = false;
   }
   net_refresh_bf16(N, st);
@@ -184,6 +213,7 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
 
 void net_destroy(Ctx* c) {
   if (!c->net) return;
+  net_train_release(c->net);
   for (void* p : c->net->allocs) cudaFree(p);
   delete c->net;
   c->net = nullptr;
@@ -258,7 +288,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
   }
   const float* xd0 = N->xg[2];
-  pool_kernel<<<(To + 7) / 8, 256, 0, st>>>(sb, xd0, d, N->pooled);
+  pool_kernel<<<To, 128, 0, st>>>(sb, xd0, d, N->pooled);
   edge_desc_off_kernel<<<(B * MH * r * r + 127) / 128, 128, 0, st>>>(sb, N->edesc_off);
   float* xcur[2];
   {
@@ -274,9 +304,12 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
       const int T = s == 0 ? Td : To;
       const int Wn = s == 0 ? L : r;
       const int nwin = T / Wn;
-      if (s == 0)
+      if (s == 0) {
+        edge_table_kernel<<<(Wn * Wn + 255) / 256, 256, 0, st>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w, W + bo.e2b, h,
+                                                                 N->etable);
         edge_bias_diag_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, st>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
-                                                                            W + bo.e2b, h, a.bias);
+                                                                            W + bo.e2b, h, N->etable, a.bias);
+      }
       else
         edge_bias_off_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, st>>>(sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
                                                                            W + bo.e2w, W + bo.e2b, h, a.bias);
@@ -285,10 +318,12 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
         GemmEpi ep = e; ep.bias = W + bo.qkvb; ep.out16 = a.qkv; ep.ld16 = 3 * d;
         NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, st));
       }
-      if (s == 0)
-        attention_kernel<64><<<dim3((T + 127) / 128, h), 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-      else
-        attention_kernel<16><<<dim3((T + 127) / 128, h), 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+      {
+        const dim3 ag((T + 127) / 128, h);
+        if (Wn == 64) attention_kernel<64><<<ag, 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else if (Wn == 32) attention_kernel<32><<<ag, 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else attention_kernel<16><<<ag, 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+      }
       {
         GemmEpi ep = e; ep.bias = W + bo.outb; ep.resid = a.x_in; ep.ldr = d; ep.out32 = a.x_mid; ep.ld32 = d;
         NET_TRY(gemm(a.o, d, W16 + o.map16(bo.outw), T, d, d, ep, st));
@@ -300,9 +335,13 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     StackAct& ad = N->act[0][l];
     StackAct& ao = N->act[1][l];
     highway_rc_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
-    highway_g_kernel<<<dim3(B, d / 32), 256, 0, st>>>(sb, ad.y2f, ao.y2f, d, N->gmean);
+    {
+      const int nch_d = (n + kGChunk - 1) / kGChunk, nch_o = (MH * r + kGChunk - 1) / kGChunk;
+      highway_g_partial_kernel<<<dim3(nch_d + nch_o, B), 128, 0, st>>>(sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
+      highway_g_final_kernel<<<B, 128, 0, st>>>(sb, N->gpart, d, nch_d + nch_o, N->gmean);
+    }
     concat_g_kernel<<<(Td + 7) / 8, 256, 0, st>>>(N->gmean, n, Td, d, ad.u);
-    highway_off_kernel<<<(To + 7) / 8, 256, 0, st>>>(sb, N->rhw, N->chw, N->gmean, d, ao.u);
+    highway_off_kernel<<<To, 128, 0, st>>>(sb, N->rhw, N->chw, N->gmean, d, ao.u);
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
       const BlockOff& bo = o.blk[s][l];
@@ -363,6 +402,14 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
     pack_nodes_kernel<bf16><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, (bf16*)packed, P);
     pack_tiles_kernel<bf16><<<Tt, 256, 0, st>>>(sb, N->offo, (bf16*)packed, P);
   }
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+int net_pack_f32(Net* N, const SysBatch& sb, float* packed, cudaStream_t st) {
+  const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
+  const int Td = sb.B * sb.n;
+  pack_nodes_kernel<float><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, packed, P);
+  pack_tiles_kernel<float><<<sb.B * sb.MH, 256, 0, st>>>(sb, N->offo, packed, P);
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 

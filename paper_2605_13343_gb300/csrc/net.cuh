@@ -23,6 +23,7 @@ struct GemmEpi {
   int ldT = 0;
   bf16* pre16 = nullptr;          // pre-activation copy (BF16)
   int ldpre = 0;
+  size_t zstride = 0;             // split-K: element offset between the partial tiles
   int* err = nullptr;
 };
 
@@ -34,6 +35,7 @@ struct GemmArgs {
   int ldb = 0;
   int M = 0, N = 0, K = 0;
   int bn = 0;                     // tile width (64/128/256); 0 = choose
+  int ksplit = 1;                 // split-K factor (FP32 partials at out32 + z * zstride)
   GemmEpi ep;
 };
 
@@ -55,7 +57,7 @@ struct WeightOff {
   int64_t total;
   // BF16 working copies live in a padded layout: every tensor starts on a
   // 64-element (128-byte) boundary so that TMA can read any weight matrix.
-  std::vector<int64_t> seg32, seg16, segn;
+  std::vector<int64_t> seg32, seg16, segn, segr, segc;   // offsets, count, rows x cols
   int64_t total16;
   int64_t map16(int64_t off32) const;
 };
@@ -85,6 +87,7 @@ struct Net {
   float* w32;        // FP32 master weights
   bf16* w16;         // BF16 copies (padded layout, see WeightOff::map16)
   int64_t* segs;     // (off32, off16, count) per tensor, on the device
+  int64_t* segs5;    // (off32, off16, count, rows, cols) per tensor, on the device
   float* grad;       // gradients (FP32, same offsets)
   float* m1; float* m2;   // AdamW moments
   int64_t step;
@@ -110,7 +113,13 @@ struct Net {
   float* gate_logit; // [Td]
   float* offo;       // [To][2r]
   float* rhw; float* chw; float* gmean;   // highway buffers (FP32)
+  double* gpart;     // per-chunk column sums for the global token
+  float* etable;     // edge-bias table of zero-coupling leaf pairs [h][L][L]
   int* err;
+  // transposed BF16 weights (same padded offsets; matrix (rows x cols) stored cols x rows)
+  bf16* w16t;
+  struct Train* tr;  // training buffers, allocated on the first train step
+  int num_sms = 148;
   // scratch for the backward pass and training
   std::vector<void*> allocs;
 };
@@ -132,5 +141,7 @@ struct SysBatch {
 
 int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, SysBatch& sb);
 int net_forward(Net* N, const SysBatch& sb, cudaStream_t st);
+int net_pack_f32(Net* N, const SysBatch& sb, float* packed, cudaStream_t st);
+void net_train_release(Net* N);
 void net_refresh_bf16(Net* N, cudaStream_t st);
 }  // namespace hm

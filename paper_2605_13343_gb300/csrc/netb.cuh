@@ -1,0 +1,879 @@
+// Training kernels (included by net_train.cu only): probes, the multi-RHS apply and its
+// backward, the cosine loss, and the backward of every network layer.
+#pragma once
+#include "net.cuh"
+
+namespace hm {
+namespace {
+
+HM_INLINE float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+HM_INLINE float gelu_grad(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
+HM_INLINE unsigned compactb(unsigned v, unsigned mask) {
+  unsigned out = 0, bit = 0;
+  while (mask) {
+    const unsigned low = mask & (0u - mask);
+    if (v & low) out |= 1u << bit;
+    ++bit;
+    mask &= mask - 1u;
+  }
+  return out;
+}
+struct TGeo { int lev, S, r0, c0, ch; };
+HM_INLINE TGeo tgeo(const SysBatch& sb, int m) {
+  TGeo g;
+  g.lev = 32 - __clz(m + 1);
+  const int t = m + 1 - (1 << (g.lev - 1));
+  g.S = sb.K >> g.lev;
+  g.r0 = 2 * t * g.S * sb.L;
+  g.c0 = (2 * t + 1) * g.S * sb.L;
+  g.ch = g.S * sb.L / sb.r;
+  return g;
+}
+
+// ------------------------------------------------------------------ probes and W = A Z
+// SplitMix64 (Steele, Lea & Flood 2014): output i of the stream keyed by `key` is
+// mix(key + (i + 1) * gamma).  Rademacher entry (i, j) of system b: bit 63 of output
+// i * nz + j of the stream keyed by mix(step_seed * 0x100000001B3 + b).
+HM_INLINE uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void probes_kernel(const SysBatch sb, uint64_t step_seed, int nz, float* __restrict__ z) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)sb.B * sb.n * nz;
+  if (idx >= tot) return;
+  const int b = (int)(idx / ((int64_t)sb.n * nz));
+  const int64_t e = idx % ((int64_t)sb.n * nz);
+  const uint64_t key = sm64_mix(step_seed * 0x100000001B3ull + (uint64_t)b);
+  const uint64_t v = sm64_mix(key + (uint64_t)(e + 1) * 0x9E3779B97F4A7C15ull);
+  z[idx] = (v >> 63) ? -1.f : 1.f;
+}
+// W = A Z with the FP64 operator (rounded to FP32), node-major [n][nz].
+__global__ void spmv_multi_kernel(const SysBatch sb, int nz, const float* __restrict__ z, float* __restrict__ w) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)sb.B * sb.n * nz) return;
+  const int c = (int)(idx % nz);
+  const int64_t t = idx / nz;
+  const int b = (int)(t / sb.n), i = (int)(t % sb.n);
+  const size_t base = (size_t)b * sb.n;
+  double acc = sb.diag[b][i] * (double)z[(base + i) * nz + c];
+  for (int a = 0; a < sb.ndim; ++a) {
+    const int jp = sb.mo.plus(i, a);
+    if (jp >= 0) acc -= sb.w[b][a][i] * (double)z[(base + jp) * nz + c];
+    const int jm = sb.mo.minus(i, a);
+    if (jm >= 0) acc -= sb.w[b][a][jm] * (double)z[(base + jm) * nz + c];
+  }
+  w[idx] = (float)acc;
+}
+
+// ------------------------------------------------------------------ multi-RHS apply (FP32 packed)
+// Packed offsets of the learned layout for one system.
+struct PackOff { int64_t B, U, V, G, P; };
+HM_INLINE PackOff pack_off(const SysBatch& sb) {
+  PackOff o;
+  o.B = (int64_t)sb.K * sb.L * sb.L;
+  o.U = o.B + (int64_t)sb.MH * sb.r * sb.r;
+  o.V = o.U + (int64_t)sb.n * sb.r;
+  o.G = o.V + (int64_t)sb.n * sb.r;
+  o.P = o.G + sb.n;
+  return o;
+}
+
+// Stage (i) and restriction for leaf (b, k) with nz right-hand sides:
+// y = F (F^T W) + g W;  uh = U~^T W;  vh = V~^T W.   (L <= 64, r <= 32, nz <= 32)
+__global__ void tapply_restrict_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
+                                       const float* __restrict__ w, float* __restrict__ y,
+                                       float* __restrict__ uh, float* __restrict__ vh) {
+  __shared__ float ws[64][33];
+  __shared__ float p1[64][33];
+  const int L = sb.L, r = sb.r;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  const PackOff o = pack_off(sb);
+  const float* P = pk + (size_t)b * o.P;
+  const float* F = P + (int64_t)k * L * L;
+  const size_t nb = (size_t)b * sb.n + (size_t)k * L;
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) ws[q / nz][q % nz] = w[(nb + q / nz) * nz + q % nz];
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
+    const int i = q / nz, c = q % nz;     // p1[i][c] = sum_a F[a][i] W[a][c]
+    float s = 0.f;
+    for (int a = 0; a < L; ++a) s = fmaf(F[a * L + i], ws[a][c], s);
+    p1[i][c] = s;
+  }
+  for (int q = threadIdx.x; q < 2 * r * nz; q += blockDim.x) {
+    const int side = q / (r * nz), e = (q / nz) % r, c = q % nz;
+    const float* Ub = P + (side ? o.V : o.U) + ((size_t)k * L) * r;
+    float s = 0.f;
+    for (int a = 0; a < L; ++a) s = fmaf(Ub[a * r + e], ws[a][c], s);
+    (side ? vh : uh)[(((size_t)b * sb.K + k) * r + e) * nz + c] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
+    const int i = q / nz, c = q % nz;
+    float s = P[o.G + (int64_t)k * L + i] * ws[i][c];
+    for (int a = 0; a < L; ++a) s = fmaf(F[i * L + a], p1[a][c], s);
+    y[(nb + i) * nz + c] = s;
+  }
+}
+
+// Strip aggregation + coupling for tile (b, m): sr = sum_R uh, sc = sum_C vh;
+// tr = B sc, tc = B^T sr (and the same for a second pair of inputs when given).
+__global__ void tapply_tile_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
+                                   const float* __restrict__ uh, const float* __restrict__ vh,
+                                   float* __restrict__ sr_out, float* __restrict__ sc_out,
+                                   float* __restrict__ tr, float* __restrict__ tc) {
+  __shared__ float sr[32][33], sc[32][33];
+  const int r = sb.r;
+  const int b = blockIdx.x / sb.MH, m = blockIdx.x % sb.MH;
+  const TGeo g = tgeo(sb, m);
+  const int kr0 = g.r0 / sb.L, kc0 = g.c0 / sb.L;
+  const PackOff o = pack_off(sb);
+  const float* Bm = pk + (size_t)b * o.P + o.B + (int64_t)m * r * r;
+  for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
+    const int e = q / nz, c = q % nz;
+    float a0 = 0.f, a1 = 0.f;
+    for (int kk = 0; kk < g.S; ++kk) {
+      a0 += uh[(((size_t)b * sb.K + kr0 + kk) * r + e) * nz + c];
+      a1 += vh[(((size_t)b * sb.K + kc0 + kk) * r + e) * nz + c];
+    }
+    sr[e][c] = a0;
+    sc[e][c] = a1;
+    if (sr_out) {
+      sr_out[(((size_t)b * sb.MH + m) * r + e) * nz + c] = a0;
+      sc_out[(((size_t)b * sb.MH + m) * r + e) * nz + c] = a1;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
+    const int e = q / nz, c = q % nz;
+    float s0 = 0.f, s1 = 0.f;
+    for (int f = 0; f < r; ++f) {
+      s0 = fmaf(Bm[e * r + f], sc[f][c], s0);   // (B sc)[e]
+      s1 = fmaf(Bm[f * r + e], sr[f][c], s1);   // (B^T sr)[e]
+    }
+    tr[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s0;
+    tc[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s1;
+  }
+}
+
+// Gather of the coupling outputs a leaf receives: au = sum over levels where the leaf
+// is in a row cluster of tr, av = sum over the others of tc.
+HM_INLINE void gather_levels(const SysBatch& sb, int b, int k, int e, int c, int nz, const float* tr,
+                             const float* tc, float& au, float& av) {
+  au = 0.f;
+  av = 0.f;
+  for (int lev = 1; lev <= sb.levels; ++lev) {
+    const int S = sb.K >> lev;
+    const int cl = k / S;
+    const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+    const size_t ix = (((size_t)b * sb.MH + m) * sb.r + e) * nz + c;
+    if (cl & 1) av += tc[ix]; else au += tr[ix];
+  }
+}
+
+// Prolongation for leaf (b, k): y += U~ au + V~ av; au / av are kept for the backward pass.
+__global__ void tapply_prolong_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
+                                      const float* __restrict__ tr, const float* __restrict__ tc,
+                                      float* __restrict__ y, float* __restrict__ au_out, float* __restrict__ av_out) {
+  __shared__ float au[32][33], av[32][33];
+  const int L = sb.L, r = sb.r;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  const PackOff o = pack_off(sb);
+  const float* P = pk + (size_t)b * o.P;
+  for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
+    const int e = q / nz, c = q % nz;
+    float a0, a1;
+    gather_levels(sb, b, k, e, c, nz, tr, tc, a0, a1);
+    au[e][c] = a0;
+    av[e][c] = a1;
+    au_out[(((size_t)b * sb.K + k) * r + e) * nz + c] = a0;
+    av_out[(((size_t)b * sb.K + k) * r + e) * nz + c] = a1;
+  }
+  __syncthreads();
+  const size_t nb = (size_t)b * sb.n + (size_t)k * L;
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
+    const int i = q / nz, c = q % nz;
+    const float* Ur = P + o.U + (nb - (size_t)b * sb.n + i) * r;
+    const float* Vr = P + o.V + (nb - (size_t)b * sb.n + i) * r;
+    float s = y[(nb + i) * nz + c];
+    for (int e = 0; e < r; ++e) s = fmaf(Ur[e], au[e][c], fmaf(Vr[e], av[e][c], s));
+    y[(nb + i) * nz + c] = s;
+  }
+}
+
+// ------------------------------------------------------------------ loss
+// Per system: zy = <Z, Y>, zz = ||Z||^2, yy = ||Y||^2 (FP64, fixed order).
+__global__ void loss_sums_kernel(const SysBatch sb, int nz, const float* __restrict__ z, const float* __restrict__ y,
+                                 double* __restrict__ sums) {
+  __shared__ double red[3][32];
+  const int b = blockIdx.x;
+  const size_t n = (size_t)sb.n * nz;
+  const float* zb = z + (size_t)b * n;
+  const float* yb = y + (size_t)b * n;
+  double zy = 0, zz = 0, yy = 0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = zb[i], c = yb[i];
+    zy += a * c; zz += a * a; yy += c * c;
+  }
+  zy = warp_sum(zy); zz = warp_sum(zz); yy = warp_sum(yy);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][w] = zy; red[1][w] = zz; red[2][w] = yy; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { s0 += red[0][q]; s1 += red[1][q]; s2 += red[2][q]; }
+    sums[3 * b] = s0; sums[3 * b + 1] = s1; sums[3 * b + 2] = s2;
+  }
+}
+// dL/dY for L = mean_b (1 - zy / sqrt(zz yy)).
+__global__ void loss_grad_kernel(const SysBatch sb, int nz, const float* __restrict__ z, const float* __restrict__ y,
+                                 const double* __restrict__ sums, float* __restrict__ dy) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)sb.n * nz;
+  if (idx >= sb.B * per) return;
+  const int b = (int)(idx / per);
+  const double zy = sums[3 * b], zz = sums[3 * b + 1], yy = sums[3 * b + 2];
+  const double nzy = sqrt(zz * yy);
+  const double c1 = -1.0 / (sb.B * nzy), c2 = zy / (sb.B * nzy * yy);
+  dy[idx] = (float)(c1 * z[idx] + c2 * y[idx]);
+}
+
+// ------------------------------------------------------------------ apply backward
+// Leaf (b, k): dF = G P1^T + W P2^T (P1 = F^T W, P2 = F^T G); dg = sum_c G W;
+// qu = U~^T G, qv = V~^T G.
+__global__ void tbwd_restrict_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
+                                     const float* __restrict__ w, const float* __restrict__ gy,
+                                     float* __restrict__ dpk, float* __restrict__ qu, float* __restrict__ qv) {
+  __shared__ float ws[64][33], gs[64][33], p1[64][33], p2[64][33];
+  const int L = sb.L, r = sb.r;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  const PackOff o = pack_off(sb);
+  const float* P = pk + (size_t)b * o.P;
+  float* D = dpk + (size_t)b * o.P;
+  const float* F = P + (int64_t)k * L * L;
+  const size_t nb = (size_t)b * sb.n + (size_t)k * L;
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
+    ws[q / nz][q % nz] = w[(nb + q / nz) * nz + q % nz];
+    gs[q / nz][q % nz] = gy[(nb + q / nz) * nz + q % nz];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
+    const int i = q / nz, c = q % nz;
+    float s1 = 0.f, s2 = 0.f;
+    for (int a = 0; a < L; ++a) { s1 = fmaf(F[a * L + i], ws[a][c], s1); s2 = fmaf(F[a * L + i], gs[a][c], s2); }
+    p1[i][c] = s1;
+    p2[i][c] = s2;
+  }
+  for (int q = threadIdx.x; q < 2 * r * nz; q += blockDim.x) {
+    const int side = q / (r * nz), e = (q / nz) % r, c = q % nz;
+    const float* Ub = P + (side ? o.V : o.U) + ((size_t)k * L) * r;
+    float s = 0.f;
+    for (int a = 0; a < L; ++a) s = fmaf(Ub[a * r + e], gs[a][c], s);
+    (side ? qv : qu)[(((size_t)b * sb.K + k) * r + e) * nz + c] = s;
+  }
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < nz; ++c) s = fmaf(gs[i][c], ws[i][c], s);
+    D[o.G + (int64_t)k * L + i] = s;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < L * L; q += blockDim.x) {
+    const int i = q / L, j = q % L;
+    float s = 0.f;
+    for (int c = 0; c < nz; ++c) s = fmaf(gs[i][c], p1[j][c], fmaf(ws[i][c], p2[j][c], s));
+    D[(int64_t)k * L * L + q] = s;
+  }
+}
+
+// Tile (b, m): qr = sum_R qu, qc = sum_C qv; dB = qr sc^T + sr qc^T; ur = B qc, uc = B^T qr.
+__global__ void tbwd_tile_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
+                                 const float* __restrict__ qu, const float* __restrict__ qv,
+                                 const float* __restrict__ srs, const float* __restrict__ scs,
+                                 float* __restrict__ dpk, float* __restrict__ ur, float* __restrict__ uc) {
+  __shared__ float qr[32][33], qc[32][33], sr[32][33], sc[32][33];
+  const int r = sb.r;
+  const int b = blockIdx.x / sb.MH, m = blockIdx.x % sb.MH;
+  const TGeo g = tgeo(sb, m);
+  const int kr0 = g.r0 / sb.L, kc0 = g.c0 / sb.L;
+  const PackOff o = pack_off(sb);
+  const float* Bm = pk + (size_t)b * o.P + o.B + (int64_t)m * r * r;
+  for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
+    const int e = q / nz, c = q % nz;
+    float a0 = 0.f, a1 = 0.f;
+    for (int kk = 0; kk < g.S; ++kk) {
+      a0 += qu[(((size_t)b * sb.K + kr0 + kk) * r + e) * nz + c];
+      a1 += qv[(((size_t)b * sb.K + kc0 + kk) * r + e) * nz + c];
+    }
+    qr[e][c] = a0;
+    qc[e][c] = a1;
+    sr[e][c] = srs[(((size_t)b * sb.MH + m) * r + e) * nz + c];
+    sc[e][c] = scs[(((size_t)b * sb.MH + m) * r + e) * nz + c];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
+    const int e = q / r, f = q % r;
+    float s = 0.f;
+    for (int c = 0; c < nz; ++c) s = fmaf(qr[e][c], sc[f][c], fmaf(sr[e][c], qc[f][c], s));
+    dpk[(size_t)b * o.P + o.B + (int64_t)m * r * r + q] = s;
+  }
+  for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
+    const int e = q / nz, c = q % nz;
+    float s0 = 0.f, s1 = 0.f;
+    for (int f = 0; f < r; ++f) {
+      s0 = fmaf(Bm[e * r + f], qc[f][c], s0);
+      s1 = fmaf(Bm[f * r + e], qr[f][c], s1);
+    }
+    ur[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s0;
+    uc[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s1;
+  }
+}
+
+// Leaf (b, k): dU~ = G au^T + W bu^T, dV~ = G av^T + W bv^T with bu / bv the gathered
+// backward couplings.
+__global__ void tbwd_prolong_kernel(const SysBatch sb, int nz, const float* __restrict__ w,
+                                    const float* __restrict__ gy, const float* __restrict__ au_s,
+                                    const float* __restrict__ av_s, const float* __restrict__ ur,
+                                    const float* __restrict__ uc, float* __restrict__ dpk) {
+  __shared__ float au[32][33], av[32][33], bu[32][33], bv[32][33];
+  const int L = sb.L, r = sb.r;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  const PackOff o = pack_off(sb);
+  for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
+    const int e = q / nz, c = q % nz;
+    au[e][c] = au_s[(((size_t)b * sb.K + k) * r + e) * nz + c];
+    av[e][c] = av_s[(((size_t)b * sb.K + k) * r + e) * nz + c];
+    float b0, b1;
+    gather_levels(sb, b, k, e, c, nz, ur, uc, b0, b1);
+    bu[e][c] = b0;
+    bv[e][c] = b1;
+  }
+  __syncthreads();
+  const size_t nb = (size_t)b * sb.n + (size_t)k * L;
+  float* D = dpk + (size_t)b * o.P;
+  for (int q = threadIdx.x; q < L * r; q += blockDim.x) {
+    const int i = q / r, e = q % r;
+    float su = 0.f, sv = 0.f;
+    for (int c = 0; c < nz; ++c) {
+      const float gg = gy[(nb + i) * nz + c], ww = w[(nb + i) * nz + c];
+      su = fmaf(gg, au[e][c], fmaf(ww, bu[e][c], su));
+      sv = fmaf(gg, av[e][c], fmaf(ww, bv[e][c], sv));
+    }
+    D[o.U + ((int64_t)k * L + i) * r + e] = su;
+    D[o.V + ((int64_t)k * L + i) * r + e] = sv;
+  }
+}
+
+// ------------------------------------------------------------------ pack backward
+// Node rows: dfrow = dF rows * s, dnodeo = [dU~, dV~] * s, dlogit = dg * sigmoid(logit) / d.
+__global__ void pack_bwd_nodes_kernel(const SysBatch sb, const float* __restrict__ dpk,
+                                      const float* __restrict__ glog, float* __restrict__ dfrow,
+                                      float* __restrict__ dnodeo, float* __restrict__ dlog) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const int L = sb.L, r = sb.r;
+  const PackOff o = pack_off(sb);
+  const float* D = dpk + (size_t)b * o.P;
+  const double di = sb.diag[b][i];
+  const float s = (float)(1.0 / sqrt(di));
+  const int k = i / L, a = i % L;
+  for (int c = lane; c < L; c += 32) dfrow[(size_t)t * L + c] = D[(int64_t)k * L * L + a * L + c] * s;
+  for (int c = lane; c < r; c += 32) {
+    dnodeo[(size_t)t * 2 * r + c] = D[o.U + (int64_t)i * r + c] * s;
+    dnodeo[(size_t)t * 2 * r + r + c] = D[o.V + (int64_t)i * r + c] * s;
+  }
+  if (lane == 0) {
+    const float x = glog[t];
+    const float sig = 1.f / (1.f + expf(-x));
+    dlog[t] = (float)(D[o.G + i] * sig / di);
+  }
+}
+// Tiles: B = U V^T  ->  dU = dB V, dV = dB^T U (into doffo rows).
+__global__ void pack_bwd_tiles_kernel(const SysBatch sb, const float* __restrict__ offo, const float* __restrict__ dpk,
+                                      float* __restrict__ doffo) {
+  const int r = sb.r;
+  const int tile = blockIdx.x;
+  const int b = tile / sb.MH, m = tile % sb.MH;
+  const PackOff o = pack_off(sb);
+  const float* dB = dpk + (size_t)b * o.P + o.B + (int64_t)m * r * r;
+  const float* base = offo + (size_t)tile * r * 2 * r;
+  float* dbase = doffo + (size_t)tile * r * 2 * r;
+  for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
+    const int a = q / r, e = q % r;
+    float su = 0.f, sv = 0.f;
+    for (int c = 0; c < r; ++c) {
+      su = fmaf(dB[a * r + c], base[c * 2 * r + r + e], su);   // dU[a][e] = sum_c dB[a][c] V[c][e]
+      sv = fmaf(dB[c * r + a], base[c * 2 * r + e], sv);       // dV[a][e] = sum_c dB[c][a] U[c][e]
+    }
+    dbase[a * 2 * r + e] = su;
+    dbase[a * 2 * r + r + e] = sv;
+  }
+}
+
+// ------------------------------------------------------------------ generic helpers
+// dY (FP32, T x N, row stride ldy) -> BF16 copy (T x N), BF16 transpose (N x T), and
+// per-64-token column sums (bias gradient partials).
+__global__ void prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int N, bf16* __restrict__ d16,
+                               bf16* __restrict__ d16t, float* __restrict__ colpart) {
+  __shared__ float tile[64][65];
+  const int t0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+    const int tt = q / 64, nn = q % 64;
+    const int t = t0 + tt, n = n0 + nn;
+    float v = (t < T && n < N) ? dy[(size_t)t * ldy + n] : 0.f;
+    tile[tt][nn] = v;
+    if (t < T && n < N && d16) d16[(size_t)t * N + n] = __float2bfloat16_rn(v);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+    const int nn = q / 64, tt = q % 64;
+    const int t = t0 + tt, n = n0 + nn;
+    if (t < T && n < N && d16t) d16t[(size_t)n * T + t] = __float2bfloat16_rn(tile[tt][nn]);
+  }
+  if (colpart) {
+    for (int nn = threadIdx.x; nn < 64; nn += blockDim.x) {
+      if (n0 + nn >= N) continue;
+      float s = 0.f;
+      for (int tt = 0; tt < 64; ++tt) s += tile[tt][nn];
+      colpart[(size_t)blockIdx.x * N + n0 + nn] = s;
+    }
+  }
+}
+// BF16 (T x K, row stride ld) -> BF16 transpose (K x T).
+__global__ void transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K, bf16* __restrict__ xt) {
+  __shared__ bf16 tile[64][66];
+  const int t0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
+  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+    const int tt = q / 64, kk = q % 64;
+    const int t = t0 + tt, k = k0 + kk;
+    tile[tt][kk] = (t < T && k < K) ? x[(size_t)t * ld + k] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+    const int kk = q / 64, tt = q % 64;
+    const int t = t0 + tt, k = k0 + kk;
+    if (t < T && k < K) xt[(size_t)k * T + t] = tile[tt][kk];
+  }
+}
+// out[j] (+)= sum over parts p of part[p * n + j], fixed order.
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int64_t n, float* __restrict__ out,
+                                    int accumulate) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float s = 0.f;
+  for (int p = 0; p < nparts; ++p) s += part[(size_t)p * n + j];
+  out[j] = accumulate ? out[j] + s : s;
+}
+// Elementwise: d_pre = d_act * gelu'(pre)  (FP32 in place).
+__global__ void gelu_bwd_kernel(float* __restrict__ g, const bf16* __restrict__ pre, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) g[i] *= gelu_grad(__bfloat162float(pre[i]));
+}
+
+// LayerNorm backward (warp per token): dx (+)= rs (dy g - mean(dy g) - xh mean(dy g xh));
+// per-CTA partials of dgamma = sum dy xh and dbeta = sum dy (8 tokens per CTA).
+__global__ void layernorm_bwd_kernel(const float* __restrict__ dy, int ldy, const float* __restrict__ x,
+                                     const float* __restrict__ mu, const float* __restrict__ rs,
+                                     const float* __restrict__ gam, int T, int d, float* __restrict__ dx,
+                                     int accumulate, float* __restrict__ gpart) {
+  __shared__ float pg[8][256], pb[8][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  const int per = d / 32;
+  float xh[8], g[8];
+  if (t < T) {
+    float s1 = 0.f, s2 = 0.f;
+    for (int q = 0; q < per; ++q) {
+      const int c = lane + 32 * q;
+      xh[q] = (x[(size_t)t * d + c] - mu[t]) * rs[t];
+      g[q] = dy[(size_t)t * ldy + c];
+      const float gg = g[q] * gam[c];
+      s1 += gg;
+      s2 += gg * xh[q];
+    }
+    s1 = warp_sum(s1) / d;
+    s2 = warp_sum(s2) / d;
+    for (int q = 0; q < per; ++q) {
+      const int c = lane + 32 * q;
+      const float v = rs[t] * (g[q] * gam[c] - s1 - xh[q] * s2);
+      dx[(size_t)t * d + c] = accumulate ? dx[(size_t)t * d + c] + v : v;
+      pg[warp][c] = g[q] * xh[q];
+      pb[warp][c] = g[q];
+    }
+  } else {
+    for (int q = 0; q < per; ++q) { pg[warp][lane + 32 * q] = 0.f; pb[warp][lane + 32 * q] = 0.f; }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    float sg = 0.f, sbb = 0.f;
+    for (int q = 0; q < 8; ++q) { sg += pg[q][c]; sbb += pb[q][c]; }
+    gpart[(size_t)blockIdx.x * 2 * d + c] = sg;
+    gpart[(size_t)blockIdx.x * 2 * d + d + c] = sbb;
+  }
+}
+
+// ------------------------------------------------------------------ attention backward
+// Two passes per (64-token block, head): pass 1 (thread = query) gives dQ and dbias,
+// pass 2 (thread = key) gives dK and dV; both recompute P from Q, K, bias and lse.
+template <int W>
+__global__ void __launch_bounds__(64) attention_bwd_kernel(const bf16* __restrict__ qkv, const float* __restrict__ bias,
+                                                            const float* __restrict__ lse, const float* __restrict__ dout,
+                                                            int T, int d, int h, float* __restrict__ dqkv,
+                                                            float* __restrict__ dbias) {
+  __shared__ float qs[64][33], ks[64][33], vs[64][33], dos[64][33];
+  __shared__ float lses[64], dd[64];
+  const int head = blockIdx.y;
+  const int t0 = blockIdx.x * 64;
+  const int tl = threadIdx.x;
+  const int t = t0 + tl;
+  const int ld = 3 * d;
+  const float scale = 0.17677669529663688f;
+  if (t < T) {
+    for (int c = 0; c < 32; ++c) {
+      qs[tl][c] = __bfloat162float(qkv[(size_t)t * ld + head * 32 + c]) * scale;
+      ks[tl][c] = __bfloat162float(qkv[(size_t)t * ld + d + head * 32 + c]);
+      vs[tl][c] = __bfloat162float(qkv[(size_t)t * ld + 2 * d + head * 32 + c]);
+      dos[tl][c] = dout[(size_t)t * d + head * 32 + c];
+    }
+    lses[tl] = lse[(size_t)t * h + head];
+  }
+  __syncthreads();
+  if (t < T) {
+    const int win = t / W, a = t % W, ws = win * W - t0;
+    const float* bp = bias + (((size_t)win * h + head) * W + a) * W;
+    float p[W], dp[W];
+    float D = 0.f;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      float s = bp[j], g = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) { s = fmaf(qs[tl][c], ks[ws + j][c], s); g = fmaf(dos[tl][c], vs[ws + j][c], g); }
+      p[j] = __expf(s - lses[tl]);
+      dp[j] = g;
+      D = fmaf(p[j], g, D);
+    }
+    dd[tl] = D;
+    float dq[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) dq[c] = 0.f;
+    float* dbp = dbias + (((size_t)win * h + head) * W + a) * W;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const float ds = p[j] * (dp[j] - D);
+      dbp[j] = ds;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) dq[c] = fmaf(ds, ks[ws + j][c], dq[c]);
+    }
+    for (int c = 0; c < 32; ++c) dqkv[(size_t)t * ld + head * 32 + c] = dq[c] * scale;
+  }
+  __syncthreads();
+  if (t < T) {
+    const int win = t / W, jj = t % W, ws = win * W - t0;
+    float dk[32], dv[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { dk[c] = 0.f; dv[c] = 0.f; }
+#pragma unroll 4
+    for (int a = 0; a < W; ++a) {
+      const int q = ws + a;
+      float s = bias[(((size_t)win * h + head) * W + a) * W + jj], g = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) { s = fmaf(qs[q][c], ks[tl][c], s); g = fmaf(dos[q][c], vs[tl][c], g); }
+      const float p = __expf(s - lses[q]);
+      const float ds = p * (g - dd[q]);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) { dv[c] = fmaf(p, dos[q][c], dv[c]); dk[c] = fmaf(ds, qs[q][c], dk[c]); }
+    }
+    for (int c = 0; c < 32; ++c) {
+      dqkv[(size_t)t * ld + d + head * 32 + c] = dk[c];
+      dqkv[(size_t)t * ld + 2 * d + head * 32 + c] = dv[c];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ edge-bias MLP backward
+// 128 pairs per CTA: per-CTA partial gradients of (w1, b1, w2, b2) in the blob order
+// w1 [32][4], b1 [32], w2 [h][32], b2 [h].
+struct EdgeW { float w1[kEdgeHidden * 4], b1[kEdgeHidden], w2[8 * kEdgeHidden], b2[8]; };
+HM_INLINE void edge_desc_leaf(const SysBatch& sb, int bsys, int k, int a, int bb, float* e) {
+  const unsigned i = k * sb.L + a, j = k * sb.L + bb;
+  for (int ax = 0; ax < 3; ++ax)
+    e[ax] = ax < sb.ndim ? ((float)compactb(j, sb.mo.mask[ax]) - (float)compactb(i, sb.mo.mask[ax])) / sb.leaf_side : 0.f;
+  float al = 0.f;
+  if (a == bb) {
+    al = 1.f;
+  } else {
+    const double* dg = sb.diag[bsys];
+    for (int ax = 0; ax < sb.ndim; ++ax) {
+      if (sb.mo.plus(i, ax) == (int)j) al = (float)(-sb.w[bsys][ax][i] / sqrt(dg[i] * dg[j]));
+      if (sb.mo.minus(i, ax) == (int)j) al = (float)(-sb.w[bsys][ax][j] / sqrt(dg[i] * dg[j]));
+    }
+  }
+  e[3] = al;
+}
+__global__ void edge_bwd_kernel(const SysBatch sb, int diag, const float* __restrict__ edesc, const float* w1,
+                                const float* b1, const float* w2, const float* b2, int h, int W,
+                                const float* __restrict__ dbias, int npairs, float* __restrict__ part) {
+  __shared__ EdgeW s;
+  __shared__ float es[128][5], zs[128][kEdgeHidden + 1], hs[128][kEdgeHidden + 1], dzs[128][kEdgeHidden + 1],
+      dos[128][9];
+  for (int q = threadIdx.x; q < kEdgeHidden * 4; q += blockDim.x) s.w1[q] = w1[q];
+  for (int q = threadIdx.x; q < kEdgeHidden; q += blockDim.x) s.b1[q] = b1[q];
+  for (int q = threadIdx.x; q < h * kEdgeHidden; q += blockDim.x) s.w2[q] = w2[q];
+  for (int q = threadIdx.x; q < h; q += blockDim.x) s.b2[q] = b2[q];
+  __syncthreads();
+  const int pl = threadIdx.x;
+  const int64_t pidx = (int64_t)blockIdx.x * 128 + pl;
+  float e[4] = {0.f, 0.f, 0.f, 0.f};
+  float dout[8];
+  for (int q = 0; q < 8; ++q) dout[q] = 0.f;
+  if (pidx < npairs) {
+    const int bb = (int)(pidx % W), a = (int)((pidx / W) % W);
+    const int64_t win = pidx / ((int64_t)W * W);
+    if (diag) edge_desc_leaf(sb, (int)(win / sb.K), (int)(win % sb.K), a, bb, e);
+    else for (int q = 0; q < 4; ++q) e[q] = edesc[pidx * 4 + q];
+    for (int hh = 0; hh < h; ++hh) dout[hh] = dbias[((win * h + hh) * W + a) * W + bb];
+  }
+  for (int q = 0; q < 4; ++q) es[pl][q] = e[q];
+  for (int hh = 0; hh < 8; ++hh) dos[pl][hh] = dout[hh];
+  for (int kk = 0; kk < kEdgeHidden; ++kk) {
+    float z = s.b1[kk];
+    for (int q = 0; q < 4; ++q) z = fmaf(s.w1[kk * 4 + q], e[q], z);
+    float dh = 0.f;
+    for (int hh = 0; hh < h; ++hh) dh = fmaf(s.w2[hh * kEdgeHidden + kk], dout[hh], dh);
+    zs[pl][kk] = z;
+    hs[pl][kk] = gelu_f(z);
+    dzs[pl][kk] = (pidx < npairs) ? dh * gelu_grad(z) : 0.f;
+  }
+  __syncthreads();
+  const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    float acc = 0.f;
+    if (q < kEdgeHidden * 4) {
+      const int kk = q / 4, c = q % 4;
+      for (int p = 0; p < 128; ++p) acc = fmaf(dzs[p][kk], es[p][c], acc);
+    } else if (q < kEdgeHidden * 5) {
+      const int kk = q - kEdgeHidden * 4;
+      for (int p = 0; p < 128; ++p) acc += dzs[p][kk];
+    } else if (q < kEdgeHidden * 5 + h * kEdgeHidden) {
+      const int u = q - kEdgeHidden * 5, hh = u / kEdgeHidden, kk = u % kEdgeHidden;
+      for (int p = 0; p < 128; ++p) acc = fmaf(dos[p][hh], hs[p][kk], acc);
+    } else {
+      const int hh = q - kEdgeHidden * 5 - h * kEdgeHidden;
+      for (int p = 0; p < 128; ++p) acc += dos[p][hh];
+    }
+    part[(size_t)blockIdx.x * np + q] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ highway backward
+// Column sums of the global-token slice of the FFN-input gradients, per system (2 stages).
+__global__ void hwb_g_partial_kernel(const SysBatch sb, const float* __restrict__ dud, const float* __restrict__ duo,
+                                     int d, int nch_d, int nch_o, double* __restrict__ part) {
+  const int b = blockIdx.y, ch = blockIdx.x;
+  const int no = sb.MH * sb.r;
+  const float* src;
+  int t0, t1;
+  if (ch < nch_d) { src = dud + (size_t)b * sb.n * 4 * d; t0 = ch * 64; t1 = min(sb.n, t0 + 64); }
+  else { src = duo + (size_t)b * no * 4 * d; t0 = (ch - nch_d) * 64; t1 = min(no, t0 + 64); }
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    double s = 0.0;
+    for (int t = t0; t < t1; ++t) s += src[(size_t)t * 4 * d + 3 * d + c];
+    part[((size_t)b * (nch_d + nch_o) + ch) * d + c] = s;
+  }
+}
+__global__ void hwb_g_final_kernel(const SysBatch sb, const double* __restrict__ part, int d, int nch,
+                                   float* __restrict__ dg) {
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nch; ++q) s += part[((size_t)b * nch + q) * d + c];
+    dg[(size_t)b * d + c] = (float)(s / (sb.n + sb.MH * sb.r));   // already divided by the token count
+  }
+}
+// Diagonal tokens: er = d r_hw / cnt_r, ec = d c_hw / cnt_c; dy2d = du_own + er + ec + dg.
+__global__ void hwb_rc_kernel(const SysBatch sb, const float* __restrict__ dud, const float* __restrict__ duo,
+                              const float* __restrict__ dg, int d, float* __restrict__ er, float* __restrict__ ec,
+                              float* __restrict__ dy2d) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const int k = i / sb.L;
+  int toks[32], chs[32];
+  int sides = 0, nl = 0;
+  for (int lev = 1; lev <= sb.levels; ++lev) {
+    const int S = sb.K >> lev;
+    const int cl = k / S;
+    const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+    const int ch = S * sb.L / sb.r;
+    const int a = (i - cl * S * sb.L) / ch;
+    toks[nl] = (b * sb.MH + m) * sb.r + a;
+    chs[nl] = ch;
+    if (cl & 1) sides |= 1 << nl;
+    ++nl;
+  }
+  const float nr = (float)(1 + (nl - __popc(sides))), nc = (float)(1 + __popc(sides));
+  for (int c = lane; c < d; c += 32) {
+    float rr = dud[(size_t)t * 4 * d + d + c], cc = dud[(size_t)t * 4 * d + 2 * d + c];
+    for (int q = 0; q < nl; ++q) {
+      if ((sides >> q) & 1) cc += duo[(size_t)toks[q] * 4 * d + 2 * d + c] / chs[q];
+      else rr += duo[(size_t)toks[q] * 4 * d + d + c] / chs[q];
+    }
+    rr /= nr;
+    cc /= nc;
+    er[(size_t)t * d + c] = rr;
+    ec[(size_t)t * d + c] = cc;
+    dy2d[(size_t)t * d + c] = dud[(size_t)t * 4 * d + c] + rr + cc + dg[(size_t)b * d + c];
+  }
+}
+// Off tokens: dy2o = du_own + sum over row chunk of er + sum over column chunk of ec + dg.
+__global__ void hwb_off_kernel(const SysBatch sb, const float* __restrict__ duo, const float* __restrict__ er,
+                               const float* __restrict__ ec, const float* __restrict__ dg, int d,
+                               float* __restrict__ dy2o) {
+  const int t = blockIdx.x;
+  const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
+  const TGeo g = tgeo(sb, m);
+  const size_t base = (size_t)b * sb.n;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    float sr = 0.f, sc = 0.f;
+    for (int q = 0; q < g.ch; ++q) {
+      sr += er[(base + g.r0 + a * g.ch + q) * d + c];
+      sc += ec[(base + g.c0 + a * g.ch + q) * d + c];
+    }
+    dy2o[(size_t)t * d + c] = duo[(size_t)t * 4 * d + c] + sr + sc + dg[(size_t)b * d + c];
+  }
+}
+
+// ------------------------------------------------------------------ pool, GCN, encoder backward
+// dx[j] += dpooled row part / ch for the token whose row chunk holds j, column part for
+// the token whose column chunk holds j (one per level).
+__global__ void pool_bwd_kernel(const SysBatch sb, const float* __restrict__ dpooled, int d, float* __restrict__ dx) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, i = t % sb.n;
+  const int k = i / sb.L;
+  for (int c = lane; c < d; c += 32) {
+    float acc = dx[(size_t)t * d + c];
+    for (int lev = 1; lev <= sb.levels; ++lev) {
+      const int S = sb.K >> lev;
+      const int cl = k / S;
+      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+      const int ch = S * sb.L / sb.r;
+      const int a = (i - cl * S * sb.L) / ch;
+      const size_t tok = ((size_t)b * sb.MH + m) * sb.r + a;
+      acc += dpooled[tok * 2 * d + ((cl & 1) ? d : 0) + c] / ch;
+    }
+    dx[(size_t)t * d + c] = acc;
+  }
+}
+// dx_g += P^T v with P = D^-1 A: (P^T v)_j = v_j - sum_{i nbr j} (w_ij / d_i) v_i.
+__global__ void prop_t_kernel(const SysBatch sb, const float* __restrict__ v, int d, float* __restrict__ dx) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= sb.B * sb.n) return;
+  const int b = t / sb.n, j = t % sb.n;
+  const size_t base = (size_t)b * sb.n;
+  const double* dg = sb.diag[b];
+  int is[6];
+  float cs[6];
+  int ni = 0;
+  for (int a = 0; a < sb.ndim; ++a) {
+    const int ip = sb.mo.plus(j, a);
+    if (ip >= 0) { is[ni] = ip; cs[ni++] = (float)(sb.w[b][a][j] / dg[ip]); }
+    const int im = sb.mo.minus(j, a);
+    if (im >= 0) { is[ni] = im; cs[ni++] = (float)(sb.w[b][a][im] / dg[im]); }
+  }
+  for (int c = lane; c < d; c += 32) {
+    float s = v[(size_t)t * d + c];
+    for (int q = 0; q < ni; ++q) s = fmaf(-cs[q], v[(base + is[q]) * d + c], s);
+    dx[(size_t)t * d + c] += s;
+  }
+}
+// Partial sums over 64-token chunks of outer products A^T B (A: T x p FP32, B: T x q FP32),
+// used for the first encoder layer (q = 20 features) and the gate row.
+__global__ void outer_partial_kernel(const float* __restrict__ A, int lda, const float* __restrict__ Bm, int ldb, int T,
+                                     int p, int q, float* __restrict__ part) {
+  const int ch = blockIdx.x;
+  const int t0 = ch * 64, t1 = min(T, t0 + 64);
+  for (int u = threadIdx.x; u < p * q; u += blockDim.x) {
+    const int i = u / q, j = u % q;
+    float s = 0.f;
+    for (int t = t0; t < t1; ++t) s = fmaf(A[(size_t)t * lda + i], Bm ? Bm[(size_t)t * ldb + j] : 1.f, s);
+    part[(size_t)ch * p * q + u] = s;
+  }
+}
+// BF16 activations -> FP32 (for small reductions that read them as B operands).
+__global__ void bf16_to_f32_kernel(const bf16* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __bfloat162float(a[i]);
+}
+// dX[t][c] (+)= sum_e dY[t][e] W[e][c] for a narrow head (q rows of W, FP32).
+__global__ void small_dx_kernel(const float* __restrict__ dy, int ldy, const float* __restrict__ w, int T, int q, int d,
+                                float* __restrict__ dx, int accumulate) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)T * d) return;
+  const int64_t t = idx / d;
+  const int c = (int)(idx % d);
+  float s = accumulate ? dx[idx] : 0.f;
+  for (int e = 0; e < q; ++e) s = fmaf(dy[t * ldy + e], w[(size_t)e * d + c], s);
+  dx[idx] = s;
+}
+
+// dyf += dlogit (x) w_gate (outer product into the node-head input gradient).
+__global__ void gate_dx_kernel(const float* __restrict__ dlog, const float* __restrict__ wg, int T, int d,
+                               float* __restrict__ dyf) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)T * d) return;
+  dyf[idx] += dlog[idx / d] * wg[idx % d];
+}
+
+// ------------------------------------------------------------------ optimiser
+__global__ void sumsq_partial_kernel(const float* __restrict__ g, int64_t n, double* __restrict__ part) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)g[i] * g[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+// Global-norm clip to max_norm, then AdamW (decoupled weight decay, bias correction).
+__global__ void adamw_kernel(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m1,
+                             float* __restrict__ m2, int64_t n, const double* __restrict__ part, int nparts,
+                             float lr, float wd, float b1, float b2, float eps, float max_norm, int64_t step) {
+  __shared__ float scale_s;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < nparts; ++q) t += part[q];
+    const double nrm = sqrt(t);
+    scale_s = (float)(nrm > max_norm ? max_norm / (nrm + 1e-6) : 1.0);
+  }
+  __syncthreads();
+  const float sc = scale_s;
+  const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i] * sc;
+    g[i] = gi;
+    float p = w[i];
+    p -= lr * wd * p;
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    p -= lr * (a / bc1) / (sqrtf(v / bc2) + eps);
+    w[i] = p;
+  }
+}
+
+}  // namespace
+}  // namespace hm

@@ -61,7 +61,7 @@ __global__ void global_stats_kernel(const SysBatch sb, double* __restrict__ gsta
   const double* dg = sb.diag[b];
   double slr = 0, sld = 0, mxr = -1e300, mnr = 1e300, mxd = -1e300, mnd = 1e300, nbd = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double lr = log(rho[i]), ld = log(dg[i]);
+    const double lr = (double)logf((float)rho[i]), ld = (double)logf((float)dg[i]);
     slr += lr; sld += ld;
     mxr = fmax(mxr, lr); mnr = fmin(mnr, lr); mxd = fmax(mxd, ld); mnd = fmin(mnd, ld);
     bool bnd = false;
@@ -78,7 +78,7 @@ __global__ void global_stats_kernel(const SysBatch sb, double* __restrict__ gsta
   const double mr = slr / n, md = sld / n, thr = 0.5 * (mxr + mnr);
   double vr = 0, vd = 0, hv = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double lr = log(rho[i]), ld = log(dg[i]);
+    const double lr = (double)logf((float)rho[i]), ld = (double)logf((float)dg[i]);
     vr += (lr - mr) * (lr - mr);
     vd += (ld - md) * (ld - md);
     hv += lr > thr ? 1.0 : 0.0;
@@ -113,11 +113,11 @@ __global__ void encoder1_kernel(const SysBatch sb, const double* __restrict__ gs
     const int jm = sb.mo.minus(i, a);
     if (jm >= 0) { off += sb.w[b][a][jm]; if (rho[jm] != ri) iface = 1.0; } else nb += 1.0;
   }
-  f[0] = (float)(log(ri) - g[4]);
+  f[0] = logf((float)ri) - (float)g[4];
   for (int a = 0; a < 3; ++a)
     f[1 + a] = a < sb.ndim ? (float)(((double)compact(i, sb.mo.mask[a]) + 0.5) / sb.dims[a] - 0.5) : 0.f;
   f[4] = (float)(nb / (2 * sb.ndim));
-  f[5] = (float)(log(di) - g[7]);
+  f[5] = logf((float)di) - (float)g[7];
   f[6] = (float)(off / di);
   f[7] = (float)iface;
   for (int q = 0; q < 12; ++q) f[8 + q] = (float)g[q];
@@ -156,16 +156,14 @@ __global__ void prop_kernel(const SysBatch sb, const float* __restrict__ x, int 
 }
 
 // Off-diagonal tokens: [mean over row chunk ; mean over column chunk] of the encoder output.
+// One CTA per token, one thread per channel (coalesced over channels).
 __global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ pooled) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  const int To = sb.B * sb.MH * sb.r;
-  if (t >= To) return;
+  const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
   const TileGeo g = tile_geo(sb, m);
   const size_t base = (size_t)b * sb.n;
   const float inv = 1.f / g.ch;
-  for (int c = lane; c < d; c += 32) {
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
     float sr = 0.f, sc = 0.f;
     for (int q = 0; q < g.ch; ++q) {
       sr += x[(base + g.r0 + a * g.ch + q) * d + c];
@@ -251,8 +249,28 @@ HM_INLINE void leaf_desc(const SysBatch& sb, int bsys, int k, int a, int bb, flo
   e[3] = al;
 }
 
+// Pairs with zero coupling (all but the diagonal and the stencil neighbours) have a
+// descriptor that depends only on the in-leaf positions (a, b), the same in every leaf:
+// their bias comes from a per-layer table table[h][a][b] built once per call.
+__global__ void edge_table_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
+                                  const float* b2, int h, float* __restrict__ table) {
+  __shared__ EdgeMlp s;
+  load_edge_mlp(s, w1, b1, w2, b2, h);
+  const int L = sb.L;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L * L) return;
+  const int bb = idx % L, a = idx / L;
+  float e[4], out[8];
+  for (int ax = 0; ax < 3; ++ax)
+    e[ax] = ax < sb.ndim ? ((float)compact(bb, sb.mo.mask[ax]) - (float)compact(a, sb.mo.mask[ax])) / sb.leaf_side : 0.f;
+  e[3] = a == bb ? 1.f : 0.f;
+  edge_mlp(s, e, h, out);
+  for (int hh = 0; hh < h; ++hh) table[((size_t)hh * L + a) * L + bb] = out[hh];
+}
+
 __global__ void edge_bias_diag_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
-                                      const float* b2, int h, float* __restrict__ bias) {
+                                      const float* b2, int h, const float* __restrict__ table,
+                                      float* __restrict__ bias) {
   __shared__ EdgeMlp s;
   load_edge_mlp(s, w1, b1, w2, b2, h);
   const int L = sb.L;
@@ -260,6 +278,14 @@ __global__ void edge_bias_diag_kernel(const SysBatch sb, const float* w1, const 
   if (idx >= sb.B * sb.K * L * L) return;
   const int bb = idx % L, a = (idx / L) % L, win = idx / (L * L);
   const int k = win % sb.K, bsys = win / sb.K;
+  const unsigned i = k * L + a, j = k * L + bb;
+  bool nbr = false;
+  for (int ax = 0; ax < sb.ndim; ++ax) nbr |= sb.mo.plus(i, ax) == (int)j || sb.mo.minus(i, ax) == (int)j;
+  if (!nbr) {
+    for (int hh = 0; hh < h; ++hh)
+      bias[(((size_t)win * h + hh) * L + a) * L + bb] = table[((size_t)hh * L + a) * L + bb];
+    return;
+  }
   float e[4], out[8];
   leaf_desc(sb, bsys, k, a, bb, e);
   edge_mlp(s, e, h, out);
@@ -402,21 +428,30 @@ __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ y
   }
 }
 
-// Global summary token: mean of y over all tokens of both stacks (per system).
-__global__ void highway_g_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo, int d,
-                                 float* __restrict__ g) {
-  __shared__ double part[8][33];
-  const int b = blockIdx.x, c = blockIdx.y * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
-  double s = 0.0;
-  for (int i = w; i < sb.n; i += 8) s += yd[((size_t)b * sb.n + i) * d + c];
+// Global summary token: mean of y over all tokens of both stacks (per system), in two
+// deterministic stages: per-chunk column sums (64 tokens per CTA), then a fixed-order sum.
+constexpr int kGChunk = 64;
+__global__ void highway_g_partial_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo,
+                                         int d, int nch_d, int nch_o, double* __restrict__ part) {
+  const int b = blockIdx.y, ch = blockIdx.x;
   const int no = sb.MH * sb.r;
-  for (int i = w; i < no; i += 8) s += yo[((size_t)b * no + i) * d + c];
-  part[w][threadIdx.x & 31] = s;
-  __syncthreads();
-  if (w == 0) {
-    double tot = 0.0;
-    for (int q = 0; q < 8; ++q) tot += part[q][threadIdx.x & 31];
-    g[(size_t)b * d + c] = (float)(tot / (sb.n + no));
+  const float* src;
+  int t0, t1;
+  if (ch < nch_d) { src = yd + (size_t)b * sb.n * d; t0 = ch * kGChunk; t1 = min(sb.n, t0 + kGChunk); }
+  else { src = yo + (size_t)b * no * d; t0 = (ch - nch_d) * kGChunk; t1 = min(no, t0 + kGChunk); }
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    double s = 0.0;
+    for (int t = t0; t < t1; ++t) s += src[(size_t)t * d + c];
+    part[((size_t)b * (nch_d + nch_o) + ch) * d + c] = s;
+  }
+}
+__global__ void highway_g_final_kernel(const SysBatch sb, const double* __restrict__ part, int d, int nch,
+                                       float* __restrict__ g) {
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nch; ++q) s += part[((size_t)b * nch + q) * d + c];
+    g[(size_t)b * d + c] = (float)(s / (sb.n + sb.MH * sb.r));
   }
 }
 
@@ -429,16 +464,15 @@ __global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d
 }
 
 // Off-diagonal token gathers: mean of r_hw over its row chunk, of c_hw over its column chunk, g.
+// One CTA per token, one thread per channel.
 __global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ rhw, const float* __restrict__ chw,
                                    const float* __restrict__ g, int d, bf16* __restrict__ uo) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  if (t >= sb.B * sb.MH * sb.r) return;
+  const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
   const TileGeo gg = tile_geo(sb, m);
   const size_t base = (size_t)b * sb.n;
   const float inv = 1.f / gg.ch;
-  for (int c = lane; c < d; c += 32) {
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
     float sr = 0.f, sc = 0.f;
     for (int q = 0; q < gg.ch; ++q) {
       sr += rhw[(base + gg.r0 + a * gg.ch + q) * d + c];

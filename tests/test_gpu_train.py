@@ -1,0 +1,101 @@
+"""GPU training step against the FP64 oracle (loss, clipped gradient, AdamW update).
+
+The GPU step runs the forward and every backward GEMM with BF16 operands and FP32
+accumulation; the clipped gradient is compared with the oracle's (torch autograd
+in FP64 on the same weights, systems and SplitMix64 probes) by cosine similarity
+and relative 2-norm error over the whole vector and over each large tensor.
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import adamw, grid, train
+
+pytestmark = pytest.mark.gpu
+h = pytest.importorskip("paper_2605_13343_gb300")
+
+SMALL = dict(d=64, n_layers=1, n_heads=2, d_mlp=64, leaf=16, rank=16)
+CFG3 = dict(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16)
+
+
+def _blob(cfg, seed, scale_heads=100.0):
+    lay = inputs.network_layout(**cfg)
+    w = inputs.network_blob(seed, **cfg)
+    off = 0
+    for name, shp in lay:
+        k = int(np.prod(shp))
+        if name in ("leaf2.w", "node.w", "off.w"):
+            w[off:off + k] *= scale_heads
+        off += k
+    return w, lay
+
+
+def _ctx(cfg, n, batch, w):
+    return h.Context(max_n=n, leaf=cfg["leaf"], rank=cfg["rank"], d_model=cfg["d"], n_layers=cfg["n_layers"],
+                     n_heads=cfg["n_heads"], d_mlp=cfg["d_mlp"], max_batch=batch, weights=w)
+
+
+def _systems(dims, seeds):
+    out_gpu, out_ref = [], []
+    for s in seeds:
+        rho = inputs.density_for_dims(s, dims, rho_heavy=float(np.exp(np.random.default_rng(s).uniform(0, np.log(100)))))
+        sg = h.System(dims)
+        h.assemble(torch.from_numpy(rho).cuda(), sg)
+        out_gpu.append(sg)
+        out_ref.append(grid.assemble(rho, dims))
+    return out_gpu, out_ref
+
+
+def _cos(a, b):
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+@pytest.mark.parametrize("cfg,dims,seeds,nz,tol_cos", [
+    (SMALL, (16, 16), [1, 2], 8, 0.995),
+    (CFG3, (16, 16, 16), [3, 4], 16, 0.98)])
+def test_train_step_gradient_parity(cfg, dims, seeds, nz, tol_cos):
+    w, lay = _blob(cfg, 5)
+    n = int(np.prod(dims))
+    ctx = _ctx(cfg, n, len(seeds), w)
+    sg, sr = _systems(dims, seeds)
+    loss_gpu = h.train_step(ctx, sg, nz, 0.0, 1234)
+    g_gpu = h.get_grads(ctx, w.size).astype(np.float64)
+    l_ref, g_ref, _ = train.batch_loss(w.astype(np.float64), lay, cfg, sr, 1234, nz)
+    g_ref = adamw.clip_global(g_ref, 1.0)
+    assert abs(loss_gpu - l_ref) <= 2e-3 * max(1.0, abs(l_ref)), (loss_gpu, l_ref)
+    assert _cos(g_gpu, g_ref) >= tol_cos, _cos(g_gpu, g_ref)
+    # large tensors one by one
+    off = 0
+    for name, shp in lay:
+        k = int(np.prod(shp))
+        a, b = g_gpu[off:off + k], g_ref[off:off + k]
+        off += k
+        if k >= 4096 and np.linalg.norm(b) > 1e-3 * np.linalg.norm(g_ref):
+            assert _cos(a, b) >= 0.95, (name, _cos(a, b))
+    # lr = 0 left the weights untouched
+    assert np.array_equal(h.get_weights(ctx, w.size), w)
+    ctx.close()
+
+
+def test_adamw_update_matches_oracle():
+    w, lay = _blob(SMALL, 6)
+    ctx = _ctx(SMALL, 256, 2, w)
+    sg, _ = _systems((16, 16), [7, 8])
+    h.train_step(ctx, sg, 8, 1e-3, 99)
+    g = h.get_grads(ctx, w.size).astype(np.float64)
+    w1 = h.get_weights(ctx, w.size).astype(np.float64)
+    p, m, v = adamw.adamw_step(w.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    assert np.abs(w1 - p).max() <= 1e-6
+    ctx.close()
+
+
+def test_training_reduces_loss():
+    w = inputs.network_blob(0, **CFG3)
+    ctx = _ctx(CFG3, 4096, 4, w)
+    losses = []
+    for step in range(40):
+        sg, _ = _systems((16, 16, 16), [100 + 4 * step + q for q in range(4)])
+        losses.append(h.train_step(ctx, sg, 16, 3e-4, step))
+    assert np.mean(losses[-8:]) < np.mean(losses[:8]) - 1e-3, losses
+    ctx.close()
