@@ -7,7 +7,7 @@
 
 namespace hm {
 int solve_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* b,
-                   double* x, const hmpcg_solve_opts* o, cudaStream_t st, int chunk_override);
+                   double* x, const hmpcg_solve_opts* o, cudaStream_t st, int chunk_override, int path);
 int apply_dispatch(Ctx* c, const hmpcg_factors* f, const float* r, float* z, cudaStream_t st);
 int assemble_launch(const double* rho, const hmpcg_system* sys, int bc, int face, cudaStream_t st);
 int spmv_launch(const hmpcg_system* sys, const float* x, float* y, cudaStream_t st);
@@ -32,6 +32,13 @@ static bool valid_grid(int32_t ndim, const int32_t* dims) {
     n *= dims[a];
   }
   return n <= (int64_t(1) << 30);
+}
+
+// HMPCG_PCG_PATH=grid forces the grid-wide PCG kernel (the cluster kernel is the default
+// for systems that fit one thread-block cluster).
+static int path_from_env() {
+  const char* e = getenv("HMPCG_PCG_PATH");
+  return (e && e[0] == 'g') ? 1 : 0;
 }
 
 static int chunk_from_env() {
@@ -186,7 +193,7 @@ int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f, cons
   if (opts && !(opts->rtol >= 0.0)) return HMPCG_E_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   if (info) HM_CUDA(cudaEventRecord(c->ev0, st));
-  int rc = solve_dispatch(c, sys, f, b, x, opts, st, chunk_from_env());
+  int rc = solve_dispatch(c, sys, f, b, x, opts, st, chunk_from_env(), path_from_env());
   if (rc) return rc;
   if (!info) return HMPCG_OK;
   HM_CUDA(cudaEventRecord(c->ev1, st));

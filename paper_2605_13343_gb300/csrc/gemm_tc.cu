@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(128)
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
   constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // align to 1024 B (128-byte swizzle atoms) by pointer arithmetic on the shared array, so
+  // that the compiler keeps knowing these are shared-memory addresses
+  uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_done;
   __shared__ uint32_t tmem_base_s;
   __shared__ int fail_s;
@@ -197,31 +199,66 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = 0.f;
     }
-    if (!ok || n0 + c >= N) continue;
+    if (!ok || n0 + c >= N) continue;   // uniform across the warp
     if (ep.out16T && rbase + lane < M) {
       // transposed copy: lanes are consecutive rows, so each column store is contiguous
-      const float* bb = ep.bias;
-      for (int j = 0; j < 32 && n0 + c + j < N; ++j) {
-        float y = v[j] + (bb ? bb[n0 + c + j] : 0.f);
-        if (ep.act == 1) y = gelu_f(y);
-        ep.out16T[(size_t)(n0 + c + j) * ep.ldT + rbase + lane] = __float2bfloat16_rn(y);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (n0 + c + j < N) {
+          float y = v[j] + (ep.bias ? ep.bias[n0 + c + j] : 0.f);
+          if (ep.act == 1) y = gelu_f(y);
+          ep.out16T[(size_t)(n0 + c + j) * ep.ldT + rbase + lane] = __float2bfloat16_rn(y);
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
     __syncwarp();
-    const int col = n0 + c + lane;
-    if (col < N) {
-      const float bias = ep.bias ? ep.bias[col] : 0.f;
-      for (int rr = 0; rr < 32; ++rr) {
+    // lane -> 4 consecutive columns of rows rg, rg + 4, ..., rg + 28: every store instruction
+    // writes 16 B per lane and 4 full 128-byte row segments per warp
+    const int cg = lane & 7, rg = lane >> 3;
+    const int col = n0 + c + 4 * cg;
+    if (col < N) {   // N % 16 == 0, so the 4 columns are all valid
+      float4 bias4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ep.bias) bias4 = make_float4(ep.bias[col], ep.bias[col + 1], ep.bias[col + 2], ep.bias[col + 3]);
+      float4 res[8];
+      if (ep.resid) {
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int row = rbase + rg + 4 * it;
+          res[it] = row < M ? *reinterpret_cast<const float4*>(ep.resid + (size_t)row * ep.ldr + col)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int rr = rg + 4 * it;
         const int row = rbase + rr;
-        if (row >= M) break;
-        float y = stage[rr * 33 + lane] + bias;
-        if (ep.pre16) ep.pre16[(size_t)row * ep.ldpre + col] = __float2bfloat16_rn(y);
-        if (ep.act == 1) y = gelu_f(y);
-        if (ep.resid) y += ep.resid[(size_t)row * ep.ldr + col];
-        if (ep.out32) ep.out32[(size_t)blockIdx.z * ep.zstride + (size_t)row * ep.ld32 + col] = y;
-        if (ep.out16) ep.out16[(size_t)row * ep.ld16 + col] = __float2bfloat16_rn(y);
+        if (row >= M) continue;
+        float t[4] = {stage[rr * 33 + 4 * cg] + bias4.x, stage[rr * 33 + 4 * cg + 1] + bias4.y,
+                      stage[rr * 33 + 4 * cg + 2] + bias4.z, stage[rr * 33 + 4 * cg + 3] + bias4.w};
+        if (ep.pre16) {
+          uint2 pk;
+          __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&pk);
+          hh[0] = __floats2bfloat162_rn(t[0], t[1]);
+          hh[1] = __floats2bfloat162_rn(t[2], t[3]);
+          *reinterpret_cast<uint2*>(ep.pre16 + (size_t)row * ep.ldpre + col) = pk;
+        }
+        if (ep.act == 1) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) t[q] = gelu_f(t[q]);
+        }
+        if (ep.resid) { t[0] += res[it].x; t[1] += res[it].y; t[2] += res[it].z; t[3] += res[it].w; }
+        if (ep.out32)
+          *reinterpret_cast<float4*>(ep.out32 + (size_t)blockIdx.z * ep.zstride + (size_t)row * ep.ld32 + col) =
+              make_float4(t[0], t[1], t[2], t[3]);
+        if (ep.out16) {
+          uint2 pk;
+          __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&pk);
+          hh[0] = __floats2bfloat162_rn(t[0], t[1]);
+          hh[1] = __floats2bfloat162_rn(t[2], t[3]);
+          *reinterpret_cast<uint2*>(ep.out16 + (size_t)row * ep.ld16 + col) = pk;
+        }
       }
     }
     __syncwarp();
@@ -284,6 +321,11 @@ static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) 
 int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return HMPCG_OK;
   if (g.K <= 0 || g.N % 16) return HMPCG_E_SHAPE;
+  auto al = [](const void* p, int bytes) { return (reinterpret_cast<uintptr_t>(p) % bytes) == 0; };
+  const GemmEpi& e = g.ep;
+  if ((e.out32 && (!al(e.out32, 16) || e.ld32 % 4 || e.zstride % 4)) || (e.resid && (!al(e.resid, 16) || e.ldr % 4)) ||
+      (e.out16 && (!al(e.out16, 8) || e.ld16 % 4)) || (e.pre16 && (!al(e.pre16, 8) || e.ldpre % 4)))
+    return HMPCG_E_INVALID;   // the epilogue moves 4 columns per lane
   if (g.ksplit > 1 && (g.ep.out16 || g.ep.out16T || g.ep.pre16 || g.ep.resid || g.ep.bias || g.ep.act))
     return HMPCG_E_INVALID;   // split-K writes raw FP32 partials only
   CUtensorMap ma;

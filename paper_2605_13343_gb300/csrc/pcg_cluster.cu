@@ -1,0 +1,640 @@
+// PCG for small systems in one thread-block cluster (Sec. 5 "Single-graph capture";
+// Sec. 6.3; Supp. G).
+//
+// One cluster of C <= 16 CTAs solves one system.  CTA c owns nodes
+// [c N/C, (c+1) N/C) and the leaves inside that range; its share of the packed
+// factors (leaf blocks, bridges, gate, and the tiles m with m % C == c) is copied
+// into shared memory once and read from there every iteration.  The PCG vectors
+// of owned nodes live in the owner's shared memory; the SpMV halo, the strip
+// sums of the off-diagonal chain and the partial dot products are read from
+// other CTAs through distributed shared memory.  Phases are separated by the
+// hardware cluster barrier (all CTAs of a cluster are co-scheduled, so no wait
+// can hang).  The arithmetic is that of the grid-wide kernel in solver.cu:
+// same stage order, FP32 vectors, FP64 dot products, alpha, beta and stop test,
+// periodic and near-convergence true-residual replacement in FP64.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <cooperative_groups.h>
+#include "ctx.cuh"
+
+namespace hm {
+
+namespace {
+
+constexpr int kCThreads = 512;
+constexpr int kLeafPad = 2;   // row padding of leaf blocks in shared memory (bank spread)
+
+// Generic pointer to the same shared-memory object in CTA `rank` of the cluster: plain
+// loads through it are ordinary memory operations that the compiler may batch.
+template <class P>
+HM_INLINE P* remote(P* local, unsigned rank) {
+  return cooperative_groups::this_cluster().map_shared_rank(local, rank);
+}
+HM_INLINE void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+HM_INLINE unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+template <class T> HM_INLINE float tf(T v);
+template <> HM_INLINE float tf<float>(float v) { return v; }
+template <> HM_INLINE float tf<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> HM_INLINE float tf<__nv_fp8_e4m3>(__nv_fp8_e4m3 v) { return float(v); }
+
+enum { CPRE_NONE = 0, CPRE_JACOBI = 1, CPRE_HMAT = 2 };
+
+template <class T>
+struct CParams {
+  SysView s;
+  FactorView<T> f;
+  const double* b;
+  double* x;
+  DevStatus* st;
+  double rtol;
+  int max_iter, recompute;
+  int C, npc, lpc, tpc;   // CTAs, nodes / leaves / tiles per CTA
+};
+
+// Shared-memory carve-up (byte offsets), identical in every CTA.
+struct CLayout {
+  size_t x, b, r, z, q, p0, p1, yd, coef, uh, tc, part, rs, ws, leaf, bridge, gate, core, total;
+};
+
+template <class T>
+__host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, int nslot, bool learned, bool hmat) {
+  CLayout o;
+  size_t p = 0;
+  auto take = [&](size_t bytes) { size_t q = p; p = (p + bytes + 15) / 16 * 16; return q; };
+  o.x = take(8 * (size_t)npc);
+  o.b = take(8 * (size_t)npc);
+  o.r = take(4 * (size_t)npc);
+  o.z = take(4 * (size_t)npc);
+  o.q = take(4 * (size_t)npc);
+  o.p0 = take(4 * (size_t)npc);
+  o.p1 = take(4 * (size_t)npc);
+  o.yd = take(4 * (size_t)npc);
+  o.coef = take(16 * (size_t)npc);             // diag32, w32[0..2] of owned nodes
+  o.uh = take(hmat ? 4 * (size_t)nslot * (2 * lpc - 1) * R : 0);   // per slot: leaves, then aligned pair, quad, ... sums
+  o.tc = take(hmat ? 4 * (size_t)tpc * 2 * R : 0);
+  o.part = take(8 * 8);
+  o.rs = take(hmat ? 4 * (size_t)lpc * L : 0);
+  o.ws = take(hmat ? 4 * (size_t)lpc * (L > nslot * R ? L : nslot * R) : 0);
+  o.leaf = take(hmat ? sizeof(T) * (size_t)lpc * L * (L + kLeafPad) : 0);
+  o.bridge = take(hmat ? sizeof(T) * (size_t)nslot * npc * R : 0);
+  o.gate = take(hmat && learned ? sizeof(T) * (size_t)npc : 0);
+  o.core = take(hmat ? sizeof(T) * (size_t)tpc * R * R : 0);
+  o.total = p;
+  return o;
+}
+
+template <class T, int PRE>
+__global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams<T> P) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  const SysView& S = P.s;
+  const FactorView<T>& F = P.f;
+  const unsigned me = cl_rank();
+  const int C = P.C, npc = P.npc;
+  const int L = F.L, R = F.r;
+  const bool hmat = PRE == CPRE_HMAT;
+  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat);
+  double* xs = reinterpret_cast<double*>(sm + lay.x);
+  double* bs = reinterpret_cast<double*>(sm + lay.b);
+  float* rv = reinterpret_cast<float*>(sm + lay.r);
+  float* zv = reinterpret_cast<float*>(sm + lay.z);
+  float* qv = reinterpret_cast<float*>(sm + lay.q);
+  float* pbuf[2] = {reinterpret_cast<float*>(sm + lay.p0), reinterpret_cast<float*>(sm + lay.p1)};
+  float* ydv = reinterpret_cast<float*>(sm + lay.yd);
+  float* coef = reinterpret_cast<float*>(sm + lay.coef);
+  float* uh = reinterpret_cast<float*>(sm + lay.uh);
+  float* tcp = reinterpret_cast<float*>(sm + lay.tc);
+  double* part = reinterpret_cast<double*>(sm + lay.part);
+  float* rs = reinterpret_cast<float*>(sm + lay.rs);
+  float* ws = reinterpret_cast<float*>(sm + lay.ws);
+  T* sleaf = reinterpret_cast<T*>(sm + lay.leaf);
+  T* sbr = reinterpret_cast<T*>(sm + lay.bridge);
+  T* sgate = reinterpret_cast<T*>(sm + lay.gate);
+  T* score = reinterpret_cast<T*>(sm + lay.core);
+  const int tid = threadIdx.x;
+  const int n0 = me * npc;
+  const int LP = L + kLeafPad;
+
+  // value of node i of an owner-distributed array (local shared memory or DSMEM)
+  auto ld_f = [&](float* base, int i) -> float {
+    const int o = i / npc;
+    return (o == (int)me) ? base[i - n0] : *remote(base + (i - o * npc), o);
+  };
+  auto ld_d = [&](double* base, int i) -> double {
+    const int o = i / npc;
+    return (o == (int)me) ? base[i - n0] : *remote(base + (i - o * npc), o);
+  };
+  // deterministic cluster sum of slot q of every CTA's `part` (loads issued together)
+  auto cl_total = [&](int q) -> double {
+    double v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = c < C ? *remote(part + q, c) : 0.0;
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) s += v[c];
+    return s;
+  };
+
+  // ---------------- load: owned b, coefficients, factor share
+  for (int i = tid; i < npc; i += blockDim.x) {
+    const int g = n0 + i;
+    bs[i] = P.b[g];
+    coef[4 * i] = S.diag32[g];
+    for (int a = 0; a < 3; ++a) coef[4 * i + 1 + a] = a < S.mo.ndim ? S.w32[a][g] : 0.f;
+  }
+  if (hmat) {
+    const int k0 = n0 / L;
+    for (int e = tid; e < P.lpc * L * L; e += blockDim.x) {
+      const int kl = e / (L * L), rr = (e / L) % L, cc = e % L;
+      sleaf[(size_t)kl * L * LP + rr * LP + cc] = F.leaf[(size_t)(k0 + kl) * L * L + rr * L + cc];
+    }
+    for (int s = 0; s < F.nslot; ++s)
+      for (int e = tid; e < npc * R; e += blockDim.x)
+        sbr[(size_t)s * npc * R + e] = F.bridge[((size_t)s * F.n + n0) * R + e];
+    if (F.learned)
+      for (int e = tid; e < npc; e += blockDim.x) sgate[e] = F.gate[n0 + e];
+    for (int tl = 0; tl < P.tpc; ++tl) {
+      const int m = me + tl * C;
+      if (m >= F.K - 1) break;
+      for (int e = tid; e < R * R; e += blockDim.x) score[(size_t)tl * R * R + e] = F.core[(size_t)m * R * R + e];
+    }
+  }
+  __syncthreads();
+
+  // ---------------- H-matrix apply pieces (factor scales for FP8 read from global)
+  const int G = blockDim.x / max(1, P.lpc);   // threads per leaf group
+  const int grp = tid / G, gl = tid % G;
+  auto sc_leaf = [&](int k) { return F.sc_leaf ? F.sc_leaf[k] : 1.f; };
+  auto sc_br = [&](int s, int k) { return F.sc_bridge ? F.sc_bridge[s * F.K + k] : 1.f; };
+  // restriction + diagonal stage of every owned leaf (group grp handles leaf grp)
+  auto restrict_leaves = [&]() {
+    if (grp < P.lpc) {
+      const int kl = grp, k = n0 / L + kl;
+      float* r_l = rs + kl * L;
+      for (int i = gl; i < L; i += G) r_l[i] = rv[kl * L + i];
+    }
+    __syncthreads();
+    if (grp < P.lpc) {
+      const int kl = grp, k = n0 / L + kl;
+      const T* blk = sleaf + (size_t)kl * L * LP;
+      const float* r_l = rs + kl * L;
+      float* w_l = ws + kl * max(L, F.nslot * R);
+      const float sb = sc_leaf(k);
+      if (F.learned) {
+        for (int j = gl; j < L; j += G) {            // w = F^T r
+          float acc = 0.f;
+          for (int i = 0; i < L; ++i) acc = fmaf(tf<T>(blk[i * LP + j]), r_l[i], acc);
+          w_l[j] = acc * sb;
+        }
+      }
+      // restriction uh[s][kl] = W_s^T r
+      for (int q = gl; q < F.nslot * R; q += G) {
+        const int s = q / R, e = q % R;
+        const T* W = sbr + ((size_t)s * npc + kl * L) * R;
+        float acc = 0.f;
+        for (int i = 0; i < L; ++i) acc = fmaf(tf<T>(W[i * R + e]), r_l[i], acc);
+        uh[((size_t)s * (2 * P.lpc - 1) + kl) * R + e] = acc * sc_br(s, k);
+      }
+    }
+    __syncthreads();
+    if (grp < P.lpc) {
+      const int kl = grp, k = n0 / L + kl;
+      const T* blk = sleaf + (size_t)kl * L * LP;
+      const float* r_l = rs + kl * L;
+      const float* w_l = ws + kl * max(L, F.nslot * R);
+      const float sb = sc_leaf(k);
+      const float sg = F.sc_gate ? F.sc_gate[k] : 1.f;
+      for (int i = gl; i < L; i += G) {
+        float acc = 0.f;
+        if (F.learned) {
+          for (int j = 0; j < L; ++j) acc = fmaf(tf<T>(blk[i * LP + j]), w_l[j], acc);
+          acc = fmaf(tf<T>(sgate[kl * L + i]) * sg, r_l[i], acc * sb);
+        } else {
+          for (int j = 0; j < L; ++j) acc = fmaf(tf<T>(blk[i * LP + j]), r_l[j], acc);
+          acc *= sb;
+        }
+        ydv[kl * L + i] = acc;
+      }
+    }
+  };
+  // per-slot sums of aligned groups of 2, 4, ..., lpc owned leaves (tree levels 1..)
+  auto build_tree = [&]() {
+    const int T1 = 2 * P.lpc - 1;
+    int base_prev = 0, n_prev = P.lpc;
+    while (n_prev > 1) {
+      __syncthreads();
+      const int base = base_prev + n_prev, nn = n_prev / 2;
+      for (int q = tid; q < F.nslot * nn * R; q += blockDim.x) {
+        const int s = q / (nn * R), g = (q / R) % nn, e = q % R;
+        float* u = uh + (size_t)s * T1 * R;
+        u[(base + g) * R + e] = u[(base_prev + 2 * g) * R + e] + u[(base_prev + 2 * g + 1) * R + e];
+      }
+      base_prev = base;
+      n_prev = nn;
+    }
+  };
+  // strip sums and coupling of the owned tiles: a strip of S <= lpc leaves is one tree node
+  // of one CTA, a longer strip is the sum of S / lpc whole-CTA roots (<= 16 remote loads)
+  auto tiles = [&]() {
+    const int T1 = 2 * P.lpc - 1;
+    int lg = 0;
+    while ((1 << lg) < P.lpc) ++lg;
+    for (int q = tid; q < P.tpc * 2 * R; q += blockDim.x) {
+      const int tl = q / (2 * R), side = (q / R) & 1, e = q % R;
+      const int m = me + tl * C;
+      if (m >= F.K - 1) continue;
+      const int lev = 32 - __clz(m + 1);
+      const int t = m + 1 - (1 << (lev - 1));
+      const int Sl = F.K >> lev;
+      const int k0 = side ? (2 * t + 1) * Sl : 2 * t * Sl;
+      const int slot = F.learned ? side : lev - 1;
+      float acc = 0.f;
+      if (Sl <= P.lpc) {
+        int j = 0, base = 0, cnt = P.lpc;
+        while ((1 << j) < Sl) { base += cnt; cnt >>= 1; ++j; }
+        const int owner = k0 / P.lpc, g = (k0 % P.lpc) >> j;
+        acc = *remote(uh + ((size_t)slot * T1 + base + g) * R + e, owner);
+      } else {
+        const int root = T1 - 1;
+        const int o0 = k0 / P.lpc, no = Sl / P.lpc;
+        float v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = c < no ? *remote(uh + ((size_t)slot * T1 + root) * R + e, o0 + c) : 0.f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc += v[c];
+      }
+      (void)lg;
+      ws[q] = acc;    // ws reused as [tile][side][e] strip sums (tpc 2 R <= lpc max(L, nslot R))
+    }
+    __syncthreads();
+    for (int q = tid; q < P.tpc * 2 * R; q += blockDim.x) {
+      const int tl = q / (2 * R), side = (q / R) & 1, e = q % R;
+      const int m = me + tl * C;
+      if (m >= F.K - 1) continue;
+      const T* Bm = score + (size_t)tl * R * R;
+      const float sB = F.sc_core ? F.sc_core[m] : 1.f;
+      const float* srow = ws + (size_t)tl * 2 * R;        // s^r
+      const float* scol = srow + R;                        // s^c
+      float acc = 0.f;
+      if (side == 0) { for (int f = 0; f < R; ++f) acc = fmaf(tf<T>(Bm[e * R + f]), scol[f], acc); }   // t^r = B s^c
+      else { for (int f = 0; f < R; ++f) acc = fmaf(tf<T>(Bm[f * R + e]), srow[f], acc); }              // t^c = B^T s^r
+      tcp[(size_t)tl * 2 * R + side * R + e] = acc * sB;
+    }
+  };
+  // prolongation of every owned leaf: z = ydiag + sum_s W_s a_s
+  auto prolong = [&]() {
+    float* as = ws;   // [lpc][nslot][R]
+    for (int q = tid; q < P.lpc * F.nslot * R; q += blockDim.x) as[q] = 0.f;
+    __syncthreads();
+    for (int q = tid; q < P.lpc * R; q += blockDim.x) {
+      const int kl = q / R, e = q % R;
+      const int k = n0 / L + kl;
+      float tv[24];
+#pragma unroll
+      for (int lev = 1; lev <= 24; ++lev) {
+        tv[lev - 1] = 0.f;
+        if (lev <= F.levels) {
+          const int Sl = F.K >> lev;
+          const int cl = k / Sl;
+          const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+          tv[lev - 1] = *remote(tcp + (size_t)(m / C) * 2 * R + (cl & 1) * R + e, m % C);
+        }
+      }
+      for (int lev = 1; lev <= F.levels; ++lev) {
+        const int cl = k / (F.K >> lev);
+        const int slot = F.learned ? (cl & 1) : lev - 1;
+        as[((size_t)kl * F.nslot + slot) * R + e] += tv[lev - 1];
+      }
+    }
+    __syncthreads();
+    for (int q = tid; q < npc; q += blockDim.x) {
+      const int kl = q / L, k = n0 / L + kl;
+      float acc = ydv[q];
+      for (int s = 0; s < F.nslot; ++s) {
+        const T* Wr = sbr + ((size_t)s * npc + q) * R;
+        const float* a = as + ((size_t)kl * F.nslot + s) * R;
+        float t = 0.f;
+        for (int e = 0; e < R; ++e) t = fmaf(tf<T>(Wr[e]), a[e], t);
+        acc = fmaf(t, sc_br(s, k), acc);
+      }
+      zv[q] = acc;
+    }
+  };
+  // FP32 SpMV row with neighbour values from get(j)
+  auto row32 = [&](int i, float vi, auto get) -> float {
+    const int il = i - n0;
+    float acc = coef[4 * il] * vi;
+    for (int a = 0; a < S.mo.ndim; ++a) {
+      const int jp = S.mo.plus(i, a);
+      if (jp >= 0) acc = fmaf(-coef[4 * il + 1 + a], get(jp), acc);
+      const int jm = S.mo.minus(i, a);
+      if (jm >= 0) {
+        const float wm = (jm / npc == (int)me) ? coef[4 * (jm - n0) + 1 + a]
+                                               : *remote(coef + 4 * (jm % npc) + 1 + a, jm / npc);
+        acc = fmaf(-wm, get(jm), acc);
+      }
+    }
+    return acc;
+  };
+  auto row64 = [&](int i, double xi, auto get) -> double {
+    double acc = S.diag[i] * xi;
+    for (int a = 0; a < S.mo.ndim; ++a) {
+      const int jp = S.mo.plus(i, a);
+      if (jp >= 0) acc = fma(-S.w[a][i], get(jp), acc);
+      const int jm = S.mo.minus(i, a);
+      if (jm >= 0) acc = fma(-S.w[a][jm], get(jm), acc);
+    }
+    return acc;
+  };
+
+  // FP64 is scarce on this part: per-thread FP64 partials are reduced by one warp, and the
+  // PCG scalars are computed by thread 0 and broadcast through shared memory.
+  __shared__ double red512[kCThreads];
+  __shared__ double scal[4];
+  __shared__ int iscal[2];
+  auto cta_part = [&](double v, int q) {
+    __syncthreads();
+    red512[tid] = v;
+    __syncthreads();
+    if (tid < 32) {
+      double s = 0.0;
+      for (int i = tid; i < (int)blockDim.x; i += 32) s += red512[i];
+      s = warp_sum(s);
+      if (tid == 0) part[q] = s;
+    }
+  };
+
+  // ---------------- init: x = 0, r = b, p = 0, z = M r
+  double acc = 0.0;
+  for (int i = tid; i < npc; i += blockDim.x) {
+    const double bi = bs[i];
+    xs[i] = 0.0;
+    rv[i] = (float)bi;
+    pbuf[0][i] = 0.f;
+    acc = fma(bi, bi, acc);
+  }
+  cta_part(acc, 0);
+  if (hmat) { __syncthreads(); restrict_leaves(); build_tree(); }
+  __syncthreads();
+  cluster_sync();
+  if (tid == 0) scal[0] = cl_total(0);
+  __syncthreads();
+  const double bb = scal[0];
+  if (hmat) {
+    tiles();
+    cluster_sync();
+    prolong();
+  }
+  __syncthreads();
+  acc = 0.0;
+  for (int i = tid; i < npc; i += blockDim.x) {
+    const float ri = rv[i];
+    float zi;
+    if (PRE == CPRE_JACOBI) { zi = ri / coef[4 * i]; zv[i] = zi; }
+    else if (PRE == CPRE_NONE) { zi = ri; zv[i] = zi; }
+    else zi = zv[i];
+    acc = fma((double)ri, (double)zi, acc);
+  }
+  cta_part(acc, 1);
+  cluster_sync();
+  if (tid == 0) {
+    const double rz0 = cl_total(1);
+    scal[1] = rz0;
+    iscal[0] = (bb == 0.0) ? HMPCG_OK
+             : (!(rz0 > 0.0) ? ((rz0 != rz0) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN) : HMPCG_NOT_CONVERGED);
+  }
+  __syncthreads();
+  double rz = scal[1];
+  int status = iscal[0];
+  int it = 0;
+  double beta = 0.0, rr = bb;
+  int cur = 0;
+  const double near_thr = 16.0 * P.rtol * P.rtol * bb;
+
+  while (status == HMPCG_NOT_CONVERGED && it < P.max_iter) {
+    // ---- p = z + beta p, q = A p, p.q
+    const float bf = (float)beta;
+    float* pc = pbuf[cur];
+    float* pn = pbuf[cur ^ 1];
+    acc = 0.0;
+    for (int i = tid; i < npc; i += blockDim.x) {
+      const int g = n0 + i;
+      const float pi = fmaf(bf, pc[i], zv[i]);
+      pn[i] = pi;
+      const float qi = row32(g, pi, [&](int j) { return fmaf(bf, ld_f(pc, j), ld_f(zv, j)); });
+      qv[i] = qi;
+      acc = fma((double)pi, (double)qi, acc);
+    }
+    cta_part(acc, 2 + (it & 1));   // alternate slots: no reader of the previous value remains
+    ++it;
+    cluster_sync();
+    if (tid == 0) {
+      const double pq = cl_total(2 + ((it - 1) & 1));
+      iscal[0] = (pq > 0.0) ? HMPCG_NOT_CONVERGED : ((pq != pq) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN);
+      scal[2] = rz / pq;
+    }
+    __syncthreads();
+    status = iscal[0];
+    if (status != HMPCG_NOT_CONVERGED) break;
+    const double alpha = scal[2];
+    const float af = (float)alpha;
+    const bool replace = (P.recompute > 0 && (it % P.recompute) == 0) || rr <= near_thr;
+    double arr = 0.0, arz = 0.0;
+    // x is updated in place after every CTA has read the old neighbour values it needs
+    double xnew[4];
+    int nl = 0;
+    for (int i = tid; i < npc; i += blockDim.x, ++nl) {
+      const int g = n0 + i;
+      const double xn = fma(alpha, (double)pn[i], xs[i]);
+      xnew[nl] = xn;
+      float ri;
+      if (replace) {
+        const double ax = row64(g, xn, [&](int j) { return fma(alpha, (double)ld_f(pn, j), ld_d(xs, j)); });
+        const double rd = bs[i] - ax;
+        ri = (float)rd;
+        arr = fma(rd, rd, arr);
+      } else {
+        ri = fmaf(-af, qv[i], rv[i]);
+        arr = fma((double)ri, (double)ri, arr);
+      }
+      rv[i] = ri;
+      if (PRE == CPRE_JACOBI) { const float zi = ri / coef[4 * i]; zv[i] = zi; arz = fma((double)ri, (double)zi, arz); }
+      if (PRE == CPRE_NONE) { zv[i] = ri; arz = fma((double)ri, (double)ri, arz); }
+    }
+    if (replace) cluster_sync();       // every CTA has read the old x of its neighbours
+    nl = 0;
+    for (int i = tid; i < npc; i += blockDim.x, ++nl) xs[i] = xnew[nl];
+    cta_part(arr, 4);
+    if (PRE != CPRE_HMAT) {
+      cta_part(arz, 5);
+    } else {
+      __syncthreads();
+      restrict_leaves();
+      build_tree();
+    }
+    cur ^= 1;
+    __syncthreads();
+    cluster_sync();
+    if (tid == 0) {
+      const double rrn = cl_total(4);
+      scal[3] = rrn;
+      iscal[0] = (rrn != rrn) ? HMPCG_E_NAN : (rrn <= P.rtol * P.rtol * bb ? HMPCG_OK : HMPCG_NOT_CONVERGED);
+      if (PRE != CPRE_HMAT && iscal[0] == HMPCG_NOT_CONVERGED) {
+        const double rzn = cl_total(5);
+        if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+        scal[1] = rzn;
+      }
+    }
+    __syncthreads();
+    rr = scal[3];
+    status = iscal[0];
+    if (status != HMPCG_NOT_CONVERGED) break;
+    if (hmat) {
+      tiles();
+      cluster_sync();
+      prolong();
+      __syncthreads();
+      arz = 0.0;
+      for (int i = tid; i < npc; i += blockDim.x) arz = fma((double)rv[i], (double)zv[i], arz);
+      cta_part(arz, 5);
+      cluster_sync();
+      if (tid == 0) {
+        const double rzn = cl_total(5);
+        if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+        scal[1] = rzn;
+      }
+      __syncthreads();
+      status = iscal[0];
+      if (status != HMPCG_NOT_CONVERGED) break;
+    }
+    if (tid == 0) scal[0] = scal[1] / rz;
+    __syncthreads();
+    beta = scal[0];
+    rz = scal[1];
+    // part[5] is rewritten in the next iteration only after two more cluster barriers
+  }
+  // ---------------- finish: x to global, true residual in FP64
+  __syncthreads();
+  cluster_sync();
+  acc = 0.0;
+  for (int i = tid; i < npc; i += blockDim.x) {
+    const int g = n0 + i;
+    const double ax = row64(g, xs[i], [&](int j) { return ld_d(xs, j); });
+    const double rd = bs[i] - ax;
+    acc = fma(rd, rd, acc);
+    P.x[g] = xs[i];
+  }
+  cta_part(acc, 6);
+  cluster_sync();
+  if (me == 0 && tid == 0) {
+    const double tr = cl_total(6);
+    P.st->iters = it;
+    P.st->status = status;
+    P.st->rel_res = bb > 0.0 ? sqrt(tr / bb) : 0.0;
+    P.st->rr_last = bb > 0.0 ? rr / bb : 0.0;
+  }
+  cluster_sync();   // nobody leaves while others may still read its shared memory
+}
+
+}  // namespace
+
+// ============================================================================ host side
+SysView make_sysview(const hmpcg_system* s);
+
+template <class T, int PRE>
+static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv, const double* b, double* x,
+                       const hmpcg_solve_opts* o, cudaStream_t st) {
+  const int n = (int)sys->n;
+  const bool hmat = PRE == CPRE_HMAT;
+  const int L = hmat ? fv->L : 64;
+  for (int C : {16, 8}) {
+    if (n % C) continue;
+    const int npc = n / C;
+    if (npc > 4 * kCThreads) continue;       // the x update keeps <= 4 values per thread
+    if (hmat && (npc % L)) continue;
+    const int lpc = hmat ? npc / L : 0;
+    if (hmat && (lpc > kCThreads / 32 || fv->levels > 24 || (lpc & (lpc - 1)))) continue;
+    if (hmat && (n / C) / L * C != fv->K) continue;
+    const int tpc = hmat ? (fv->K - 1 + C - 1) / C : 0;
+    const int R = hmat ? fv->r : 16, nslot = hmat ? fv->nslot : 1;
+    const CLayout lay = c_layout<T>(npc, lpc, tpc, L, R, nslot, hmat && fv->learned, hmat);
+    if (hmat && (size_t)tpc * 2 * R > (size_t)lpc * std::max(L, nslot * R)) continue;
+    if (hmat && (size_t)lpc * nslot * R > (size_t)lpc * std::max(L, nslot * R)) continue;
+    if (lay.total > 220 * 1024) continue;
+    auto kern = pcg_cluster_kernel<T, PRE>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.dynamicSmemBytes = lay.total;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // function attributes and the cluster-occupancy query run once per (kernel, C, smem)
+    static std::map<std::tuple<const void*, int, size_t>, bool> feasible;
+    static std::mutex mu;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      const auto key = std::make_tuple((const void*)kern, C, lay.total);
+      auto it = feasible.find(key);
+      if (it == feasible.end()) {
+        bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total) == cudaSuccess;
+        if (ok && C > 8) ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+        int nclusters = 0;
+        if (ok) ok = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1;
+        cudaGetLastError();
+        it = feasible.emplace(key, ok).first;
+      }
+      if (!it->second) continue;
+    }
+    CParams<T> P;
+    P.s = make_sysview(sys);
+    if (fv) P.f = *fv; else memset(&P.f, 0, sizeof(P.f));
+    P.b = b; P.x = x; P.st = c->s.st;
+    P.rtol = o ? o->rtol : 1e-6;
+    P.max_iter = (o && o->max_iter > 0) ? o->max_iter : (int)std::min<int64_t>(10 * sys->n, 1 << 30);
+    P.recompute = o ? o->recompute_every : 10;
+    P.C = C; P.npc = npc; P.lpc = lpc; P.tpc = tpc;
+    HM_CUDA(cudaMemsetAsync(c->s.st, 0, sizeof(DevStatus), st));
+    if (cudaLaunchKernelEx(&cfg, kern, P) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    return HMPCG_OK;
+  }
+  return 1;   // not applicable: caller uses the grid-wide kernel
+}
+
+int solve_cluster_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* b, double* x,
+                           const hmpcg_solve_opts* o, cudaStream_t st) {
+  const int kind = f ? f->kind : HMPCG_PRE_NONE;
+  if (kind == HMPCG_PRE_NONE) return try_cluster<float, CPRE_NONE>(c, sys, nullptr, b, x, o, st);
+  if (kind == HMPCG_PRE_JACOBI) return try_cluster<float, CPRE_JACOBI>(c, sys, nullptr, b, x, o, st);
+  return 1;
+}
+
+template <class T>
+int solve_cluster_hmat(Ctx* c, const hmpcg_system* sys, const FactorView<T>& v, const double* b, double* x,
+                       const hmpcg_solve_opts* o, cudaStream_t st) {
+  return try_cluster<T, CPRE_HMAT>(c, sys, &v, b, x, o, st);
+}
+template int solve_cluster_hmat<float>(Ctx*, const hmpcg_system*, const FactorView<float>&, const double*, double*,
+                                       const hmpcg_solve_opts*, cudaStream_t);
+template int solve_cluster_hmat<__nv_bfloat16>(Ctx*, const hmpcg_system*, const FactorView<__nv_bfloat16>&,
+                                               const double*, double*, const hmpcg_solve_opts*, cudaStream_t);
+template int solve_cluster_hmat<__nv_fp8_e4m3>(Ctx*, const hmpcg_system*, const FactorView<__nv_fp8_e4m3>&,
+                                               const double*, double*, const hmpcg_solve_opts*, cudaStream_t);
+
+}  // namespace hm

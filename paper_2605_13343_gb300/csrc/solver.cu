@@ -311,41 +311,44 @@ struct PcgParams {
   int chunk;       // nodes owned per work unit (multiple of L for the H-matrix apply)
 };
 
-// Deterministic CTA sum of one double per thread; result valid in every thread.
-HM_INLINE double cta_sum(double v, double* red8) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5;
+// FP64 is scarce on this part (about 2 FP64 FMA per clock per SM): every thread keeps its
+// own FP64 partial, one warp reduces the CTA's partials, one warp reduces the grid's, and
+// thread 0 computes alpha, beta and the stop test and broadcasts them.
+HM_INLINE void cta_part(double v, double* red, double* dst) {
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red8[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) s += red8[i];
-  return s;
-}
-
-// Deterministic sum of part[0..G) computed identically by every CTA.
-HM_INLINE double grid_sum(const double* part, double* red8) {
+  red[threadIdx.x] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
     double s = 0.0;
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += red[i];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *dst = s;
+  }
+}
+
+// Deterministic sum of part[0..G) computed identically by every CTA (warp 0; result in
+// thread 0 only).
+HM_INLINE double grid_sum0(const double* part) {
+  double s = 0.0;
+  if (threadIdx.x < 32) {
     for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) s += __ldcg(part + i);
     s = warp_sum(s);
-    if (threadIdx.x == 0) red8[8] = s;
   }
-  __syncthreads();
-  return red8[8];
+  return s;
 }
 
 template <class T, int PRE>
 __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
   extern __shared__ float sm[];
-  __shared__ double red8[16];
+  __shared__ double red[kThreads];
+  __shared__ double scal[4];
+  __shared__ int iscal[2];
   const SysView& S = P.s;
   const FactorView<T>& F = P.f;
   Scratch W = P.w;
   GridSync gs{W.counter, W.st, 0u};
   const int G = gridDim.x;
+  const int tid = threadIdx.x;
   const int nchunk = S.n / P.chunk;
   const int lpc = (PRE == PRE_HMAT) ? P.chunk / F.L : 0;   // leaves per chunk
   double* part_pq = W.part;
@@ -367,13 +370,17 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     P.x[i] = 0.0;
     W.r[i] = (float)bi;
     W.p0[i] = 0.f;
-    acc += bi * bi;
+    acc = fma(bi, bi, acc);
   }
-  double v = cta_sum(acc, red8);
-  if (threadIdx.x == 0) part_bb[blockIdx.x] = v;
+  cta_part(acc, red, part_bb + blockIdx.x);
   if (PRE == PRE_HMAT) { __syncthreads(); OWN_LEAVES(k) phase_restrict<T>(F, k, W.r, W.ydiag, W.uhat, sm); }
   if (!gs.sync(0)) return;
-  const double bb = grid_sum(part_bb, red8);
+  {
+    const double v = grid_sum0(part_bb);
+    if (tid == 0) scal[0] = v;
+    __syncthreads();
+  }
+  const double bb = scal[0];
   if (PRE == PRE_HMAT) {
     for (int m = blockIdx.x; m < F.K - 1; m += G) phase_tile<T>(F, m, W.uhat, W.tcoup, sm);
     if (!gs.sync(1)) return;
@@ -386,14 +393,21 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     if (PRE == PRE_JACOBI) { zi = ri / S.diag32[i]; W.z[i] = zi; }
     else if (PRE == PRE_NONE) { zi = ri; W.z[i] = zi; }
     else zi = W.z[i];
-    acc += (double)ri * (double)zi;
+    acc = fma((double)ri, (double)zi, acc);
   }
-  v = cta_sum(acc, red8);
-  if (threadIdx.x == 0) part_rz[blockIdx.x] = v;
+  cta_part(acc, red, part_rz + blockIdx.x);
   if (!gs.sync(2)) return;
-  double rz = grid_sum(part_rz, red8);
-
-  int status = HMPCG_NOT_CONVERGED;
+  {
+    const double rz0 = grid_sum0(part_rz);
+    if (tid == 0) {
+      scal[1] = rz0;
+      iscal[0] = (bb == 0.0) ? HMPCG_OK
+               : (!(rz0 > 0.0) ? ((rz0 != rz0) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN) : HMPCG_NOT_CONVERGED);
+    }
+    __syncthreads();
+  }
+  double rz = scal[1];
+  int status = iscal[0];
   int it = 0;
   double beta = 0.0;
   float* pcur = W.p0;
@@ -401,8 +415,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
   double* xcur = P.x;
   double* xnext = W.x2;
   double rr = bb;
-  if (bb == 0.0) status = HMPCG_OK;
-  else if (!(rz > 0.0)) status = (rz != rz) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+  const double near_thr = 16.0 * P.rtol * P.rtol * bb;
 
   while (status == HMPCG_NOT_CONVERGED && it < P.max_iter) {
     // ---- p = z + beta p, q = A p, p.q
@@ -414,19 +427,26 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
       const float qi = spmv_row32(S, (unsigned)i, pi,
                                   [&](int j) { return fmaf(bf, __ldcg(pcur + j), __ldcg(W.z + j)); });
       W.q[i] = qi;
-      acc += (double)pi * (double)qi;
+      acc = fma((double)pi, (double)qi, acc);
     }
-    v = cta_sum(acc, red8);
-    if (threadIdx.x == 0) part_pq[blockIdx.x] = v;
+    cta_part(acc, red, part_pq + blockIdx.x);
     ++it;
     if (!gs.sync(3)) return;
-    const double pq = grid_sum(part_pq, red8);
-    if (!(pq > 0.0)) { status = (pq != pq) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN; break; }
-    const double alpha = rz / pq;
+    {
+      const double pq = grid_sum0(part_pq);
+      if (tid == 0) {
+        iscal[0] = (pq > 0.0) ? HMPCG_NOT_CONVERGED : ((pq != pq) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN);
+        scal[2] = rz / pq;
+      }
+      __syncthreads();
+    }
+    status = iscal[0];
+    if (status != HMPCG_NOT_CONVERGED) break;
+    const double alpha = scal[2];
     const float af = (float)alpha;
     // periodic true-residual replacement, and every iteration once the recursive residual is
     // within 4x of the target, so that the stop test is always taken on b - A x in FP64
-    const bool replace = (P.recompute > 0 && (it % P.recompute) == 0) || rr <= 16.0 * P.rtol * P.rtol * bb;
+    const bool replace = (P.recompute > 0 && (it % P.recompute) == 0) || rr <= near_thr;
     // ---- x += alpha p, r -= alpha q (or r = b - A x), ||r||^2, z = M r (local part)
     double arr = 0.0, arz = 0.0;
     OWN_NODES(i) {
@@ -439,20 +459,18 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
         });
         const double rd = P.b[i] - ax;
         ri = (float)rd;
-        arr += rd * rd;
+        arr = fma(rd, rd, arr);
       } else {
         ri = fmaf(-af, W.q[i], W.r[i]);
-        arr += (double)ri * (double)ri;
+        arr = fma((double)ri, (double)ri, arr);
       }
       W.r[i] = ri;
-      if (PRE == PRE_JACOBI) { const float zi = ri / S.diag32[i]; W.z[i] = zi; arz += (double)ri * zi; }
-      if (PRE == PRE_NONE) { W.z[i] = ri; arz += (double)ri * ri; }
+      if (PRE == PRE_JACOBI) { const float zi = ri / S.diag32[i]; W.z[i] = zi; arz = fma((double)ri, (double)zi, arz); }
+      if (PRE == PRE_NONE) { W.z[i] = ri; arz = fma((double)ri, (double)ri, arz); }
     }
-    v = cta_sum(arr, red8);
-    if (threadIdx.x == 0) part_rr[blockIdx.x] = v;
+    cta_part(arr, red, part_rr + blockIdx.x);
     if (PRE != PRE_HMAT) {
-      v = cta_sum(arz, red8);
-      if (threadIdx.x == 0) part_rz[blockIdx.x] = v;
+      cta_part(arz, red, part_rz + blockIdx.x);
     } else {
       __syncthreads();
       OWN_LEAVES(k) phase_restrict<T>(F, k, W.r, W.ydiag, W.uhat, sm);
@@ -460,23 +478,43 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     { double* t = xcur; xcur = xnext; xnext = t; }
     { float* t = pcur; pcur = pnext; pnext = t; }
     if (!gs.sync(4)) return;
-    rr = grid_sum(part_rr, red8);
-    if (rr != rr) { status = HMPCG_E_NAN; break; }
-    if (rr <= P.rtol * P.rtol * bb) { status = HMPCG_OK; break; }
+    {
+      const double rrn = grid_sum0(part_rr);
+      const double rzn = (PRE != PRE_HMAT) ? grid_sum0(part_rz) : 0.0;
+      if (tid == 0) {
+        scal[3] = rrn;
+        iscal[0] = (rrn != rrn) ? HMPCG_E_NAN : (rrn <= P.rtol * P.rtol * bb ? HMPCG_OK : HMPCG_NOT_CONVERGED);
+        if (PRE != PRE_HMAT && iscal[0] == HMPCG_NOT_CONVERGED) {
+          if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+          scal[1] = rzn;
+        }
+      }
+      __syncthreads();
+    }
+    rr = scal[3];
+    status = iscal[0];
+    if (status != HMPCG_NOT_CONVERGED) break;
     if (PRE == PRE_HMAT) {
       for (int m = blockIdx.x; m < F.K - 1; m += G) phase_tile<T>(F, m, W.uhat, W.tcoup, sm);
       if (!gs.sync(5)) return;
       arz = 0.0;
       OWN_LEAVES(k) phase_prolong<T>(F, k, W.tcoup, W.ydiag, W.z, sm);
-      OWN_NODES(i) arz += (double)W.r[i] * (double)W.z[i];
-      v = cta_sum(arz, red8);
-      if (threadIdx.x == 0) part_rz[blockIdx.x] = v;
+      OWN_NODES(i) arz = fma((double)W.r[i], (double)W.z[i], arz);
+      cta_part(arz, red, part_rz + blockIdx.x);
       if (!gs.sync(6)) return;
+      const double rzn = grid_sum0(part_rz);
+      if (tid == 0) {
+        if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+        scal[1] = rzn;
+      }
+      __syncthreads();
+      status = iscal[0];
+      if (status != HMPCG_NOT_CONVERGED) break;
     }
-    const double rzn = grid_sum(part_rz, red8);
-    if (!(rzn > 0.0)) { status = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN; break; }
-    beta = rzn / rz;
-    rz = rzn;
+    if (tid == 0) scal[0] = scal[1] / rz;
+    __syncthreads();
+    beta = scal[0];
+    rz = scal[1];
   }
   // ---------------- finish: copy x to the caller's buffer, true residual in FP64
   if (!gs.sync(7)) return;
@@ -485,14 +523,13 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     const double xi = xcur[i];
     const double ax = spmv_row64(S, (unsigned)i, xi, [&](int j) { return __ldcg(xcur + j); });
     const double rd = P.b[i] - ax;
-    acc += rd * rd;
+    acc = fma(rd, rd, acc);
   }
-  v = cta_sum(acc, red8);
-  if (threadIdx.x == 0) part_pq[blockIdx.x] = v;
+  cta_part(acc, red, part_pq + blockIdx.x);
   if (!gs.sync(8)) return;
   if (xcur != P.x) { OWN_NODES(i) P.x[i] = xcur[i]; }
   if (blockIdx.x == 0) {
-    const double tr = grid_sum(part_pq, red8);
+    const double tr = grid_sum0(part_pq);
     if (threadIdx.x == 0) {
       W.st->iters = it;
       W.st->status = status;
@@ -596,10 +633,21 @@ int launch_pcg(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv, const d
 
 template <class T> static bool fits_scratch(const Ctx* c, const FactorView<T>& v);
 
-// explicit dispatch used by api.cu
+int solve_cluster_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* b, double* x,
+                           const hmpcg_solve_opts* o, cudaStream_t st);
+template <class T>
+int solve_cluster_hmat(Ctx* c, const hmpcg_system* sys, const FactorView<T>& v, const double* b, double* x,
+                       const hmpcg_solve_opts* o, cudaStream_t st);
+
+// explicit dispatch used by api.cu.  path: 0 = cluster kernel when the system fits one
+// thread-block cluster, else the grid-wide kernel; 1 = grid-wide kernel only.
 int solve_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* b,
-                   double* x, const hmpcg_solve_opts* o, cudaStream_t st, int chunk_override) {
+                   double* x, const hmpcg_solve_opts* o, cudaStream_t st, int chunk_override, int path) {
   const int kind = f ? f->kind : HMPCG_PRE_NONE;
+  if (path == 0 && (kind == HMPCG_PRE_NONE || kind == HMPCG_PRE_JACOBI)) {
+    const int rc = solve_cluster_dispatch(c, sys, f, b, x, o, st);
+    if (rc <= 0) return rc;
+  }
   if (kind == HMPCG_PRE_NONE) return launch_pcg<float, PRE_NONE>(c, sys, nullptr, b, x, o, st, chunk_override);
   if (kind == HMPCG_PRE_JACOBI) return launch_pcg<float, PRE_JACOBI>(c, sys, nullptr, b, x, o, st, chunk_override);
   if (kind != HMPCG_PRE_SVDH && kind != HMPCG_PRE_LEARNED) return HMPCG_E_INVALID;
@@ -609,14 +657,17 @@ int solve_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, cons
   switch (f->dtype) {
     case HMPCG_F32: {
       FactorView<float> v; if ((rc = make_factor_view(f, v))) return rc; if (!fits_scratch(c, v)) return HMPCG_E_SHAPE;
+      if (path == 0) { const int rc2 = solve_cluster_hmat<float>(c, sys, v, b, x, o, st); if (rc2 <= 0) return rc2; }
       return launch_pcg<float, PRE_HMAT>(c, sys, &v, b, x, o, st, chunk_override);
     }
     case HMPCG_BF16: {
       FactorView<__nv_bfloat16> v; if ((rc = make_factor_view(f, v))) return rc; if (!fits_scratch(c, v)) return HMPCG_E_SHAPE;
+      if (path == 0) { const int rc2 = solve_cluster_hmat<__nv_bfloat16>(c, sys, v, b, x, o, st); if (rc2 <= 0) return rc2; }
       return launch_pcg<__nv_bfloat16, PRE_HMAT>(c, sys, &v, b, x, o, st, chunk_override);
     }
     case HMPCG_FP8E4M3: {
       FactorView<__nv_fp8_e4m3> v; if ((rc = make_factor_view(f, v))) return rc; if (!fits_scratch(c, v)) return HMPCG_E_SHAPE;
+      if (path == 0) { const int rc2 = solve_cluster_hmat<__nv_fp8_e4m3>(c, sys, v, b, x, o, st); if (rc2 <= 0) return rc2; }
       return launch_pcg<__nv_fp8_e4m3, PRE_HMAT>(c, sys, &v, b, x, o, st, chunk_override);
     }
   }

@@ -1,0 +1,150 @@
+"""Train the hierarchical-transformer preconditioner with hmpcg_train_step (Sec. 6; Supp. C).
+
+Systems are drawn from two seeded pools assembled on the device once (the cached
+training contexts of Sec. 6.3 / Supp. D): 16^3 boxes with contrast log-uniform in
+[1, 100] and 32x16x16 boxes with 5-12 spheres of contrast 100.  Each step takes a
+random batch from one pool (every `--big-every`-th step from the larger grid),
+16 Rademacher probes per system, AdamW with global-norm clipping (inside the
+step) and a reduce-on-plateau learning-rate schedule (factor 0.5, patience 5 log
+steps, relative threshold 5e-3; Supp. C).  Every `--eval-every` steps the PCG
+iteration count on held-out 32x16x16 frames is measured (inference + PCG, BF16
+factors, rtol 1e-6) next to Jacobi PCG; the best checkpoint by mean iterations
+is written to `--out` as a flat float32 file in the weight-blob order.
+
+    python -m paper_2605_13343_gb300.train --steps 3000 --out weights.f32
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+import paper_2605_13343_gb300 as h  # noqa: E402
+
+CFG = dict(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16)
+
+
+class Plateau:
+    """Reduce-on-plateau on a minimised quantity (relative threshold)."""
+
+    def __init__(self, lr, factor=0.5, patience=5, threshold=5e-3, min_lr=1e-6):
+        self.lr, self.factor, self.patience, self.threshold, self.min_lr = lr, factor, patience, threshold, min_lr
+        self.best = float("inf")
+        self.bad = 0
+
+    def step(self, value):
+        if value < self.best * (1.0 - self.threshold):
+            self.best = value
+            self.bad = 0
+        else:
+            self.bad += 1
+            if self.bad > self.patience:
+                self.lr = max(self.min_lr, self.lr * self.factor)
+                self.bad = 0
+        return self.lr
+
+
+def make_pool(family, seeds):
+    out = []
+    for s in seeds:
+        fr = inputs.frame(family, s)
+        sg = h.System(fr["dims"])
+        h.assemble(torch.from_numpy(fr["rho"]).cuda(), sg)
+        out.append((sg, torch.from_numpy(fr["b"]).cuda()))
+    return out
+
+
+def evaluate(ctx, frames, rtol=1e-6):
+    n = frames[0][0].n
+    P = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+    packed = torch.empty(P, dtype=torch.bfloat16, device="cuda")
+    fac = h.factors(h.PRE_LEARNED, packed, n, 64, 16)
+    jac = h.Factors()
+    jac.kind = h.PRE_JACOBI
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    it_l, it_j, ok = [], [], True
+    for sg, b in frames:
+        h.infer_factors(ctx, [sg], packed)
+        info = h.solve(ctx, sg, fac, b, x, rtol=rtol, allow=(h.OK, h.NOT_CONVERGED, h.E_BREAKDOWN, h.E_NAN))
+        ok = ok and info.status == h.OK
+        it_l.append(info.iters if info.status == h.OK else 10 ** 6)
+        it_j.append(h.solve(ctx, sg, jac, b, x, rtol=rtol).iters)
+    return float(np.mean(it_l)), float(np.mean(it_j)), ok
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--probes", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=3e-4)
+    ap.add_argument("--big-every", type=int, default=4)
+    ap.add_argument("--eval-every", type=int, default=250)
+    ap.add_argument("--log-every", type=int, default=50)
+    ap.add_argument("--pool", type=int, default=256)
+    ap.add_argument("--init", default=None)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                                  "hmpcg_d128_l4.f32"))
+    ap.add_argument("--log", default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+
+    w0 = np.fromfile(args.init, dtype=np.float32) if args.init else inputs.network_blob(args.seed, **CFG)
+    ctx = h.Context(max_n=8192, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
+                    max_batch=args.batch, weights=w0)
+    small = make_pool("spheres3d_4096_lu", range(args.pool))
+    big = make_pool("spheres3d_8192", range(10000, 10000 + args.pool // 2))
+    held = make_pool("spheres3d_8192", range(20000, 20008))
+    rng = np.random.default_rng(args.seed)
+    sched = Plateau(args.lr)
+    lr = args.lr
+    logf = open(args.log, "w") if args.log else None
+    best = float("inf")
+    t0 = time.time()
+    window = []
+    it_l, it_j, ok = evaluate(ctx, held)
+    rec = dict(step=0, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, t=0.0)
+    print(json.dumps(rec), flush=True)
+    for step in range(1, args.steps + 1):
+        if args.big_every and step % args.big_every == 0:
+            pick = rng.choice(len(big), size=max(1, args.batch // 2), replace=False)
+            batch = [big[i][0] for i in pick]
+        else:
+            pick = rng.choice(len(small), size=args.batch, replace=False)
+            batch = [small[i][0] for i in pick]
+        want = step % args.log_every == 0
+        loss = h.train_step(ctx, batch, args.probes, lr, int(rng.integers(1 << 62)), want_loss=want)
+        if want:
+            window.append(loss)
+            lr = sched.step(float(np.mean(window[-1:])))
+            rec = dict(step=step, loss=loss, lr=lr, t=time.time() - t0)
+            if logf:
+                logf.write(json.dumps(rec) + "\n")
+                logf.flush()
+        if step % args.eval_every == 0 or step == args.steps:
+            it_l, it_j, ok = evaluate(ctx, held)
+            rec = dict(step=step, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, loss=window[-1] if window else None,
+                       t=time.time() - t0)
+            print(json.dumps(rec), flush=True)
+            if logf:
+                logf.write(json.dumps(rec) + "\n")
+                logf.flush()
+            if ok and it_l < best:
+                best = it_l
+                os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+                h.get_weights(ctx, w0.size).tofile(args.out)
+    print(json.dumps(dict(done=True, best_iters=best, seconds=time.time() - t0)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -24,6 +24,13 @@ def _gpu_system(dims, rho, bc=0, face=0):
     return s
 
 
+@pytest.fixture(params=["cluster", "grid"])
+def path(request, monkeypatch):
+    """Run a PCG test through the thread-block-cluster kernel and the grid-wide kernel."""
+    monkeypatch.setenv("HMPCG_PCG_PATH", request.param)
+    return request.param
+
+
 @pytest.fixture(scope="module")
 def ctx():
     c = h.Context(max_n=1 << 16, leaf=64, rank=16)
@@ -197,7 +204,7 @@ def _true_rel(a, b, x):
 
 @pytest.mark.parametrize("family,seed", [("disc2d_1024", 0), ("spheres3d_8192", 0),
                                          ("spheres3d_8192", 3), ("discs2d_16384", 1)])
-def test_pcg_jacobi_parity(ctx, family, seed):
+def test_pcg_jacobi_parity(ctx, path, family, seed):
     fr = inputs.frame(family, seed)
     ref = grid.assemble(fr["rho"], fr["dims"])
     s = _gpu_system(fr["dims"], fr["rho"])
@@ -215,7 +222,7 @@ def test_pcg_jacobi_parity(ctx, family, seed):
     assert np.linalg.norm(xg - out["x"]) <= 1e-3 * np.linalg.norm(out["x"])
 
 
-def test_pcg_cg_and_iteration_cap(ctx):
+def test_pcg_cg_and_iteration_cap(ctx, path):
     fr = inputs.frame("disc2d_1024", 2)
     ref = grid.assemble(fr["rho"], fr["dims"])
     s = _gpu_system(fr["dims"], fr["rho"])
@@ -234,7 +241,7 @@ def test_pcg_cg_and_iteration_cap(ctx):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_pcg_svdh_parity(ctx, dtype):
+def test_pcg_svdh_parity(ctx, path, dtype):
     fr = inputs.frame("disc2d_1024", 0)
     ref = grid.assemble(fr["rho"], fr["dims"])
     ad = grid.dense_matrix(ref)
@@ -251,7 +258,7 @@ def test_pcg_svdh_parity(ctx, dtype):
     assert _true_rel(a, fr["b"], x.cpu().numpy()) <= 1e-6
 
 
-def test_pcg_exact_inverse_one_iteration(ctx):
+def test_pcg_exact_inverse_one_iteration(ctx, path):
     dims = (16, 16)
     rho = inputs.density_discs(3, dims, 1, (4.0, 4.0), 10.0)
     ref = grid.assemble(rho, dims)
@@ -266,7 +273,7 @@ def test_pcg_exact_inverse_one_iteration(ctx):
 
 
 @pytest.mark.parametrize("how", ["negated", "block_inverse_leaves"])
-def test_pcg_breakdown_indefinite(ctx, how):
+def test_pcg_breakdown_indefinite(ctx, path, how):
     # (A_kk)^-1 leaves with truncated tiles are indefinite on this frame (the oracle breaks
     # down at the first iteration too); a negated M is indefinite by construction
     fr = inputs.frame("disc2d_1024", 0)
@@ -288,7 +295,7 @@ def test_pcg_breakdown_indefinite(ctx, how):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
-def test_pcg_learned_layout_random_spd(ctx, dtype):
+def test_pcg_learned_layout_random_spd(ctx, path, dtype):
     # M = Jacobi gate + small PSD leaf term + small tiles: SPD, close to Jacobi
     fr = inputs.frame("spheres3d_8192", 2)
     ref = grid.assemble(fr["rho"], fr["dims"])
