@@ -147,12 +147,14 @@ int hmpcg_create(void** out, const hmpcg_config* cfg, const float* weights, int6
   c->uhat_cap = (int64_t)nr * std::max(2, c->levels_max) * widen;
   c->tcoup_cap = 2 * (int64_t)nr * widen;
   s.uhat = (float*)alloc(4 * (size_t)c->uhat_cap);
+  c->tree_cap = 2 * c->uhat_cap;
+  c->tree = (float*)alloc(4 * (size_t)c->tree_cap);
   s.tcoup = (float*)alloc(4 * (size_t)c->tcoup_cap);
   s.x2 = (double*)alloc(8 * n);
   s.part = (double*)alloc(8 * 4 * kMaxGrid);
   s.counter = (unsigned*)alloc(256);
   s.st = (DevStatus*)alloc(sizeof(DevStatus));
-  bool ok = s.r && s.z && s.q && s.p0 && s.p1 && s.ydiag && s.uhat && s.tcoup && s.x2 && s.part &&
+  bool ok = c->tree && s.r && s.z && s.q && s.p0 && s.p1 && s.ydiag && s.uhat && s.tcoup && s.x2 && s.part &&
             s.counter && s.st;
   ok = ok && cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
   if (!ok) { hmpcg_destroy(c); return HMPCG_E_NOMEM; }

@@ -48,6 +48,8 @@ struct Ctx {
   int max_nrhs;
   int levels_max;
   int64_t uhat_cap, tcoup_cap;   // floats in Scratch::uhat / Scratch::tcoup
+  float* tree;                  // strip-sum tree of the bandwidth apply (nslot 2K r floats)
+  int64_t tree_cap;
   Scratch s;
   int num_sms;
   int coop_blocks_hmat[3];   // max co-resident CTAs per dtype for the H-matrix PCG

@@ -62,7 +62,7 @@ struct CParams {
 
 // Shared-memory carve-up (byte offsets), identical in every CTA.
 struct CLayout {
-  size_t x, b, r, z, q, p0, p1, yd, coef, uh, tc, part, rs, ws, leaf, bridge, gate, core, total;
+  size_t x, b, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tc, part, rs, ws, leaf, bridge, gate, core, total;
 };
 
 template <class T>
@@ -79,6 +79,8 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
   o.p1 = take(4 * (size_t)npc);
   o.yd = take(4 * (size_t)npc);
   o.coef = take(16 * (size_t)npc);             // diag32, w32[0..2] of owned nodes
+  o.nbr = take(24 * (size_t)npc);              // 6 neighbours: (owner << 16) | local index, -1 at the boundary
+  o.wm = take(12 * (size_t)npc);               // w32 of the -a face of each owned node
   o.uh = take(hmat ? 4 * (size_t)nslot * (2 * lpc - 1) * R : 0);   // per slot: leaves, then aligned pair, quad, ... sums
   o.tc = take(hmat ? 4 * (size_t)tpc * 2 * R : 0);
   o.part = take(8 * 8);
@@ -110,6 +112,8 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
   float* pbuf[2] = {reinterpret_cast<float*>(sm + lay.p0), reinterpret_cast<float*>(sm + lay.p1)};
   float* ydv = reinterpret_cast<float*>(sm + lay.yd);
   float* coef = reinterpret_cast<float*>(sm + lay.coef);
+  int* nbt = reinterpret_cast<int*>(sm + lay.nbr);
+  float* wmv = reinterpret_cast<float*>(sm + lay.wm);
   float* uh = reinterpret_cast<float*>(sm + lay.uh);
   float* tcp = reinterpret_cast<float*>(sm + lay.tc);
   double* part = reinterpret_cast<double*>(sm + lay.part);
@@ -137,10 +141,11 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
     double v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = c < C ? *remote(part + q, c) : 0.0;
-    double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) s += v[c];
-    return s;
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+      for (int k = 0; k < w; ++k) v[k] += v[k + w];
+    return v[0];
   };
 
   // ---------------- load: owned b, coefficients, factor share
@@ -148,7 +153,14 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
     const int g = n0 + i;
     bs[i] = P.b[g];
     coef[4 * i] = S.diag32[g];
-    for (int a = 0; a < 3; ++a) coef[4 * i + 1 + a] = a < S.mo.ndim ? S.w32[a][g] : 0.f;
+    for (int a = 0; a < 3; ++a) {
+      coef[4 * i + 1 + a] = a < S.mo.ndim ? S.w32[a][g] : 0.f;
+      const int jp = a < S.mo.ndim ? S.mo.plus(g, a) : -1;
+      const int jm = a < S.mo.ndim ? S.mo.minus(g, a) : -1;
+      nbt[6 * i + 2 * a] = jp < 0 ? -1 : (((jp / npc) << 16) | (jp % npc));
+      nbt[6 * i + 2 * a + 1] = jm < 0 ? -1 : (((jm / npc) << 16) | (jm % npc));
+      wmv[3 * i + a] = jm < 0 ? 0.f : S.w32[a][jm];
+    }
   }
   if (hmat) {
     const int k0 = n0 / L;
@@ -329,31 +341,34 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
     }
   };
   // FP32 SpMV row with neighbour values from get(j)
-  auto row32 = [&](int i, float vi, auto get) -> float {
-    const int il = i - n0;
+  // FP32 SpMV row of owned node il with neighbour values get(owner, local)
+  auto row32 = [&](int il, float vi, auto get) -> float {
     float acc = coef[4 * il] * vi;
-    for (int a = 0; a < S.mo.ndim; ++a) {
-      const int jp = S.mo.plus(i, a);
-      if (jp >= 0) acc = fmaf(-coef[4 * il + 1 + a], get(jp), acc);
-      const int jm = S.mo.minus(i, a);
-      if (jm >= 0) {
-        const float wm = (jm / npc == (int)me) ? coef[4 * (jm - n0) + 1 + a]
-                                               : *remote(coef + 4 * (jm % npc) + 1 + a, jm / npc);
-        acc = fmaf(-wm, get(jm), acc);
-      }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ep = nbt[6 * il + 2 * a], em = nbt[6 * il + 2 * a + 1];
+      if (ep >= 0) acc = fmaf(-coef[4 * il + 1 + a], get(ep >> 16, ep & 0xFFFF), acc);
+      if (em >= 0) acc = fmaf(-wmv[3 * il + a], get(em >> 16, em & 0xFFFF), acc);
     }
     return acc;
   };
   auto row64 = [&](int i, double xi, auto get) -> double {
+    const int il = i - n0;
     double acc = S.diag[i] * xi;
-    for (int a = 0; a < S.mo.ndim; ++a) {
-      const int jp = S.mo.plus(i, a);
-      if (jp >= 0) acc = fma(-S.w[a][i], get(jp), acc);
-      const int jm = S.mo.minus(i, a);
-      if (jm >= 0) acc = fma(-S.w[a][jm], get(jm), acc);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ep = nbt[6 * il + 2 * a], em = nbt[6 * il + 2 * a + 1];
+      if (ep >= 0) acc = fma(-S.w[a][i], get(ep >> 16, ep & 0xFFFF), acc);
+      if (em >= 0) {
+        const int o = em >> 16, l = em & 0xFFFF;
+        acc = fma(-S.w[a][o * npc + l], get(o, l), acc);
+      }
     }
     return acc;
   };
+  // value of an owner-distributed array at (owner, local)
+  auto gf = [&](float* base, int o, int l) -> float { return o == (int)me ? base[l] : *remote(base + l, o); };
+  auto gd = [&](double* base, int o, int l) -> double { return o == (int)me ? base[l] : *remote(base + l, o); };
 
   // FP64 is scarce on this part: per-thread FP64 partials are reduced by one warp, and the
   // PCG scalars are computed by thread 0 and broadcast through shared memory.
@@ -365,9 +380,15 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
     red512[tid] = v;
     __syncthreads();
     if (tid < 32) {
-      double s = 0.0;
-      for (int i = tid; i < (int)blockDim.x; i += 32) s += red512[i];
-      s = warp_sum(s);
+      // fixed pairwise tree: 16 values per lane, then the warp
+      double a[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) a[k] = (tid + 32 * k < (int)blockDim.x) ? red512[tid + 32 * k] : 0.0;
+#pragma unroll
+      for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; ++k) a[k] += a[k + w];
+      const double s = warp_sum(a[0]);
       if (tid == 0) part[q] = s;
     }
   };
@@ -429,7 +450,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
       const int g = n0 + i;
       const float pi = fmaf(bf, pc[i], zv[i]);
       pn[i] = pi;
-      const float qi = row32(g, pi, [&](int j) { return fmaf(bf, ld_f(pc, j), ld_f(zv, j)); });
+      const float qi = row32(i, pi, [&](int o, int l) { return fmaf(bf, gf(pc, o, l), gf(zv, o, l)); });
       qv[i] = qi;
       acc = fma((double)pi, (double)qi, acc);
     }
@@ -457,7 +478,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
       xnew[nl] = xn;
       float ri;
       if (replace) {
-        const double ax = row64(g, xn, [&](int j) { return fma(alpha, (double)ld_f(pn, j), ld_d(xs, j)); });
+        const double ax = row64(g, xn, [&](int o, int l) { return fma(alpha, (double)gf(pn, o, l), gd(xs, o, l)); });
         const double rd = bs[i] - ax;
         ri = (float)rd;
         arr = fma(rd, rd, arr);
@@ -527,7 +548,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
   acc = 0.0;
   for (int i = tid; i < npc; i += blockDim.x) {
     const int g = n0 + i;
-    const double ax = row64(g, xs[i], [&](int j) { return ld_d(xs, j); });
+    const double ax = row64(g, xs[i], [&](int o, int l) { return gd(xs, o, l); });
     const double rd = bs[i] - ax;
     acc = fma(rd, rd, acc);
     P.x[g] = xs[i];

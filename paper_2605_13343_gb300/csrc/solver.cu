@@ -7,6 +7,7 @@
 // (Sec. 6.3, Supp. G).
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 #include "ctx.cuh"
 
 namespace hm {
@@ -589,8 +590,23 @@ size_t apply_smem_bytes(int L, int R, int nslot) {
   return std::max(a, std::max(b, c)) * sizeof(float);
 }
 
+int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r, float* z, float* ydiag,
+                      float* uhat, float* tcoup, cudaStream_t st,
+                      void (*tile_launch)(const FactorView<__nv_bfloat16>&, const float*, float*, int, cudaStream_t));
+
+static void tile_launch_bf16(const FactorView<__nv_bfloat16>& f, const float* uhat, float* tcoup, int num_sms,
+                             cudaStream_t st) {
+  const size_t smem = apply_smem_bytes(f.L, f.r, f.nslot);
+  apply_tile_kernel<__nv_bfloat16><<<std::max(1, std::min(f.K - 1, num_sms * 8)), kThreads, smem, st>>>(f, uhat, tcoup);
+}
+
 template <class T>
 int launch_apply(Ctx* c, const FactorView<T>& f, const float* r, float* z, cudaStream_t st) {
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    // warp-per-leaf kernels for the common BF16, leaf-64 shapes
+    const int rc = apply_warp_launch(c, f, r, z, c->s.ydiag, c->s.uhat, c->s.tcoup, st, tile_launch_bf16);
+    if (rc <= 0) return rc;
+  }
   const size_t smem = apply_smem_bytes(f.L, f.r, f.nslot);
   const int g1 = std::min(f.K, c->num_sms * 8);
   apply_restrict_kernel<T><<<g1, kThreads, smem, st>>>(f, r, c->s.ydiag, c->s.uhat);
@@ -742,7 +758,11 @@ int assemble_launch(const double* rho, const hmpcg_system* sys, int bc, int face
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
+int spmv_cube_launch(const hmpcg_system* sys, const float* x, float* y, cudaStream_t st);
+
 int spmv_launch(const hmpcg_system* sys, const float* x, float* y, cudaStream_t st) {
+  const int rc = spmv_cube_launch(sys, x, y, st);
+  if (rc <= 0) return rc;
   SysView v = make_sysview(sys);
   const unsigned n = (unsigned)sys->n;
   spmv_kernel<<<(n + 255) / 256, 256, 0, st>>>(v, x, y);
