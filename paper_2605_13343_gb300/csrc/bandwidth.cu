@@ -73,40 +73,65 @@ HM_INLINE float2 bf2(uint32_t u) {
 
 // Vectorised restriction of one bridge slot (W: 64 x R row-major BF16 = 8R chunks of 16 B).
 // Lane holds chunks c = q*32 + lane (q < R/4): row c / (R/8), columns (lane % (R/8))*8 .. +7.
+// L2 policies: the leaf blocks stream through once per apply (evict first); the bridges are
+// read again by the prolongation, which walks the leaves in the opposite order, so the most
+// recently restricted ones are still in L2 (evict last).
+HM_INLINE uint64_t pol_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+HM_INLINE uint64_t pol_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+HM_INLINE uint4 ld_hint(const uint4* a, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(a), "l"(pol));
+  return v;
+}
 template <int R>
-HM_INLINE void restrict_load(const __nv_bfloat16* __restrict__ W, uint4 (&wv)[R / 4], int lane) {
+HM_INLINE void restrict_load(const __nv_bfloat16* __restrict__ W, uint4 (&wv)[R / 4], int lane, uint64_t pol) {
   const uint4* src = reinterpret_cast<const uint4*>(W);
 #pragma unroll
-  for (int q = 0; q < R / 4; ++q) wv[q] = __ldg(src + q * 32 + lane);
+  for (int q = 0; q < R / 4; ++q) wv[q] = ld_hint(src + q * 32 + lane, pol);
 }
-// Sums the slot's restriction and stores the R results (lanes < R/8 write 8 each).
+// Sums the slot's restriction and stores its R results.  Partial sums use packed FP32x2 FMAs;
+// the cross-lane sum is a reduce-scatter over the row bits (16, 8, 4 halve the 8 columns a
+// lane holds; bits 2 and 1, where they are row bits, finish the sum), so each result ends in
+// one lane: column (lane % G)*8 + 4*b4 + 2*b3 + b2.
 template <int R>
 HM_INLINE void restrict_finish(const uint4 (&wv)[R / 4], float r0, float r1, int lane, float* __restrict__ out) {
   constexpr int G = R / 8;                  // lanes per row
-  float acc[8];
+  float2 acc[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+  for (int t = 0; t < 4; ++t) acc[t] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int q = 0; q < R / 4; ++q) {
     const int row = q * (32 / G) + lane / G;           // < 32 exactly when q < G
     const float ri = __shfl_sync(0xffffffffu, q < G ? r0 : r1, row & 31);
-    const uint32_t u[4] = {wv[q].x, wv[q].y, wv[q].z, wv[q].w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float2 v = bf2(u[t]);
-      acc[2 * t] = fmaf(v.x, ri, acc[2 * t]);
-      acc[2 * t + 1] = fmaf(v.y, ri, acc[2 * t + 1]);
-    }
+    const float2 rr = make_float2(ri, ri);
+    acc[0] = __ffma2_rn(bf2(wv[q].x), rr, acc[0]);
+    acc[1] = __ffma2_rn(bf2(wv[q].y), rr, acc[1]);
+    acc[2] = __ffma2_rn(bf2(wv[q].z), rr, acc[2]);
+    acc[3] = __ffma2_rn(bf2(wv[q].w), rr, acc[3]);
   }
+  const float v[8] = {acc[0].x, acc[0].y, acc[1].x, acc[1].y, acc[2].x, acc[2].y, acc[3].x, acc[3].y};
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+  float a4[4], a2[2];
 #pragma unroll
-  for (int o = G; o < 32; o <<= 1)
+  for (int t = 0; t < 4; ++t)
+    a4[t] = (h4 ? v[4 + t] : v[t]) + __shfl_xor_sync(0xffffffffu, h4 ? v[t] : v[4 + t], 16);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-  if (lane < G) {
-    float4* d = reinterpret_cast<float4*>(out + lane * 8);
-    d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    d[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-  }
+  for (int t = 0; t < 2; ++t)
+    a2[t] = (h3 ? a4[2 + t] : a4[t]) + __shfl_xor_sync(0xffffffffu, h3 ? a4[t] : a4[2 + t], 8);
+  float a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 4);
+  if (G < 4) a1 += __shfl_xor_sync(0xffffffffu, a1, 2);
+  if (G < 2) a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+  if ((lane & 3 & ~(G - 1)) == 0) out[(lane % G) * 8 + (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0)] = a1;
 }
 
 HM_INLINE uint32_t s32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -121,12 +146,12 @@ HM_INLINE bool bar_wait(uint32_t bar, uint32_t parity) {
 }
 // TMA: 64x64 BF16 leaf block k (rows k*64 .. k*64+63 of the (K*64) x 64 view), 128-byte
 // swizzle, into a 1024-byte-aligned 8 KB tile.
-HM_INLINE void leaf_tma(const CUtensorMap* map, uint4* tile, int k, uint32_t bar) {
+HM_INLINE void leaf_tma(const CUtensorMap* map, uint4* tile, int k, uint32_t bar, uint64_t pol) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(8192u) : "memory");
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          s32(tile)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(k * 64), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%2, %3}], "
+      "[%4], %5;" ::"r"(s32(tile)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(k * 64), "r"(bar), "l"(pol)
       : "memory");
 }
 
@@ -140,9 +165,17 @@ __global__ void __launch_bounds__(32 * kRWarps) apply_warp_restrict_kernel(const
                                                                            float* __restrict__ uhat) {
   extern __shared__ uint8_t sraw[];
   __shared__ __align__(8) uint64_t bars[kRWarps][2];
+  __shared__ __align__(16) float rstage[kRWarps][64], wstage[kRWarps][64];
   uint8_t* sal = sraw + ((1024u - (s32(sraw) & 1023u)) & 1023u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint4* tiles2 = reinterpret_cast<uint4*>(sal) + warp * 1024;     // two 8 KB tiles per warp
+  const float4* rs4 = reinterpret_cast<const float4*>(rstage[warp]);
+  const float4* ws4 = reinterpret_cast<const float4*>(wstage[warp]);
+  // word offset, within a 128-byte row, of the lane's column pair (2 lane, 2 lane + 1) under
+  // the 128-byte swizzle, for each of the 8 row phases
+  int cw[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) cw[c] = (((lane >> 2) ^ c) << 2) | (lane & 3);
   const uint32_t b0 = s32(&bars[warp][0]), b1 = s32(&bars[warp][1]);
   if (lane == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0) : "memory");
@@ -152,7 +185,8 @@ __global__ void __launch_bounds__(32 * kRWarps) apply_warp_restrict_kernel(const
   }
   __syncwarp();
   const int k0 = blockIdx.x * kRWarps + warp, ks = gridDim.x * kRWarps;
-  if (lane == 0 && k0 < f.K) leaf_tma(&fmap, tiles2, k0, b0);
+  const uint64_t pol_f = pol_evict_first(), pol_b = pol_evict_last();
+  if (lane == 0 && k0 < f.K) leaf_tma(&fmap, tiles2, k0, b0, pol_f);
   int it = 0, k = k0;
   bool fail = false;
   for (; k < f.K; k += ks, ++it) {
@@ -162,60 +196,60 @@ __global__ void __launch_bounds__(32 * kRWarps) apply_warp_restrict_kernel(const
     // prefetch the next leaf into the other buffer (its readers finished in the previous pass)
     if (lane == 0 && k + ks < f.K) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      leaf_tma(&fmap, tiles2 + (buf ^ 1) * 512, k + ks, buf ? b0 : b1);
+      leaf_tma(&fmap, tiles2 + (buf ^ 1) * 512, k + ks, buf ? b0 : b1, pol_f);
     }
     uint4 wv0[R / 4], wv1[R / 4];
     if (f.nslot == 2) {
-      restrict_load<R>(f.bridge + (size_t)k * 64 * R, wv0, lane);
-      restrict_load<R>(f.bridge + ((size_t)f.n + (size_t)k * 64) * R, wv1, lane);
+      restrict_load<R>(f.bridge + (size_t)k * 64 * R, wv0, lane, pol_b);
+      restrict_load<R>(f.bridge + ((size_t)f.n + (size_t)k * 64) * R, wv1, lane, pol_b);
     }
     const float r0 = r[(size_t)k * 64 + lane], r1 = r[(size_t)k * 64 + 32 + lane];
     float ga = 0.f, gb = 0.f;
     if (f.learned) { ga = __bfloat162float(f.gate[(size_t)k * 64 + lane]); gb = __bfloat162float(f.gate[(size_t)k * 64 + 32 + lane]); }
     if (!bar_wait(buf ? b1 : b0, (it >> 1) & 1)) { fail = true; break; }
-    float y0 = 0.f, y1 = 0.f;
+    // r (and, for the learned block, w = F^T r) are staged per warp and read back as 16-byte
+    // broadcasts; the leaf tile is read in the swizzled layout TMA wrote
+    rstage[warp][lane] = r0;
+    rstage[warp][32 + lane] = r1;
+    __syncwarp();
+    const float4* xs4 = rs4;                       // the vector the row pass multiplies
     if (f.learned) {
-      float w0 = 0.f, w1 = 0.f;
-#pragma unroll 8
-      for (int i = 0; i < 64; ++i) {
-        const float ri = __shfl_sync(0xffffffffu, i < 32 ? r0 : r1, i & 31);
-        const int ch = (lane >> 2) ^ (i & 7);
-        const float2 fv = bf2(tw[i * 32 + ch * 4 + (lane & 3)]);
-        w0 = fmaf(fv.x, ri, w0);
-        w1 = fmaf(fv.y, ri, w1);
-      }
+      float2 w = make_float2(0.f, 0.f);            // columns 2 lane, 2 lane + 1
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const uint4 a = tile[lane * 8 + (c ^ (lane & 7))];
-        const uint4 b = tile[(lane + 32) * 8 + (c ^ (lane & 7))];
-        const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+      for (int i4 = 0; i4 < 16; ++i4) {
+        const float4 rv = rs4[i4];
+        const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int m = c * 4 + u;
-          const float wa = __shfl_sync(0xffffffffu, w0, m), wb = __shfl_sync(0xffffffffu, w1, m);
-          const float2 fa = bf2(av[u]), fb = bf2(bv[u]);
-          y0 = fmaf(fa.x, wa, fmaf(fa.y, wb, y0));
-          y1 = fmaf(fb.x, wa, fmaf(fb.y, wb, y1));
+          const int i = i4 * 4 + u;
+          w = __ffma2_rn(bf2(tw[i * 32 + cw[i & 7]]), make_float2(rr[u], rr[u]), w);
         }
       }
+      reinterpret_cast<float2*>(wstage[warp])[lane] = w;
+      __syncwarp();
+      xs4 = ws4;
+    }
+    float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);   // rows lane, lane + 32
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint4 a = tile[lane * 8 + (c ^ (lane & 7))];
+      const uint4 b = tile[(lane + 32) * 8 + (c ^ (lane & 7))];
+      const float4 x0 = xs4[2 * c], x1 = xs4[2 * c + 1];
+      const float2 xa = make_float2(x0.x, x0.y), xb = make_float2(x0.z, x0.w);
+      const float2 xc = make_float2(x1.x, x1.y), xd = make_float2(x1.z, x1.w);
+      ya = __ffma2_rn(bf2(a.x), xa, ya);
+      ya = __ffma2_rn(bf2(a.y), xb, ya);
+      ya = __ffma2_rn(bf2(a.z), xc, ya);
+      ya = __ffma2_rn(bf2(a.w), xd, ya);
+      yb = __ffma2_rn(bf2(b.x), xa, yb);
+      yb = __ffma2_rn(bf2(b.y), xb, yb);
+      yb = __ffma2_rn(bf2(b.z), xc, yb);
+      yb = __ffma2_rn(bf2(b.w), xd, yb);
+    }
+    float y0 = ya.x + ya.y, y1 = yb.x + yb.y;
+    if (f.learned) {
       y0 = fmaf(ga, r0, y0);
       y1 = fmaf(gb, r1, y1);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const uint4 a = tile[lane * 8 + (c ^ (lane & 7))];
-        const uint4 b = tile[(lane + 32) * 8 + (c ^ (lane & 7))];
-        const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = 2 * (c * 4 + u);
-          const float ra = __shfl_sync(0xffffffffu, j < 32 ? r0 : r1, j & 31);
-          const float rb = __shfl_sync(0xffffffffu, j + 1 < 32 ? r0 : r1, (j + 1) & 31);
-          const float2 fa = bf2(av[u]), fb = bf2(bv[u]);
-          y0 = fmaf(fa.x, ra, fmaf(fa.y, rb, y0));
-          y1 = fmaf(fb.x, ra, fmaf(fb.y, rb, y1));
-        }
-      }
     }
     ydiag[(size_t)k * 64 + lane] = y0;
     ydiag[(size_t)k * 64 + 32 + lane] = y1;
@@ -224,7 +258,7 @@ __global__ void __launch_bounds__(32 * kRWarps) apply_warp_restrict_kernel(const
       restrict_finish<R>(wv1, r0, r1, lane, uhat + ((size_t)f.K + k) * R);
     } else {
       for (int sl = 0; sl < f.nslot; ++sl) {
-        restrict_load<R>(f.bridge + ((size_t)sl * f.n + (size_t)k * 64) * R, wv0, lane);
+        restrict_load<R>(f.bridge + ((size_t)sl * f.n + (size_t)k * 64) * R, wv0, lane, pol_b);
         restrict_finish<R>(wv0, r0, r1, lane, uhat + ((size_t)sl * f.K + k) * R);
       }
     }
@@ -241,50 +275,89 @@ __global__ void __launch_bounds__(32 * kRWarps) apply_warp_restrict_kernel(const
   }
 }
 
+// Row pass of the prolongation for one slot: y_i += sum_e W[i][e] a[e] for the lane's rows
+// i = lane and lane + 32 (W rows of R BF16 values; a[e] held by lane e).
+template <int R>
+HM_INLINE void prolong_rows(const uint4 (&p)[R / 8], const uint4 (&q)[R / 8], float a, float& y0, float& y1) {
+#pragma unroll
+  for (int c = 0; c < R / 8; ++c) {
+    const uint32_t pv[4] = {p[c].x, p[c].y, p[c].z, p[c].w}, qv[4] = {q[c].x, q[c].y, q[c].z, q[c].w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = c * 8 + 2 * u;
+      const float ae = __shfl_sync(0xffffffffu, a, e), af = __shfl_sync(0xffffffffu, a, e + 1);
+      const float2 fp = bf2(pv[u]), fq = bf2(qv[u]);
+      y0 = fmaf(fp.x, ae, fmaf(fp.y, af, y0));
+      y1 = fmaf(fq.x, ae, fmaf(fq.y, af, y1));
+    }
+  }
+}
+
+// Prolongation + diagonal: z_k = ydiag_k + sum_slots W_{s,k} a_{s,k}.  Leaves are visited in
+// descending order (the restriction ascends), so recently read bridges hit in L2.  With acoup
+// the per-leaf coupling inputs are precomputed; otherwise they are gathered here per level.
 template <int R>
 __global__ void __launch_bounds__(32 * kWarps) apply_warp_prolong_kernel(FactorView<__nv_bfloat16> f,
                                                                          const float* __restrict__ tcoup,
+                                                                         const float* __restrict__ acoup,
                                                                          const float* __restrict__ ydiag,
                                                                          float* __restrict__ z) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = blockIdx.x * kWarps + warp; k < f.K; k += gridDim.x * kWarps) {
+  const uint64_t pol = pol_evict_first();
+  for (int kk = blockIdx.x * kWarps + warp; kk < f.K; kk += gridDim.x * kWarps) {
+    const int k = f.K - 1 - kk;
     float y0 = ydiag[(size_t)k * 64 + lane], y1 = ydiag[(size_t)k * 64 + 32 + lane];
-    for (int sl = 0; sl < f.nslot; ++sl) {
-      // a_s[e] (lane e < R): coupling outputs of the tiles whose bridge slot is sl
-      float a = 0.f;
-      if (lane < R) {
-        // all level loads first (independent), then the sum in level order
-        float tv[24];
-#pragma unroll
-        for (int lev = 1; lev <= 24; ++lev) {
-          tv[lev - 1] = 0.f;
-          if (lev <= f.levels) {
-            const int S = f.K >> lev;
-            const int cl = k / S;
-            const int side = cl & 1;
-            const int slot = f.learned ? side : lev - 1;
-            const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-            if (slot == sl) tv[lev - 1] = tcoup[((size_t)m * 2 + side) * R + lane];
-          }
-        }
-#pragma unroll
-        for (int lev = 0; lev < 24; ++lev) a += tv[lev];
-      }
-      const __nv_bfloat16* W = f.bridge + ((size_t)sl * f.n + (size_t)k * 64) * R;
-      const uint4* w0 = reinterpret_cast<const uint4*>(W + (size_t)lane * R);
-      const uint4* w1 = reinterpret_cast<const uint4*>(W + (size_t)(lane + 32) * R);
+    if (acoup && f.nslot == 2) {
+      const uint4* w0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane) * R);
+      const uint4* w1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane + 32) * R);
+      const uint4* v0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane) * R);
+      const uint4* v1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane + 32) * R);
+      uint4 p0[R / 8], q0[R / 8], p1[R / 8], q1[R / 8];
 #pragma unroll
       for (int c = 0; c < R / 8; ++c) {
-        const uint4 p = __ldg(w0 + c), q = __ldg(w1 + c);
-        const uint32_t pv[4] = {p.x, p.y, p.z, p.w}, qv[4] = {q.x, q.y, q.z, q.w};
+        p0[c] = ld_hint(w0 + c, pol);
+        q0[c] = ld_hint(w1 + c, pol);
+        p1[c] = ld_hint(v0 + c, pol);
+        q1[c] = ld_hint(v1 + c, pol);
+      }
+      const float a0 = lane < R ? acoup[(size_t)k * R + lane] : 0.f;
+      const float a1 = lane < R ? acoup[((size_t)f.K + k) * R + lane] : 0.f;
+      prolong_rows<R>(p0, q0, a0, y0, y1);
+      prolong_rows<R>(p1, q1, a1, y0, y1);
+    } else {
+      for (int sl = 0; sl < f.nslot; ++sl) {
+        // a_s[e] (lane e < R): coupling outputs of the tiles whose bridge slot is sl
+        float a = 0.f;
+        if (acoup) {
+          if (lane < R) a = acoup[((size_t)sl * f.K + k) * R + lane];
+        } else if (lane < R) {
+          // all level loads first (independent), then the sum in level order
+          float tv[24];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int e = c * 8 + 2 * u;
-          const float ae = __shfl_sync(0xffffffffu, a, e), af = __shfl_sync(0xffffffffu, a, e + 1);
-          const float2 fp = bf2(pv[u]), fq = bf2(qv[u]);
-          y0 = fmaf(fp.x, ae, fmaf(fp.y, af, y0));
-          y1 = fmaf(fq.x, ae, fmaf(fq.y, af, y1));
+          for (int lev = 1; lev <= 24; ++lev) {
+            tv[lev - 1] = 0.f;
+            if (lev <= f.levels) {
+              const int S = f.K >> lev;
+              const int cl = k / S;
+              const int side = cl & 1;
+              const int slot = f.learned ? side : lev - 1;
+              const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+              if (slot == sl) tv[lev - 1] = tcoup[((size_t)m * 2 + side) * R + lane];
+            }
+          }
+#pragma unroll
+          for (int lev = 0; lev < 24; ++lev) a += tv[lev];
         }
+        const __nv_bfloat16* W = f.bridge + ((size_t)sl * f.n + (size_t)k * 64) * R;
+        const uint4* w0 = reinterpret_cast<const uint4*>(W + (size_t)lane * R);
+        const uint4* w1 = reinterpret_cast<const uint4*>(W + (size_t)(lane + 32) * R);
+        uint4 p[R / 8], q[R / 8];
+#pragma unroll
+        for (int c = 0; c < R / 8; ++c) {
+          p[c] = ld_hint(w0 + c, pol);
+          q[c] = ld_hint(w1 + c, pol);
+        }
+        prolong_rows<R>(p, q, a, y0, y1);
       }
     }
     z[(size_t)k * 64 + lane] = y0;
@@ -298,16 +371,16 @@ __global__ void __launch_bounds__(32 * kWarps) apply_warp_prolong_kernel(FactorV
 // 1..8 inside one CTA per 256 leaves; pass 2 (one CTA) builds the levels above.
 HM_INLINE int64_t tree_off(int K, int j) { return 2LL * K - 2LL * (K >> j); }
 
+// Level 0 is uhat itself and is not copied.
+template <int R>
 __global__ void __launch_bounds__(256) tree_local_kernel(const float* __restrict__ uhat, float* __restrict__ tree,
-                                                         int K, int R, int nslot, int jmax) {
-  __shared__ float buf[2][256 * 32 / 2 + 32];
+                                                         int K, int jmax) {
+  __shared__ float buf[2][128 * R];
   const int s = blockIdx.y;
   const int k0 = blockIdx.x * 256;
   const int nl = min(256, K - k0);
   const float* src = uhat + ((size_t)s * K + k0) * R;
   float* dst = tree + (size_t)s * 2 * K * R;
-  // level 0: copy the leaves
-  for (int q = threadIdx.x; q < nl * R; q += blockDim.x) dst[((int64_t)k0) * R + q] = src[q];
   int cnt = nl;
   const float* prev = src;
   int pb = 0;
@@ -316,19 +389,19 @@ __global__ void __launch_bounds__(256) tree_local_kernel(const float* __restrict
     float* cur = buf[pb];
     for (int q = threadIdx.x; q < nn * R; q += blockDim.x) {
       const int g = q / R, e = q % R;
-      cur[q] = prev[(2 * g) * R + e] + prev[(2 * g + 1) * R + e];
+      const float v = prev[(2 * g) * R + e] + prev[(2 * g + 1) * R + e];
+      cur[q] = v;
+      dst[(tree_off(K, j) + (k0 >> j)) * R + q] = v;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < nn * R; q += blockDim.x)
-      dst[(tree_off(K, j) + (k0 >> j)) * R + q] = cur[q];
     prev = cur;
     pb ^= 1;
     cnt = nn;
-    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) tree_top_kernel(float* __restrict__ tree, int K, int R, int j0) {
+template <int R>
+__global__ void __launch_bounds__(1024) tree_top_kernel(float* __restrict__ tree, int K, int j0) {
   const int s = blockIdx.x;
   float* t = tree + (size_t)s * 2 * K * R;
   for (int j = j0 + 1; (K >> j) >= 1; ++j) {
@@ -341,28 +414,293 @@ __global__ void __launch_bounds__(256) tree_top_kernel(float* __restrict__ tree,
   }
 }
 
-// Coupling of tile m from the two cluster sums: t^r = B s^c, t^c = B^T s^r.
+// Coupling of tile m from the two cluster sums: t^r = B s^c, t^c = B^T s^r.  One warp per
+// tile: lanes [0, R) produce t^r[e] from core row e (16-byte loads), lanes [16, 16 + R)
+// produce t^c[e] from core column e (R <= 16); for R = 32 every lane produces both.  The
+// next tile's operands are loaded before the current one is reduced.
 template <int R>
-__global__ void __launch_bounds__(256) tile_from_tree_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ tree,
-                                                             float* __restrict__ tcoup) {
+__global__ void __launch_bounds__(256) tile_from_tree_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ uhat,
+                                                             const float* __restrict__ tree, float* __restrict__ tcoup) {
+  constexpr bool kBoth = R > 16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int m = blockIdx.x * 8 + warp; m < f.K - 1; m += gridDim.x * 8) {
+  const int e = kBoth ? lane : (lane & 15);
+  const bool row_lane = kBoth || lane < 16;
+  const bool active = e < R;
+  auto sums = [&](int m, const float*& srow, const float*& scol) {
     const int lev = 32 - __clz(m + 1);
     const int t = m + 1 - (1 << (lev - 1));
     const int j = f.levels - lev;                 // cluster of 2^j leaves
     const int sl = f.learned ? 0 : lev - 1, sr = f.learned ? 1 : lev - 1;
-    const float* srow = tree + ((size_t)sl * 2 * f.K + tree_off(f.K, j) + 2 * t) * R;
-    const float* scol = tree + ((size_t)sr * 2 * f.K + tree_off(f.K, j) + 2 * t + 1) * R;
-    const __nv_bfloat16* Bm = f.core + (size_t)m * R * R;
-    if (lane < R) {
-      float tr = 0.f, tc = 0.f;
-      for (int q = 0; q < R; ++q) {
-        tr = fmaf(__bfloat162float(Bm[lane * R + q]), scol[q], tr);
-        tc = fmaf(__bfloat162float(Bm[q * R + lane]), srow[q], tc);
-      }
-      tcoup[((size_t)m * 2 + 0) * R + lane] = tr;
-      tcoup[((size_t)m * 2 + 1) * R + lane] = tc;
+    srow = j == 0 ? uhat + ((size_t)sl * f.K + 2 * t) * R : tree + ((size_t)sl * 2 * f.K + tree_off(f.K, j) + 2 * t) * R;
+    scol = j == 0 ? uhat + ((size_t)sr * f.K + 2 * t + 1) * R
+                  : tree + ((size_t)sr * 2 * f.K + tree_off(f.K, j) + 2 * t + 1) * R;
+  };
+  const int stride = gridDim.x * 8;
+  int m = blockIdx.x * 8 + warp;
+  // operands of the current tile: core row e (row lanes), core column e (column lanes), and
+  // v = s^c[e] on row lanes, s^r[e] on column lanes (for R = 32: both, in v and v2)
+  uint4 brow[R / 8];
+  __nv_bfloat16 bcol[R];
+  float v = 0.f, v2 = 0.f;
+  auto load = [&](int mm) {
+    if (mm >= f.K - 1 || !active) return;
+    const float *srow, *scol;
+    sums(mm, srow, scol);
+    const __nv_bfloat16* Bm = f.core + (size_t)mm * R * R;
+    if (row_lane) {
+      const uint4* src = reinterpret_cast<const uint4*>(Bm + (size_t)e * R);
+#pragma unroll
+      for (int c = 0; c < R / 8; ++c) brow[c] = __ldg(src + c);
+      v = scol[e];
     }
+    if (kBoth || !row_lane) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) bcol[q] = Bm[(size_t)q * R + e];
+      if (kBoth) v2 = srow[e]; else v = srow[e];
+    }
+  };
+  load(m);
+  for (; m < f.K - 1; m += stride) {
+    uint4 cr[R / 8];
+    __nv_bfloat16 cc[R];
+#pragma unroll
+    for (int c = 0; c < R / 8; ++c) cr[c] = brow[c];
+#pragma unroll
+    for (int q = 0; q < R; ++q) cc[q] = bcol[q];
+    const float cv = v, cv2 = v2;
+    load(m + stride);
+    float tr = 0.f, tc = 0.f;
+    if (kBoth) {
+#pragma unroll
+      for (int c = 0; c < R / 8; ++c) {
+        const uint32_t u[4] = {cr[c].x, cr[c].y, cr[c].z, cr[c].w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const float2 b2 = bf2(u[w]);
+          tr = fmaf(b2.x, __shfl_sync(0xffffffffu, cv, c * 8 + 2 * w), tr);
+          tr = fmaf(b2.y, __shfl_sync(0xffffffffu, cv, c * 8 + 2 * w + 1), tr);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) tc = fmaf(__bfloat162float(cc[q]), __shfl_sync(0xffffffffu, cv2, q), tc);
+    } else {
+      // one shuffle per q: row lanes take s^c[q] (row lane q), column lanes s^r[q] (lane 16 + q)
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const float s = __shfl_sync(0xffffffffu, cv, row_lane ? q : 16 + q);
+        if (row_lane) {
+          const uint4 ch = cr[q / 8];
+          const uint32_t uu = (q % 8 < 2) ? ch.x : (q % 8 < 4) ? ch.y : (q % 8 < 6) ? ch.z : ch.w;
+          const float2 b2 = bf2(uu);
+          tr = fmaf((q & 1) ? b2.y : b2.x, s, tr);
+        } else {
+          tc = fmaf(__bfloat162float(cc[q]), s, tc);
+        }
+      }
+    }
+    if (active) {
+      if (row_lane) tcoup[((size_t)m * 2 + 0) * R + e] = tr;
+      if (kBoth || !row_lane) tcoup[((size_t)m * 2 + 1) * R + e] = tc;
+    }
+  }
+}
+
+// Per-leaf coupling input a[s][k][e]: sum, over the levels whose bridge slot is s, of the
+// coupling output of the tile holding leaf k (t^r for a row-side leaf, t^c otherwise).
+template <int R>
+__global__ void __launch_bounds__(256) leaf_coupling_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ tcoup,
+                                                            float* __restrict__ acoup) {
+  const int sl = blockIdx.y;
+  const int e = threadIdx.x % R;
+  for (int k = (blockIdx.x * 256 + threadIdx.x) / R; k < f.K; k += gridDim.x * (256 / R)) {
+    float tv[24];
+#pragma unroll
+    for (int lev = 1; lev <= 24; ++lev) {       // all loads first, then the sum in level order
+      tv[lev - 1] = 0.f;
+      if (lev <= f.levels) {
+        const int cl = k >> (f.levels - lev);   // cluster of leaf k at this level
+        const int side = cl & 1;
+        const int slot = f.learned ? side : lev - 1;
+        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+        if (slot == sl) tv[lev - 1] = __ldg(tcoup + ((size_t)m * 2 + side) * R + e);
+      }
+    }
+    float a = 0.f;
+#pragma unroll
+    for (int lev = 0; lev < 24; ++lev) a += tv[lev];
+    acoup[((size_t)sl * f.K + k) * R + e] = a;
+  }
+}
+
+// ---------------------------------------------------------------- blocked strip sums (learned)
+// The coupling stage for learned factors (bridge slot = side) in three passes over blocks of
+// up to 256 consecutive items (leaves, or block totals one level up):
+//   block_up:   per block, the sums of aligned groups of 2^j items (slot 0 and slot 1) in shared
+//               memory, then the couplings t^r = B s^c, t^c = B^T s^r of every tile whose two
+//               clusters lie inside the block; optionally the block's totals per slot.
+//   (block_up again on the block totals, one CTA, for the tiles above the blocks)
+//   block_down: per leaf, a[s] = sum over the levels where the leaf is on side s of that
+//               tile's coupling output (row side t^r, column side t^c).
+constexpr int kBlk = 256;           // items per block
+constexpr int kBlkLog = 8;
+HM_INLINE int node_off(int n, int j) { return 2 * n - 2 * (n >> j); }   // level j of an n-item tree
+HM_INLINE constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+// Tile lt of a block of n = 2^jl items, tiles listed level after level (level j holds
+// n >> (j + 1) tiles): its level j and index tl within the level.
+HM_INLINE void tile_level(int jl, int lt, int& j, int& tl) {
+  const int n = 1 << jl;
+  j = jl - (32 - __clz(n - lt - 1));
+  tl = lt - (n - (n >> j));
+}
+// Copies total elements to shared memory with BATCH independent loads in flight per thread.
+template <int BATCH, class T, class Src>
+HM_INLINE void stage_batched(T* dst, int total, int tid, int nthr, Src src_of) {
+  for (int base = tid; base < total; base += nthr * BATCH) {
+    T v[BATCH];
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int q = base + b * nthr;
+      if (q < total) v[b] = __ldg(src_of(q));
+    }
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int q = base + b * nthr;
+      if (q < total) dst[q] = v[b];
+    }
+  }
+}
+HM_INLINE float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+// One CTA per block of 2^jl items of src [2][n_items][R] (blockIdx.x), computing the tiles
+// lt = blockIdx.y + i * gridDim.y of the block (every CTA of a block builds the block's sums).
+// Tile (j, tl) of the block (clusters of 2^j items) is global tile m = 2^(lev-1) - 1 + t with
+// lev = levels - jbase - j and t = (block * 2^jl >> (j + 1)) + tl.  A half-warp computes one
+// tile: lane e < R of it gives t^r[e] (core row e) and t^c[e] (core column e).
+template <int R>
+__global__ void __launch_bounds__(1024) block_up_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ src,
+                                                        int n_items, int jl, int jbase, float* __restrict__ bsum,
+                                                        float* __restrict__ tcoup) {
+  static_assert(R <= 16, "one output pair per lane of a half-warp");
+  constexpr int Q = R / 4, LQ = ilog2(Q);          // float4 per node
+  constexpr int C = R * R / 8, LC = ilog2(C);      // 16-byte chunks per core
+  extern __shared__ __align__(16) uint8_t smraw[];
+  const int nb = 1 << jl, nodes = 2 * nb - 1;
+  float4* sums4 = reinterpret_cast<float4*>(smraw);                                 // [2][nodes][Q]
+  __nv_bfloat16* cores = reinterpret_cast<__nv_bfloat16*>(sums4 + 2 * nodes * Q);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int blk = blockIdx.x, i0 = blk * nb;
+  const int part = blockIdx.y, nparts = gridDim.y;
+  const int ntile = (nb - 1 - part + nparts - 1) / nparts;    // tiles of this CTA
+  stage_batched<8>(reinterpret_cast<uint4*>(cores), ntile * C, tid, nthr, [&](int q) {
+    int j, tl;
+    tile_level(jl, part + (q >> LC) * nparts, j, tl);
+    const int m = (1 << (f.levels - jbase - j - 1)) - 1 + (i0 >> (j + 1)) + tl;
+    return reinterpret_cast<const uint4*>(f.core) + (size_t)m * C + (q & (C - 1));
+  });
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    stage_batched<2>(sums4 + s * nodes * Q, nb * Q, tid, nthr, [&](int q) {
+      return reinterpret_cast<const float4*>(src + ((size_t)s * n_items + i0) * R) + q;
+    });
+  __syncthreads();
+  for (int j = 1; j <= jl; ++j) {
+    const int lnq = jl - j + LQ;                   // log2(nodes at level j * Q)
+    for (int q = tid; q < (2 << lnq); q += nthr) {
+      const int s = q >> lnq, rem = q & ((1 << lnq) - 1), g = rem >> LQ, e4 = rem & (Q - 1);
+      float4* t = sums4 + s * nodes * Q;
+      t[(node_off(nb, j) + g) * Q + e4] =
+          add4(t[(node_off(nb, j - 1) + 2 * g) * Q + e4], t[(node_off(nb, j - 1) + 2 * g + 1) * Q + e4]);
+    }
+    __syncthreads();
+  }
+  if (bsum && part == 0 && tid < 2 * Q) {
+    const int s = tid >> LQ, e4 = tid & (Q - 1);
+    reinterpret_cast<float4*>(bsum)[((size_t)s * gridDim.x + blk) * Q + e4] = sums4[(s * nodes + node_off(nb, jl)) * Q + e4];
+  }
+  const int half = tid >> 4, e = tid & 15, nhalf = nthr >> 4;
+  if (e >= R) return;
+  const float* sums = reinterpret_cast<const float*>(sums4);
+  for (int it = half; it < ntile; it += nhalf) {
+    const int lt = part + it * nparts;
+    int j, tl;
+    tile_level(jl, lt, j, tl);
+    const int m = (1 << (f.levels - jbase - j - 1)) - 1 + (i0 >> (j + 1)) + tl;
+    const float* sr = sums + (0 * nodes + node_off(nb, j) + 2 * tl) * R;       // row cluster, slot 0
+    const float* sc = sums + (1 * nodes + node_off(nb, j) + 2 * tl + 1) * R;   // column cluster, slot 1
+    const __nv_bfloat16* Bs = cores + (size_t)it * R * R;
+    const uint4* row = reinterpret_cast<const uint4*>(Bs + e * R);
+    const float4* sc4 = reinterpret_cast<const float4*>(sc);
+    const float4* sr4 = reinterpret_cast<const float4*>(sr);
+    float2 a2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < R / 8; ++c) {
+      const uint4 u = row[c];
+      const float4 s0 = sc4[2 * c], s1 = sc4[2 * c + 1];
+      a2 = __ffma2_rn(bf2(u.x), make_float2(s0.x, s0.y), a2);
+      a2 = __ffma2_rn(bf2(u.y), make_float2(s0.z, s0.w), a2);
+      a2 = __ffma2_rn(bf2(u.z), make_float2(s1.x, s1.y), a2);
+      a2 = __ffma2_rn(bf2(u.w), make_float2(s1.z, s1.w), a2);
+    }
+    float tc = 0.f;
+#pragma unroll
+    for (int q4 = 0; q4 < Q; ++q4) {
+      const float4 v = sr4[q4];
+      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 0) * R + e]), v.x, tc);
+      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 1) * R + e]), v.y, tc);
+      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 2) * R + e]), v.z, tc);
+      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 3) * R + e]), v.w, tc);
+    }
+    tcoup[(size_t)m * 2 * R + e] = a2.x + a2.y;
+    tcoup[(size_t)m * 2 * R + R + e] = tc;
+  }
+}
+
+// Per-leaf coupling inputs for one block of kBlk leaves: levels inside the block from the
+// staged tile outputs, levels above it from global memory.  Sums run from the top level down.
+template <int R>
+__global__ void __launch_bounds__(1024) block_down_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ tcoup,
+                                                          float* __restrict__ acoup) {
+  constexpr int Q = R / 4, LQ = ilog2(Q);
+  constexpr int H = 2 * Q, LH = ilog2(H);            // float4 per tile ([t^r | t^c])
+  __shared__ __align__(16) float4 st[(kBlk - 1) * H];  // local tiles, level-major
+  __shared__ __align__(16) float4 top[2 * Q];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int blk = gridDim.x - 1 - blockIdx.x, k0 = blk * kBlk;
+  stage_batched<4>(st, (kBlk - 1) * H, tid, nthr, [&](int q) {
+    int j, tl;
+    tile_level(kBlkLog, q >> LH, j, tl);
+    const int m = (1 << (f.levels - j - 1)) - 1 + (k0 >> (j + 1)) + tl;
+    return reinterpret_cast<const float4*>(tcoup + (size_t)m * 2 * R) + (q & (H - 1));
+  });
+  if (tid < 2 * R) {
+    const int s = tid / R, e = tid % R;
+    float tv[24];
+#pragma unroll
+    for (int lev = 1; lev <= 24; ++lev) {
+      tv[lev - 1] = 0.f;
+      if (lev <= f.levels - kBlkLog) {
+        const int cl = k0 >> (f.levels - lev);
+        const int side = cl & 1;
+        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+        if (side == s) tv[lev - 1] = tcoup[((size_t)m * 2 + side) * R + e];
+      }
+    }
+    float a = 0.f;
+#pragma unroll
+    for (int lev = 0; lev < 24; ++lev) a += tv[lev];
+    reinterpret_cast<float*>(top)[tid] = a;
+  }
+  __syncthreads();
+  float4* out4 = reinterpret_cast<float4*>(acoup);
+  for (int q = tid; q < 2 * kBlk * Q; q += nthr) {
+    const int s = q >> (kBlkLog + LQ), g = (q >> LQ) & (kBlk - 1), e4 = q & (Q - 1);
+    float4 a = top[s * Q + e4];
+#pragma unroll
+    for (int j = kBlkLog - 1; j >= 0; --j) {
+      const int cl = g >> j;
+      if ((cl & 1) == s) a = add4(a, st[((kBlk - (kBlk >> j)) + (cl >> 1)) * H + s * Q + e4]);
+    }
+    out4[((size_t)s * f.K + k0 + g) * Q + e4] = a;
   }
 }
 
@@ -401,7 +739,8 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
       return 1;
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  if ((reinterpret_cast<uintptr_t>(f.leaf) & 15) || (reinterpret_cast<uintptr_t>(f.bridge) & 15)) return 1;
+  if ((reinterpret_cast<uintptr_t>(f.leaf) | reinterpret_cast<uintptr_t>(f.bridge) | reinterpret_cast<uintptr_t>(f.core)) & 15)
+    return 1;
   CUtensorMap fmap;
   {
     cuuint64_t dims[2] = {64, (cuuint64_t)f.K * 64};
@@ -428,24 +767,62 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
     default: apply_warp_restrict_kernel<32><<<grid, 32 * kRWarps, smem, st>>>(fmap, f, r, ydiag, uhat); break;
   }
   const int gridp = std::max(1, std::min((f.K + kWarps - 1) / kWarps, c->num_sms * 8));
-  if (f.K >= 512 && c->tree && (int64_t)f.nslot * 2 * f.K * f.r <= c->tree_cap) {
-    // cluster sums by a tree: every tile reads two precomputed sums
-    const int jl = 8;
-    tree_local_kernel<<<dim3((f.K + 255) / 256, f.nslot), 256, 0, st>>>(uhat, c->tree, f.K, f.r, f.nslot, jl);
-    tree_top_kernel<<<f.nslot, 256, 0, st>>>(c->tree, f.K, f.r, jl);
-    const int gt = std::max(1, std::min((f.K - 1 + 7) / 8, c->num_sms * 8));
-    switch (f.r) {
-      case 8: tile_from_tree_kernel<8><<<gt, 256, 0, st>>>(f, c->tree, tcoup); break;
-      case 16: tile_from_tree_kernel<16><<<gt, 256, 0, st>>>(f, c->tree, tcoup); break;
-      default: tile_from_tree_kernel<32><<<gt, 256, 0, st>>>(f, c->tree, tcoup); break;
+  const float* acoup = nullptr;
+  const bool blocked = f.learned && f.nslot == 2 && f.r <= 16 && f.K >= 2 * kBlk && f.K <= kBlk * kBlk && c->tree &&
+                       4LL * f.K * f.r <= c->tree_cap;
+  if (blocked) {
+    // learned factors: blocked strip sums, tile couplings and per-leaf inputs in three passes
+    const int nb = f.K / kBlk;
+    float* a_out = c->tree;                              // [2][K][R]
+    float* bsum = c->tree + 2LL * f.K * f.r;             // [2][nb][R]
+    int jnb = 0;
+    while ((1 << jnb) < nb) ++jnb;
+    const int parts = std::max(1, std::min(16, nb / 16));     // CTAs sharing the tiles above the blocks
+    auto smem_up = [&](int items) { return (size_t)2 * (2 * items - 1) * f.r * 4 + (size_t)(items - 1) * f.r * f.r * 2; };
+    static bool attr_up = false;
+    if (!attr_up) {
+      cudaFuncSetAttribute(block_up_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(block_up_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr_up = true;
     }
+    if (f.r == 8) {
+      block_up_kernel<8><<<nb, 1024, smem_up(kBlk), st>>>(f, uhat, f.K, kBlkLog, 0, bsum, tcoup);
+      block_up_kernel<8><<<dim3(1, parts), 1024, smem_up(nb), st>>>(f, bsum, nb, jnb, kBlkLog, nullptr, tcoup);
+      block_down_kernel<8><<<nb, 1024, 0, st>>>(f, tcoup, a_out);
+    } else {
+      block_up_kernel<16><<<nb, 1024, smem_up(kBlk), st>>>(f, uhat, f.K, kBlkLog, 0, bsum, tcoup);
+      block_up_kernel<16><<<dim3(1, parts), 1024, smem_up(nb), st>>>(f, bsum, nb, jnb, kBlkLog, nullptr, tcoup);
+      block_down_kernel<16><<<nb, 1024, 0, st>>>(f, tcoup, a_out);
+    }
+    acoup = a_out;
+  } else if (f.K >= 512 && c->tree && (int64_t)f.nslot * 2 * f.K * f.r <= c->tree_cap) {
+    // cluster sums by a tree: every tile reads two precomputed sums; then one pass gathers each
+    // leaf's coupling input into the tree buffer, which is free again by then
+    const int jl = 8;
+    const int gt = std::max(1, std::min((f.K - 1 + 7) / 8, c->num_sms * 8));
+    const int ga = std::max(1, std::min((int)(((int64_t)f.K * f.r + 255) / 256), c->num_sms * 16 / f.nslot + 1));
+    switch (f.r) {
+#define HM_TREE_CASE(RR)                                                                              \
+  case RR:                                                                                            \
+    tree_local_kernel<RR><<<dim3((f.K + 255) / 256, f.nslot), 256, 0, st>>>(uhat, c->tree, f.K, jl); \
+    tree_top_kernel<RR><<<f.nslot, 1024, 0, st>>>(c->tree, f.K, jl);                                  \
+    tile_from_tree_kernel<RR><<<gt, 256, 0, st>>>(f, uhat, c->tree, tcoup);                           \
+    leaf_coupling_kernel<RR><<<dim3(ga, f.nslot), 256, 0, st>>>(f, tcoup, c->tree);                             \
+    break;
+      HM_TREE_CASE(8)
+      HM_TREE_CASE(16)
+      HM_TREE_CASE(32)
+#undef HM_TREE_CASE
+      default: return 1;
+    }
+    acoup = c->tree;
   } else {
     tile_launch(f, uhat, tcoup, c->num_sms, st);
   }
   switch (f.r) {
-    case 8: apply_warp_prolong_kernel<8><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, ydiag, z); break;
-    case 16: apply_warp_prolong_kernel<16><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, ydiag, z); break;
-    default: apply_warp_prolong_kernel<32><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, ydiag, z); break;
+    case 8: apply_warp_prolong_kernel<8><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, acoup, ydiag, z); break;
+    case 16: apply_warp_prolong_kernel<16><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, acoup, ydiag, z); break;
+    default: apply_warp_prolong_kernel<32><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, acoup, ydiag, z); break;
   }
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }

@@ -154,10 +154,14 @@ def _fp8_pack(f):
 
 
 @pytest.mark.parametrize("n,leaf,rank", [(1024, 64, 16), (128, 64, 16), (8192, 64, 16),
-                                         (4096, 128, 32), (512, 8, 8), (65536, 64, 16)])
+                                         (4096, 128, 32), (512, 8, 8), (65536, 64, 16),
+                                         (65536, 64, 8), (65536, 64, 32), (131072, 64, 16)])
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
 def test_apply_learned_layout(ctx, n, leaf, rank, dtype):
-    if leaf != 64 or rank != 16:
+    """Learned layout vs the oracle's structured apply; K >= 512 takes the blocked
+    strip-sum path for rank <= 16 (two block levels at N = 131072) and the level tree
+    for rank 32."""
+    if leaf != 64 or rank != 16 or n > (1 << 16):
         c = h.Context(max_n=n, leaf=leaf, rank=rank)
     else:
         c = ctx
@@ -173,6 +177,23 @@ def test_apply_learned_layout(ctx, n, leaf, rank, dtype):
     want = hmatrix.apply(deq, r.astype(np.float64))
     got = z.cpu().numpy()
     assert np.linalg.norm(got - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_apply_svdh_layout_random_large(ctx, dtype):
+    """SVD-H layout (one bridge per level) with random factors at K = 1024 leaves: the
+    level-tree strip sums of the large-K path against the oracle's structured apply."""
+    n, leaf, rank = 65536, 64, 16
+    rng = np.random.default_rng(11)
+    w = hmatrix.packed_width(n, leaf, rank, "svdh")
+    f = hmatrix.unpack(rng.standard_normal(w), n, leaf, rank, "svdh")
+    packed, sc, deq = _upload(f, torch.float32 if dtype == "f32" else torch.bfloat16)
+    fac = h.factors(h.PRE_SVDH, packed, n, leaf, rank)
+    r = np.random.default_rng(8).standard_normal(n).astype(np.float32)
+    z = torch.empty(n, dtype=torch.float32, device="cuda")
+    h.apply(ctx, fac, torch.from_numpy(r).cuda(), z)
+    want = hmatrix.apply(deq, r.astype(np.float64))
+    assert np.linalg.norm(z.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
