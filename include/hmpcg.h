@@ -158,6 +158,37 @@ int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f,
                 const double* b, double* x, const hmpcg_solve_opts* opts,
                 hmpcg_solve_info* info, void* stream);
 
+/* Many independent systems of uneven n in one call (the paper solves one
+ * system per frame, Sec. 5; batching is this library's extension of that
+ * loop).  Each system i is solved exactly as hmpcg_solve would with factors[i]
+ * (NULL for all-unpreconditioned), b[i] and x[i] (host arrays of nsys device
+ * pointers).  Every system runs on one thread-block cluster of C CTAs
+ * (C = 4, 8 or 16: the value hmpcg_autotune_batch chose for its
+ * (kind, dtype, n), else the smallest C with n / C <= 1024); one persistent
+ * kernel per cluster size takes systems from a work list, longest first, and
+ * launches of different cluster sizes run concurrently on side streams that
+ * join `stream` again (graph-capturable).  Constraints: nsys <= 256; all
+ * factors share kind and dtype; n / C <= 2048 and, with H-matrix factors,
+ * n / (C leaf) a power of two <= 16 (so n <= 16384 for leaf 64), else
+ * HMPCG_E_SHAPE.  If infos (host, nsys entries) is non-NULL the stream is
+ * synchronised, infos written (ms_solve = the whole batch) and the first
+ * error status, else the first non-OK status, is returned.  No allocation. */
+int hmpcg_solve_batch(void* ctx, const hmpcg_system* systems,
+                      const hmpcg_factors* factors, const double* const* b,
+                      double* const* x, int32_t nsys, const hmpcg_solve_opts* opts,
+                      hmpcg_solve_info* infos, void* stream);
+
+/* Autotuner of hmpcg_solve_batch: for each distinct n among the systems, solves
+ * those systems with every feasible cluster size C in {4, 8, 16} (one warm-up
+ * and one timed run each, CUDA events on `stream`), keeps the fastest per
+ * (kind, dtype, n) in the context, and writes the chosen C of every system to
+ * cluster_out (host, nsys entries) if non-NULL.  Synchronises the stream;
+ * not capturable.  x[i] is overwritten with a solution. */
+int hmpcg_autotune_batch(void* ctx, const hmpcg_system* systems,
+                         const hmpcg_factors* factors, const double* const* b,
+                         double* const* x, int32_t nsys, const hmpcg_solve_opts* opts,
+                         int32_t* cluster_out, void* stream);
+
 /* ------------------------------------------------------------------ network */
 /* Infer the learned factors of `nsys` systems (Sec. 4; Supp. B): encoder ->
  * diagonal and off-diagonal attention stacks with highways -> decoder heads ->

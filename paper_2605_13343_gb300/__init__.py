@@ -78,6 +78,12 @@ EXPORTS = {
     "hmpcg_apply_noalloc": (C.c_int, [C.POINTER(Factors), C.c_void_p, C.c_void_p, C.c_void_p]),
     "hmpcg_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                   C.c_void_p, C.c_int32, C.c_void_p]),
+    "hmpcg_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.POINTER(Factors),
+                                    C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
+                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.c_void_p]),
+    "hmpcg_autotune_batch": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.POINTER(Factors),
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
+                                       C.POINTER(SolveOpts), C.POINTER(C.c_int32), C.c_void_p]),
 }
 
 
@@ -272,6 +278,48 @@ def solve(ctx, system, f, b, x, rtol=1e-6, max_iter=0, recompute_every=10, strea
                            _ptr(b), _ptr(x), C.byref(o), C.byref(inf) if info else None, _stream(stream))
     _check(rc, "solve", allow=allow)
     return inf
+
+
+def _batch_args(systems, facs, bs, xs):
+    n = len(systems)
+    assert len(bs) == n and len(xs) == n and (facs is None or len(facs) == n)
+    sysarr = systems_array(systems)
+    facarr = None
+    if facs is not None:
+        facarr = (Factors * n)()
+        for i, f in enumerate(facs):
+            facarr[i] = f
+    for t in list(bs) + list(xs):
+        assert t.dtype == torch.float64 and t.is_cuda
+    barr = (C.c_void_p * n)(*[t.data_ptr() for t in bs])
+    xarr = (C.c_void_p * n)(*[t.data_ptr() for t in xs])
+    return sysarr, facarr, barr, xarr
+
+
+def solve_batch(ctx, systems, facs, bs, xs, rtol=1e-6, max_iter=0, recompute_every=10, stream=None,
+                info=True, allow=(OK, NOT_CONVERGED)):
+    """hmpcg_solve_batch: independent systems of uneven size, one persistent cluster launch per
+    cluster size.  facs: list of Factors (same kind and dtype) or None.  Returns the list of
+    per-system SolveInfo (info=True)."""
+    sysarr, facarr, barr, xarr = _batch_args(systems, facs, bs, xs)
+    o = SolveOpts(rtol=rtol, max_iter=max_iter, recompute_every=recompute_every)
+    n = len(systems)
+    infos = (SolveInfo * n)() if info else None
+    rc = lib().hmpcg_solve_batch(ctx.h, sysarr, facarr, barr, xarr, n, C.byref(o), infos, _stream(stream))
+    _check(rc, "solve_batch", allow=allow)
+    return list(infos) if info else None
+
+
+def autotune_batch(ctx, systems, facs, bs, xs, rtol=1e-6, max_iter=0, recompute_every=10, stream=None):
+    """hmpcg_autotune_batch: time each cluster size per distinct n, keep the fastest in the
+    context; returns the chosen cluster size of every system."""
+    sysarr, facarr, barr, xarr = _batch_args(systems, facs, bs, xs)
+    o = SolveOpts(rtol=rtol, max_iter=max_iter, recompute_every=recompute_every)
+    n = len(systems)
+    out = (C.c_int32 * n)()
+    _check(lib().hmpcg_autotune_batch(ctx.h, sysarr, facarr, barr, xarr, n, C.byref(o), out, _stream(stream)),
+           "autotune_batch")
+    return list(out)
 
 
 def infer_factors(ctx, systems, packed, scales=None, stream=None):

@@ -2,6 +2,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <map>
+#include <vector>
 #include "ctx.cuh"
 #include "net.cuh"
 
@@ -20,9 +22,14 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int n_probes, 
                    uint64_t seed, float* loss_out, cudaStream_t st);
 int net_get_weights(Ctx* c, float* w, int64_t count);
 int net_get_grads(Ctx* c, float* g, int64_t count);
+int solve_batch_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* const* b,
+                         double* const* x, int nsys, const hmpcg_solve_opts* o, const int* csize, cudaStream_t st);
+void batch_cluster_sizes(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, int nsys, int* csize);
 }  // namespace hm
 
 using namespace hm;
+
+constexpr int kMaxBatchSystems = 256;   // systems per hmpcg_solve_batch call
 
 static bool valid_grid(int32_t ndim, const int32_t* dims) {
   if (ndim < 1 || ndim > 3 || !dims) return false;
@@ -154,9 +161,17 @@ int hmpcg_create(void** out, const hmpcg_config* cfg, const float* weights, int6
   s.part = (double*)alloc(8 * 4 * kMaxGrid);
   s.counter = (unsigned*)alloc(256);
   s.st = (DevStatus*)alloc(sizeof(DevStatus));
+  c->bcap = kMaxBatchSystems;
+  c->bst = (DevStatus*)alloc(sizeof(DevStatus) * (size_t)c->bcap);
+  c->bcounter = (int*)alloc(sizeof(int) * 64);
   bool ok = c->tree && s.r && s.z && s.q && s.p0 && s.p1 && s.ydiag && s.uhat && s.tcoup && s.x2 && s.part &&
             s.counter && s.st;
+  ok = ok && c->bst && c->bcounter;
   ok = ok && cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&c->bfork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 3 && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&c->bside[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->bjoin[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) { hmpcg_destroy(c); return HMPCG_E_NOMEM; }
   if (weights || cfg->d_model > 0) {
     int rc = net_create(c, weights, n_weights, (cudaStream_t)stream);
@@ -175,6 +190,11 @@ int hmpcg_destroy(void* ctx) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->bfork) cudaEventDestroy(c->bfork);
+  for (int i = 0; i < 3; ++i) {
+    if (c->bside[i]) cudaStreamDestroy(c->bside[i]);
+    if (c->bjoin[i]) cudaEventDestroy(c->bjoin[i]);
+  }
   delete c;
   return HMPCG_OK;
 }
@@ -215,6 +235,106 @@ int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f, cons
   info->status = ds.status;
   info->rel_res_true = ds.rel_res;
   return ds.status;
+}
+
+static int batch_args_ok(Ctx* c, const hmpcg_system* systems, const hmpcg_factors* factors,
+                         const double* const* b, double* const* x, int32_t nsys,
+                         const hmpcg_solve_opts* opts) {
+  if (!systems || !b || !x || nsys <= 0) return HMPCG_E_INVALID;
+  if (nsys > c->bcap) return HMPCG_E_SHAPE;
+  if (opts && !(opts->rtol >= 0.0)) return HMPCG_E_INVALID;
+  for (int i = 0; i < nsys; ++i) {
+    if (!b[i] || !x[i] || !systems[i].diag) return HMPCG_E_INVALID;
+    if (systems[i].n > c->max_n) return HMPCG_E_SHAPE;
+    if (factors && factors[i].kind >= HMPCG_PRE_SVDH && !factors[i].packed) return HMPCG_E_INVALID;
+  }
+  return HMPCG_OK;
+}
+
+int hmpcg_solve_batch(void* ctx, const hmpcg_system* systems, const hmpcg_factors* factors,
+                      const double* const* b, double* const* x, int32_t nsys,
+                      const hmpcg_solve_opts* opts, hmpcg_solve_info* infos, void* stream) {
+  if (!ctx) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  int rc = batch_args_ok(c, systems, factors, b, x, nsys, opts);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> cs(nsys);
+  batch_cluster_sizes(c, systems, factors, nsys, cs.data());
+  if (infos) HM_CUDA(cudaEventRecord(c->ev0, st));
+  rc = solve_batch_dispatch(c, systems, factors, b, x, nsys, opts, cs.data(), st);
+  if (rc) return rc;
+  if (!infos) return HMPCG_OK;
+  HM_CUDA(cudaEventRecord(c->ev1, st));
+  std::vector<DevStatus> ds(nsys);
+  HM_CUDA(cudaMemcpyAsync(ds.data(), c->bst, sizeof(DevStatus) * nsys, cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  int worst = HMPCG_OK;
+  for (int i = 0; i < nsys; ++i) {
+    infos[i].iters = ds[i].iters;
+    infos[i].ms_solve = ms;
+    if (ds[i].err) {
+      infos[i].status = ds[i].err;
+      infos[i].rel_res_true = -1.0;
+    } else {
+      infos[i].status = ds[i].status;
+      infos[i].rel_res_true = ds[i].rel_res;
+    }
+    if (worst == HMPCG_OK || (infos[i].status < 0 && worst > 0)) worst = infos[i].status;
+  }
+  return worst;
+}
+
+int hmpcg_autotune_batch(void* ctx, const hmpcg_system* systems, const hmpcg_factors* factors,
+                         const double* const* b, double* const* x, int32_t nsys,
+                         const hmpcg_solve_opts* opts, int32_t* cluster_out, void* stream) {
+  if (!ctx) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  int rc = batch_args_ok(c, systems, factors, b, x, nsys, opts);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int kind = factors ? factors[0].kind : HMPCG_PRE_NONE;
+  const int dt = factors ? factors[0].dtype : 0;
+  // every distinct size on its own: time each cluster shape on those systems, keep the fastest
+  std::map<int64_t, std::vector<int>> by_n;
+  for (int i = 0; i < nsys; ++i) by_n[systems[i].n].push_back(i);
+  for (auto& kv : by_n) {
+    const std::vector<int>& ids = kv.second;
+    std::vector<hmpcg_system> ss;
+    std::vector<hmpcg_factors> ff;
+    std::vector<const double*> bb;
+    std::vector<double*> xx;
+    for (int i : ids) {
+      ss.push_back(systems[i]);
+      if (factors) ff.push_back(factors[i]);
+      bb.push_back(b[i]);
+      xx.push_back(x[i]);
+    }
+    const int m = (int)ids.size();
+    float best = 1e30f;
+    int best_c = 0;
+    for (int C : {4, 8, 16}) {
+      std::vector<int> cs(m, C);
+      const hmpcg_factors* fp = factors ? ff.data() : nullptr;
+      if (solve_batch_dispatch(c, ss.data(), fp, bb.data(), xx.data(), m, opts, cs.data(), st)) {
+        cudaGetLastError();
+        continue;   // shape not possible for these systems
+      }
+      HM_CUDA(cudaEventRecord(c->ev0, st));
+      if (solve_batch_dispatch(c, ss.data(), fp, bb.data(), xx.data(), m, opts, cs.data(), st)) continue;
+      HM_CUDA(cudaEventRecord(c->ev1, st));
+      HM_CUDA(cudaStreamSynchronize(st));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+      if (ms < best) { best = ms; best_c = C; }
+    }
+    if (!best_c) return HMPCG_E_SHAPE;
+    c->tune[std::make_tuple(kind, dt, kv.first)] = best_c;
+  }
+  if (cluster_out) batch_cluster_sizes(c, systems, factors, nsys, cluster_out);
+  return HMPCG_OK;
 }
 
 int hmpcg_infer_factors(void* ctx, const hmpcg_system* systems, int32_t nsys, void* packed,

@@ -1,5 +1,7 @@
 // Internal context and views shared by the hmpcg translation units.
 #pragma once
+#include <map>
+#include <tuple>
 #include <vector>
 #include "common.cuh"
 
@@ -55,6 +57,14 @@ struct Ctx {
   int coop_blocks_hmat[3];   // max co-resident CTAs per dtype for the H-matrix PCG
   int coop_blocks_simple;    // for NONE / JACOBI
   cudaEvent_t ev0, ev1;
+  // batched solves: per-system status, work-list counters, side streams for concurrent groups,
+  // and the tuned cluster size per (preconditioner kind, dtype, n)
+  DevStatus* bst;
+  int* bcounter;
+  int bcap;
+  cudaStream_t bside[3];
+  cudaEvent_t bfork, bjoin[3];
+  std::map<std::tuple<int, int, int64_t>, int> tune;
   Net* net;
   std::vector<void*> allocs;
 };

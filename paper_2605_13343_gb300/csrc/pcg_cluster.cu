@@ -58,6 +58,7 @@ struct CParams {
   double rtol;
   int max_iter, recompute;
   int C, npc, lpc, tpc;   // CTAs, nodes / leaves / tiles per CTA
+  int fsm;                // 1: the CTA's factor share is copied to shared memory; 0: read from L2
 };
 
 // Shared-memory carve-up (byte offsets), identical in every CTA.
@@ -66,7 +67,8 @@ struct CLayout {
 };
 
 template <class T>
-__host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, int nslot, bool learned, bool hmat) {
+__host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, int nslot, bool learned, bool hmat,
+                                     bool fsm) {
   CLayout o;
   size_t p = 0;
   auto take = [&](size_t bytes) { size_t q = p; p = (p + bytes + 15) / 16 * 16; return q; };
@@ -86,16 +88,18 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
   o.part = take(8 * 8);
   o.rs = take(hmat ? 4 * (size_t)lpc * L : 0);
   o.ws = take(hmat ? 4 * (size_t)lpc * (L > nslot * R ? L : nslot * R) : 0);
-  o.leaf = take(hmat ? sizeof(T) * (size_t)lpc * L * (L + kLeafPad) : 0);
-  o.bridge = take(hmat ? sizeof(T) * (size_t)nslot * npc * R : 0);
-  o.gate = take(hmat && learned ? sizeof(T) * (size_t)npc : 0);
-  o.core = take(hmat ? sizeof(T) * (size_t)tpc * R * R : 0);
+  o.leaf = take(hmat && fsm ? sizeof(T) * (size_t)lpc * L * (L + kLeafPad) : 0);
+  o.bridge = take(hmat && fsm ? sizeof(T) * (size_t)nslot * npc * R : 0);
+  o.gate = take(hmat && fsm && learned ? sizeof(T) * (size_t)npc : 0);
+  o.core = take(hmat && fsm ? sizeof(T) * (size_t)tpc * R * R : 0);
   o.total = p;
   return o;
 }
 
+// One system on the calling cluster.  Returns after a final cluster barrier, so the caller may
+// reuse the shared memory at once.
 template <class T, int PRE>
-__global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams<T> P) {
+__device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   extern __shared__ __align__(16) uint8_t sm[];
   const SysView& S = P.s;
   const FactorView<T>& F = P.f;
@@ -103,7 +107,8 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
   const int C = P.C, npc = P.npc;
   const int L = F.L, R = F.r;
   const bool hmat = PRE == CPRE_HMAT;
-  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat);
+  const bool fsm = P.fsm != 0;
+  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, fsm);
   double* xs = reinterpret_cast<double*>(sm + lay.x);
   double* bs = reinterpret_cast<double*>(sm + lay.b);
   float* rv = reinterpret_cast<float*>(sm + lay.r);
@@ -126,6 +131,13 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
   const int tid = threadIdx.x;
   const int n0 = me * npc;
   const int LP = L + kLeafPad;
+  // factor share: shared-memory copies (fsm) or the packed tensor itself (L2-resident)
+  const int LPs = fsm ? LP : L;
+  const T* lf = fsm ? sleaf : (hmat ? F.leaf + (size_t)(n0 / L) * L * L : nullptr);
+  const T* brf = fsm ? sbr : (hmat ? F.bridge + (size_t)n0 * R : nullptr);
+  const size_t brs = fsm ? (size_t)npc * R : (size_t)F.n * R;          // slot stride
+  const T* gtf = fsm ? sgate : (hmat && F.learned ? F.gate + n0 : nullptr);
+  auto core_of = [&](int tl, int m) -> const T* { return fsm ? score + (size_t)tl * R * R : F.core + (size_t)m * R * R; };
 
   // value of node i of an owner-distributed array (local shared memory or DSMEM)
   auto ld_f = [&](float* base, int i) -> float {
@@ -162,7 +174,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
       wmv[3 * i + a] = jm < 0 ? 0.f : S.w32[a][jm];
     }
   }
-  if (hmat) {
+  if (hmat && fsm) {
     const int k0 = n0 / L;
     for (int e = tid; e < P.lpc * L * L; e += blockDim.x) {
       const int kl = e / (L * L), rr = (e / L) % L, cc = e % L;
@@ -196,21 +208,21 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
     __syncthreads();
     if (grp < P.lpc) {
       const int kl = grp, k = n0 / L + kl;
-      const T* blk = sleaf + (size_t)kl * L * LP;
+      const T* blk = lf + (size_t)kl * L * LPs;
       const float* r_l = rs + kl * L;
       float* w_l = ws + kl * max(L, F.nslot * R);
       const float sb = sc_leaf(k);
       if (F.learned) {
         for (int j = gl; j < L; j += G) {            // w = F^T r
           float acc = 0.f;
-          for (int i = 0; i < L; ++i) acc = fmaf(tf<T>(blk[i * LP + j]), r_l[i], acc);
+          for (int i = 0; i < L; ++i) acc = fmaf(tf<T>(blk[i * LPs + j]), r_l[i], acc);
           w_l[j] = acc * sb;
         }
       }
       // restriction uh[s][kl] = W_s^T r
       for (int q = gl; q < F.nslot * R; q += G) {
         const int s = q / R, e = q % R;
-        const T* W = sbr + ((size_t)s * npc + kl * L) * R;
+        const T* W = brf + (size_t)s * brs + (size_t)kl * L * R;
         float acc = 0.f;
         for (int i = 0; i < L; ++i) acc = fmaf(tf<T>(W[i * R + e]), r_l[i], acc);
         uh[((size_t)s * (2 * P.lpc - 1) + kl) * R + e] = acc * sc_br(s, k);
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
     __syncthreads();
     if (grp < P.lpc) {
       const int kl = grp, k = n0 / L + kl;
-      const T* blk = sleaf + (size_t)kl * L * LP;
+      const T* blk = lf + (size_t)kl * L * LPs;
       const float* r_l = rs + kl * L;
       const float* w_l = ws + kl * max(L, F.nslot * R);
       const float sb = sc_leaf(k);
@@ -227,10 +239,10 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
       for (int i = gl; i < L; i += G) {
         float acc = 0.f;
         if (F.learned) {
-          for (int j = 0; j < L; ++j) acc = fmaf(tf<T>(blk[i * LP + j]), w_l[j], acc);
-          acc = fmaf(tf<T>(sgate[kl * L + i]) * sg, r_l[i], acc * sb);
+          for (int j = 0; j < L; ++j) acc = fmaf(tf<T>(blk[i * LPs + j]), w_l[j], acc);
+          acc = fmaf(tf<T>(gtf[kl * L + i]) * sg, r_l[i], acc * sb);
         } else {
-          for (int j = 0; j < L; ++j) acc = fmaf(tf<T>(blk[i * LP + j]), r_l[j], acc);
+          for (int j = 0; j < L; ++j) acc = fmaf(tf<T>(blk[i * LPs + j]), r_l[j], acc);
           acc *= sb;
         }
         ydv[kl * L + i] = acc;
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
       const int tl = q / (2 * R), side = (q / R) & 1, e = q % R;
       const int m = me + tl * C;
       if (m >= F.K - 1) continue;
-      const T* Bm = score + (size_t)tl * R * R;
+      const T* Bm = core_of(tl, m);
       const float sB = F.sc_core ? F.sc_core[m] : 1.f;
       const float* srow = ws + (size_t)tl * 2 * R;        // s^r
       const float* scol = srow + R;                        // s^c
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
       const int kl = q / L, k = n0 / L + kl;
       float acc = ydv[q];
       for (int s = 0; s < F.nslot; ++s) {
-        const T* Wr = sbr + ((size_t)s * npc + q) * R;
+        const T* Wr = brf + (size_t)s * brs + (size_t)q * R;
         const float* a = as + ((size_t)kl * F.nslot + s) * R;
         float t = 0.f;
         for (int e = 0; e < R; ++e) t = fmaf(tf<T>(Wr[e]), a[e], t);
@@ -565,37 +577,91 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams
   cluster_sync();   // nobody leaves while others may still read its shared memory
 }
 
+template <class T, int PRE>
+__global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams<T> P) {
+  pcg_cluster_body<T, PRE>(P);
+}
+
+// Many systems, one persistent launch: each cluster takes the next system of the work list
+// (ordered longest first by the host) until the list is exhausted.
+constexpr int kBatchMax = 64;
+template <class T>
+struct CBatch {
+  int nsys;
+  CParams<T> p[kBatchMax];
+};
+
+template <class T, int PRE>
+__global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_batch_kernel(const __grid_constant__ CBatch<T> B,
+                                                                         int* __restrict__ counter) {
+  __shared__ int pick;
+  for (;;) {
+    if (cl_rank() == 0 && threadIdx.x == 0) pick = atomicAdd(counter, 1);
+    cluster_sync();
+    const int i = *remote(&pick, 0);
+    cluster_sync();   // every CTA has read the pick before rank 0 takes the next one
+    if (i >= B.nsys) break;
+    pcg_cluster_body<T, PRE>(B.p[i]);
+  }
+}
+
 }  // namespace
 
 // ============================================================================ host side
 SysView make_sysview(const hmpcg_system* s);
 
+// Parameters and shared-memory bytes of one system on a cluster of C CTAs with the factor share
+// in shared memory (fsm) or read from L2; false when the system does not fit that shape.
 template <class T, int PRE>
-static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv, const double* b, double* x,
-                       const hmpcg_solve_opts* o, cudaStream_t st) {
+static bool plan_cluster(const hmpcg_system* sys, const FactorView<T>* fv, int C, bool fsm, CParams<T>& P,
+                         size_t& smem) {
   const int n = (int)sys->n;
   const bool hmat = PRE == CPRE_HMAT;
   const int L = hmat ? fv->L : 64;
-  for (int C : {16, 8}) {
-    if (n % C) continue;
-    const int npc = n / C;
-    if (npc > 4 * kCThreads) continue;       // the x update keeps <= 4 values per thread
-    if (hmat && (npc % L)) continue;
-    const int lpc = hmat ? npc / L : 0;
-    if (hmat && (lpc > kCThreads / 32 || fv->levels > 24 || (lpc & (lpc - 1)))) continue;
-    if (hmat && (n / C) / L * C != fv->K) continue;
-    const int tpc = hmat ? (fv->K - 1 + C - 1) / C : 0;
-    const int R = hmat ? fv->r : 16, nslot = hmat ? fv->nslot : 1;
-    const CLayout lay = c_layout<T>(npc, lpc, tpc, L, R, nslot, hmat && fv->learned, hmat);
-    if (hmat && (size_t)tpc * 2 * R > (size_t)lpc * std::max(L, nslot * R)) continue;
-    if (hmat && (size_t)lpc * nslot * R > (size_t)lpc * std::max(L, nslot * R)) continue;
-    if (lay.total > 220 * 1024) continue;
-    auto kern = pcg_cluster_kernel<T, PRE>;
+  if (n % C) return false;
+  const int npc = n / C;
+  if (npc > 4 * kCThreads || npc >= (1 << 16)) return false;   // <= 4 x values per thread; 16-bit local index
+  if (hmat && (npc % L)) return false;
+  const int lpc = hmat ? npc / L : 0;
+  if (hmat && (lpc > kCThreads / 32 || fv->levels > 24 || (lpc & (lpc - 1)))) return false;
+  if (hmat && (n / C) / L * C != fv->K) return false;
+  const int tpc = hmat ? (fv->K - 1 + C - 1) / C : 0;
+  const int R = hmat ? fv->r : 16, nslot = hmat ? fv->nslot : 1;
+  const CLayout lay = c_layout<T>(npc, lpc, tpc, L, R, nslot, hmat && fv->learned, hmat, fsm);
+  if (hmat && (size_t)tpc * 2 * R > (size_t)lpc * std::max(L, nslot * R)) return false;
+  if (hmat && (size_t)lpc * nslot * R > (size_t)lpc * std::max(L, nslot * R)) return false;
+  if (lay.total > 220 * 1024) return false;
+  P.s = make_sysview(sys);
+  if (fv) P.f = *fv; else memset(&P.f, 0, sizeof(P.f));
+  P.C = C; P.npc = npc; P.lpc = lpc; P.tpc = tpc; P.fsm = fsm ? 1 : 0;
+  smem = lay.total;
+  return true;
+}
+
+template <class T>
+static void set_opts(CParams<T>& P, const hmpcg_system* sys, const hmpcg_solve_opts* o) {
+  P.rtol = o ? o->rtol : 1e-6;
+  P.max_iter = (o && o->max_iter > 0) ? o->max_iter : (int)std::min<int64_t>(10 * sys->n, 1 << 30);
+  P.recompute = o ? o->recompute_every : 10;
+}
+
+// Function attributes and the cluster-occupancy query, once per (kernel, C, smem): the number
+// of clusters that can be resident at once (0 = shape not launchable).
+static int cluster_capacity(const void* kern, int C, size_t smem) {
+  static std::map<std::tuple<const void*, int, size_t>, int> cap;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(kern, C, smem);
+  auto it = cap.find(key);
+  if (it != cap.end()) return it->second;
+  bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+  if (ok && C > 8) ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+  int nclusters = 0;
+  if (ok) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kCThreads);
-    cfg.dynamicSmemBytes = lay.total;
-    cfg.stream = st;
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
@@ -603,37 +669,45 @@ static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // function attributes and the cluster-occupancy query run once per (kernel, C, smem)
-    static std::map<std::tuple<const void*, int, size_t>, bool> feasible;
-    static std::mutex mu;
-    {
-      std::lock_guard<std::mutex> lock(mu);
-      const auto key = std::make_tuple((const void*)kern, C, lay.total);
-      auto it = feasible.find(key);
-      if (it == feasible.end()) {
-        bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total) == cudaSuccess;
-        if (ok && C > 8) ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
-        int nclusters = 0;
-        if (ok) ok = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) nclusters = 0;
+  }
+  cudaGetLastError();
+  cap.emplace(key, nclusters);
+  return nclusters;
+}
+
+template <class T, int PRE>
+static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv, const double* b, double* x,
+                       const hmpcg_solve_opts* o, cudaStream_t st) {
+  for (int fsm = 1; fsm >= 0; --fsm) {
+    if (!fsm && PRE != CPRE_HMAT) break;
+    for (int C : {16, 8}) {
+      CParams<T> P;
+      size_t smem = 0;
+      if (!plan_cluster<T, PRE>(sys, fv, C, fsm != 0, P, smem)) continue;
+      auto kern = pcg_cluster_kernel<T, PRE>;
+      if (cluster_capacity((const void*)kern, C, smem) < 1) continue;
+      P.b = b; P.x = x; P.st = c->s.st;
+      set_opts(P, sys, o);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(kCThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      HM_CUDA(cudaMemsetAsync(c->s.st, 0, sizeof(DevStatus), st));
+      if (cudaLaunchKernelEx(&cfg, kern, P) != cudaSuccess) {
         cudaGetLastError();
-        it = feasible.emplace(key, ok).first;
+        continue;
       }
-      if (!it->second) continue;
+      return HMPCG_OK;
     }
-    CParams<T> P;
-    P.s = make_sysview(sys);
-    if (fv) P.f = *fv; else memset(&P.f, 0, sizeof(P.f));
-    P.b = b; P.x = x; P.st = c->s.st;
-    P.rtol = o ? o->rtol : 1e-6;
-    P.max_iter = (o && o->max_iter > 0) ? o->max_iter : (int)std::min<int64_t>(10 * sys->n, 1 << 30);
-    P.recompute = o ? o->recompute_every : 10;
-    P.C = C; P.npc = npc; P.lpc = lpc; P.tpc = tpc;
-    HM_CUDA(cudaMemsetAsync(c->s.st, 0, sizeof(DevStatus), st));
-    if (cudaLaunchKernelEx(&cfg, kern, P) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    return HMPCG_OK;
   }
   return 1;   // not applicable: caller uses the grid-wide kernel
 }
@@ -657,5 +731,121 @@ template int solve_cluster_hmat<__nv_bfloat16>(Ctx*, const hmpcg_system*, const 
                                                const double*, double*, const hmpcg_solve_opts*, cudaStream_t);
 template int solve_cluster_hmat<__nv_fp8_e4m3>(Ctx*, const hmpcg_system*, const FactorView<__nv_fp8_e4m3>&,
                                                const double*, double*, const hmpcg_solve_opts*, cudaStream_t);
+
+// ---------------------------------------------------------------- batched solves
+template <class T> int make_factor_view(const hmpcg_factors* fp, FactorView<T>& f);
+
+// Default cluster size of an n-node system: the smallest shape with at most 1024 nodes per CTA
+// (fewer SMs per small system leaves room for more systems at once).
+static int default_cluster(int64_t n) {
+  for (int C : {4, 8, 16})
+    if (n / C <= 1024) return C;
+  return 16;
+}
+
+template <class T, int PRE>
+static int run_batch_typed(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* const* b,
+                           double* const* x, int nsys, const hmpcg_solve_opts* o, const int* csize,
+                           cudaStream_t st) {
+  static_assert(sizeof(CBatch<T>) <= 32000, "kernel parameter block");
+  std::vector<FactorView<T>> fv(PRE == CPRE_HMAT ? nsys : 0);
+  if (PRE == CPRE_HMAT)
+    for (int i = 0; i < nsys; ++i) {
+      const int rc = make_factor_view(&f[i], fv[i]);
+      if (rc) return rc;
+      if (f[i].n != sys[i].n) return HMPCG_E_SHAPE;
+    }
+  // plans, grouped by cluster size
+  std::map<int, std::vector<int>> groups;
+  std::vector<CParams<T>> plan(nsys);
+  std::map<int, size_t> smem_of;
+  for (int i = 0; i < nsys; ++i) {
+    const int C = csize[i];
+    size_t sm = 0;
+    bool ok = plan_cluster<T, PRE>(&sys[i], PRE == CPRE_HMAT ? &fv[i] : nullptr, C, true, plan[i], sm);
+    if (!ok && PRE == CPRE_HMAT) ok = plan_cluster<T, PRE>(&sys[i], &fv[i], C, false, plan[i], sm);
+    if (!ok) return HMPCG_E_SHAPE;
+    plan[i].b = b[i]; plan[i].x = x[i]; plan[i].st = c->bst + i;
+    set_opts(plan[i], &sys[i], o);
+    groups[C].push_back(i);
+    smem_of[C] = std::max(smem_of[C], sm);
+  }
+  // SM share of each group in proportion to its node count
+  double total = 0.0;
+  for (int i = 0; i < nsys; ++i) total += (double)sys[i].n;
+  HM_CUDA(cudaMemsetAsync(c->bst, 0, sizeof(DevStatus) * nsys, st));
+  HM_CUDA(cudaMemsetAsync(c->bcounter, 0, sizeof(int) * 64, st));
+  const int ng = (int)groups.size();
+  if (ng > 1) HM_CUDA(cudaEventRecord(c->bfork, st));
+  int gi = 0, chunk_id = 0;
+  for (auto& kv : groups) {
+    const int C = kv.first;
+    std::vector<int>& ids = kv.second;
+    std::stable_sort(ids.begin(), ids.end(), [&](int a, int b2) { return sys[a].n > sys[b2].n; });
+    cudaStream_t gs = (gi == 0) ? st : c->bside[(gi - 1) % 3];
+    if (gi > 0) HM_CUDA(cudaStreamWaitEvent(gs, c->bfork, 0));
+    auto kern = pcg_cluster_batch_kernel<T, PRE>;
+    const size_t smem = smem_of[C];
+    const int capn = cluster_capacity((const void*)kern, C, smem);
+    if (capn < 1) return HMPCG_E_SHAPE;
+    double work = 0.0;
+    for (int i : ids) work += (double)sys[i].n;
+    const int share = std::max(1, (int)((double)c->num_sms * work / total) / C);
+    for (size_t s0 = 0; s0 < ids.size(); s0 += kBatchMax, ++chunk_id) {
+      if (chunk_id >= 64) return HMPCG_E_SHAPE;
+      CBatch<T> B;
+      B.nsys = (int)std::min<size_t>(kBatchMax, ids.size() - s0);
+      for (int q = 0; q < B.nsys; ++q) B.p[q] = plan[ids[s0 + q]];
+      const int ncl = std::max(1, std::min({B.nsys, capn, ng > 1 ? share : capn}));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(ncl * C);
+      cfg.blockDim = dim3(kCThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = gs;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      HM_CUDA(cudaLaunchKernelEx(&cfg, kern, B, c->bcounter + chunk_id));
+    }
+    if (gi > 0) {
+      HM_CUDA(cudaEventRecord(c->bjoin[(gi - 1) % 3], gs));
+      HM_CUDA(cudaStreamWaitEvent(st, c->bjoin[(gi - 1) % 3], 0));
+    }
+    ++gi;
+  }
+  return HMPCG_OK;
+}
+
+// Solves nsys independent systems with one persistent cluster launch per cluster size.
+// csize[i] is the cluster size of system i (from the tuner or default_cluster).
+int solve_batch_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* const* b,
+                         double* const* x, int nsys, const hmpcg_solve_opts* o, const int* csize, cudaStream_t st) {
+  const int kind = f ? f[0].kind : HMPCG_PRE_NONE;
+  for (int i = 1; f && i < nsys; ++i)
+    if (f[i].kind != kind || f[i].dtype != f[0].dtype) return HMPCG_E_INVALID;
+  if (kind == HMPCG_PRE_NONE) return run_batch_typed<float, CPRE_NONE>(c, sys, f, b, x, nsys, o, csize, st);
+  if (kind == HMPCG_PRE_JACOBI) return run_batch_typed<float, CPRE_JACOBI>(c, sys, f, b, x, nsys, o, csize, st);
+  if (kind != HMPCG_PRE_SVDH && kind != HMPCG_PRE_LEARNED) return HMPCG_E_INVALID;
+  switch (f[0].dtype) {
+    case HMPCG_F32: return run_batch_typed<float, CPRE_HMAT>(c, sys, f, b, x, nsys, o, csize, st);
+    case HMPCG_BF16: return run_batch_typed<__nv_bfloat16, CPRE_HMAT>(c, sys, f, b, x, nsys, o, csize, st);
+    case HMPCG_FP8E4M3: return run_batch_typed<__nv_fp8_e4m3, CPRE_HMAT>(c, sys, f, b, x, nsys, o, csize, st);
+  }
+  return HMPCG_E_INVALID;
+}
+
+// Cluster size of each system: the tuned choice for its (kind, dtype, n), else the default.
+void batch_cluster_sizes(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, int nsys, int* csize) {
+  const int kind = f ? f[0].kind : HMPCG_PRE_NONE;
+  const int dt = f ? f[0].dtype : 0;
+  for (int i = 0; i < nsys; ++i) {
+    auto it = c->tune.find(std::make_tuple(kind, dt, (int64_t)sys[i].n));
+    csize[i] = it != c->tune.end() ? it->second : default_cluster(sys[i].n);
+  }
+}
 
 }  // namespace hm

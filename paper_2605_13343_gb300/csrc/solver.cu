@@ -769,4 +769,8 @@ int spmv_launch(const hmpcg_system* sys, const float* x, float* y, cudaStream_t 
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
+template int make_factor_view<float>(const hmpcg_factors*, FactorView<float>&);
+template int make_factor_view<__nv_bfloat16>(const hmpcg_factors*, FactorView<__nv_bfloat16>&);
+template int make_factor_view<__nv_fp8_e4m3>(const hmpcg_factors*, FactorView<__nv_fp8_e4m3>&);
+
 }  // namespace hm
