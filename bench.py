@@ -132,6 +132,9 @@ def main():
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2605_13343_gb300", "weights",
                                                       "hmpcg_d128_l4.f32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384"],
+                    help="frame8192: the per-frame headline; batch64: 64 ragged systems in one graph; "
+                         "precision16384: FP32/BF16/FP8 apply sweep with SVD-H factors")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -157,6 +160,10 @@ def main():
     else:
         w = inputs.network_blob(0, **CFG)
         wsrc = "seeded init"
+    if args.workload == "precision16384":
+        return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind)
+    if args.workload == "batch64":
+        return bench_batch(args, h, torch, np, inputs, w, wsrc)
     n = 8192
     ctx = h.Context(max_n=n, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
                     max_batch=1, weights=w)
@@ -344,6 +351,243 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- secondary workloads
+def _dense_from_system(torch, s):
+    """Dense FP64 A (Morton order) from an assembled system, on the device."""
+    n, dims = s.n, s.dims
+    dev = s.diag.device
+    perm = s.perm.long()
+    inv = torch.empty_like(perm)
+    inv[perm] = torch.arange(n, device=dev)
+    a = torch.zeros(n, n, dtype=torch.float64, device=dev)
+    ar = torch.arange(n, device=dev)
+    a[ar, ar] = s.diag
+    stride = 1
+    for ax, d in enumerate(dims):
+        c = (perm // stride) % d
+        has = c < d - 1
+        i = ar[has]
+        j = inv[perm[has] + stride]
+        w = s.wplus(ax)[has]
+        a[i, j] = -w
+        a[j, i] = -w
+        stride *= d
+    return a
+
+
+def _svdh_torch(torch, ainv, leaf, rank):
+    """SVD-H factors of a dense inverse (leaves (A^-1)_kk, tiles' truncated SVD), packed in the
+    SVD-H layout [G][Sigma][W per level].  Tiles wider than 1024 use a randomized truncated
+    SVD (8 extra columns, 6 power iterations)."""
+    n = ainv.shape[0]
+    K = n // leaf
+    levels = K.bit_length() - 1
+    G = ainv.reshape(K, leaf, K, leaf).diagonal(dim1=0, dim2=2).permute(2, 0, 1).contiguous()
+    sig = torch.zeros(K - 1, rank, rank, dtype=torch.float64, device=ainv.device)
+    W = torch.zeros(levels, n, rank, dtype=torch.float64, device=ainv.device)
+    for lev in range(1, levels + 1):
+        S = (K >> lev) * leaf
+        for t in range(1 << (lev - 1)):
+            m = (1 << (lev - 1)) - 1 + t
+            r0, c0 = 2 * t * S, (2 * t + 1) * S
+            X = ainv[r0:r0 + S, c0:c0 + S]
+            rr = min(rank, S)
+            if S <= 1024:
+                U, sv, Vh = torch.linalg.svd(X)
+                V = Vh.mH
+            else:
+                U, sv, V = torch.svd_lowrank(X, q=rr + 8, niter=6)
+            sig[m, torch.arange(rr), torch.arange(rr)] = sv[:rr]
+            W[lev - 1, r0:r0 + S, :rr] = U[:, :rr]
+            W[lev - 1, c0:c0 + S, :rr] = V[:, :rr]
+    return G, sig, W
+
+
+def _fp8_blocks(torch, blocks):
+    """Per-block FP8-E4M3 quantisation: (stored, scale) with value = stored * scale."""
+    flat = blocks.reshape(blocks.shape[0], -1)
+    amax = flat.abs().amax(dim=1).clamp_min(1e-300)
+    sc = amax / 448.0
+    q = (flat / sc[:, None]).to(torch.float32).to(torch.float8_e4m3fn)
+    return q.flatten(), sc.to(torch.float32)
+
+
+def bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind):
+    """Apply precision sweep: 2D 128x128, 20 discs of contrast 100, SVD-H leaf 64 rank 32;
+    PCG with the apply in FP32, BF16 and FP8-E4M3 (per-block scales), FP64 scalars, true
+    residual every 10 iterations.  A step is one solve."""
+    fr = inputs.frame("discs2d_16384", 0)
+    n, leaf, rank = 16384, 64, 32
+    s = h.System(fr["dims"])
+    h.assemble(torch.from_numpy(fr["rho"]).cuda(), s)
+    b = torch.from_numpy(fr["b"]).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = _dense_from_system(torch, s)
+    ainv = torch.cholesky_inverse(torch.linalg.cholesky(a))
+    xstar = ainv @ b
+    G, sig, W = _svdh_torch(torch, ainv, leaf, rank)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    K = n // leaf
+    ctx = h.Context(max_n=n, leaf=leaf, rank=rank)
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    keep = []
+
+    def run(fac, label):
+        for _ in range(args.warmup):
+            h.solve(ctx, s, fac, b, x, rtol=1e-6, info=False)
+        ts = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.solve(ctx, s, fac, b, x, rtol=1e-6, info=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        info = h.solve(ctx, s, fac, b, x, rtol=1e-6, allow=(h.OK, h.NOT_CONVERGED, h.E_BREAKDOWN, h.E_NAN))
+        err = float(torch.linalg.norm(x - xstar) / torch.linalg.norm(xstar))
+        out[label] = {"ms_per_solve": statistics.mean(ts), "iters": info.iters, "status": info.status,
+                      "true_rel_res": info.rel_res_true, "rel_err_vs_fp64_direct": err}
+
+    for label, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        packed = torch.cat([G.flatten(), sig.flatten(), W.flatten()]).to(dt)
+        keep.append(packed)
+        run(h.factors(h.PRE_SVDH, packed, n, leaf, rank), label)
+    gq, gs = _fp8_blocks(torch, G)
+    cq, cs = _fp8_blocks(torch, sig)
+    wq, ws = _fp8_blocks(torch, W.reshape(-1, leaf, rank))
+    packed8 = torch.cat([gq, cq, wq])
+    sc8 = torch.cat([gs, cs, ws]).cuda()
+    keep += [packed8, sc8]
+    run(h.factors(h.PRE_SVDH, packed8, n, leaf, rank, sc8), "fp8e4m3")
+    jac = h.Factors()
+    jac.kind = h.PRE_JACOBI
+    run(jac, "jacobi")
+    line = {"metric": "ms/solve and iterations by apply precision, N=16384 2D 128x128, SVD-H leaf 64 "
+                      "rank 32, rtol 1e-6", "value": out["bf16"]["ms_per_solve"], "unit": "ms/solve",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["bf16"]["ms_per_solve"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "precision sweep: discs2d_16384 seed 0 (20 discs 1:100), SVD-H from the "
+                                   "dense FP64 inverse on the device (torch), apply FP32/BF16/FP8",
+                       "l2": "flushed (256 MiB write) before every solve, outside the timing",
+                       "svdh_build_seconds": build_s},
+            "sweep": out}
+    print(json.dumps(line), flush=True)
+
+
+def bench_batch(args, h, torch, np, inputs, w, wsrc):
+    """64 ragged systems (N uniform over {1024 ... 16384}, 2D and 3D alternating, 1:100): learned-H
+    inference per grid shape plus one hmpcg_solve_batch, captured as one CUDA graph; Jacobi batch
+    beside it.  A step is one whole batch."""
+    count = 64
+    dims = inputs.batch_mixed_dims(7, count)
+    frames = []
+    for i, d in enumerate(dims):
+        n = int(np.prod(d))
+        frames.append(dict(dims=d, n=n, rho=inputs.density_for_dims(7000 + i, d), b=inputs.rhs(7000 + i, n)))
+    groups = {}
+    for i, fr in enumerate(frames):
+        groups.setdefault(tuple(fr["dims"]), []).append(i)
+    gmax = max(len(v) for v in groups.values())
+    ctx = h.Context(max_n=16384, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
+                    max_batch=gmax, weights=w)
+    systems, bs, xs = [], [], []
+    for fr in frames:
+        s = h.System(fr["dims"])
+        h.assemble(torch.from_numpy(fr["rho"]).cuda(), s)
+        systems.append(s)
+        bs.append(torch.from_numpy(fr["b"]).cuda())
+        xs.append(torch.zeros(fr["n"], dtype=torch.float64, device="cuda"))
+    facs = [None] * count
+    gbufs = {}
+    for key, ids in groups.items():
+        n = frames[ids[0]]["n"]
+        P = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+        buf = torch.empty(len(ids) * P, dtype=torch.bfloat16, device="cuda")
+        gbufs[key] = buf
+        for j, i in enumerate(ids):
+            facs[i] = h.factors(h.PRE_LEARNED, buf[j * P:(j + 1) * P], n, 64, 16)
+    jac = h.Factors()
+    jac.kind = h.PRE_JACOBI
+    jacs = [jac] * count
+
+    def infer_all():
+        for key, ids in groups.items():
+            h.infer_factors(ctx, [systems[i] for i in ids], gbufs[key])
+
+    infer_all()
+    csz = h.autotune_batch(ctx, systems, facs, bs, xs, rtol=1e-6)
+    h.autotune_batch(ctx, systems, jacs, bs, xs, rtol=1e-6)
+    allow = (h.OK, h.NOT_CONVERGED, h.E_BREAKDOWN, h.E_NAN)
+
+    def learned_body():
+        infer_all()
+        h.solve_batch(ctx, systems, facs, bs, xs, rtol=1e-6, info=False, allow=allow, fallback=True)
+
+    def jacobi_body():
+        h.solve_batch(ctx, systems, jacs, bs, xs, rtol=1e-6, info=False, allow=allow)
+
+    graphs = {}
+    for name, fn in (("learned", learned_body), ("jacobi", jacobi_body)):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            fn()
+        graphs[name] = g
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(g):
+        for _ in range(args.warmup):
+            g.replay()
+        ts = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    clk = ClockSampler()
+    clk.start()
+    ms_l = timed(graphs["learned"])
+    ms_j = timed(graphs["jacobi"])
+    clocks = clk.stop()
+    infer_all()
+    inf_l = h.solve_batch(ctx, systems, facs, bs, xs, rtol=1e-6, allow=allow, fallback=True)
+    inf_j = h.solve_batch(ctx, systems, jacs, bs, xs, rtol=1e-6, allow=allow)
+    per = [{"n": fr["n"], "dims": list(fr["dims"]), "cluster": c, "iters_learned": a.iters, "status_learned": a.status,
+            "fallback": a.fallback, "iters_jacobi": j.iters, "status_jacobi": j.status}
+           for fr, c, a, j in zip(frames, csz, inf_l, inf_j)]
+    ok_l = sum(1 for a in inf_l if a.status == h.OK)
+    line = {"metric": "solves/s, 64 ragged systems N in {1024..16384} 2D/3D 1:100, learned-H (infer + PCG) "
+                      "to rtol 1e-6", "value": count / (ms_l * 1e-3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "batch of 64 (inputs.batch_mixed_dims seed 7), one CUDA graph: inference "
+                                   "per grid shape + hmpcg_solve_batch (persistent cluster kernels, tuned "
+                                   "cluster sizes, Jacobi fallback on breakdown)", "weights": wsrc,
+                       "l2": "flushed (256 MiB write) before every batch, outside the timing"},
+            "jacobi": {"solves_per_s": count / (ms_j * 1e-3), "ms_per_batch": ms_j,
+                       "converged": sum(1 for j in inf_j if j.status == h.OK)},
+            "learned_converged": ok_l, "jacobi_fallbacks": sum(1 for a in inf_l if a.fallback),
+            "iters_mean": {"learned": statistics.mean(a.iters for a in inf_l),
+                           "jacobi": statistics.mean(j.iters for j in inf_j)},
+            "clocks": clocks, "systems": per}
+    print(json.dumps(line), flush=True)
 
 
 def _cpu_baseline():

@@ -102,6 +102,10 @@ typedef struct {
   double rtol;            /* stop when ||r_k|| / ||r_0|| <= rtol (Supp. A)     */
   int32_t max_iter;       /* <= 0: 10 N                                       */
   int32_t recompute_every;/* true-residual replacement period, 0 = never       */
+  int32_t fallback;       /* hmpcg_solve_batch with H-matrix factors: 1 = a
+                             system whose solve breaks down (E_BREAKDOWN or
+                             E_NAN) is solved again from x0 = 0 with Jacobi on
+                             the same cluster; 0 = report the failure        */
 } hmpcg_solve_opts;
 
 typedef struct {
@@ -109,6 +113,10 @@ typedef struct {
   int32_t status;         /* hmpcg_status of the solve                        */
   double rel_res_true;    /* ||b - A x||_2 / ||b||_2, FP64, at exit           */
   float ms_solve;         /* device time of the solve (CUDA events)           */
+  int32_t fallback;       /* 1: the H-matrix attempt broke down and the system
+                             was solved again with Jacobi; status and
+                             rel_res_true describe that solve, iters counts
+                             the A p products of both attempts             */
 } hmpcg_solve_info;
 
 /* ------------------------------------------------------------------ context */

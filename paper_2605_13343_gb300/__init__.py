@@ -48,12 +48,13 @@ class Factors(C.Structure):
 
 
 class SolveOpts(C.Structure):
-    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("recompute_every", C.c_int32)]
+    _fields_ = [("rtol", C.c_double), ("max_iter", C.c_int32), ("recompute_every", C.c_int32),
+                ("fallback", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("rel_res_true", C.c_double),
-                ("ms_solve", C.c_float)]
+                ("ms_solve", C.c_float), ("fallback", C.c_int32)]
 
 
 EXPORTS = {
@@ -297,12 +298,12 @@ def _batch_args(systems, facs, bs, xs):
 
 
 def solve_batch(ctx, systems, facs, bs, xs, rtol=1e-6, max_iter=0, recompute_every=10, stream=None,
-                info=True, allow=(OK, NOT_CONVERGED)):
+                info=True, allow=(OK, NOT_CONVERGED), fallback=False):
     """hmpcg_solve_batch: independent systems of uneven size, one persistent cluster launch per
     cluster size.  facs: list of Factors (same kind and dtype) or None.  Returns the list of
     per-system SolveInfo (info=True)."""
     sysarr, facarr, barr, xarr = _batch_args(systems, facs, bs, xs)
-    o = SolveOpts(rtol=rtol, max_iter=max_iter, recompute_every=recompute_every)
+    o = SolveOpts(rtol=rtol, max_iter=max_iter, recompute_every=recompute_every, fallback=int(fallback))
     n = len(systems)
     infos = (SolveInfo * n)() if info else None
     rc = lib().hmpcg_solve_batch(ctx.h, sysarr, facarr, barr, xarr, n, C.byref(o), infos, _stream(stream))

@@ -225,6 +225,7 @@ int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f, cons
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   info->ms_solve = ms;
+  info->fallback = 0;
   if (ds.err) {
     info->iters = ds.iters;
     info->status = ds.err;
@@ -275,6 +276,7 @@ int hmpcg_solve_batch(void* ctx, const hmpcg_system* systems, const hmpcg_factor
   for (int i = 0; i < nsys; ++i) {
     infos[i].iters = ds[i].iters;
     infos[i].ms_solve = ms;
+    infos[i].fallback = ds[i].fallback;
     if (ds[i].err) {
       infos[i].status = ds[i].err;
       infos[i].rel_res_true = -1.0;

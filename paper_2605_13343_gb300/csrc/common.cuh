@@ -19,6 +19,7 @@ struct DevStatus {
   int status;
   double rel_res;   // true relative residual at exit
   double rr_last;   // last recursive ||r||^2 / ||b||^2
+  int fallback;         // batched solves: 1 = Jacobi re-solve after an H-matrix breakdown
 };
 
 // ------------------------------------------------------------------ warp helpers

@@ -185,6 +185,8 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
   N->gpart = (double*)alloc(8 * B * ((n + 63) / 64 + (MH * r + 63) / 64) * d);
   N->etable = (float*)alloc(4 * h * L * L);
   N->err = (int*)alloc(256);
+  for (int i = 0; i < 2 && ok; ++i) ok = cudaStreamCreateWithFlags(&N->side[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 32 && ok; ++i) ok = cudaEventCreateWithFlags(&N->ev[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) { c->net = N; net_destroy(c); return HMPCG_E_NOMEM; }
   if (weights) {
     if (cudaMemcpyAsync(N->w32, weights, 4 * N->nw, cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
@@ -214,6 +216,10 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
 void net_destroy(Ctx* c) {
   if (!c->net) return;
   net_train_release(c->net);
+  for (int i = 0; i < 2; ++i)
+    if (c->net->side[i]) cudaStreamDestroy(c->net->side[i]);
+  for (int i = 0; i < 32; ++i)
+    if (c->net->ev[i]) cudaEventDestroy(c->net->ev[i]);
   for (void* p : c->net->allocs) cudaFree(p);
   delete c->net;
   c->net = nullptr;
@@ -274,8 +280,41 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
   GemmEpi e;
   e.err = N->err;
 
+  // The edge biases of every layer depend only on the system: they run on side stream 0 while
+  // the encoder runs here.  In each layer the diagonal stack runs here and the off-diagonal
+  // stack on side stream 1 (they meet at the highways).  Every fork and join is an event, so
+  // the forward can be captured into a CUDA graph (the branches become parallel nodes).
+  int evi = 0;
+  auto fork = [&](cudaStream_t from, cudaStream_t to) -> int {
+    if (evi >= 32) return HMPCG_E_INVALID;
+    if (cudaEventRecord(N->ev[evi], from) != cudaSuccess) return HMPCG_E_CUDA;
+    if (cudaStreamWaitEvent(to, N->ev[evi], 0) != cudaSuccess) return HMPCG_E_CUDA;
+    ++evi;
+    return HMPCG_OK;
+  };
+  cudaStream_t sE = N->side[0], sO = N->side[1];
+  NET_TRY(fork(st, sE));
+  edge_desc_off_kernel<<<(B * MH * r * r + 127) / 128, 128, 0, sE>>>(sb, N->edesc_off);
+  for (int l = 0; l < cf.n_layers; ++l)
+    for (int s = 0; s < 2; ++s) {
+      StackAct& a = N->act[s][l];
+      const BlockOff& bo = o.blk[s][l];
+      const int T = s == 0 ? Td : To;
+      const int Wn = s == 0 ? L : r;
+      const int nwin = T / Wn;
+      if (s == 0) {
+        edge_table_kernel<<<(Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w, W + bo.e2b, h,
+                                                                 N->etable);
+        edge_bias_diag_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
+                                                                            W + bo.e2b, h, N->etable, a.bias);
+      } else {
+        edge_bias_off_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
+                                                                           W + bo.e2w, W + bo.e2b, h, a.bias);
+      }
+    }
+
   // ---- features and encoder
-  global_stats_kernel<<<B, 256, 0, st>>>(sb, N->gstat);
+  global_stats_kernel<<<B, 1024, 0, st>>>(sb, N->gstat);
   encoder1_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, N->gstat, W + o.enc1w, W + o.enc1b, d, N->feat, N->h1, N->h1pre);
   {
     GemmEpi ep = e; ep.bias = W + o.enc2b; ep.out32 = N->xg[0]; ep.ld32 = d;
@@ -288,49 +327,43 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
   }
   const float* xd0 = N->xg[2];
-  pool_kernel<<<To, 128, 0, st>>>(sb, xd0, d, N->pooled);
-  edge_desc_off_kernel<<<(B * MH * r * r + 127) / 128, 128, 0, st>>>(sb, N->edesc_off);
+  const dim3 pool_blk(d % 128 == 0 ? 128 : 64, kPoolRows);   // channels x row groups
+  pool_kernel<<<To, pool_blk, 0, st>>>(sb, xd0, d, N->pooled);
   float* xcur[2];
   {
     GemmEpi ep = e; ep.bias = W + o.poolb; ep.out32 = N->act[1][0].x_in; ep.ld32 = d;
     NET_TRY(gemm(N->pooled, 2 * d, W16 + o.map16(o.poolw), To, d, 2 * d, ep, st));
   }
   cudaMemcpyAsync(N->act[0][0].x_in, xd0, sizeof(float) * (size_t)Td * d, cudaMemcpyDeviceToDevice, st);
+  NET_TRY(fork(sE, st));   // edge biases ready
 
   for (int l = 0; l < cf.n_layers; ++l) {
+    NET_TRY(fork(st, sO));
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
       const BlockOff& bo = o.blk[s][l];
       const int T = s == 0 ? Td : To;
       const int Wn = s == 0 ? L : r;
-      const int nwin = T / Wn;
-      if (s == 0) {
-        edge_table_kernel<<<(Wn * Wn + 255) / 256, 256, 0, st>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w, W + bo.e2b, h,
-                                                                 N->etable);
-        edge_bias_diag_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, st>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
-                                                                            W + bo.e2b, h, N->etable, a.bias);
-      }
-      else
-        edge_bias_off_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, st>>>(sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
-                                                                           W + bo.e2w, W + bo.e2b, h, a.bias);
-      layernorm_kernel<<<(T + 7) / 8, 256, 0, st>>>(a.x_in, W + bo.ln1g, W + bo.ln1b, T, d, a.y1, nullptr, a.mu1, a.rs1);
+      const cudaStream_t ss = s == 0 ? st : sO;
+      layernorm_kernel<<<(T + 7) / 8, 256, 0, ss>>>(a.x_in, W + bo.ln1g, W + bo.ln1b, T, d, a.y1, nullptr, a.mu1, a.rs1);
       {
         GemmEpi ep = e; ep.bias = W + bo.qkvb; ep.out16 = a.qkv; ep.ld16 = 3 * d;
-        NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, st));
+        NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, ss));
       }
       {
         const dim3 ag((T + 127) / 128, h);
-        if (Wn == 64) attention_kernel<64><<<ag, 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else if (Wn == 32) attention_kernel<32><<<ag, 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else attention_kernel<16><<<ag, 128, 0, st>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        if (Wn == 64) attention_kernel<64><<<ag, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else if (Wn == 32) attention_kernel<32><<<ag, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else attention_kernel<16><<<ag, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
       }
       {
         GemmEpi ep = e; ep.bias = W + bo.outb; ep.resid = a.x_in; ep.ldr = d; ep.out32 = a.x_mid; ep.ld32 = d;
-        NET_TRY(gemm(a.o, d, W16 + o.map16(bo.outw), T, d, d, ep, st));
+        NET_TRY(gemm(a.o, d, W16 + o.map16(bo.outw), T, d, d, ep, ss));
       }
-      layernorm_kernel<<<(T + 7) / 8, 256, 0, st>>>(a.x_mid, W + bo.ln2g, W + bo.ln2b, T, d, a.u, a.y2f, a.mu2, a.rs2,
+      layernorm_kernel<<<(T + 7) / 8, 256, 0, ss>>>(a.x_mid, W + bo.ln2g, W + bo.ln2b, T, d, a.u, a.y2f, a.mu2, a.rs2,
                                                    4 * d);
     }
+    NET_TRY(fork(sO, st));
     // ---- highways (Sec. 4.3) from LN2 outputs of both stacks
     StackAct& ad = N->act[0][l];
     StackAct& ao = N->act[1][l];
@@ -338,26 +371,29 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     {
       const int nch_d = (n + kGChunk - 1) / kGChunk, nch_o = (MH * r + kGChunk - 1) / kGChunk;
       highway_g_partial_kernel<<<dim3(nch_d + nch_o, B), 128, 0, st>>>(sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
-      highway_g_final_kernel<<<B, 128, 0, st>>>(sb, N->gpart, d, nch_d + nch_o, N->gmean);
+      highway_g_final_kernel<<<(B * d + 7) / 8, 256, 0, st>>>(sb, N->gpart, d, nch_d + nch_o, N->gmean);
     }
     concat_g_kernel<<<(Td + 7) / 8, 256, 0, st>>>(N->gmean, n, Td, d, ad.u);
-    highway_off_kernel<<<To, 128, 0, st>>>(sb, N->rhw, N->chw, N->gmean, d, ao.u);
+    highway_off_kernel<<<To, pool_blk, 0, st>>>(sb, N->rhw, N->chw, N->gmean, d, ao.u);
+    NET_TRY(fork(st, sO));
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
       const BlockOff& bo = o.blk[s][l];
       const int T = s == 0 ? Td : To;
+      const cudaStream_t ss = s == 0 ? st : sO;
       float* xout = (l + 1 < cf.n_layers) ? N->act[s][l + 1].x_in : N->x_final[s];
       {
         GemmEpi ep = e; ep.bias = W + bo.f1b; ep.act = 1; ep.out16 = a.hact; ep.ld16 = dm; ep.pre16 = a.hpre; ep.ldpre = dm;
-        NET_TRY(gemm(a.u, 4 * d, W16 + o.map16(bo.f1w), T, dm, 4 * d, ep, st));
+        NET_TRY(gemm(a.u, 4 * d, W16 + o.map16(bo.f1w), T, dm, 4 * d, ep, ss));
       }
       {
         GemmEpi ep = e; ep.bias = W + bo.f2b; ep.resid = a.x_mid; ep.ldr = d; ep.out32 = xout; ep.ld32 = d;
-        NET_TRY(gemm(a.hact, dm, W16 + o.map16(bo.f2w), T, d, dm, ep, st));
+        NET_TRY(gemm(a.hact, dm, W16 + o.map16(bo.f2w), T, d, dm, ep, ss));
       }
     }
   }
   (void)xcur;
+  NET_TRY(fork(sO, st));
   // ---- final norms and heads
   for (int s = 0; s < 2; ++s) {
     const int T = s == 0 ? Td : To;

@@ -116,6 +116,9 @@ struct Net {
   double* gpart;     // per-chunk column sums for the global token
   float* etable;     // edge-bias table of zero-coupling leaf pairs [h][L][L]
   int* err;
+  // forward concurrency: side streams (edge biases; the off-diagonal stack) and fork/join events
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[32] = {};
   // transposed BF16 weights (same padded offsets; matrix (rows x cols) stored cols x rows)
   bf16* w16t;
   struct Train* tr;  // training buffers, allocated on the first train step

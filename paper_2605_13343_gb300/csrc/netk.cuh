@@ -53,43 +53,44 @@ HM_INLINE double block_max_d(double v, double* red, bool is_max) {
   return s;
 }
 
-// d_glob = 12 per-system statistics (FP64, deterministic order).
-__global__ void global_stats_kernel(const SysBatch sb, double* __restrict__ gstat) {
+// d_glob = 12 per-system statistics.  FP64 is slow on this part: each thread keeps FP32
+// partials over its nodes (a handful), the CTA reductions are FP64 in a fixed order.
+__global__ void __launch_bounds__(1024) global_stats_kernel(const SysBatch sb, double* __restrict__ gstat) {
   __shared__ double red[32];
   const int b = blockIdx.x, n = sb.n;
   const double* rho = sb.rho[b];
   const double* dg = sb.diag[b];
-  double slr = 0, sld = 0, mxr = -1e300, mnr = 1e300, mxd = -1e300, mnd = 1e300, nbd = 0;
+  float slr = 0.f, sld = 0.f, mxr = -3e38f, mnr = 3e38f, mxd = -3e38f, mnd = 3e38f, nbd = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double lr = (double)logf((float)rho[i]), ld = (double)logf((float)dg[i]);
+    const float lr = logf((float)rho[i]), ld = logf((float)dg[i]);
     slr += lr; sld += ld;
-    mxr = fmax(mxr, lr); mnr = fmin(mnr, lr); mxd = fmax(mxd, ld); mnd = fmin(mnd, ld);
+    mxr = fmaxf(mxr, lr); mnr = fminf(mnr, lr); mxd = fmaxf(mxd, ld); mnd = fminf(mnd, ld);
     bool bnd = false;
     for (int a = 0; a < sb.ndim; ++a) {
       const unsigned m = sb.mo.mask[a];
       if ((i & m) == m || (i & m) == 0u) bnd = true;
     }
-    nbd += bnd ? 1.0 : 0.0;
+    nbd += bnd ? 1.f : 0.f;
   }
-  slr = block_sum_d(slr, red); sld = block_sum_d(sld, red);
-  mxr = block_max_d(mxr, red, true); mnr = block_max_d(mnr, red, false);
-  mxd = block_max_d(mxd, red, true); mnd = block_max_d(mnd, red, false);
-  nbd = block_sum_d(nbd, red);
-  const double mr = slr / n, md = sld / n, thr = 0.5 * (mxr + mnr);
-  double vr = 0, vd = 0, hv = 0;
+  const double Slr = block_sum_d(slr, red), Sld = block_sum_d(sld, red);
+  const double Mxr = block_max_d(mxr, red, true), Mnr = block_max_d(mnr, red, false);
+  const double Mxd = block_max_d(mxd, red, true), Mnd = block_max_d(mnd, red, false);
+  const double Nbd = block_sum_d(nbd, red);
+  const float mr = (float)(Slr / n), md = (float)(Sld / n), thr = (float)(0.5 * (Mxr + Mnr));
+  float vr = 0.f, vd = 0.f, hv = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double lr = (double)logf((float)rho[i]), ld = (double)logf((float)dg[i]);
-    vr += (lr - mr) * (lr - mr);
-    vd += (ld - md) * (ld - md);
-    hv += lr > thr ? 1.0 : 0.0;
+    const float lr = logf((float)rho[i]), ld = logf((float)dg[i]);
+    vr = fmaf(lr - mr, lr - mr, vr);
+    vd = fmaf(ld - md, ld - md, vd);
+    hv += lr > thr ? 1.f : 0.f;
   }
-  vr = block_sum_d(vr, red); vd = block_sum_d(vd, red); hv = block_sum_d(hv, red);
+  const double Vr = block_sum_d(vr, red), Vd = block_sum_d(vd, red), Hv = block_sum_d(hv, red);
   if (threadIdx.x == 0) {
     double* g = gstat + 12 * b;
     g[0] = log2((double)n) / 16.0;
     g[1] = sb.ndim == 3 ? 1.0 : 0.0;
-    g[2] = mxr; g[3] = mnr; g[4] = mr; g[5] = sqrt(vr / n); g[6] = hv / n;
-    g[7] = md; g[8] = sqrt(vd / n); g[9] = mxd; g[10] = mnd; g[11] = nbd / n;
+    g[2] = Mxr; g[3] = Mnr; g[4] = Slr / n; g[5] = sqrt(Vr / n); g[6] = Hv / n;
+    g[7] = Sld / n; g[8] = sqrt(Vd / n); g[9] = Mxd; g[10] = Mnd; g[11] = Nbd / n;
   }
 }
 
@@ -104,22 +105,23 @@ __global__ void encoder1_kernel(const SysBatch sb, const double* __restrict__ gs
   const double* rho = sb.rho[b];
   const double* dg = sb.diag[b];
   const double* g = gstat + 12 * b;
-  const double ri = rho[i], di = dg[i];
-  double off = 0.0, nb = 0.0, iface = 0.0;
+  const double ri = rho[i];
+  const float di = (float)dg[i];
+  float off = 0.f, nb = 0.f, iface = 0.f;
   float f[kFeat];
   for (int a = 0; a < sb.ndim; ++a) {
     const int jp = sb.mo.plus(i, a);
-    if (jp >= 0) { off += sb.w[b][a][i]; if (rho[jp] != ri) iface = 1.0; } else nb += 1.0;
+    if (jp >= 0) { off += (float)sb.w[b][a][i]; if (rho[jp] != ri) iface = 1.f; } else nb += 1.f;
     const int jm = sb.mo.minus(i, a);
-    if (jm >= 0) { off += sb.w[b][a][jm]; if (rho[jm] != ri) iface = 1.0; } else nb += 1.0;
+    if (jm >= 0) { off += (float)sb.w[b][a][jm]; if (rho[jm] != ri) iface = 1.f; } else nb += 1.f;
   }
   f[0] = logf((float)ri) - (float)g[4];
   for (int a = 0; a < 3; ++a)
     f[1 + a] = a < sb.ndim ? (float)(((double)compact(i, sb.mo.mask[a]) + 0.5) / sb.dims[a] - 0.5) : 0.f;
-  f[4] = (float)(nb / (2 * sb.ndim));
-  f[5] = logf((float)di) - (float)g[7];
-  f[6] = (float)(off / di);
-  f[7] = (float)iface;
+  f[4] = nb / (float)(2 * sb.ndim);
+  f[5] = logf(di) - (float)g[7];
+  f[6] = off / di;
+  f[7] = iface;
   for (int q = 0; q < 12; ++q) f[8 + q] = (float)g[q];
   if (lane < kFeat) feat[(size_t)t * kFeat + lane] = f[lane];
   for (int j = lane; j < d; j += 32) {
@@ -138,15 +140,15 @@ __global__ void prop_kernel(const SysBatch sb, const float* __restrict__ x, int 
   if (t >= sb.B * sb.n) return;
   const int b = t / sb.n, i = t % sb.n;
   const size_t base = (size_t)b * sb.n;
-  const double di = sb.diag[b][i];
+  const float di = (float)sb.diag[b][i];
   int js[6];
   float cs[6];
   int nj = 0;
   for (int a = 0; a < sb.ndim; ++a) {
     const int jp = sb.mo.plus(i, a);
-    if (jp >= 0) { js[nj] = jp; cs[nj++] = (float)(sb.w[b][a][i] / di); }
+    if (jp >= 0) { js[nj] = jp; cs[nj++] = (float)sb.w[b][a][i] / di; }
     const int jm = sb.mo.minus(i, a);
-    if (jm >= 0) { js[nj] = jm; cs[nj++] = (float)(sb.w[b][a][jm] / di); }
+    if (jm >= 0) { js[nj] = jm; cs[nj++] = (float)sb.w[b][a][jm] / di; }
   }
   for (int c = lane; c < d; c += 32) {
     float v = x[(base + i) * d + c];
@@ -157,6 +159,27 @@ __global__ void prop_kernel(const SysBatch sb, const float* __restrict__ x, int 
 
 // Off-diagonal tokens: [mean over row chunk ; mean over column chunk] of the encoder output.
 // One CTA per token, one thread per channel (coalesced over channels).
+// Sums of `ch` consecutive rows (stride d) of two arrays for channel group threadIdx.x, split
+// over blockDim.y row groups and combined in shared memory in a fixed order.  Valid in
+// threadIdx.y == 0.
+constexpr int kPoolRows = 8;
+HM_INLINE void chunk_sums(const float* __restrict__ xr, const float* __restrict__ xc, int ch, int d, int c, float& sr,
+                          float& sc) {
+  __shared__ float red[2][kPoolRows][128];
+  float ar = 0.f, ac = 0.f;
+  for (int q = threadIdx.y; q < ch; q += blockDim.y) {
+    ar += xr[(size_t)q * d + c];
+    ac += xc[(size_t)q * d + c];
+  }
+  red[0][threadIdx.y][threadIdx.x] = ar;
+  red[1][threadIdx.y][threadIdx.x] = ac;
+  __syncthreads();
+  sr = 0.f; sc = 0.f;
+  if (threadIdx.y == 0)
+    for (int y = 0; y < (int)blockDim.y; ++y) { sr += red[0][y][threadIdx.x]; sc += red[1][y][threadIdx.x]; }
+  __syncthreads();
+}
+// One CTA per token: blockDim = (128 channels, kPoolRows row groups); d % 128 == 0.
 __global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ pooled) {
   const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
@@ -164,13 +187,12 @@ __global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int 
   const size_t base = (size_t)b * sb.n;
   const float inv = 1.f / g.ch;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    float sr = 0.f, sc = 0.f;
-    for (int q = 0; q < g.ch; ++q) {
-      sr += x[(base + g.r0 + a * g.ch + q) * d + c];
-      sc += x[(base + g.c0 + a * g.ch + q) * d + c];
+    float sr, sc;
+    chunk_sums(x + (base + g.r0 + (size_t)a * g.ch) * d, x + (base + g.c0 + (size_t)a * g.ch) * d, g.ch, d, c, sr, sc);
+    if (threadIdx.y == 0) {
+      pooled[(size_t)t * 2 * d + c] = __float2bfloat16_rn(sr * inv);
+      pooled[(size_t)t * 2 * d + d + c] = __float2bfloat16_rn(sc * inv);
     }
-    pooled[(size_t)t * 2 * d + c] = __float2bfloat16_rn(sr * inv);
-    pooled[(size_t)t * 2 * d + d + c] = __float2bfloat16_rn(sc * inv);
   }
 }
 
@@ -181,25 +203,27 @@ __global__ void edge_desc_off_kernel(const SysBatch sb, float* __restrict__ e) {
   if (idx >= sb.B * sb.MH * r * r) return;
   const int bb = idx % r, a = (idx / r) % r, m = (idx / (r * r)) % sb.MH, b = idx / (r * r * sb.MH);
   const TileGeo g = tile_geo(sb, m);
-  const double side = pow((double)g.S * sb.L, 1.0 / sb.ndim);
+  // cube root / square root of a power of two: exact in FP32
+  const float side = sb.ndim == 3 ? cbrtf((float)g.S * sb.L) : sqrtf((float)g.S * sb.L);
   const unsigned low = (unsigned)g.ch - 1u;
   const unsigned fr = g.r0 + a * g.ch, fc = g.c0 + bb * g.ch;
   float* out = e + (size_t)idx * 4;
   for (int ax = 0; ax < 3; ++ax) {
     if (ax >= sb.ndim) { out[ax] = 0.f; continue; }
-    const double ext = (double)(1u << __popc(sb.mo.mask[ax] & low));
-    const double cr = compact(fr, sb.mo.mask[ax]) + 0.5 * (ext - 1.0);
-    const double cc = compact(fc, sb.mo.mask[ax]) + 0.5 * (ext - 1.0);
-    out[ax] = (float)((cc - cr) / side);
+    const float ext = (float)(1u << __popc(sb.mo.mask[ax] & low));
+    const float cr = (float)compact(fr, sb.mo.mask[ax]) + 0.5f * (ext - 1.f);
+    const float cc = (float)compact(fc, sb.mo.mask[ax]) + 0.5f * (ext - 1.f);
+    out[ax] = (cc - cr) / side;
   }
   const double* dg = sb.diag[b];
-  double acc = 0.0;
+  float acc = 0.f;
   for (unsigned i = fr; i < fr + g.ch; ++i)
     for (int ax = 0; ax < sb.ndim; ++ax) {
       const int j = sb.mo.plus(i, ax);
-      if (j >= (int)fc && j < (int)(fc + g.ch)) acc += -sb.w[b][ax][i] / sqrt(dg[i] * dg[j]);
+      if (j >= (int)fc && j < (int)(fc + g.ch))
+        acc += -(float)sb.w[b][ax][i] * rsqrtf((float)dg[i] * (float)dg[j]);
     }
-  out[3] = (float)(acc / ((double)g.ch * g.ch));
+  out[3] = acc / ((float)g.ch * (float)g.ch);
 }
 
 // Edge-bias MLP 4 -> 32 (GELU) -> h, weights staged in shared memory.
@@ -241,9 +265,10 @@ HM_INLINE void leaf_desc(const SysBatch& sb, int bsys, int k, int a, int bb, flo
     al = 1.f;
   } else {
     const double* dg = sb.diag[bsys];
+    const float rs = rsqrtf((float)dg[i] * (float)dg[j]);
     for (int ax = 0; ax < sb.ndim; ++ax) {
-      if (sb.mo.plus(i, ax) == (int)j) al = (float)(-sb.w[bsys][ax][i] / sqrt(dg[i] * dg[j]));
-      if (sb.mo.minus(i, ax) == (int)j) al = (float)(-sb.w[bsys][ax][j] / sqrt(dg[i] * dg[j]));
+      if (sb.mo.plus(i, ax) == (int)j) al = -(float)sb.w[bsys][ax][i] * rs;
+      if (sb.mo.minus(i, ax) == (int)j) al = -(float)sb.w[bsys][ax][j] * rs;
     }
   }
   e[3] = al;
@@ -399,9 +424,9 @@ __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ y
   if (t >= sb.B * sb.n) return;
   const int b = t / sb.n, i = t % sb.n;
   const int k = i / sb.L;
-  int toks[32];
+  int toks[24];
   int sides = 0, nl = 0;
-  for (int lev = 1; lev <= sb.levels; ++lev) {
+  for (int lev = 1; lev <= sb.levels && lev <= 24; ++lev) {
     const int S = sb.K >> lev;
     const int cl = k / S;
     const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
@@ -411,20 +436,30 @@ __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ y
     if (cl & 1) sides |= 1 << nl;
     ++nl;
   }
-  const int nr = 1 + (nl - __popc(sides)), nc = 1 + __popc(sides);
-  for (int c = lane; c < d; c += 32) {
-    const float y = yd[(size_t)t * d + c];
-    float rs = y, cs = y;
-    for (int q = 0; q < nl; ++q) {
-      const float v = yo[(size_t)toks[q] * d + c];
-      if ((sides >> q) & 1) cs += v; else rs += v;
+  const float inr = 1.f / (float)(1 + (nl - __popc(sides))), inc = 1.f / (float)(1 + __popc(sides));
+  // 4 channels per lane per pass; every level's load issued before the sums
+  for (int c = 4 * lane; c < d; c += 128) {
+    const float4 y = *reinterpret_cast<const float4*>(yd + (size_t)t * d + c);
+    float4 v[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q)
+      v[q] = q < nl ? *reinterpret_cast<const float4*>(yo + (size_t)toks[q] * d + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 rs = y, cs = y;
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+      const bool col = (sides >> q) & 1;      // levels past nl hold zeros
+      rs.x += col ? 0.f : v[q].x; rs.y += col ? 0.f : v[q].y; rs.z += col ? 0.f : v[q].z; rs.w += col ? 0.f : v[q].w;
+      cs.x += col ? v[q].x : 0.f; cs.y += col ? v[q].y : 0.f; cs.z += col ? v[q].z : 0.f; cs.w += col ? v[q].w : 0.f;
     }
-    rs /= (float)nr;
-    cs /= (float)nc;
-    rhw[(size_t)t * d + c] = rs;
-    chw[(size_t)t * d + c] = cs;
-    ud[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(rs);
-    ud[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(cs);
+    rs.x *= inr; rs.y *= inr; rs.z *= inr; rs.w *= inr;
+    cs.x *= inc; cs.y *= inc; cs.z *= inc; cs.w *= inc;
+    *reinterpret_cast<float4*>(rhw + (size_t)t * d + c) = rs;
+    *reinterpret_cast<float4*>(chw + (size_t)t * d + c) = cs;
+    bf16* u = ud + (size_t)t * 4 * d;
+    u[d + c] = __float2bfloat16_rn(rs.x); u[d + c + 1] = __float2bfloat16_rn(rs.y);
+    u[d + c + 2] = __float2bfloat16_rn(rs.z); u[d + c + 3] = __float2bfloat16_rn(rs.w);
+    u[2 * d + c] = __float2bfloat16_rn(cs.x); u[2 * d + c + 1] = __float2bfloat16_rn(cs.y);
+    u[2 * d + c + 2] = __float2bfloat16_rn(cs.z); u[2 * d + c + 3] = __float2bfloat16_rn(cs.w);
   }
 }
 
@@ -440,19 +475,30 @@ __global__ void highway_g_partial_kernel(const SysBatch sb, const float* __restr
   if (ch < nch_d) { src = yd + (size_t)b * sb.n * d; t0 = ch * kGChunk; t1 = min(sb.n, t0 + kGChunk); }
   else { src = yo + (size_t)b * no * d; t0 = (ch - nch_d) * kGChunk; t1 = min(no, t0 + kGChunk); }
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    double s = 0.0;
-    for (int t = t0; t < t1; ++t) s += src[(size_t)t * d + c];
-    part[((size_t)b * (nch_d + nch_o) + ch) * d + c] = s;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int t = t0;
+    for (; t + 3 < t1; t += 4) {
+      s0 += src[(size_t)t * d + c];
+      s1 += src[(size_t)(t + 1) * d + c];
+      s2 += src[(size_t)(t + 2) * d + c];
+      s3 += src[(size_t)(t + 3) * d + c];
+    }
+    for (; t < t1; ++t) s0 += src[(size_t)t * d + c];
+    part[((size_t)b * (nch_d + nch_o) + ch) * d + c] = (double)((s0 + s1) + (s2 + s3));
   }
 }
+// One warp per (system, channel): lanes take chunks q = lane, lane + 32, ..., then a fixed
+// shuffle tree.
 __global__ void highway_g_final_kernel(const SysBatch sb, const double* __restrict__ part, int d, int nch,
                                        float* __restrict__ g) {
-  const int b = blockIdx.x;
-  for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < nch; ++q) s += part[((size_t)b * nch + q) * d + c];
-    g[(size_t)b * d + c] = (float)(s / (sb.n + sb.MH * sb.r));
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (wid >= sb.B * d) return;
+  const int b = wid / d, c = wid % d;
+  float s = 0.f;
+  for (int q = lane; q < nch; q += 32) s += (float)part[((size_t)b * nch + q) * d + c];
+  s = warp_sum(s);
+  if (lane == 0) g[(size_t)b * d + c] = s / (float)(sb.n + sb.MH * sb.r);
 }
 
 __global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d, bf16* __restrict__ u) {
@@ -473,14 +519,14 @@ __global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ 
   const size_t base = (size_t)b * sb.n;
   const float inv = 1.f / gg.ch;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    float sr = 0.f, sc = 0.f;
-    for (int q = 0; q < gg.ch; ++q) {
-      sr += rhw[(base + gg.r0 + a * gg.ch + q) * d + c];
-      sc += chw[(base + gg.c0 + a * gg.ch + q) * d + c];
+    float sr, sc;
+    chunk_sums(rhw + (base + gg.r0 + (size_t)a * gg.ch) * d, chw + (base + gg.c0 + (size_t)a * gg.ch) * d, gg.ch, d, c,
+               sr, sc);
+    if (threadIdx.y == 0) {
+      uo[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(sr * inv);
+      uo[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(sc * inv);
+      uo[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
     }
-    uo[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(sr * inv);
-    uo[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(sc * inv);
-    uo[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
   }
 }
 

@@ -59,6 +59,7 @@ struct CParams {
   int max_iter, recompute;
   int C, npc, lpc, tpc;   // CTAs, nodes / leaves / tiles per CTA
   int fsm;                // 1: the CTA's factor share is copied to shared memory; 0: read from L2
+  int fallback;           // batched H-matrix solves: re-solve with Jacobi after a breakdown
 };
 
 // Shared-memory carve-up (byte offsets), identical in every CTA.
@@ -602,6 +603,24 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_batch_kernel(const _
     cluster_sync();   // every CTA has read the pick before rank 0 takes the next one
     if (i >= B.nsys) break;
     pcg_cluster_body<T, PRE>(B.p[i]);
+    if (PRE == CPRE_HMAT && B.p[i].fallback) {
+      // rank 0 wrote the status before the body's last cluster barrier
+      volatile DevStatus* ds = B.p[i].st;
+      const int stt = ds->status, first = ds->iters;
+      if (ds->err == 0 && (stt == HMPCG_E_BREAKDOWN || stt == HMPCG_E_NAN)) {
+        CParams<float> J;
+        J.s = B.p[i].s;
+        memset(&J.f, 0, sizeof(J.f));
+        J.b = B.p[i].b; J.x = B.p[i].x; J.st = B.p[i].st;
+        J.rtol = B.p[i].rtol; J.max_iter = B.p[i].max_iter; J.recompute = B.p[i].recompute;
+        J.C = B.p[i].C; J.npc = B.p[i].npc; J.lpc = 0; J.tpc = 0; J.fsm = 0; J.fallback = 0;
+        pcg_cluster_body<float, CPRE_JACOBI>(J);
+        if (cl_rank() == 0 && threadIdx.x == 0) {
+          ds->fallback = 1;
+          ds->iters = ds->iters + first;
+        }
+      }
+    }
   }
 }
 
@@ -649,12 +668,18 @@ static void set_opts(CParams<T>& P, const hmpcg_system* sys, const hmpcg_solve_o
 // of clusters that can be resident at once (0 = shape not launchable).
 static int cluster_capacity(const void* kern, int C, size_t smem) {
   static std::map<std::tuple<const void*, int, size_t>, int> cap;
+  static std::map<const void*, size_t> smem_set;   // the kernel's shared-memory limit only grows
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
+  bool ok = true;
+  size_t& lim = smem_set[kern];
+  if (smem > lim) {
+    ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    if (ok) lim = smem;
+  }
   const auto key = std::make_tuple(kern, C, smem);
   auto it = cap.find(key);
-  if (it != cap.end()) return it->second;
-  bool ok = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+  if (it != cap.end()) return ok ? it->second : 0;
   if (ok && C > 8) ok = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
   int nclusters = 0;
   if (ok) {
@@ -685,6 +710,7 @@ static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv,
       CParams<T> P;
       size_t smem = 0;
       if (!plan_cluster<T, PRE>(sys, fv, C, fsm != 0, P, smem)) continue;
+      P.fallback = 0;
       auto kern = pcg_cluster_kernel<T, PRE>;
       if (cluster_capacity((const void*)kern, C, smem) < 1) continue;
       P.b = b; P.x = x; P.st = c->s.st;
@@ -766,6 +792,7 @@ static int run_batch_typed(Ctx* c, const hmpcg_system* sys, const hmpcg_factors*
     if (!ok && PRE == CPRE_HMAT) ok = plan_cluster<T, PRE>(&sys[i], &fv[i], C, false, plan[i], sm);
     if (!ok) return HMPCG_E_SHAPE;
     plan[i].b = b[i]; plan[i].x = x[i]; plan[i].st = c->bst + i;
+    plan[i].fallback = (PRE == CPRE_HMAT && o && o->fallback) ? 1 : 0;
     set_opts(plan[i], &sys[i], o);
     groups[C].push_back(i);
     smem_of[C] = std::max(smem_of[C], sm);

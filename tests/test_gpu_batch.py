@@ -119,6 +119,37 @@ def test_batch_learned_ragged_and_autotune():
     ctx.close()
 
 
+def test_batch_fallback_to_jacobi():
+    """A system whose H-matrix preconditioner is negative definite breaks down at once; with
+    fallback on it is solved again with Jacobi on the same cluster (iteration count of the
+    oracle's Jacobi PCG), the SPD neighbour in the same batch is untouched."""
+    batch = _batch(2, 9)
+    ctx = h.Context(max_n=16384, leaf=64, rank=16)
+    systems, bs, xs = _upload(batch)
+    facs, keep, deqs = [], [], []
+    for i, fr in enumerate(batch):
+        ref = grid.assemble(fr["rho"], fr["dims"])
+        f = _spd_learned(ref, 70 + i)
+        packed = torch.from_numpy(hmatrix.pack(f).astype(np.float32)).to(torch.bfloat16).cuda()
+        if i == 0:
+            packed = -packed
+        keep.append(packed)
+        facs.append(h.factors(h.PRE_LEARNED, packed, fr["n"], 64, 16))
+        deqs.append(hmatrix.unpack(packed.double().cpu().numpy(), fr["n"], 64, 16, "learned"))
+    infos = h.solve_batch(ctx, systems, facs, bs, xs, rtol=1e-6, allow=(h.OK, h.E_BREAKDOWN))
+    assert infos[0].status == h.E_BREAKDOWN and infos[0].fallback == 0
+    for x in xs:
+        x.zero_()
+    infos = h.solve_batch(ctx, systems, facs, bs, xs, rtol=1e-6, fallback=True)
+    out, a = _oracle(batch[0], lambda ref: (lambda v: v / ref["diag"]))
+    assert infos[0].fallback == 1       # broke down before its first iteration: iters are Jacobi's
+    _check(batch[0], infos[0], xs[0], out, a)
+    out, a = _oracle(batch[1], lambda ref, deq=deqs[1]: (lambda v: hmatrix.apply(deq, v)))
+    assert infos[1].fallback == 0
+    _check(batch[1], infos[1], xs[1], out, a)
+    ctx.close()
+
+
 def test_batch_matches_single_solves_and_rejects_oversize():
     """A batch entry equals the single-system cluster solve of the same system (same kernel
     body, same cluster size 16 for N = 8192 when tuned so); an N the cluster shapes cannot
