@@ -294,7 +294,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
   };
   cudaStream_t sE = N->side[0], sO = N->side[1];
   NET_TRY(fork(st, sE));
-  edge_desc_off_kernel<<<(B * MH * r * r + 127) / 128, 128, 0, sE>>>(sb, N->edesc_off);
+  edge_desc_off_kernel<<<(B * MH * r * r + 7) / 8, 256, 0, sE>>>(sb, N->edesc_off);
   for (int l = 0; l < cf.n_layers; ++l)
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
@@ -305,8 +305,11 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
       if (s == 0) {
         edge_table_kernel<<<(Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w, W + bo.e2b, h,
                                                                  N->etable);
-        edge_bias_diag_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
-                                                                            W + bo.e2b, h, N->etable, a.bias);
+        const int64_t nq = (int64_t)nwin * h * Wn * Wn / 4;
+        edge_bias_fill_kernel<<<(int)std::min<int64_t>((nq + 255) / 256, 8 * N->num_sms), 256, 0, sE>>>(sb, h, N->etable,
+                                                                                                     a.bias);
+        edge_bias_nbr_kernel<<<(nwin * Wn * 2 * sb.ndim + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
+                                                                                    W + bo.e2b, h, a.bias);
       } else {
         edge_bias_off_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
                                                                            W + bo.e2w, W + bo.e2b, h, a.bias);

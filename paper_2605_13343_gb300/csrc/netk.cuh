@@ -31,32 +31,45 @@ HM_INLINE TileGeo tile_geo(const SysBatch& sb, int m) {
   return g;
 }
 
-HM_INLINE double block_sum_d(double v, double* red) {
-  v = warp_sum(v);
+// CTA reductions of one value per thread, result in every thread.  The per-warp results are
+// combined by warp 0 alone (FP64 is slow on this part) in a fixed order.  red: >= 33 doubles.
+HM_INLINE double block_sum_d(float v, double* red) {
+  v = warp_sum(v);                      // FP32 within a warp, FP64 across warps
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-  return s;
-}
-HM_INLINE double block_max_d(double v, double* red, bool is_max) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const double u = __shfl_xor_sync(0xffffffffu, v, o);
-    v = is_max ? fmax(v, u) : fmin(v, u);
+  if (threadIdx.x < 32) {
+    double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) red[32] = s;
   }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  return red[32];
+}
+HM_INLINE double block_max_d(float v, double* red, bool is_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = is_max ? fmaxf(v, u) : fminf(v, u);
+  }
   __syncthreads();
-  double s = red[0];
-  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) s = is_max ? fmax(s, red[i]) : fmin(s, red[i]);
-  return s;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = red[threadIdx.x < (blockDim.x >> 5) ? threadIdx.x : 0];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, s, o);
+      s = is_max ? fmax(s, u) : fmin(s, u);
+    }
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
 }
 
 // d_glob = 12 per-system statistics.  FP64 is slow on this part: each thread keeps FP32
 // partials over its nodes (a handful), the CTA reductions are FP64 in a fixed order.
 __global__ void __launch_bounds__(1024) global_stats_kernel(const SysBatch sb, double* __restrict__ gstat) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   const int b = blockIdx.x, n = sb.n;
   const double* rho = sb.rho[b];
   const double* dg = sb.diag[b];
@@ -196,34 +209,41 @@ __global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int 
   }
 }
 
-// Tile edge descriptors: chunk-centroid offset / tile side, mean normalised coupling.
+// Tile edge descriptors: chunk-centroid offset / tile side, mean normalised coupling.  One
+// warp per (tile, row chunk, column chunk); the lanes split the row chunk's nodes.
 __global__ void edge_desc_off_kernel(const SysBatch sb, float* __restrict__ e) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + warp;
   const int r = sb.r;
   if (idx >= sb.B * sb.MH * r * r) return;
   const int bb = idx % r, a = (idx / r) % r, m = (idx / (r * r)) % sb.MH, b = idx / (r * r * sb.MH);
   const TileGeo g = tile_geo(sb, m);
-  // cube root / square root of a power of two: exact in FP32
-  const float side = sb.ndim == 3 ? cbrtf((float)g.S * sb.L) : sqrtf((float)g.S * sb.L);
-  const unsigned low = (unsigned)g.ch - 1u;
   const unsigned fr = g.r0 + a * g.ch, fc = g.c0 + bb * g.ch;
   float* out = e + (size_t)idx * 4;
-  for (int ax = 0; ax < 3; ++ax) {
-    if (ax >= sb.ndim) { out[ax] = 0.f; continue; }
-    const float ext = (float)(1u << __popc(sb.mo.mask[ax] & low));
-    const float cr = (float)compact(fr, sb.mo.mask[ax]) + 0.5f * (ext - 1.f);
-    const float cc = (float)compact(fc, sb.mo.mask[ax]) + 0.5f * (ext - 1.f);
-    out[ax] = (cc - cr) / side;
+  if (lane < 3) {
+    // cube root / square root of a power of two: exact in FP32
+    const float side = sb.ndim == 3 ? cbrtf((float)g.S * sb.L) : sqrtf((float)g.S * sb.L);
+    const unsigned low = (unsigned)g.ch - 1u;
+    const int ax = lane;
+    float v = 0.f;
+    if (ax < sb.ndim) {
+      const float ext = (float)(1u << __popc(sb.mo.mask[ax] & low));
+      const float cr = (float)compact(fr, sb.mo.mask[ax]) + 0.5f * (ext - 1.f);
+      const float cc = (float)compact(fc, sb.mo.mask[ax]) + 0.5f * (ext - 1.f);
+      v = (cc - cr) / side;
+    }
+    out[ax] = v;
   }
   const double* dg = sb.diag[b];
   float acc = 0.f;
-  for (unsigned i = fr; i < fr + g.ch; ++i)
+  for (unsigned i = fr + lane; i < fr + g.ch; i += 32)
     for (int ax = 0; ax < sb.ndim; ++ax) {
       const int j = sb.mo.plus(i, ax);
       if (j >= (int)fc && j < (int)(fc + g.ch))
         acc += -(float)sb.w[b][ax][i] * rsqrtf((float)dg[i] * (float)dg[j]);
     }
-  out[3] = acc / ((float)g.ch * (float)g.ch);
+  acc = warp_sum(acc);
+  if (lane == 0) out[3] = acc / ((float)g.ch * (float)g.ch);
 }
 
 // Edge-bias MLP 4 -> 32 (GELU) -> h, weights staged in shared memory.
@@ -293,24 +313,31 @@ __global__ void edge_table_kernel(const SysBatch sb, const float* w1, const floa
   for (int hh = 0; hh < h; ++hh) table[((size_t)hh * L + a) * L + bb] = out[hh];
 }
 
-__global__ void edge_bias_diag_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
-                                      const float* b2, int h, const float* __restrict__ table,
+// Diagonal-window biases in two passes: every pair takes the table entry of its in-leaf
+// positions (16-byte copies), then the stencil-neighbour pairs (at most 2 ndim per row) are
+// overwritten with the MLP of their own descriptor.
+__global__ void edge_bias_fill_kernel(const SysBatch sb, int h, const float* __restrict__ table,
                                       float* __restrict__ bias) {
+  const int L2q = sb.L * sb.L / 4;
+  const int64_t total = (int64_t)sb.B * sb.K * h * L2q;
+  const float4* t4 = reinterpret_cast<const float4*>(table);
+  float4* b4 = reinterpret_cast<float4*>(bias);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+    b4[q] = t4[q % ((int64_t)h * L2q)];
+}
+__global__ void edge_bias_nbr_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
+                                     const float* b2, int h, float* __restrict__ bias) {
   __shared__ EdgeMlp s;
   load_edge_mlp(s, w1, b1, w2, b2, h);
-  const int L = sb.L;
+  const int L = sb.L, nd = 2 * sb.ndim;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= sb.B * sb.K * L * L) return;
-  const int bb = idx % L, a = (idx / L) % L, win = idx / (L * L);
+  if (idx >= sb.B * sb.K * L * nd) return;
+  const int dir = idx % nd, a = (idx / nd) % L, win = idx / (nd * L);
   const int k = win % sb.K, bsys = win / sb.K;
-  const unsigned i = k * L + a, j = k * L + bb;
-  bool nbr = false;
-  for (int ax = 0; ax < sb.ndim; ++ax) nbr |= sb.mo.plus(i, ax) == (int)j || sb.mo.minus(i, ax) == (int)j;
-  if (!nbr) {
-    for (int hh = 0; hh < h; ++hh)
-      bias[(((size_t)win * h + hh) * L + a) * L + bb] = table[((size_t)hh * L + a) * L + bb];
-    return;
-  }
+  const int i = k * L + a;
+  const int j = (dir & 1) ? sb.mo.minus(i, dir >> 1) : sb.mo.plus(i, dir >> 1);
+  if (j < 0 || j / L != k) return;
+  const int bb = j - k * L;
   float e[4], out[8];
   leaf_desc(sb, bsys, k, a, bb, e);
   edge_mlp(s, e, h, out);
