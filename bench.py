@@ -132,7 +132,7 @@ def main():
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2605_13343_gb300", "weights",
                                                       "hmpcg_d128_l4.f32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384"],
+    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192"],
                     help="frame8192: the per-frame headline; batch64: 64 ragged systems in one graph; "
                          "precision16384: FP32/BF16/FP8 apply sweep with SVD-H factors")
     args = ap.parse_args()
@@ -162,6 +162,8 @@ def main():
         wsrc = "seeded init"
     if args.workload == "precision16384":
         return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind)
+    if args.workload == "svdh8192":
+        return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind, family=FAMILY)
     if args.workload == "batch64":
         return bench_batch(args, h, torch, np, inputs, w, wsrc)
     n = 8192
@@ -290,22 +292,28 @@ def main():
         frame_e2e(k)
     t_e2e = timed(frame_e2e, ks)
 
-    # launches per frame (one profiled, untimed frame through direct launches)
+    # launches per frame (one profiled, untimed frame through direct launches): device-side
+    # kernel records of our library (memcpy / memset records excluded)
     launches = None
     try:
         from torch.profiler import profile, ProfilerActivity
         with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            slot_rho.copy_(rho_dev[0]); slot_b.copy_(bs[0])
+            torch.cuda.synchronize()
             body()
             torch.cuda.synchronize()
         cnt = 0
-        for ev in prof.key_averages():
-            nm = ev.key
-            if "Memcpy" in nm or "Memset" in nm or "memcpy" in nm or "memset" in nm:
+        for ev in prof.events():
+            nm = ev.name
+            if getattr(ev, "device_type", None) != torch.autograd.DeviceType.CUDA:
                 continue
-            if getattr(ev, "self_device_time_total", 0) > 0 or getattr(ev, "device_time_total", 0) > 0:
-                cnt += ev.count
+            if "hm::" in nm or "hmpcg" in nm:
+                cnt += 1
         launches = cnt or None
-    except Exception:
+        if not launches:
+            print("gpu_launches: profiler saw no kernels of the library", file=sys.stderr)
+    except Exception as exc:
+        print(f"gpu_launches: profiler failed: {exc}", file=sys.stderr)
         launches = None
 
     # roofline of the dominant kernel: the persistent PCG kernel (solve share of the frame)
@@ -414,12 +422,13 @@ def _fp8_blocks(torch, blocks):
     return q.flatten(), sc.to(torch.float32)
 
 
-def bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind):
-    """Apply precision sweep: 2D 128x128, 20 discs of contrast 100, SVD-H leaf 64 rank 32;
-    PCG with the apply in FP32, BF16 and FP8-E4M3 (per-block scales), FP64 scalars, true
-    residual every 10 iterations.  A step is one solve."""
-    fr = inputs.frame("discs2d_16384", 0)
-    n, leaf, rank = 16384, 64, 32
+def bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind, family="discs2d_16384"):
+    """SVD-H PCG by apply precision.  discs2d_16384 (the precision sweep): 2D 128x128, 20 discs
+    of contrast 100, leaf 64, rank 32; spheres3d_8192: the per-frame workload's grid with SVD-H
+    leaf 64, rank 16.  PCG with the apply in FP32, BF16 and FP8-E4M3 (per-block scales), FP64
+    scalars, true residual every 10 iterations.  A step is one solve."""
+    fr = inputs.frame(family, 0)
+    n, leaf, rank = int(np.prod(fr["dims"])), fr["leaf"], fr["rank"]
     s = h.System(fr["dims"])
     h.assemble(torch.from_numpy(fr["rho"]).cuda(), s)
     b = torch.from_numpy(fr["b"]).cuda()
@@ -470,13 +479,13 @@ def bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind):
     jac = h.Factors()
     jac.kind = h.PRE_JACOBI
     run(jac, "jacobi")
-    line = {"metric": "ms/solve and iterations by apply precision, N=16384 2D 128x128, SVD-H leaf 64 "
-                      "rank 32, rtol 1e-6", "value": out["bf16"]["ms_per_solve"], "unit": "ms/solve",
+    line = {"metric": f"ms/solve and iterations by apply precision, {family} (N={n}), SVD-H leaf {leaf} "
+                      f"rank {rank}, rtol 1e-6", "value": out["bf16"]["ms_per_solve"], "unit": "ms/solve",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["bf16"]["ms_per_solve"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
-            "config": {"workload": "precision sweep: discs2d_16384 seed 0 (20 discs 1:100), SVD-H from the "
-                                   "dense FP64 inverse on the device (torch), apply FP32/BF16/FP8",
+            "config": {"workload": f"SVD-H precision sweep: {family} seed 0, SVD-H from the dense FP64 inverse "
+                                   "on the device (torch, setup outside the timing), apply FP32/BF16/FP8",
                        "l2": "flushed (256 MiB write) before every solve, outside the timing",
                        "svdh_build_seconds": build_s},
             "sweep": out}

@@ -354,10 +354,10 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
         NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, ss));
       }
       {
-        const dim3 ag((T + 127) / 128, h);
-        if (Wn == 64) attention_kernel<64><<<ag, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else if (Wn == 32) attention_kernel<32><<<ag, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else attention_kernel<16><<<ag, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        const int nwh = (T / Wn) * h;   // window-heads; a CTA takes 64 / Wn of them
+        if (Wn == 64) attention_kernel<64><<<nwh, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else if (Wn == 32) attention_kernel<32><<<(nwh + 1) / 2, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else attention_kernel<16><<<(nwh + 3) / 4, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
       }
       {
         GemmEpi ep = e; ep.bias = W + bo.outb; ep.resid = a.x_in; ep.ldr = d; ep.out32 = a.x_mid; ep.ld32 = d;

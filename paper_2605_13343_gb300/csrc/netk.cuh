@@ -385,61 +385,138 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
   if (lane == 0) { mu[t] = mean; rs[t] = rstd; }
 }
 
-// Window attention with additive per-head bias; one thread per (query token, head),
-// a 128-token block of whole windows per CTA.  Head dim 32.
+// Window attention on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulators):
+// per (window, head), S = Q K^T / sqrt(32) + bias, softmax by rows, O = P V (P rounded to BF16
+// for the second product).  A warp owns 16 query rows; K and V of the window-head are staged in
+// shared memory (rows padded to 80 bytes: conflict-free 8x8 matrix loads).  lse = max + log(sum)
+// per row for the backward pass.
+HM_INLINE uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+HM_INLINE void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+HM_INLINE void ldsm_x2(uint32_t& r0, uint32_t& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r0), "=r"(r1) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+HM_INLINE void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r0), "=r"(r1) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
 template <int W>
 __global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__ qkv, const float* __restrict__ bias,
                                                         int T, int d, int h, bf16* __restrict__ out,
                                                         float* __restrict__ lse) {
-  __shared__ float ks[128][33];
-  __shared__ float vs[128][33];
-  const int head = blockIdx.y;
-  const int t0 = blockIdx.x * 128;
-  const int t = t0 + threadIdx.x;
-  const int ld = 3 * d;
-  if (t < T) {
-    const bf16* kp = qkv + (size_t)t * ld + d + head * 32;
-    const bf16* vp = qkv + (size_t)t * ld + 2 * d + head * 32;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) { ks[threadIdx.x][c] = __bfloat162float(kp[c]); vs[threadIdx.x][c] = __bfloat162float(vp[c]); }
+  constexpr int WPH = W / 16;      // warps per window-head
+  constexpr int HPC = 4 / WPH;     // window-heads per CTA
+  constexpr int RS = 40;           // shared row stride in BF16 elements (80 bytes)
+  __shared__ __align__(16) bf16 ks[HPC][W][RS];
+  __shared__ __align__(16) bf16 vs[HPC][W][RS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwh = (T / W) * h;
+  const size_t ld = 3 * (size_t)d;
+  for (int q = threadIdx.x; q < HPC * W * 8; q += blockDim.x) {   // 8 x 16 bytes per key row
+    const int slot = q / (W * 8), rem = q % (W * 8), row = rem >> 3, part = rem & 7;
+    const int wh = blockIdx.x * HPC + slot;
+    if (wh >= nwh) continue;
+    const int win = wh / h, head = wh % h;
+    const size_t t = (size_t)win * W + row;
+    const bf16* src = qkv + t * ld + (part < 4 ? d : 2 * d) + head * 32 + (part & 3) * 8;
+    bf16* dst = (part < 4 ? &ks[slot][row][0] : &vs[slot][row][0]) + (part & 3) * 8;
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
   }
   __syncthreads();
-  if (t >= T) return;
-  float q[32];
-  const bf16* qp = qkv + (size_t)t * ld + head * 32;
-  const float scale = 0.17677669529663688f;  // 1 / sqrt(32)
+  const int slot = warp / WPH, rb = warp % WPH;
+  const int wh = blockIdx.x * HPC + slot;
+  if (wh >= nwh) return;
+  const int win = wh / h, head = wh % h;
+  const int a0 = rb * 16 + (lane >> 2), a1 = a0 + 8;      // this thread's two query rows
+  const size_t t0 = (size_t)win * W + a0, t1 = t0 + 8;
+  const int cq = 2 * (lane & 3);
+  uint32_t qa[2][4];
 #pragma unroll
-  for (int c = 0; c < 32; ++c) q[c] = __bfloat162float(qp[c]) * scale;
-  const int win = t / W, a = t % W;
-  const int ws = win * W - t0;
-  const float* bp = bias + (((size_t)win * h + head) * W + a) * W;
-  float s[W];
-  float mx = -1e30f;
-#pragma unroll
-  for (int j = 0; j < W; ++j) {
-    float v = bp[j];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) v = fmaf(q[c], ks[ws + j][c], v);
-    s[j] = v;
-    mx = fmaxf(mx, v);
+  for (int kk = 0; kk < 2; ++kk) {
+    const bf16* q0 = qkv + t0 * ld + head * 32 + 16 * kk + cq;
+    const bf16* q1 = qkv + t1 * ld + head * 32 + 16 * kk + cq;
+    qa[kk][0] = *reinterpret_cast<const uint32_t*>(q0);
+    qa[kk][1] = *reinterpret_cast<const uint32_t*>(q1);
+    qa[kk][2] = *reinterpret_cast<const uint32_t*>(q0 + 8);
+    qa[kk][3] = *reinterpret_cast<const uint32_t*>(q1 + 8);
   }
-  float sum = 0.f;
+  float s[W / 8][4];
 #pragma unroll
-  for (int j = 0; j < W; ++j) { s[j] = __expf(s[j] - mx); sum += s[j]; }
-  const float inv = 1.f / sum;
-  float o[32];
+  for (int j = 0; j < W / 8; ++j) {
+    s[j][0] = s[j][1] = s[j][2] = s[j][3] = 0.f;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) o[c] = 0.f;
-#pragma unroll
-  for (int j = 0; j < W; ++j) {
-    const float p = s[j] * inv;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) o[c] = fmaf(p, vs[ws + j][c], o[c]);
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t b0, b1;
+      ldsm_x2(b0, b1, &ks[slot][8 * j + (lane & 7)][16 * kk + ((lane >> 3) & 1) * 8]);
+      mma_bf16(s[j], qa[kk], b0, b1);
+    }
   }
-  bf16* op = out + (size_t)t * d + head * 32;
+  const float scale = 0.17677669529663688f;   // 1 / sqrt(32)
+  const float* bp0 = bias + (((size_t)win * h + head) * W + a0) * W;
+  const float* bp1 = bp0 + 8 * (size_t)W;
+  float m0 = -3e38f, m1 = -3e38f;
 #pragma unroll
-  for (int c = 0; c < 32; c += 2) *reinterpret_cast<__nv_bfloat162*>(op + c) = __floats2bfloat162_rn(o[c], o[c + 1]);
-  lse[(size_t)t * h + head] = mx + logf(sum);
+  for (int j = 0; j < W / 8; ++j) {
+    const float2 b0 = *reinterpret_cast<const float2*>(bp0 + 8 * j + cq);
+    const float2 b1 = *reinterpret_cast<const float2*>(bp1 + 8 * j + cq);
+    s[j][0] = fmaf(s[j][0], scale, b0.x); s[j][1] = fmaf(s[j][1], scale, b0.y);
+    s[j][2] = fmaf(s[j][2], scale, b1.x); s[j][3] = fmaf(s[j][3], scale, b1.y);
+    m0 = fmaxf(m0, fmaxf(s[j][0], s[j][1]));
+    m1 = fmaxf(m1, fmaxf(s[j][2], s[j][3]));
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  float l0 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < W / 8; ++j) {
+    s[j][0] = __expf(s[j][0] - m0); s[j][1] = __expf(s[j][1] - m0);
+    s[j][2] = __expf(s[j][2] - m1); s[j][3] = __expf(s[j][3] - m1);
+    l0 += s[j][0] + s[j][1];
+    l1 += s[j][2] + s[j][3];
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  float oc[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) oc[nt][0] = oc[nt][1] = oc[nt][2] = oc[nt][3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < W / 16; ++kk) {
+    const uint32_t pa[4] = {pack_bf16(s[2 * kk][0], s[2 * kk][1]), pack_bf16(s[2 * kk][2], s[2 * kk][3]),
+                            pack_bf16(s[2 * kk + 1][0], s[2 * kk + 1][1]), pack_bf16(s[2 * kk + 1][2], s[2 * kk + 1][3])};
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      uint32_t b0, b1;
+      ldsm_x2_t(b0, b1, &vs[slot][16 * kk + (lane & 15)][8 * nt]);
+      mma_bf16(oc[nt], pa, b0, b1);
+    }
+  }
+  const float i0 = 1.f / l0, i1 = 1.f / l1;
+  bf16* o0 = out + t0 * d + head * 32 + cq;
+  bf16* o1 = out + t1 * d + head * 32 + cq;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    *reinterpret_cast<__nv_bfloat162*>(o0 + 8 * nt) = __floats2bfloat162_rn(oc[nt][0] * i0, oc[nt][1] * i0);
+    *reinterpret_cast<__nv_bfloat162*>(o1 + 8 * nt) = __floats2bfloat162_rn(oc[nt][2] * i1, oc[nt][3] * i1);
+  }
+  if ((lane & 3) == 0) {
+    lse[t0 * h + head] = m0 + logf(l0);
+    lse[t1 * h + head] = m1 + logf(l1);
+  }
 }
 
 // Axial highway buffers for the diagonal tokens (mean over the tokens covering each
