@@ -132,7 +132,7 @@ def main():
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2605_13343_gb300", "weights",
                                                       "hmpcg_d128_l4.f32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192"],
+    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192", "bandwidth"],
                     help="frame8192: the per-frame headline; batch64: 64 ragged systems in one graph; "
                          "precision16384: FP32/BF16/FP8 apply sweep with SVD-H factors")
     args = ap.parse_args()
@@ -162,6 +162,8 @@ def main():
         wsrc = "seeded init"
     if args.workload == "precision16384":
         return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind)
+    if args.workload == "bandwidth":
+        return bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind)
     if args.workload == "svdh8192":
         return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind, family=FAMILY)
     if args.workload == "batch64":
@@ -596,6 +598,59 @@ def bench_batch(args, h, torch, np, inputs, w, wsrc):
             "iters_mean": {"learned": statistics.mean(a.iters for a in inf_l),
                            "jacobi": statistics.mean(j.iters for j in inf_j)},
             "clocks": clocks, "systems": per}
+    print(json.dumps(line), flush=True)
+
+
+def bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind):
+    """HBM roofline of the bandwidth-bound kernels at sizes larger than L2: the 7/5-point SpMV
+    (algorithmic bytes 24 N in 3D, 20 N in 2D: x, y, faces, diag in FP32) and the BF16 learned
+    H-apply (2 P + 12 N bytes: the packed factors once, r, z and the diagonal-stage vector).
+    A step is one call; CUDA events around `steps` calls after `warmup` calls."""
+    stream = torch.cuda.current_stream()
+
+    def timeit(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    rows = []
+    for dims in [(256, 256, 256), (4096, 4096)]:
+        n = int(np.prod(dims))
+        s = h.System(dims)
+        h.assemble(torch.ones(n, dtype=torch.float64, device="cuda"), s)
+        x = torch.randn(n, device="cuda")
+        y = torch.empty_like(x)
+        ms = timeit(lambda: h.spmv(s, x, y))
+        byts = (24 if len(dims) == 3 else 20) * n
+        rows.append({"kernel": "spmv", "dims": list(dims), "n": n, "us": ms * 1e3, "bytes": byts,
+                     "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak})
+        del s, x, y
+    ctx = h.Context(max_n=1 << 22, leaf=64, rank=16)
+    for n in [1 << 20, 1 << 21, 1 << 22]:
+        w = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+        pk = (torch.randn(w, device="cuda") * 0.01).to(torch.bfloat16)
+        fac = h.factors(h.PRE_LEARNED, pk, n, 64, 16)
+        r = torch.randn(n, device="cuda")
+        z = torch.empty_like(r)
+        ms = timeit(lambda: h.apply(ctx, fac, r, z))
+        byts = 2 * w + 12 * n
+        rows.append({"kernel": "apply_bf16_learned", "n": n, "us": ms * 1e3, "bytes": byts,
+                     "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak})
+    top = rows[-1]
+    line = {"metric": "HBM roofline fraction of SpMV and BF16 learned H-apply (algorithmic bytes / time)",
+            "value": top["frac"], "unit": f"fraction of {peak_kind} HBM {hbm_peak:.0f} GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": top["us"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "SpMV 256^3 and 4096^2 (rho = 1), apply N = 2^20..2^22 leaf 64 rank 16 with "
+                                   "random BF16 factors", "l2": "inputs larger than L2"},
+            "rows": rows}
     print(json.dumps(line), flush=True)
 
 
