@@ -294,29 +294,9 @@ def main():
         frame_e2e(k)
     t_e2e = timed(frame_e2e, ks)
 
-    # launches per frame (one profiled, untimed frame through direct launches): device-side
-    # kernel records of our library (memcpy / memset records excluded)
-    launches = None
-    try:
-        from torch.profiler import profile, ProfilerActivity
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            slot_rho.copy_(rho_dev[0]); slot_b.copy_(bs[0])
-            torch.cuda.synchronize()
-            body()
-            torch.cuda.synchronize()
-        cnt = 0
-        for ev in prof.events():
-            nm = ev.name
-            if getattr(ev, "device_type", None) != torch.autograd.DeviceType.CUDA:
-                continue
-            if "hm::" in nm or "hmpcg" in nm:
-                cnt += 1
-        launches = cnt or None
-        if not launches:
-            print("gpu_launches: profiler saw no kernels of the library", file=sys.stderr)
-    except Exception as exc:
-        print(f"gpu_launches: profiler failed: {exc}", file=sys.stderr)
-        launches = None
+    # launches per frame: capture one frame's calls into a CUDA graph with the driver API and
+    # count its kernel nodes (every kernel of a frame is ours: assembly, inference, solve)
+    launches = _count_kernel_nodes(torch, body)
 
     # roofline of the dominant kernel: the persistent PCG kernel (solve share of the frame)
     # algorithmic bytes per iteration (FP32 vectors, BF16 factors): SpMV 24 N + apply
@@ -652,6 +632,38 @@ def bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind):
                                    "random BF16 factors", "l2": "inputs larger than L2"},
             "rows": rows}
     print(json.dumps(line), flush=True)
+
+
+def _count_kernel_nodes(torch, fn):
+    """Kernel nodes of a driver-API stream capture of fn() (None if the capture fails)."""
+    import ctypes
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+        st = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        h = ctypes.c_void_p(st.cuda_stream)
+        if cu.cuStreamBeginCapture_v2(h, ctypes.c_int(2)) != 0:      # relaxed capture mode
+            return None
+        with torch.cuda.stream(st):
+            fn()
+        graph = ctypes.c_void_p()
+        if cu.cuStreamEndCapture(h, ctypes.byref(graph)) != 0:
+            return None
+        n = ctypes.c_size_t(0)
+        cu.cuGraphGetNodes(graph, None, ctypes.byref(n))
+        nodes = (ctypes.c_void_p * n.value)()
+        cu.cuGraphGetNodes(graph, nodes, ctypes.byref(n))
+        kernels = 0
+        for i in range(n.value):
+            t = ctypes.c_int(-1)
+            cu.cuGraphNodeGetType(ctypes.c_void_p(nodes[i]), ctypes.byref(t))
+            kernels += 1 if t.value == 0 else 0                       # CU_GRAPH_NODE_TYPE_KERNEL
+        cu.cuGraphDestroy(graph)
+        torch.cuda.synchronize()
+        return kernels
+    except Exception as exc:  # reported, not fatal
+        print(f"gpu_launches: capture failed: {exc}", file=sys.stderr)
+        return None
 
 
 def _cpu_baseline():
