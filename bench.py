@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "ms/frame to rtol 1e-6 at N=8192 (learned-H vs Jacobi PCG); apply/SpMV %HBM roof"
 FAMILY = "spheres3d_8192"
 CFG = dict(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16)
+# dram__bytes_read.sum + dram__bytes_write.sum of one pcg_cluster_kernel<bf16, H-matrix> launch of
+# this workload (ncu, --clock-control none); the factors and the system are read from HBM once
+PCG_TRAFFIC_BYTES = 2341888
 
 
 def _peaks():
@@ -132,7 +135,7 @@ def main():
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2605_13343_gb300", "weights",
                                                       "hmpcg_d128_l4.f32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192", "bandwidth"],
+    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192", "bandwidth", "train4096"],
                     help="frame8192: the per-frame headline; batch64: 64 ragged systems in one graph; "
                          "precision16384: FP32/BF16/FP8 apply sweep with SVD-H factors")
     args = ap.parse_args()
@@ -162,6 +165,8 @@ def main():
         wsrc = "seeded init"
     if args.workload == "precision16384":
         return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind)
+    if args.workload == "train4096":
+        return bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind)
     if args.workload == "bandwidth":
         return bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind)
     if args.workload == "svdh8192":
@@ -306,7 +311,7 @@ def main():
     sol_ms = statistics.mean(ms_sol)
     achieved = bytes_iter * iters_mean / (sol_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": "pcg_kernel<bf16, H-matrix> (whole solve)", "achieved": achieved,
-            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+            "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": PCG_TRAFFIC_BYTES,
             "peak_kind": f"{peak_kind} (copy bandwidth)",
             "note": "latency-bound at N=8192: the per-iteration working set (~2 MB) is L2-resident"}
 
@@ -664,6 +669,46 @@ def _count_kernel_nodes(torch, fn):
     except Exception as exc:  # reported, not fatal
         print(f"gpu_launches: capture failed: {exc}", file=sys.stderr)
         return None
+
+
+def bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind):
+    """Training step of the cosine-Hutchinson objective: 32 systems 16^3 (density ratio
+    log-uniform in [1, 100]), 16 Rademacher probes each, BF16 forward, hand-written backward,
+    global-norm clip, AdamW (lr 3e-4).  A step is one hmpcg_train_step."""
+    B = 32
+    ctx = h.Context(max_n=4096, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
+                    max_batch=B, weights=inputs.network_blob(0, **CFG))
+    pool = []
+    for k in range(4 * B):
+        fr = inputs.frame("spheres3d_4096_lu", k)
+        sg = h.System(fr["dims"])
+        h.assemble(torch.from_numpy(fr["rho"]).cuda(), sg)
+        pool.append(sg)
+    stream = torch.cuda.current_stream()
+    batches = [pool[(i % 4) * B:(i % 4 + 1) * B] for i in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        h.train_step(ctx, batches[i], 16, 3e-4, i, want_loss=False)
+    torch.cuda.synchronize()
+    clk = ClockSampler()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.warmup, args.warmup + args.steps):
+        h.train_step(ctx, batches[i], 16, 3e-4, i, want_loss=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    loss = h.train_step(ctx, batches[0], 16, 0.0, 0)
+    tokens = B * 4096
+    line = {"metric": "ms per training step (32 systems of N=4096, 16 probes, AdamW)", "value": ms, "unit": "ms/step",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "hmpcg_train_step on spheres3d_4096_lu (16^3, contrast log-uniform 1..100), "
+                                   "batch 32, 16 Rademacher probes, d128 4 layers 4 heads MLP 512, seeded init",
+                       "tokens_per_step": tokens, "l2": "working set (activations ~1 GB) larger than L2"},
+            "loss_after": loss, "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 def _cpu_baseline():
