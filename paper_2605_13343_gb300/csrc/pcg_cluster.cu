@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <cooperative_groups.h>
 #include "ctx.cuh"
 
@@ -24,7 +25,7 @@ namespace hm {
 namespace {
 
 constexpr int kCThreads = 512;
-constexpr int kLeafPad = 2;   // row padding of leaf blocks in shared memory (bank spread)
+constexpr int kLeafPad = 8;   // row padding of leaf blocks in shared memory (16-byte rows, bank spread)
 
 // Generic pointer to the same shared-memory object in CTA `rank` of the cluster: plain
 // loads through it are ordinary memory operations that the compiler may batch.
@@ -98,15 +99,16 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
 }
 
 // One system on the calling cluster.  Returns after a final cluster barrier, so the caller may
-// reuse the shared memory at once.
-template <class T, int PRE>
+// reuse the shared memory at once.  LC, RC > 0 fix the leaf size and rank at compile time (the
+// per-leaf loops then unroll); 0 reads them from the factors.
+template <class T, int PRE, int LC = 0, int RC = 0>
 __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   extern __shared__ __align__(16) uint8_t sm[];
   const SysView& S = P.s;
   const FactorView<T>& F = P.f;
   const unsigned me = cl_rank();
   const int C = P.C, npc = P.npc;
-  const int L = F.L, R = F.r;
+  const int L = LC ? LC : F.L, R = RC ? RC : F.r;
   const bool hmat = PRE == CPRE_HMAT;
   const bool fsm = P.fsm != 0;
   const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, fsm);
@@ -200,6 +202,75 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   auto sc_leaf = [&](int k) { return F.sc_leaf ? F.sc_leaf[k] : 1.f; };
   auto sc_br = [&](int s, int k) { return F.sc_bridge ? F.sc_bridge[s * F.K + k] : 1.f; };
   // restriction + diagonal stage of every owned leaf (group grp handles leaf grp)
+  // BF16 learned factors with leaf 64 and rank 16, factors in shared memory: vector reads (bf16
+  // pairs down a column, 16-byte chunks along a row), the column pass and the restriction on
+  // different threads of a leaf group.
+  constexpr bool kVec = std::is_same<T, __nv_bfloat16>::value && LC == 64 && RC == 16;
+  auto restrict_leaves_vec = [&]() {
+    if (grp < P.lpc) {
+      float* r_l = rs + grp * L;
+      for (int i = gl; i < L; i += G) r_l[i] = rv[grp * L + i];
+    }
+    __syncthreads();
+    if (grp < P.lpc) {
+      const int kl = grp, k = n0 / L + kl;
+      const T* blk = lf + (size_t)kl * L * LPs;
+      const float4* r4 = reinterpret_cast<const float4*>(rs + kl * L);
+      float* w_l = ws + kl * max(L, F.nslot * R);
+      if (gl < 32) {                                   // w = F^T r, columns 2 gl, 2 gl + 1
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int i4 = 0; i4 < 16; ++i4) {
+          const float4 rr = r4[i4];
+          const float rv4[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(blk + (4 * i4 + u) * LPs + 2 * gl));
+            acc = __ffma2_rn(f, make_float2(rv4[u], rv4[u]), acc);
+          }
+        }
+        const float sb = sc_leaf(k);
+        w_l[2 * gl] = acc.x * sb;
+        w_l[2 * gl + 1] = acc.y * sb;
+      } else if (gl < 32 + F.nslot * (R / 2)) {          // restriction, components 2 c, 2 c + 1 of slot sl
+        const int q = gl - 32, sl = q / (R / 2), c = q % (R / 2);
+        const T* W = brf + (size_t)sl * brs + (size_t)kl * L * R;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int i4 = 0; i4 < 16; ++i4) {
+          const float4 rr = r4[i4];
+          const float rv4[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(W + (4 * i4 + u) * R + 2 * c));
+            acc = __ffma2_rn(f, make_float2(rv4[u], rv4[u]), acc);
+          }
+        }
+        const float sc = sc_br(sl, k);
+        uh[((size_t)sl * (2 * P.lpc - 1) + kl) * R + 2 * c] = acc.x * sc;
+        uh[((size_t)sl * (2 * P.lpc - 1) + kl) * R + 2 * c + 1] = acc.y * sc;
+      }
+    }
+    __syncthreads();
+    if (grp < P.lpc) {                                   // y = F w + g r, row gl
+      const int kl = grp, k = n0 / L + kl;
+      const uint4* row = reinterpret_cast<const uint4*>(lf + (size_t)kl * L * LPs + (size_t)gl * LPs);
+      const float4* w4 = reinterpret_cast<const float4*>(ws + kl * max(L, F.nslot * R));
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const uint4 u = row[c];
+        const float4 wa = w4[2 * c], wb = w4[2 * c + 1];
+        acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x)), make_float2(wa.x, wa.y), acc);
+        acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y)), make_float2(wa.z, wa.w), acc);
+        acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.z)), make_float2(wb.x, wb.y), acc);
+        acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.w)), make_float2(wb.z, wb.w), acc);
+      }
+      const float sg = F.sc_gate ? F.sc_gate[k] : 1.f;
+      const float r_i = rs[kl * L + gl];
+      ydv[kl * L + gl] = fmaf(tf<T>(gtf[kl * L + gl]) * sg, r_i, (acc.x + acc.y) * sc_leaf(k));
+    }
+  };
   auto restrict_leaves = [&]() {
     if (grp < P.lpc) {
       const int kl = grp, k = n0 / L + kl;
@@ -252,18 +323,18 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   };
   // per-slot sums of aligned groups of 2, 4, ..., lpc owned leaves (tree levels 1..)
   auto build_tree = [&]() {
-    const int T1 = 2 * P.lpc - 1;
-    int base_prev = 0, n_prev = P.lpc;
-    while (n_prev > 1) {
-      __syncthreads();
-      const int base = base_prev + n_prev, nn = n_prev / 2;
-      for (int q = tid; q < F.nslot * nn * R; q += blockDim.x) {
-        const int s = q / (nn * R), g = (q / R) % nn, e = q % R;
-        float* u = uh + (size_t)s * T1 * R;
-        u[(base + g) * R + e] = u[(base_prev + 2 * g) * R + e] + u[(base_prev + 2 * g + 1) * R + e];
-      }
-      base_prev = base;
-      n_prev = nn;
+    // every internal node sums its 2^j leaves directly (one barrier instead of one per level)
+    const int T1 = 2 * P.lpc - 1, nint = P.lpc - 1;
+    __syncthreads();
+    for (int q = tid; q < F.nslot * nint * R; q += blockDim.x) {
+      const int e = q % R, rest = q / R, node = rest % nint, sl = rest / nint;
+      int j = 1, base = 0, cnt = P.lpc >> 1;
+      while (node >= base + cnt) { base += cnt; cnt >>= 1; ++j; }
+      const int g = node - base, w = 1 << j;
+      float* u = uh + (size_t)sl * T1 * R;
+      float acc = 0.f;
+      for (int l = 0; l < w; ++l) acc += u[(g * w + l) * R + e];
+      u[(P.lpc + node) * R + e] = acc;
     }
   };
   // strip sums and coupling of the owned tiles: a strip of S <= lpc leaves is one tree node
@@ -317,8 +388,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   // prolongation of every owned leaf: z = ydiag + sum_s W_s a_s
   auto prolong = [&]() {
     float* as = ws;   // [lpc][nslot][R]
-    for (int q = tid; q < P.lpc * F.nslot * R; q += blockDim.x) as[q] = 0.f;
-    __syncthreads();
+    const int lgC = 31 - __clz(C);   // C is a power of two
     for (int q = tid; q < P.lpc * R; q += blockDim.x) {
       const int kl = q / R, e = q % R;
       const int k = n0 / L + kl;
@@ -327,16 +397,24 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       for (int lev = 1; lev <= 24; ++lev) {
         tv[lev - 1] = 0.f;
         if (lev <= F.levels) {
-          const int Sl = F.K >> lev;
-          const int cl = k / Sl;
+          const int cl = k >> (F.levels - lev);                  // cluster of leaf k at this level
           const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-          tv[lev - 1] = *remote(tcp + (size_t)(m / C) * 2 * R + (cl & 1) * R + e, m % C);
+          tv[lev - 1] = *remote(tcp + (size_t)(m >> lgC) * 2 * R + (cl & 1) * R + e, m & (C - 1));
         }
       }
-      for (int lev = 1; lev <= F.levels; ++lev) {
-        const int cl = k / (F.K >> lev);
-        const int slot = F.learned ? (cl & 1) : lev - 1;
-        as[((size_t)kl * F.nslot + slot) * R + e] += tv[lev - 1];
+      if (F.learned) {
+        float a0 = 0.f, a1 = 0.f;   // slot = side, summed in level order
+#pragma unroll
+        for (int lev = 1; lev <= 24; ++lev)
+          if (lev <= F.levels) {
+            if ((k >> (F.levels - lev)) & 1) a1 += tv[lev - 1]; else a0 += tv[lev - 1];
+          }
+        as[((size_t)kl * 2 + 0) * R + e] = a0;
+        as[((size_t)kl * 2 + 1) * R + e] = a1;
+      } else {
+#pragma unroll
+        for (int lev = 1; lev <= 24; ++lev)
+          if (lev <= F.levels) as[((size_t)kl * F.nslot + lev - 1) * R + e] = tv[lev - 1];
       }
     }
     __syncthreads();
@@ -347,7 +425,25 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
         const T* Wr = brf + (size_t)s * brs + (size_t)q * R;
         const float* a = as + ((size_t)kl * F.nslot + s) * R;
         float t = 0.f;
-        for (int e = 0; e < R; ++e) t = fmaf(tf<T>(Wr[e]), a[e], t);
+        if constexpr (std::is_same<T, __nv_bfloat16>::value && RC == 16) {
+          const uint4* wv = reinterpret_cast<const uint4*>(Wr);
+          const float4* a4 = reinterpret_cast<const float4*>(a);
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const uint4 u = wv[h2];
+            const float4 x0 = a4[2 * h2], x1 = a4[2 * h2 + 1];
+            const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+            const float xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float2 f2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&uu[c]));
+              t = fmaf(f2.x, xa[2 * c], t);
+              t = fmaf(f2.y, xa[2 * c + 1], t);
+            }
+          }
+        } else {
+          for (int e = 0; e < R; ++e) t = fmaf(tf<T>(Wr[e]), a[e], t);
+        }
         acc = fmaf(t, sc_br(s, k), acc);
       }
       zv[q] = acc;
@@ -416,7 +512,11 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     acc = fma(bi, bi, acc);
   }
   cta_part(acc, 0);
-  if (hmat) { __syncthreads(); restrict_leaves(); build_tree(); }
+  if (hmat) {
+    __syncthreads();
+    if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
+    build_tree();
+  }
   __syncthreads();
   cluster_sync();
   if (tid == 0) scal[0] = cl_total(0);
@@ -511,7 +611,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       cta_part(arz, 5);
     } else {
       __syncthreads();
-      restrict_leaves();
+      if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
       build_tree();
     }
     cur ^= 1;
@@ -578,9 +678,9 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   cluster_sync();   // nobody leaves while others may still read its shared memory
 }
 
-template <class T, int PRE>
+template <class T, int PRE, int LC, int RC>
 __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_kernel(const CParams<T> P) {
-  pcg_cluster_body<T, PRE>(P);
+  pcg_cluster_body<T, PRE, LC, RC>(P);
 }
 
 // Many systems, one persistent launch: each cluster takes the next system of the work list
@@ -592,7 +692,7 @@ struct CBatch {
   CParams<T> p[kBatchMax];
 };
 
-template <class T, int PRE>
+template <class T, int PRE, int LC, int RC>
 __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_batch_kernel(const __grid_constant__ CBatch<T> B,
                                                                          int* __restrict__ counter) {
   __shared__ int pick;
@@ -602,7 +702,7 @@ __global__ void __launch_bounds__(kCThreads, 1) pcg_cluster_batch_kernel(const _
     const int i = *remote(&pick, 0);
     cluster_sync();   // every CTA has read the pick before rank 0 takes the next one
     if (i >= B.nsys) break;
-    pcg_cluster_body<T, PRE>(B.p[i]);
+    pcg_cluster_body<T, PRE, LC, RC>(B.p[i]);
     if (PRE == CPRE_HMAT && B.p[i].fallback) {
       // rank 0 wrote the status before the body's last cluster barrier
       volatile DevStatus* ds = B.p[i].st;
@@ -711,7 +811,8 @@ static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv,
       size_t smem = 0;
       if (!plan_cluster<T, PRE>(sys, fv, C, fsm != 0, P, smem)) continue;
       P.fallback = 0;
-      auto kern = pcg_cluster_kernel<T, PRE>;
+      const bool spec = PRE == CPRE_HMAT && fv->L == 64 && fv->r == 16;
+      auto kern = spec ? pcg_cluster_kernel<T, PRE, 64, 16> : pcg_cluster_kernel<T, PRE, 0, 0>;
       if (cluster_capacity((const void*)kern, C, smem) < 1) continue;
       P.b = b; P.x = x; P.st = c->s.st;
       set_opts(P, sys, o);
@@ -811,7 +912,9 @@ static int run_batch_typed(Ctx* c, const hmpcg_system* sys, const hmpcg_factors*
     std::stable_sort(ids.begin(), ids.end(), [&](int a, int b2) { return sys[a].n > sys[b2].n; });
     cudaStream_t gs = (gi == 0) ? st : c->bside[(gi - 1) % 3];
     if (gi > 0) HM_CUDA(cudaStreamWaitEvent(gs, c->bfork, 0));
-    auto kern = pcg_cluster_batch_kernel<T, PRE>;
+    bool spec = PRE == CPRE_HMAT;
+    for (int i : ids) spec = spec && fv[i].L == 64 && fv[i].r == 16;
+    auto kern = spec ? pcg_cluster_batch_kernel<T, PRE, 64, 16> : pcg_cluster_batch_kernel<T, PRE, 0, 0>;
     const size_t smem = smem_of[C];
     const int capn = cluster_capacity((const void*)kern, C, smem);
     if (capn < 1) return HMPCG_E_SHAPE;
