@@ -13,6 +13,7 @@
 #include <cudaTypedefs.h>
 #include <cstdio>
 #include <mutex>
+#include <algorithm>
 #include "ctx.cuh"
 #include "net.cuh"
 
@@ -331,7 +332,19 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
   CUtensorMap ma;
   if (!make_map(&ma, g.A, g.M, g.K, g.lda, 128)) return HMPCG_E_INVALID;
   int bn = g.bn;
-  if (bn == 0) bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
+  if (bn == 0) {
+    bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
+    // fewer 128-wide tiles than SMs: halve the tile width so that more SMs take part
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 1;
+    }
+    const int64_t tiles128 = ((int64_t)(g.M + 127) / 128) * ((g.N + 127) / 128) * std::max(1, g.ksplit);
+    if (bn == 128 && tiles128 < sms) bn = 64;
+  }
   if (g.N < bn) bn = 64;
   switch (bn) {
     case 64: return launch_bn<64>(g, ma, st);
