@@ -22,6 +22,15 @@ struct DevStatus {
   int fallback;         // batched solves: 1 = Jacobi re-solve after an H-matrix breakdown
 };
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialisation may
+// be scheduled while its predecessor in the stream is still running; it waits here until the
+// predecessor has completed and its writes are visible, then allows its own successor to be
+// scheduled.  Without such a launch both instructions return at once.
+HM_INLINE void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ warp helpers
 HM_INLINE float warp_sum(float v) {
 #pragma unroll

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_s;
+  pdl_entry();   // the set-up above overlaps the previous kernel; operands are read only after it
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -315,7 +316,18 @@ static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) 
   CUtensorMap mb;
   if (!make_map(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
   dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, std::max(1, g.ksplit));
-  gemm_bf16_tc_kernel<BN><<<grid, 128, smem, st>>>(ma, mb, g.ep, g.M, g.N, g.K);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, gemm_bf16_tc_kernel<BN>, ma, mb, g.ep, g.M, g.N, g.K) != cudaSuccess)
+    return HMPCG_E_CUDA;
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 

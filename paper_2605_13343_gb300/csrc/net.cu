@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include "net.cuh"
+#include <utility>
 #include "netk.cuh"
 
 namespace hm {
@@ -261,6 +262,23 @@ int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, Sy
 }
 
 // ============================================================================ forward
+// Launch with programmatic stream serialisation: the forward kernels start with pdl_entry(),
+// so each may be scheduled while its predecessor in the stream finishes.
+template <class... KArgs, class... Args>
+static void pdl_launch(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(a)...);
+}
+
 static int gemm(const bf16* A, int lda, const bf16* Bw, int M, int Nn, int Kk, const GemmEpi& ep, cudaStream_t st) {
   GemmArgs g;
   g.A = A; g.lda = lda; g.B = Bw; g.ldb = Kk; g.M = M; g.N = Nn; g.K = Kk; g.ep = ep;
@@ -294,7 +312,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
   };
   cudaStream_t sE = N->side[0], sO = N->side[1];
   NET_TRY(fork(st, sE));
-  edge_desc_off_kernel<<<(B * MH * r * r + 7) / 8, 256, 0, sE>>>(sb, N->edesc_off);
+  pdl_launch(edge_desc_off_kernel, dim3((B * MH * r * r + 7) / 8), dim3(256), 0, sE, sb, N->edesc_off);
   for (int l = 0; l < cf.n_layers; ++l)
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
@@ -303,35 +321,35 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
       const int Wn = s == 0 ? L : r;
       const int nwin = T / Wn;
       if (s == 0) {
-        edge_table_kernel<<<(Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w, W + bo.e2b, h,
+        pdl_launch(edge_table_kernel, dim3((Wn * Wn + 255) / 256), dim3(256), 0, sE, sb, W + bo.e1w, W + bo.e1b, W + bo.e2w, W + bo.e2b, h,
                                                                  N->etable);
         const int64_t nq = (int64_t)nwin * h * Wn * Wn / 4;
-        edge_bias_fill_kernel<<<(int)std::min<int64_t>((nq + 255) / 256, 8 * N->num_sms), 256, 0, sE>>>(sb, h, N->etable,
+        pdl_launch(edge_bias_fill_kernel, dim3((int)std::min<int64_t>((nq + 255) / 256, 8 * N->num_sms)), dim3(256), 0, sE, sb, h, N->etable,
                                                                                                      a.bias);
-        edge_bias_nbr_kernel<<<(nwin * Wn * 2 * sb.ndim + 255) / 256, 256, 0, sE>>>(sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
+        pdl_launch(edge_bias_nbr_kernel, dim3((nwin * Wn * 2 * sb.ndim + 255) / 256), dim3(256), 0, sE, sb, W + bo.e1w, W + bo.e1b, W + bo.e2w,
                                                                                     W + bo.e2b, h, a.bias);
       } else {
-        edge_bias_off_kernel<<<(nwin * Wn * Wn + 255) / 256, 256, 0, sE>>>(sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
+        pdl_launch(edge_bias_off_kernel, dim3((nwin * Wn * Wn + 255) / 256), dim3(256), 0, sE, sb, N->edesc_off, W + bo.e1w, W + bo.e1b,
                                                                            W + bo.e2w, W + bo.e2b, h, a.bias);
       }
     }
 
   // ---- features and encoder
-  global_stats_kernel<<<B, 1024, 0, st>>>(sb, N->gstat);
-  encoder1_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, N->gstat, W + o.enc1w, W + o.enc1b, d, N->feat, N->h1, N->h1pre);
+  pdl_launch(global_stats_kernel, dim3(B), dim3(1024), 0, st, sb, N->gstat);
+  pdl_launch(encoder1_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->gstat, W + o.enc1w, W + o.enc1b, d, N->feat, N->h1, N->h1pre);
   {
     GemmEpi ep = e; ep.bias = W + o.enc2b; ep.out32 = N->xg[0]; ep.ld32 = d;
     NET_TRY(gemm(N->h1, d, W16 + o.map16(o.enc2w), Td, d, d, ep, st));
   }
   for (int g = 0; g < 2; ++g) {
-    prop_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, N->xg[g], d, N->pm[g]);
+    pdl_launch(prop_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->xg[g], d, N->pm[g]);
     GemmEpi ep = e; ep.bias = W + o.gcnb[g]; ep.act = 1; ep.resid = N->xg[g]; ep.ldr = d;
     ep.out32 = N->xg[g + 1]; ep.ld32 = d; ep.pre16 = N->gpre[g]; ep.ldpre = d;
     NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
   }
   const float* xd0 = N->xg[2];
   const dim3 pool_blk(d % 128 == 0 ? 128 : 64, kPoolRows);   // channels x row groups
-  pool_kernel<<<To, pool_blk, 0, st>>>(sb, xd0, d, N->pooled);
+  pdl_launch(pool_kernel, dim3(To), dim3(pool_blk), 0, st, sb, xd0, d, N->pooled);
   float* xcur[2];
   {
     GemmEpi ep = e; ep.bias = W + o.poolb; ep.out32 = N->act[1][0].x_in; ep.ld32 = d;
@@ -348,36 +366,37 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
       const int T = s == 0 ? Td : To;
       const int Wn = s == 0 ? L : r;
       const cudaStream_t ss = s == 0 ? st : sO;
-      layernorm_kernel<<<(T + 7) / 8, 256, 0, ss>>>(a.x_in, W + bo.ln1g, W + bo.ln1b, T, d, a.y1, nullptr, a.mu1, a.rs1);
+      pdl_launch(layernorm_kernel, dim3((T + 7) / 8), dim3(256), 0, ss, a.x_in, W + bo.ln1g, W + bo.ln1b, T, d, a.y1,
+                 (float*)nullptr, a.mu1, a.rs1, 0);
       {
         GemmEpi ep = e; ep.bias = W + bo.qkvb; ep.out16 = a.qkv; ep.ld16 = 3 * d;
         NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, ss));
       }
       {
         const int nwh = (T / Wn) * h;   // window-heads; a CTA takes 64 / Wn of them
-        if (Wn == 64) attention_kernel<64><<<nwh, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else if (Wn == 32) attention_kernel<32><<<(nwh + 1) / 2, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else attention_kernel<16><<<(nwh + 3) / 4, 128, 0, ss>>>(a.qkv, a.bias, T, d, h, a.o, a.lse);
+        if (Wn == 64) pdl_launch(attention_kernel<64>, dim3(nwh), dim3(128), 0, ss, a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else if (Wn == 32) pdl_launch(attention_kernel<32>, dim3((nwh + 1) / 2), dim3(128), 0, ss, a.qkv, a.bias, T, d, h, a.o, a.lse);
+        else pdl_launch(attention_kernel<16>, dim3((nwh + 3) / 4), dim3(128), 0, ss, a.qkv, a.bias, T, d, h, a.o, a.lse);
       }
       {
         GemmEpi ep = e; ep.bias = W + bo.outb; ep.resid = a.x_in; ep.ldr = d; ep.out32 = a.x_mid; ep.ld32 = d;
         NET_TRY(gemm(a.o, d, W16 + o.map16(bo.outw), T, d, d, ep, ss));
       }
-      layernorm_kernel<<<(T + 7) / 8, 256, 0, ss>>>(a.x_mid, W + bo.ln2g, W + bo.ln2b, T, d, a.u, a.y2f, a.mu2, a.rs2,
+      pdl_launch(layernorm_kernel, dim3((T + 7) / 8), dim3(256), 0, ss, a.x_mid, W + bo.ln2g, W + bo.ln2b, T, d, a.u, a.y2f, a.mu2, a.rs2,
                                                    4 * d);
     }
     NET_TRY(fork(sO, st));
     // ---- highways (Sec. 4.3) from LN2 outputs of both stacks
     StackAct& ad = N->act[0][l];
     StackAct& ao = N->act[1][l];
-    highway_rc_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+    pdl_launch(highway_rc_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
     {
       const int nch_d = (n + kGChunk - 1) / kGChunk, nch_o = (MH * r + kGChunk - 1) / kGChunk;
-      highway_g_partial_kernel<<<dim3(nch_d + nch_o, B), 128, 0, st>>>(sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
-      highway_g_final_kernel<<<(B * d + 7) / 8, 256, 0, st>>>(sb, N->gpart, d, nch_d + nch_o, N->gmean);
+      pdl_launch(highway_g_partial_kernel, dim3(dim3(nch_d + nch_o, B)), dim3(128), 0, st, sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
+      pdl_launch(highway_g_final_kernel, dim3((B * d + 7) / 8), dim3(256), 0, st, sb, N->gpart, d, nch_d + nch_o, N->gmean);
     }
-    concat_g_kernel<<<(Td + 7) / 8, 256, 0, st>>>(N->gmean, n, Td, d, ad.u);
-    highway_off_kernel<<<To, pool_blk, 0, st>>>(sb, N->rhw, N->chw, N->gmean, d, ao.u);
+    pdl_launch(concat_g_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, N->gmean, n, Td, d, ad.u);
+    pdl_launch(highway_off_kernel, dim3(To), dim3(pool_blk), 0, st, sb, N->rhw, N->chw, N->gmean, d, ao.u);
     NET_TRY(fork(st, sO));
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
@@ -400,8 +419,8 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
   // ---- final norms and heads
   for (int s = 0; s < 2; ++s) {
     const int T = s == 0 ? Td : To;
-    layernorm_kernel<<<(T + 7) / 8, 256, 0, st>>>(N->x_final[s], W + o.lnfg[s], W + o.lnfb[s], T, d, N->yf[s], nullptr,
-                                                 N->muf[s], N->rsf[s]);
+    pdl_launch(layernorm_kernel, dim3((T + 7) / 8), dim3(256), 0, st, N->x_final[s], W + o.lnfg[s], W + o.lnfb[s], T, d, N->yf[s],
+               (float*)nullptr, N->muf[s], N->rsf[s], 0);
   }
   {
     GemmEpi ep = e; ep.bias = W + o.leaf1b; ep.act = 1; ep.out16 = N->leafh; ep.ld16 = d; ep.pre16 = N->leafhpre; ep.ldpre = d;
@@ -415,7 +434,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     GemmEpi ep = e; ep.bias = W + o.nodeb; ep.out32 = N->nodeo; ep.ld32 = 2 * r;
     NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.nodew), Td, 2 * r, d, ep, st));
   }
-  gate_logit_kernel<<<(Td + 7) / 8, 256, 0, st>>>(N->yf[0], W + o.nodew + (int64_t)2 * r * d, W + o.nodeb + 2 * r, Td, d,
+  pdl_launch(gate_logit_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, N->yf[0], W + o.nodew + (int64_t)2 * r * d, W + o.nodeb + 2 * r, Td, d,
                                                  N->gate_logit);
   {
     GemmEpi ep = e; ep.bias = W + o.offb; ep.out32 = N->offo; ep.ld32 = 2 * r;
@@ -435,11 +454,11 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
   const int Td = sb.B * sb.n;
   const int Tt = sb.B * sb.MH;
   if (dtype == HMPCG_F32) {
-    pack_nodes_kernel<float><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, (float*)packed, P);
-    pack_tiles_kernel<float><<<Tt, 256, 0, st>>>(sb, N->offo, (float*)packed, P);
+    pdl_launch(pack_nodes_kernel<float>, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->frow, N->nodeo, N->gate_logit, (float*)packed, P);
+    pdl_launch(pack_tiles_kernel<float>, dim3(Tt), dim3(256), 0, st, sb, N->offo, (float*)packed, P);
   } else {
-    pack_nodes_kernel<bf16><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, (bf16*)packed, P);
-    pack_tiles_kernel<bf16><<<Tt, 256, 0, st>>>(sb, N->offo, (bf16*)packed, P);
+    pdl_launch(pack_nodes_kernel<bf16>, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->frow, N->nodeo, N->gate_logit, (bf16*)packed, P);
+    pdl_launch(pack_tiles_kernel<bf16>, dim3(Tt), dim3(256), 0, st, sb, N->offo, (bf16*)packed, P);
   }
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
@@ -447,8 +466,8 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
 int net_pack_f32(Net* N, const SysBatch& sb, float* packed, cudaStream_t st) {
   const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
   const int Td = sb.B * sb.n;
-  pack_nodes_kernel<float><<<(Td + 7) / 8, 256, 0, st>>>(sb, N->frow, N->nodeo, N->gate_logit, packed, P);
-  pack_tiles_kernel<float><<<sb.B * sb.MH, 256, 0, st>>>(sb, N->offo, packed, P);
+  pdl_launch(pack_nodes_kernel<float>, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->frow, N->nodeo, N->gate_logit, packed, P);
+  pdl_launch(pack_tiles_kernel<float>, dim3(sb.B * sb.MH), dim3(256), 0, st, sb, N->offo, packed, P);
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 

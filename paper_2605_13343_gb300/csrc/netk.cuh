@@ -69,6 +69,7 @@ HM_INLINE double block_max_d(float v, double* red, bool is_max) {
 // d_glob = 12 per-system statistics.  FP64 is slow on this part: each thread keeps FP32
 // partials over its nodes (a handful), the CTA reductions are FP64 in a fixed order.
 __global__ void __launch_bounds__(1024) global_stats_kernel(const SysBatch sb, double* __restrict__ gstat) {
+  pdl_entry();
   __shared__ double red[33];
   const int b = blockIdx.x, n = sb.n;
   const double* rho = sb.rho[b];
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(1024) global_stats_kernel(const SysBatch sb, d
 __global__ void encoder1_kernel(const SysBatch sb, const double* __restrict__ gstat, const float* __restrict__ w1,
                                 const float* __restrict__ b1, int d, float* __restrict__ feat, bf16* __restrict__ h1,
                                 bf16* __restrict__ h1pre) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= sb.B * sb.n) return;
@@ -148,6 +150,7 @@ __global__ void encoder1_kernel(const SysBatch sb, const double* __restrict__ gs
 
 // GCN message passing with P = D^-1 A: out_i = x_i - sum_j (w_ij / d_i) x_j.
 __global__ void prop_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ out) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= sb.B * sb.n) return;
@@ -194,6 +197,7 @@ HM_INLINE void chunk_sums(const float* __restrict__ xr, const float* __restrict_
 }
 // One CTA per token: blockDim = (128 channels, kPoolRows row groups); d % 128 == 0.
 __global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ pooled) {
+  pdl_entry();
   const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
   const TileGeo g = tile_geo(sb, m);
@@ -212,6 +216,7 @@ __global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int 
 // Tile edge descriptors: chunk-centroid offset / tile side, mean normalised coupling.  One
 // warp per (tile, row chunk, column chunk); the lanes split the row chunk's nodes.
 __global__ void edge_desc_off_kernel(const SysBatch sb, float* __restrict__ e) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int idx = blockIdx.x * (blockDim.x >> 5) + warp;
   const int r = sb.r;
@@ -299,6 +304,7 @@ HM_INLINE void leaf_desc(const SysBatch& sb, int bsys, int k, int a, int bb, flo
 // their bias comes from a per-layer table table[h][a][b] built once per call.
 __global__ void edge_table_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
                                   const float* b2, int h, float* __restrict__ table) {
+  pdl_entry();
   __shared__ EdgeMlp s;
   load_edge_mlp(s, w1, b1, w2, b2, h);
   const int L = sb.L;
@@ -318,6 +324,7 @@ __global__ void edge_table_kernel(const SysBatch sb, const float* w1, const floa
 // overwritten with the MLP of their own descriptor.
 __global__ void edge_bias_fill_kernel(const SysBatch sb, int h, const float* __restrict__ table,
                                       float* __restrict__ bias) {
+  pdl_entry();
   const int L2q = sb.L * sb.L / 4;
   const int64_t total = (int64_t)sb.B * sb.K * h * L2q;
   const float4* t4 = reinterpret_cast<const float4*>(table);
@@ -327,6 +334,7 @@ __global__ void edge_bias_fill_kernel(const SysBatch sb, int h, const float* __r
 }
 __global__ void edge_bias_nbr_kernel(const SysBatch sb, const float* w1, const float* b1, const float* w2,
                                      const float* b2, int h, float* __restrict__ bias) {
+  pdl_entry();
   __shared__ EdgeMlp s;
   load_edge_mlp(s, w1, b1, w2, b2, h);
   const int L = sb.L, nd = 2 * sb.ndim;
@@ -346,6 +354,7 @@ __global__ void edge_bias_nbr_kernel(const SysBatch sb, const float* w1, const f
 
 __global__ void edge_bias_off_kernel(const SysBatch sb, const float* __restrict__ edesc, const float* w1, const float* b1,
                                      const float* w2, const float* b2, int h, float* __restrict__ bias) {
+  pdl_entry();
   __shared__ EdgeMlp s;
   load_edge_mlp(s, w1, b1, w2, b2, h);
   const int r = sb.r;
@@ -362,6 +371,7 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
                                  const float* __restrict__ bet, int T, int d, bf16* __restrict__ out16,
                                  float* __restrict__ out32, float* __restrict__ mu, float* __restrict__ rs,
                                  int ld16 = 0) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= T) return;
@@ -413,6 +423,7 @@ template <int W>
 __global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__ qkv, const float* __restrict__ bias,
                                                         int T, int d, int h, bf16* __restrict__ out,
                                                         float* __restrict__ lse) {
+  pdl_entry();
   constexpr int WPH = W / 16;      // warps per window-head
   constexpr int HPC = 4 / WPH;     // window-heads per CTA
   constexpr int RS = 40;           // shared row stride in BF16 elements (80 bytes)
@@ -523,6 +534,7 @@ __global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__
 // row / column) and their BF16 copies into the FFN input (columns d..3d).
 __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo, int d,
                                   float* __restrict__ rhw, float* __restrict__ chw, bf16* __restrict__ ud) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= sb.B * sb.n) return;
@@ -572,6 +584,7 @@ __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ y
 constexpr int kGChunk = 64;
 __global__ void highway_g_partial_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo,
                                          int d, int nch_d, int nch_o, double* __restrict__ part) {
+  pdl_entry();
   const int b = blockIdx.y, ch = blockIdx.x;
   const int no = sb.MH * sb.r;
   const float* src;
@@ -595,6 +608,7 @@ __global__ void highway_g_partial_kernel(const SysBatch sb, const float* __restr
 // shuffle tree.
 __global__ void highway_g_final_kernel(const SysBatch sb, const double* __restrict__ part, int d, int nch,
                                        float* __restrict__ g) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wid = blockIdx.x * (blockDim.x >> 5) + warp;
   if (wid >= sb.B * d) return;
@@ -606,6 +620,7 @@ __global__ void highway_g_final_kernel(const SysBatch sb, const double* __restri
 }
 
 __global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d, bf16* __restrict__ u) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= T) return;
@@ -617,6 +632,7 @@ __global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d
 // One CTA per token, one thread per channel.
 __global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ rhw, const float* __restrict__ chw,
                                    const float* __restrict__ g, int d, bf16* __restrict__ uo) {
+  pdl_entry();
   const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
   const TileGeo gg = tile_geo(sb, m);
@@ -636,6 +652,7 @@ __global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ 
 
 __global__ void gate_logit_kernel(const bf16* __restrict__ y, const float* __restrict__ wg, const float* __restrict__ bg,
                                   int T, int d, float* __restrict__ out) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= T) return;
@@ -655,6 +672,7 @@ HM_INLINE float softplus_f(float x) { return x > 20.f ? x : log1pf(expf(x)); }
 template <class T>
 __global__ void pack_nodes_kernel(const SysBatch sb, const float* __restrict__ frow, const float* __restrict__ nodeo,
                                   const float* __restrict__ glog, T* __restrict__ packed, int64_t P) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= sb.B * sb.n) return;
@@ -676,6 +694,7 @@ __global__ void pack_nodes_kernel(const SysBatch sb, const float* __restrict__ f
 // Tile cores B_m = U_m V_m^T from the off-diagonal head (one CTA per tile).
 template <class T>
 __global__ void pack_tiles_kernel(const SysBatch sb, const float* __restrict__ offo, T* __restrict__ packed, int64_t P) {
+  pdl_entry();
   const int r = sb.r;
   const int tile = blockIdx.x;
   const int b = tile / sb.MH, m = tile % sb.MH;
