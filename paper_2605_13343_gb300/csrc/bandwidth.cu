@@ -20,48 +20,66 @@ namespace {
 
 // ------------------------------------------------------------------ SpMV
 template <int ND>
+HM_INLINE void load_cube(const float* __restrict__ p, float (&v)[1 << ND]) {
+#pragma unroll
+  for (int q = 0; q < (1 << ND); q += 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p + q));
+    v[q] = a.x; v[q + 1] = a.y; v[q + 2] = a.z; v[q + 3] = a.w;
+  }
+}
+// One thread per aligned 2x2(x2) Morton cube (the low ND bits of the index are x0, y0[, z0]):
+// the cube's own values and, per axis, the whole facing neighbour cube are read as 16-byte
+// vectors; a node's outward neighbour along axis a is node q ^ (1 << a) of that cube.
+template <int ND>
 __global__ void __launch_bounds__(256) spmv_cube_kernel(SysView s, const float* __restrict__ x, float* __restrict__ y,
                                                         int ncubes) {
   constexpr int G = 1 << ND;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncubes) return;
   const unsigned base = (unsigned)t * G;
-  float xv[G], dv[G], wv[ND][G];
+  float xv[G], acc[G];
+  load_cube<ND>(x + base, xv);
+  {
+    float dv[G];
+    load_cube<ND>(s.diag32 + base, dv);
 #pragma unroll
-  for (int q = 0; q < G; q += 4) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(x + base + q));
-    const float4 b = __ldg(reinterpret_cast<const float4*>(s.diag32 + base + q));
-    xv[q] = a.x; xv[q + 1] = a.y; xv[q + 2] = a.z; xv[q + 3] = a.w;
-    dv[q] = b.x; dv[q + 1] = b.y; dv[q + 2] = b.z; dv[q + 3] = b.w;
-#pragma unroll
-    for (int ax = 0; ax < ND; ++ax) {
-      const float4 c = __ldg(reinterpret_cast<const float4*>(s.w32[ax] + base + q));
-      wv[ax][q] = c.x; wv[ax][q + 1] = c.y; wv[ax][q + 2] = c.z; wv[ax][q + 3] = c.w;
-    }
+    for (int q = 0; q < G; ++q) acc[q] = dv[q] * xv[q];
   }
-  float out[G];
 #pragma unroll
-  for (int q = 0; q < G; ++q) {
-    float acc = dv[q] * xv[q];
+  for (int ax = 0; ax < ND; ++ax) {
+    const int bit = 1 << ax;
+    float wv[G];
+    load_cube<ND>(s.w32[ax] + base, wv);
+    // faces inside the cube: the node with the bit clear owns the weight
 #pragma unroll
-    for (int ax = 0; ax < ND; ++ax) {
-      const int bit = 1 << ax;
-      if (q & bit) {
-        // -a neighbour inside the cube, +a neighbour outside
-        acc = fmaf(-wv[ax][q ^ bit], xv[q ^ bit], acc);
-        const int jp = s.mo.plus(base + q, ax);
-        if (jp >= 0) acc = fmaf(-wv[ax][q], __ldg(x + jp), acc);
-      } else {
-        acc = fmaf(-wv[ax][q], xv[q ^ bit], acc);
-        const int jm = s.mo.minus(base + q, ax);
-        if (jm >= 0) acc = fmaf(-__ldg(s.w32[ax] + jm), __ldg(x + jm), acc);
-      }
+    for (int q = 0; q < G; ++q) {
+      if (q & bit) acc[q] = fmaf(-wv[q ^ bit], xv[q ^ bit], acc[q]);
+      else acc[q] = fmaf(-wv[q], xv[q ^ bit], acc[q]);
     }
-    out[q] = acc;
+    // +a neighbour cube: its nodes with the bit clear face our nodes with the bit set
+    const int jp = s.mo.plus(base | bit, ax);
+    if (jp >= 0) {
+      float xn[G];
+      load_cube<ND>(x + (jp & ~(G - 1)), xn);
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (q & bit) acc[q] = fmaf(-wv[q], xn[q ^ bit], acc[q]);
+    }
+    // -a neighbour cube: its nodes with the bit set own the weights of the faces they share
+    const int jm = s.mo.minus(base, ax);
+    if (jm >= 0) {
+      const unsigned nb = (unsigned)jm & ~(unsigned)(G - 1);
+      float xn[G], wn[G];
+      load_cube<ND>(x + nb, xn);
+      load_cube<ND>(s.w32[ax] + nb, wn);
+#pragma unroll
+      for (int q = 0; q < G; ++q)
+        if (!(q & bit)) acc[q] = fmaf(-wn[q ^ bit], xn[q ^ bit], acc[q]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < G; q += 4)
-    *reinterpret_cast<float4*>(y + base + q) = make_float4(out[q], out[q + 1], out[q + 2], out[q + 3]);
+    *reinterpret_cast<float4*>(y + base + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
 }
 
 // ------------------------------------------------------------------ apply, BF16, leaf 64
