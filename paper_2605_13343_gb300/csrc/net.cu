@@ -182,6 +182,14 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
   N->offo = (float*)alloc(4 * To * 2 * r);
   N->rhw = (float*)alloc(4 * Td * d);
   N->chw = (float*)alloc(4 * Td * d);
+  {
+    // chunk-sum trees: levels j >= j0 = log2(L / r) hold sum_j Td >> j <= Td >> (j0 - 1) rows
+    int j0 = 0;
+    while ((1 << (j0 + 1)) <= L / std::max<int64_t>(1, r)) ++j0;
+    const int64_t rows = (j0 >= 1 ? (Td >> (j0 - 1)) : 2 * Td) + 256;
+    N->tree_a = (float*)alloc(4 * rows * d);
+    N->tree_b = (float*)alloc(4 * rows * d);
+  }
   N->gmean = (float*)alloc(4 * B * d);
   N->gpart = (double*)alloc(8 * B * ((n + 63) / 64 + (MH * r + 63) / 64) * d);
   N->etable = (float*)alloc(4 * h * L * L);
@@ -279,6 +287,18 @@ static void pdl_launch(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStrea
   cudaLaunchKernelEx(&cfg, k, std::forward<Args>(a)...);
 }
 
+// Chunk-sum trees of x0 (and x1) for chunk sizes 2^j0 .. 2^j1 rows.
+static void chunk_trees(Net* N, const float* x0, const float* x1, int T, int d, int j0, int j1, cudaStream_t st) {
+  const int nsrc = x1 ? 2 : 1;
+  pdl_launch(chunk_tree_kernel, dim3((T + kTreeRows - 1) / kTreeRows, d / kTreeCols, nsrc), dim3(256), 0, st, x0, x1, T, d,
+             j0, j1, N->tree_a, N->tree_b);
+  for (int j = 9; j <= j1; ++j) {
+    const int64_t tot = (int64_t)(T >> j) * d;
+    pdl_launch(chunk_tree_up_kernel, dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 4096)), nsrc),
+               dim3(256), 0, st, T, d, j0, j, N->tree_a, N->tree_b);
+  }
+}
+
 static int gemm(const bf16* A, int lda, const bf16* Bw, int M, int Nn, int Kk, const GemmEpi& ep, cudaStream_t st) {
   GemmArgs g;
   g.A = A; g.lda = lda; g.B = Bw; g.ldb = Kk; g.M = M; g.N = Nn; g.K = Kk; g.ep = ep;
@@ -348,8 +368,12 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
   }
   const float* xd0 = N->xg[2];
-  const dim3 pool_blk(d % 128 == 0 ? 128 : 64, kPoolRows);   // channels x row groups
-  pdl_launch(pool_kernel, dim3(To), dim3(pool_blk), 0, st, sb, xd0, d, N->pooled);
+  // chunk sizes of the off-diagonal tokens: S L / r for S = K/2 .. 1 leaves
+  const int tj0 = 31 - __builtin_clz((unsigned)(L / r)), tj1 = tj0 + sb.levels - 1;
+  if ((L % r) || (L / r) & (L / r - 1) || d % kTreeCols) return HMPCG_E_SHAPE;
+  if (To <= 0) return HMPCG_E_SHAPE;   // a single leaf has no off-diagonal tokens
+  chunk_trees(N, xd0, nullptr, Td, d, tj0, tj1, st);
+  pdl_launch(pool_kernel, dim3(To), dim3(128), 0, st, sb, N->tree_a, tj0, d, N->pooled);
   float* xcur[2];
   {
     GemmEpi ep = e; ep.bias = W + o.poolb; ep.out32 = N->act[1][0].x_in; ep.ld32 = d;
@@ -389,14 +413,19 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     // ---- highways (Sec. 4.3) from LN2 outputs of both stacks
     StackAct& ad = N->act[0][l];
     StackAct& ao = N->act[1][l];
-    pdl_launch(highway_rc_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+    // the global token (side stream) and the row/column highways (here) run concurrently; the
+    // off-diagonal gathers need both
+    NET_TRY(fork(st, sO));
     {
       const int nch_d = (n + kGChunk - 1) / kGChunk, nch_o = (MH * r + kGChunk - 1) / kGChunk;
-      pdl_launch(highway_g_partial_kernel, dim3(dim3(nch_d + nch_o, B)), dim3(128), 0, st, sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
-      pdl_launch(highway_g_final_kernel, dim3((B * d + 7) / 8), dim3(256), 0, st, sb, N->gpart, d, nch_d + nch_o, N->gmean);
+      pdl_launch(highway_g_partial_kernel, dim3(dim3(nch_d + nch_o, B)), dim3(128), 0, sO, sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
+      pdl_launch(highway_g_final_kernel, dim3((B * d + 7) / 8), dim3(256), 0, sO, sb, N->gpart, d, nch_d + nch_o, N->gmean);
+      pdl_launch(concat_g_kernel, dim3((Td + 7) / 8), dim3(256), 0, sO, N->gmean, n, Td, d, ad.u);
     }
-    pdl_launch(concat_g_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, N->gmean, n, Td, d, ad.u);
-    pdl_launch(highway_off_kernel, dim3(To), dim3(pool_blk), 0, st, sb, N->rhw, N->chw, N->gmean, d, ao.u);
+    pdl_launch(highway_rc_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+    NET_TRY(fork(sO, st));
+    chunk_trees(N, N->rhw, N->chw, Td, d, tj0, tj1, st);
+    pdl_launch(highway_off_kernel, dim3(To), dim3(128), 0, st, sb, N->tree_a, N->tree_b, tj0, N->gmean, d, ao.u);
     NET_TRY(fork(st, sO));
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];

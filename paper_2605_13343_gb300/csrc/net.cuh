@@ -113,6 +113,7 @@ struct Net {
   float* gate_logit; // [Td]
   float* offo;       // [To][2r]
   float* rhw; float* chw; float* gmean;   // highway buffers (FP32)
+  float* tree_a; float* tree_b;           // chunk-sum trees ([levels][T >> j][d]) of the pooled arrays
   double* gpart;     // per-chunk column sums for the global token
   float* etable;     // edge-bias table of zero-coupling leaf pairs [h][L][L]
   int* err;

@@ -175,41 +175,77 @@ __global__ void prop_kernel(const SysBatch sb, const float* __restrict__ x, int 
 
 // Off-diagonal tokens: [mean over row chunk ; mean over column chunk] of the encoder output.
 // One CTA per token, one thread per channel (coalesced over channels).
-// Sums of `ch` consecutive rows (stride d) of two arrays for channel group threadIdx.x, split
-// over blockDim.y row groups and combined in shared memory in a fixed order.  Valid in
-// threadIdx.y == 0.
-constexpr int kPoolRows = 8;
-HM_INLINE void chunk_sums(const float* __restrict__ xr, const float* __restrict__ xc, int ch, int d, int c, float& sr,
-                          float& sc) {
-  __shared__ float red[2][kPoolRows][128];
-  float ar = 0.f, ac = 0.f;
-  for (int q = threadIdx.y; q < ch; q += blockDim.y) {
-    ar += xr[(size_t)q * d + c];
-    ac += xc[(size_t)q * d + c];
-  }
-  red[0][threadIdx.y][threadIdx.x] = ar;
-  red[1][threadIdx.y][threadIdx.x] = ac;
-  __syncthreads();
-  sr = 0.f; sc = 0.f;
-  if (threadIdx.y == 0)
-    for (int y = 0; y < (int)blockDim.y; ++y) { sr += red[0][y][threadIdx.x]; sc += red[1][y][threadIdx.x]; }
-  __syncthreads();
+// Aligned chunk sums for the off-diagonal tokens' means (Sec. 4.2 pooling, Sec. 4.3 gathers):
+// level j of source s holds the sums of the 2^j consecutive rows starting at multiples of 2^j,
+// for j in [j0, j1], stored level after level (level j at row offset sum_{i=j0}^{j-1} T >> i).
+// One CTA per (256-row block, 16-column slice, source); levels above 8 come from
+// chunk_tree_up_kernel.  Chunks never straddle systems: n is a power of two >= every chunk.
+constexpr int kTreeRows = 256, kTreeCols = 16;
+HM_INLINE int64_t tree_level_off(int T, int j0, int j) {
+  int64_t o = 0;
+  for (int i = j0; i < j; ++i) o += T >> i;
+  return o;
 }
-// One CTA per token: blockDim = (128 channels, kPoolRows row groups); d % 128 == 0.
-__global__ void pool_kernel(const SysBatch sb, const float* __restrict__ x, int d, bf16* __restrict__ pooled) {
+__global__ void __launch_bounds__(256) chunk_tree_kernel(const float* __restrict__ x0, const float* __restrict__ x1,
+                                                         int T, int d, int j0, int j1, float* __restrict__ t0,
+                                                         float* __restrict__ t1) {
+  pdl_entry();
+  __shared__ float buf[kTreeRows][kTreeCols + 1];
+  const float* x = blockIdx.z ? x1 : x0;
+  float* tt = blockIdx.z ? t1 : t0;
+  const int r0 = blockIdx.x * kTreeRows, c0 = blockIdx.y * kTreeCols;
+  for (int q = threadIdx.x; q < kTreeRows * kTreeCols / 4; q += blockDim.x) {
+    const int row = q / (kTreeCols / 4), c4 = q % (kTreeCols / 4);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r0 + row < T) v = *reinterpret_cast<const float4*>(x + (size_t)(r0 + row) * d + c0 + 4 * c4);
+    buf[row][4 * c4] = v.x; buf[row][4 * c4 + 1] = v.y; buf[row][4 * c4 + 2] = v.z; buf[row][4 * c4 + 3] = v.w;
+  }
+  __syncthreads();
+  if (j0 == 0)   // chunks of single rows: level 0 is the array itself
+    for (int q = threadIdx.x; q < kTreeRows * kTreeCols; q += blockDim.x) {
+      const int row = q / kTreeCols, c = q % kTreeCols;
+      if (r0 + row < T) tt[(size_t)(r0 + row) * d + c0 + c] = buf[row][c];
+    }
+  const int jt = min(j1, 8);
+  for (int j = 1; j <= jt; ++j) {
+    const int cnt = kTreeRows >> j;
+    for (int q = threadIdx.x; q < cnt * kTreeCols; q += blockDim.x) {
+      const int g = q / kTreeCols, c = q % kTreeCols;
+      const float v = buf[g << j][c] + buf[(g << j) + (1 << (j - 1))][c];
+      buf[g << j][c] = v;
+      if (j >= j0 && (r0 >> j) + g < (T >> j))
+        tt[(tree_level_off(T, j0, j) + (r0 >> j) + g) * d + c0 + c] = v;
+    }
+    __syncthreads();
+  }
+}
+__global__ void chunk_tree_up_kernel(int T, int d, int j0, int j, float* __restrict__ t0, float* __restrict__ t1) {
+  pdl_entry();
+  float* tt = blockIdx.y ? t1 : t0;
+  const int64_t prev = tree_level_off(T, j0, j - 1), cur = tree_level_off(T, j0, j);
+  const int64_t total = (int64_t)(T >> j) * d;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = q / d, c = q % d;
+    tt[(cur + g) * d + c] = tt[(prev + 2 * g) * d + c] + tt[(prev + 2 * g + 1) * d + c];
+  }
+}
+HM_INLINE int ilog2i(int v) { return 31 - __clz(v); }
+
+// Off-diagonal tokens: [mean over row chunk ; mean over column chunk] of the encoder output,
+// read from the chunk-sum tree of x.  One CTA per token, one thread per channel.
+__global__ void pool_kernel(const SysBatch sb, const float* __restrict__ tree, int j0, int d, bf16* __restrict__ pooled) {
   pdl_entry();
   const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
   const TileGeo g = tile_geo(sb, m);
-  const size_t base = (size_t)b * sb.n;
+  const int T = sb.B * sb.n, j = ilog2i(g.ch);
+  const int64_t lo = tree_level_off(T, j0, j);
+  const int64_t rr = lo + (((int64_t)b * sb.n + g.r0 + (int64_t)a * g.ch) >> j);
+  const int64_t rc = lo + (((int64_t)b * sb.n + g.c0 + (int64_t)a * g.ch) >> j);
   const float inv = 1.f / g.ch;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    float sr, sc;
-    chunk_sums(x + (base + g.r0 + (size_t)a * g.ch) * d, x + (base + g.c0 + (size_t)a * g.ch) * d, g.ch, d, c, sr, sc);
-    if (threadIdx.y == 0) {
-      pooled[(size_t)t * 2 * d + c] = __float2bfloat16_rn(sr * inv);
-      pooled[(size_t)t * 2 * d + d + c] = __float2bfloat16_rn(sc * inv);
-    }
+    pooled[(size_t)t * 2 * d + c] = __float2bfloat16_rn(tree[rr * d + c] * inv);
+    pooled[(size_t)t * 2 * d + d + c] = __float2bfloat16_rn(tree[rc * d + c] * inv);
   }
 }
 
@@ -628,25 +664,23 @@ __global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d
   for (int c = lane; c < d; c += 32) u[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
 }
 
-// Off-diagonal token gathers: mean of r_hw over its row chunk, of c_hw over its column chunk, g.
-// One CTA per token, one thread per channel.
-__global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ rhw, const float* __restrict__ chw,
-                                   const float* __restrict__ g, int d, bf16* __restrict__ uo) {
+// Off-diagonal token gathers: mean of r_hw over its row chunk, of c_hw over its column chunk, g
+// (chunk sums from the trees of r_hw and c_hw).  One CTA per token, one thread per channel.
+__global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ trr, const float* __restrict__ trc,
+                                   int j0, const float* __restrict__ g, int d, bf16* __restrict__ uo) {
   pdl_entry();
   const int t = blockIdx.x;
   const int a = t % sb.r, m = (t / sb.r) % sb.MH, b = t / (sb.r * sb.MH);
   const TileGeo gg = tile_geo(sb, m);
-  const size_t base = (size_t)b * sb.n;
+  const int T = sb.B * sb.n, j = ilog2i(gg.ch);
+  const int64_t lo = tree_level_off(T, j0, j);
+  const int64_t rr = lo + (((int64_t)b * sb.n + gg.r0 + (int64_t)a * gg.ch) >> j);
+  const int64_t rc = lo + (((int64_t)b * sb.n + gg.c0 + (int64_t)a * gg.ch) >> j);
   const float inv = 1.f / gg.ch;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
-    float sr, sc;
-    chunk_sums(rhw + (base + gg.r0 + (size_t)a * gg.ch) * d, chw + (base + gg.c0 + (size_t)a * gg.ch) * d, gg.ch, d, c,
-               sr, sc);
-    if (threadIdx.y == 0) {
-      uo[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(sr * inv);
-      uo[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(sc * inv);
-      uo[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
-    }
+    uo[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(trr[rr * d + c] * inv);
+    uo[(size_t)t * 4 * d + 2 * d + c] = __float2bfloat16_rn(trc[rc * d + c] * inv);
+    uo[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
   }
 }
 
