@@ -578,12 +578,13 @@ __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ y
   const int k = i / sb.L;
   int toks[24];
   int sides = 0, nl = 0;
+  // K, L, r and every chunk are powers of two: shifts instead of divisions
+  const int lgL = ilog2i(sb.L), lgr = ilog2i(sb.r);
   for (int lev = 1; lev <= sb.levels && lev <= 24; ++lev) {
-    const int S = sb.K >> lev;
-    const int cl = k / S;
+    const int lgS = sb.levels - lev;                     // S = K >> lev leaves per side
+    const int cl = k >> lgS;
     const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-    const int ch = S * sb.L / sb.r;
-    const int a = (i - cl * S * sb.L) / ch;
+    const int a = (i - (cl << (lgS + lgL))) >> (lgS + lgL - lgr);
     toks[nl] = (b * sb.MH + m) * sb.r + a;
     if (cl & 1) sides |= 1 << nl;
     ++nl;
@@ -608,10 +609,12 @@ __global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ y
     *reinterpret_cast<float4*>(rhw + (size_t)t * d + c) = rs;
     *reinterpret_cast<float4*>(chw + (size_t)t * d + c) = cs;
     bf16* u = ud + (size_t)t * 4 * d;
-    u[d + c] = __float2bfloat16_rn(rs.x); u[d + c + 1] = __float2bfloat16_rn(rs.y);
-    u[d + c + 2] = __float2bfloat16_rn(rs.z); u[d + c + 3] = __float2bfloat16_rn(rs.w);
-    u[2 * d + c] = __float2bfloat16_rn(cs.x); u[2 * d + c + 1] = __float2bfloat16_rn(cs.y);
-    u[2 * d + c + 2] = __float2bfloat16_rn(cs.z); u[2 * d + c + 3] = __float2bfloat16_rn(cs.w);
+    const __nv_bfloat162 r01 = __floats2bfloat162_rn(rs.x, rs.y), r23 = __floats2bfloat162_rn(rs.z, rs.w);
+    const __nv_bfloat162 c01 = __floats2bfloat162_rn(cs.x, cs.y), c23 = __floats2bfloat162_rn(cs.z, cs.w);
+    *reinterpret_cast<uint2*>(u + d + c) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&r01), *reinterpret_cast<const uint32_t*>(&r23));
+    *reinterpret_cast<uint2*>(u + 2 * d + c) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&c01), *reinterpret_cast<const uint32_t*>(&c23));
   }
 }
 
