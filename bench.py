@@ -98,7 +98,7 @@ def reference_arm(args):
     if rank != 0:
         return
     torch.set_num_threads(os.cpu_count() or 1)
-    blob = inputs.network_blob(0, **CFG)
+    blob = _weights_blob(args.weights, inputs)
     p = network.unflatten(blob, inputs.network_layout(**CFG))
     times, iters = [], []
     nframes = max(1, min(args.steps, 2))
@@ -318,7 +318,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cpu = _cpu_baseline()
+            cpu = _cpu_baseline(args.weights)
         except Exception as e:  # pragma: no cover - reported, not fatal
             cpu = {"error": str(e)}
 
@@ -711,22 +711,30 @@ def bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind):
     print(json.dumps(line), flush=True)
 
 
-def _cpu_baseline():
+def _weights_blob(path, inputs):
+    """The network weights of the workload: the trained checkpoint if present, else the seeded init."""
+    import numpy as np
+    if path and os.path.exists(path):
+        return np.fromfile(path, dtype=np.float32)
+    return inputs.network_blob(0, **CFG)
+
+
+def _cpu_baseline(weights):
     """Oracle (FP64, CPU) on one frame of the same workload, in a spawned process
     so that no process pool is forked after CUDA initialisation."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(1) as pool:
-        return pool.apply(_cpu_baseline_worker)
+        return pool.apply(_cpu_baseline_worker, (weights,))
 
 
-def _cpu_baseline_worker():
+def _cpu_baseline_worker(weights):
     import numpy as np
     import torch
     import inputs
     from oracle import grid, hmatrix, network, pcg
     torch.set_num_threads(os.cpu_count() or 1)
-    p = network.unflatten(inputs.network_blob(0, **CFG), inputs.network_layout(**CFG))
+    p = network.unflatten(_weights_blob(weights, inputs), inputs.network_layout(**CFG))
     fr = inputs.frame(FAMILY, 1000)
     sys_ = grid.assemble(fr["rho"], fr["dims"])
     a = grid.sparse_matrix(sys_)
