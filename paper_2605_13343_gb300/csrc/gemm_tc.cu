@@ -13,6 +13,8 @@
 #include <cudaTypedefs.h>
 #include <cstdio>
 #include <mutex>
+#include <tuple>
+#include <map>
 #include <algorithm>
 #include "ctx.cuh"
 #include "net.cuh"
@@ -345,8 +347,10 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
   if (!make_map(&ma, g.A, g.M, g.K, g.lda, 128)) return HMPCG_E_INVALID;
   int bn = g.bn;
   if (bn == 0) {
+    // tile-width autotuner: the first call of a shape outside stream capture times every
+    // candidate width (warm-up + 3 timed runs each, CUDA events) and keeps the fastest; calls
+    // during capture, GEMMs that add into their own output, and split-K use the rule below
     bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
-    // fewer 128-wide tiles than SMs: halve the tile width so that more SMs take part
     static int sms = 0;
     if (!sms) {
       int dev = 0;
@@ -355,7 +359,43 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
       if (sms <= 0) sms = 1;
     }
     const int64_t tiles128 = ((int64_t)(g.M + 127) / 128) * ((g.N + 127) / 128) * std::max(1, g.ksplit);
-    if (bn == 128 && tiles128 < sms) bn = 64;
+    if (bn == 128 && tiles128 < sms) bn = 64;   // rule: fewer 128-wide tiles than SMs -> narrower tiles
+    static std::map<std::tuple<int, int, int, int, int>, int> tuned;
+    static std::mutex mu;
+    const auto key = std::make_tuple(g.M, g.N, g.K, g.ksplit, (int)(g.ep.act != 0) | (g.ep.out16 ? 2 : 0));
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto it = tuned.find(key);
+      if (it != tuned.end()) { bn = it->second; have = true; }
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    const bool in_place = g.ep.resid && g.ep.resid == g.ep.out32;
+    if (!have && cs == cudaStreamCaptureStatusNone && !in_place && g.ksplit <= 1 && g.N % 128 == 0) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best = 1e30f;
+      int best_bn = bn;
+      for (int cand : {64, 128}) {
+        auto run = [&]() { return cand == 64 ? launch_bn<64>(g, ma, st) : launch_bn<128>(g, ma, st); };
+        if (run() != HMPCG_OK) continue;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3; ++rep) run();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_bn = cand; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      cudaGetLastError();
+      bn = best_bn;
+      std::lock_guard<std::mutex> lock(mu);
+      tuned[key] = bn;
+    }
   }
   if (g.N < bn) bn = 64;
   switch (bn) {
