@@ -28,6 +28,7 @@ struct Train {
   float* dbias;
   bf16 *d16, *d16t, *xt;
   float *colpart, *dwpart, *part2, *edgepart, *lnpart;
+  int64_t part2_cap;   // floats in part2
   float* featdw;
   double* gpart;
   double* nrmpart;
@@ -93,7 +94,8 @@ static int train_alloc(Net* N, int nz) {
   T->xt = (bf16*)alloc(2 * Tmax * wide);
   T->colpart = (float*)alloc(4 * ((Tmax + 63) / 64) * wide);
   T->dwpart = (float*)alloc(4 * 256 * wide * wide);
-  T->part2 = (float*)alloc(4 * 1024 * std::max<int64_t>(wide * 2, d * kFeat + 64));
+  T->part2_cap = 1024 * std::max<int64_t>(wide * 2, d * kFeat + 64);
+  T->part2 = (float*)alloc(4 * T->part2_cap);
   T->edgepart = (float*)alloc(4 * ((std::max(Td * L, To * r) + 127) / 128) * 300);
   T->lnpart = (float*)alloc(4 * ((Tmax + 7) / 8) * 2 * d);
   T->featdw = (float*)alloc(4 * ((Td + 63) / 64) * d * kFeat);
@@ -107,17 +109,18 @@ static int train_alloc(Net* N, int nz) {
 }
 
 // out[j] (+)= sum_p part[p][j] with a first pass over groups of 256 parts when needed.
+// Column sums of nparts partial results in two launches at most: groups of G parts (G = 64, or
+// larger when the group sums would not fit T->part2), then the group sums.
 static void reduce_parts(Train* T, const float* part, int nparts, int64_t n, float* out, int acc, cudaStream_t st) {
   const int grid = (int)((n + 255) / 256);
-  if (nparts <= 256) {
+  int G = 64;
+  if (nparts <= G) {
     reduce_parts_kernel<<<grid, 256, 0, st>>>(part, nparts, n, out, acc);
     return;
   }
-  const int groups = (nparts + 255) / 256;
-  for (int g = 0; g < groups; ++g) {
-    const int np = std::min(256, nparts - g * 256);
-    reduce_parts_kernel<<<grid, 256, 0, st>>>(part + (size_t)g * 256 * n, np, n, T->part2 + (size_t)g * n, 0);
-  }
+  while ((int64_t)((nparts + G - 1) / G) * n > T->part2_cap) G *= 2;
+  const int groups = (nparts + G - 1) / G;
+  reduce_parts_group_kernel<<<dim3(grid, groups), 256, 0, st>>>(part, nparts, G, n, T->part2);
   reduce_parts_kernel<<<grid, 256, 0, st>>>(T->part2, groups, n, out, acc);
 }
 

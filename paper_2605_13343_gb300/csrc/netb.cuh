@@ -460,13 +460,34 @@ __global__ void transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T,
   }
 }
 // out[j] (+)= sum over parts p of part[p * n + j], fixed order.
+// Column sums of partial results part[p][j] over p in [p0, p1) with four independent running
+// sums (fixed order: p = p0 + 4 i + k into sum k, then (s0 + s1) + (s2 + s3)).
+HM_INLINE float sum_parts(const float* __restrict__ part, int p0, int p1, int64_t n, int64_t j) {
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  int p = p0;
+  for (; p + 3 < p1; p += 4) {
+    s0 += part[(size_t)p * n + j];
+    s1 += part[(size_t)(p + 1) * n + j];
+    s2 += part[(size_t)(p + 2) * n + j];
+    s3 += part[(size_t)(p + 3) * n + j];
+  }
+  for (; p < p1; ++p) s0 += part[(size_t)p * n + j];
+  return (s0 + s1) + (s2 + s3);
+}
 __global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int64_t n, float* __restrict__ out,
                                     int accumulate) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
-  float s = 0.f;
-  for (int p = 0; p < nparts; ++p) s += part[(size_t)p * n + j];
+  const float s = sum_parts(part, 0, nparts, n, j);
   out[j] = accumulate ? out[j] + s : s;
+}
+// First stage of a two-stage column sum: CTA row blockIdx.y sums parts [y G, (y + 1) G).
+__global__ void reduce_parts_group_kernel(const float* __restrict__ part, int nparts, int G, int64_t n,
+                                          float* __restrict__ out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int p0 = blockIdx.y * G, p1 = min(nparts, p0 + G);
+  out[(size_t)blockIdx.y * n + j] = sum_parts(part, p0, p1, n, j);
 }
 // Elementwise: d_pre = d_act * gelu'(pre)  (FP32 in place).
 __global__ void gelu_bwd_kernel(float* __restrict__ g, const bf16* __restrict__ pre, int64_t n) {
