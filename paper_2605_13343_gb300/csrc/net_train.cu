@@ -26,6 +26,7 @@ struct Train {
   float* gO[2];
   float *gP, *gT, *gM, *er, *ec, *dgh;
   float* dbias;
+  float* dsum;     // diagonal-stack dbias summed over windows [h][L][L]
   bf16 *d16, *d16t, *xt;
   float *colpart, *dwpart, *part2, *edgepart, *lnpart;
   int64_t part2_cap;   // floats in part2
@@ -88,6 +89,7 @@ static int train_alloc(Net* N, int nz) {
   T->ec = (float*)alloc(4 * Td * d);
   T->dgh = (float*)alloc(4 * B * d);
   T->dbias = (float*)alloc(4 * std::max(Td * h * L, To * h * r));
+  T->dsum = (float*)alloc(4 * h * L * L);
   const int64_t Tmax = std::max(Td, To);
   T->d16 = (bf16*)alloc(2 * Tmax * wide);
   T->d16t = (bf16*)alloc(2 * Tmax * wide);
@@ -268,12 +270,26 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
           attention_bwd_kernel<16><<<ag, 64, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
       }
       {
-        const int npairs = (Tt / Wn) * Wn * Wn;
-        const int nb = (npairs + 127) / 128;
-        edge_bwd_kernel<<<nb, 128, 0, st>>>(sb, s == 0, N->edesc_off, N->w32 + bo.e1w, N->w32 + bo.e1b,
-                                            N->w32 + bo.e2w, N->w32 + bo.e2b, h, Wn, T->dbias, npairs, T->edgepart);
         const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;
-        reduce_parts(T, T->edgepart, nb, np, N->grad + bo.e1w, 0, st);
+        if (s == 0) {
+          // diagonal stack: table pairs once with the window sums, neighbour pairs per window
+          const int nwin = Tt / Wn;
+          reduce_parts(T, T->dbias, nwin, (int64_t)h * Wn * Wn, T->dsum, 0, st);
+          const int n0 = Wn * Wn, nb0 = (n0 + 127) / 128;
+          const int n1 = nwin * Wn * 2 * sb.ndim, nb1 = (n1 + 127) / 128;
+          edge_bwd_leaf_kernel<<<nb0, 128, 0, st>>>(sb, 0, N->w32 + bo.e1w, N->w32 + bo.e1b, N->w32 + bo.e2w,
+                                                    N->w32 + bo.e2b, h, T->dsum, T->dbias, n0, T->edgepart);
+          edge_bwd_leaf_kernel<<<nb1, 128, 0, st>>>(sb, 1, N->w32 + bo.e1w, N->w32 + bo.e1b, N->w32 + bo.e2w,
+                                                    N->w32 + bo.e2b, h, T->dsum, T->dbias, n1,
+                                                    T->edgepart + (size_t)nb0 * np);
+          reduce_parts(T, T->edgepart, nb0 + nb1, np, N->grad + bo.e1w, 0, st);
+        } else {
+          const int npairs = (Tt / Wn) * Wn * Wn;
+          const int nb = (npairs + 127) / 128;
+          edge_bwd_kernel<<<nb, 128, 0, st>>>(sb, 0, N->edesc_off, N->w32 + bo.e1w, N->w32 + bo.e1b,
+                                              N->w32 + bo.e2w, N->w32 + bo.e2b, h, Wn, T->dbias, npairs, T->edgepart);
+          reduce_parts(T, T->edgepart, nb, np, N->grad + bo.e1w, 0, st);
+        }
       }
       TR_TRY(linear_bwd(N, T->gH[s], 3 * d, a.y1, d, Tt, 3 * d, d, bo.qkvw, bo.qkvb, T->gY[s], 0, st));
       ln_bwd(N, T->gY[s], d, a.x_in, a.mu1, a.rs1, bo.ln1g, bo.ln1b, Tt, T->gx[s], 1, st);

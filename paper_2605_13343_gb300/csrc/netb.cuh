@@ -690,6 +690,90 @@ __global__ void edge_bwd_kernel(const SysBatch sb, int diag, const float* __rest
   }
 }
 
+// Diagonal-stack edge-bias backward without a per-pair pass over every window.  A pair (a, b)
+// of a leaf that is not a stencil neighbour has the same descriptor in every leaf (the table
+// entry), so its MLP gradient is J(e_ab)^T (sum over windows of dbias): mode 0 runs the MLP
+// backward once per (a, b) with those window sums (neighbour pairs masked out).  Mode 1 runs it
+// per (window, a, direction) for the stencil-neighbour pairs inside a leaf, whose descriptor
+// carries the window's coupling.  Both write per-CTA partials of the parameter gradients in the
+// layout of edge_bwd_kernel.
+__global__ void edge_bwd_leaf_kernel(const SysBatch sb, int mode, const float* w1, const float* b1, const float* w2,
+                                     const float* b2, int h, const float* __restrict__ dsum,
+                                     const float* __restrict__ dbias, int nunits, float* __restrict__ part) {
+  __shared__ EdgeW s;
+  __shared__ float es[128][5], zs[128][kEdgeHidden + 1], hs[128][kEdgeHidden + 1], dzs[128][kEdgeHidden + 1],
+      dos[128][9];
+  for (int q = threadIdx.x; q < kEdgeHidden * 4; q += blockDim.x) s.w1[q] = w1[q];
+  for (int q = threadIdx.x; q < kEdgeHidden; q += blockDim.x) s.b1[q] = b1[q];
+  for (int q = threadIdx.x; q < h * kEdgeHidden; q += blockDim.x) s.w2[q] = w2[q];
+  for (int q = threadIdx.x; q < h; q += blockDim.x) s.b2[q] = b2[q];
+  __syncthreads();
+  const int L = sb.L, pl = threadIdx.x;
+  const int64_t u = (int64_t)blockIdx.x * 128 + pl;
+  float e[4] = {0.f, 0.f, 0.f, 0.f};
+  float dout[8];
+  for (int q = 0; q < 8; ++q) dout[q] = 0.f;
+  bool valid = false;
+  if (u < nunits) {
+    if (mode == 0) {
+      const int a = (int)(u / L), bb = (int)(u % L);
+      bool nbr = false;
+      for (int ax = 0; ax < sb.ndim; ++ax) nbr |= sb.mo.plus(a, ax) == bb || sb.mo.minus(a, ax) == bb;
+      if (!nbr) {
+        for (int ax = 0; ax < 3; ++ax)
+          e[ax] = ax < sb.ndim ? ((float)compactb(bb, sb.mo.mask[ax]) - (float)compactb(a, sb.mo.mask[ax])) / sb.leaf_side
+                               : 0.f;
+        e[3] = a == bb ? 1.f : 0.f;
+        for (int hh = 0; hh < h; ++hh) dout[hh] = dsum[((size_t)hh * L + a) * L + bb];
+        valid = true;
+      }
+    } else {
+      const int nd = 2 * sb.ndim;
+      const int dir = (int)(u % nd), a = (int)((u / nd) % L);
+      const int64_t win = u / ((int64_t)nd * L);
+      const int k = (int)(win % sb.K), bsys = (int)(win / sb.K);
+      const int i = k * L + a;
+      const int j = (dir & 1) ? sb.mo.minus(i, dir >> 1) : sb.mo.plus(i, dir >> 1);
+      if (j >= 0 && j / L == k) {
+        const int bb = j - k * L;
+        edge_desc_leaf(sb, bsys, k, a, bb, e);
+        for (int hh = 0; hh < h; ++hh) dout[hh] = dbias[((win * h + hh) * L + a) * L + bb];
+        valid = true;
+      }
+    }
+  }
+  for (int q = 0; q < 4; ++q) es[pl][q] = e[q];
+  for (int hh = 0; hh < 8; ++hh) dos[pl][hh] = dout[hh];
+  for (int kk = 0; kk < kEdgeHidden; ++kk) {
+    float z = s.b1[kk];
+    for (int q = 0; q < 4; ++q) z = fmaf(s.w1[kk * 4 + q], e[q], z);
+    float dh = 0.f;
+    for (int hh = 0; hh < h; ++hh) dh = fmaf(s.w2[hh * kEdgeHidden + kk], dout[hh], dh);
+    zs[pl][kk] = z;
+    hs[pl][kk] = valid ? gelu_f(z) : 0.f;
+    dzs[pl][kk] = valid ? dh * gelu_grad(z) : 0.f;
+  }
+  __syncthreads();
+  const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    float acc = 0.f;
+    if (q < kEdgeHidden * 4) {
+      const int kk = q / 4, c = q % 4;
+      for (int p = 0; p < 128; ++p) acc = fmaf(dzs[p][kk], es[p][c], acc);
+    } else if (q < kEdgeHidden * 5) {
+      const int kk = q - kEdgeHidden * 4;
+      for (int p = 0; p < 128; ++p) acc += dzs[p][kk];
+    } else if (q < kEdgeHidden * 5 + h * kEdgeHidden) {
+      const int uu = q - kEdgeHidden * 5, hh = uu / kEdgeHidden, kk = uu % kEdgeHidden;
+      for (int p = 0; p < 128; ++p) acc = fmaf(dos[p][hh], hs[p][kk], acc);
+    } else {
+      const int hh = q - kEdgeHidden * 5 - h * kEdgeHidden;
+      for (int p = 0; p < 128; ++p) acc += dos[p][hh];
+    }
+    part[(size_t)blockIdx.x * np + q] = acc;
+  }
+}
+
 // ------------------------------------------------------------------ highway backward
 // Column sums of the global-token slice of the FFN-input gradients, per system (2 stages).
 __global__ void hwb_g_partial_kernel(const SysBatch sb, const float* __restrict__ dud, const float* __restrict__ duo,
