@@ -444,22 +444,30 @@ __global__ void prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int
   }
 }
 // BF16 (T x K, row stride ld) -> BF16 transpose (K x T).
+// xt[k][t] = x[t][k] for a 64 x 64 tile per CTA, moved as BF16 pairs (T, K and ld even).
 __global__ void transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K, bf16* __restrict__ xt) {
   __shared__ bf16 tile[64][66];
   const int t0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
-  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
-    const int tt = q / 64, kk = q % 64;
+  for (int q = threadIdx.x; q < 64 * 32; q += blockDim.x) {
+    const int tt = q / 32, kk = 2 * (q % 32);
     const int t = t0 + tt, k = k0 + kk;
-    tile[tt][kk] = (t < T && k < K) ? x[(size_t)t * ld + k] : __float2bfloat16_rn(0.f);
+    __nv_bfloat162 v = __floats2bfloat162_rn(0.f, 0.f);
+    if (t < T && k < K) v = *reinterpret_cast<const __nv_bfloat162*>(x + (size_t)t * ld + k);
+    tile[tt][kk] = v.x;
+    tile[tt][kk + 1] = v.y;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
-    const int kk = q / 64, tt = q % 64;
+  for (int q = threadIdx.x; q < 64 * 32; q += blockDim.x) {
+    const int kk = q / 32, tt = 2 * (q % 32);
     const int t = t0 + tt, k = k0 + kk;
-    if (t < T && k < K) xt[(size_t)k * T + t] = tile[tt][kk];
+    if (t < T && k < K) {
+      __nv_bfloat162 v;
+      v.x = tile[tt][kk];
+      v.y = tile[tt + 1][kk];
+      *reinterpret_cast<__nv_bfloat162*>(xt + (size_t)k * T + t) = v;
+    }
   }
 }
-// out[j] (+)= sum over parts p of part[p * n + j], fixed order.
 // Column sums of partial results part[p][j] over p in [p0, p1) with four independent running
 // sums (fixed order: p = p0 + 4 i + k into sum k, then (s0 + s1) + (s2 + s3)).
 HM_INLINE float sum_parts(const float* __restrict__ part, int p0, int p1, int64_t n, int64_t j) {

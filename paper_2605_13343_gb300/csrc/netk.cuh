@@ -132,7 +132,7 @@ __global__ void encoder1_kernel(const SysBatch sb, const double* __restrict__ gs
   }
   f[0] = logf((float)ri) - (float)g[4];
   for (int a = 0; a < 3; ++a)
-    f[1 + a] = a < sb.ndim ? (float)(((double)compact(i, sb.mo.mask[a]) + 0.5) / sb.dims[a] - 0.5) : 0.f;
+    f[1 + a] = a < sb.ndim ? ((float)compact(i, sb.mo.mask[a]) + 0.5f) / (float)sb.dims[a] - 0.5f : 0.f;   // exact: dims are powers of two
   f[4] = nb / (float)(2 * sb.ndim);
   f[5] = logf(di) - (float)g[7];
   f[6] = off / di;
