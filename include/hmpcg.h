@@ -159,7 +159,9 @@ int hmpcg_apply(void* ctx, const hmpcg_factors* f, const float* r, float* z,
  * device vectors (x is written; the start is x0 = 0).  Vectors r, z, p, q
  * are FP32; every dot product, alpha, beta, the stop test and the periodic
  * true-residual replacement are FP64.  The whole loop runs in one persistent
- * cooperative kernel with a device-side stop test.  If `info` (host) is
+ * kernel with a device-side stop test: one thread-block cluster of up to 16
+ * CTAs when the system's share fits (vectors and factors in shared memory,
+ * or factors read from L2), else a cooperative grid-wide kernel.  If `info` (host) is
  * non-NULL the stream is synchronised and info written; the return value is
  * then info->status.  No allocation. */
 int hmpcg_solve(void* ctx, const hmpcg_system* sys, const hmpcg_factors* f,
