@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY.  Nothing on the product path imports, calls or links
 anything in this package: only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` use it.  It shares no code with the CUDA path;
+CPU-baseline and ``--impl reference`` legs of ``bench.py`` use it.  It shares no code with the CUDA path;
 both sides read their inputs from the ``inputs`` generator module.
 
 Each function follows the paper's definition in its own plain form (loops,
@@ -17,6 +17,7 @@ and cites the passage it implements.  Modules:
 * ``loss``     cosine-Hutchinson loss and probes (Sec. 6.1, Eq. 7, Eq. 8)
 * ``network``  the hierarchical transformer forward pass (Sec. 4, Supp. B)
 * ``adamw``    AdamW with global-norm clipping (Supp. C)
+* ``train``    batch loss and its gradient by autograd through ``network`` (Sec. 6, Supp. C)
 
 Pins for every function live in ``tests/test_oracle_*.py``.
 """
