@@ -315,6 +315,16 @@ def main():
             "peak_kind": f"{peak_kind} (copy bandwidth)",
             "note": "latency-bound at N=8192: the per-iteration working set (~2 MB) is L2-resident"}
 
+    # HBM rooflines of the bandwidth kernels (SpMV, H-apply) at sizes above L2, measured after
+    # the timed region so that the frame numbers are unaffected
+    bw_rows = None
+    if rank == 0:
+        try:
+            bw_rows = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r_.items()}
+                       for r_ in bandwidth_rows(h, torch, np, hbm_peak, 10, 3)]
+        except Exception as exc:  # reported, not fatal
+            bw_rows = [{"error": str(exc)[:200]}]
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -336,6 +346,7 @@ def main():
                       "jacobi_ms_per_frame": statistics.mean(t_jac), "iters_jacobi": statistics.mean(it_j),
                       "jacobi_speedup": statistics.mean(t_jac) / ms},
         "roofline": roof,
+        "roofline_bandwidth_kernels": bw_rows,
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": (launches * len(ks)) if launches else None,
         "cuda_graph": graph is not None if graph_error is None else f"direct launches ({graph_error[:80]})",
@@ -591,7 +602,22 @@ def bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind):
     (algorithmic bytes 24 N in 3D, 20 N in 2D: x, y, faces, diag in FP32) and the BF16 learned
     H-apply (2 P + 12 N bytes: the packed factors once, r, z and the diagonal-stage vector).
     A step is one call; CUDA events around `steps` calls after `warmup` calls."""
+    rows = bandwidth_rows(h, torch, np, hbm_peak, args.steps, args.warmup)
+    top = rows[-1]
+    line = {"metric": "HBM roofline fraction of SpMV and BF16 learned H-apply (algorithmic bytes / time)",
+            "value": top["frac"], "unit": f"fraction of {peak_kind} HBM {hbm_peak:.0f} GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": top["us"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "SpMV 256^3 and 4096^2 (rho = 1), apply N = 2^20..2^22 leaf 64 rank 16 with "
+                                   "random BF16 factors", "l2": "inputs larger than L2"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def bandwidth_rows(h, torch, np, hbm_peak, steps, warmup):
+    """SpMV (256^3, 4096^2) and BF16 learned apply (N = 2^20..2^22) timings and HBM fractions."""
     stream = torch.cuda.current_stream()
+    args = argparse.Namespace(steps=steps, warmup=warmup)
 
     def timeit(fn):
         for _ in range(max(3, args.warmup)):
@@ -628,15 +654,10 @@ def bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind):
         byts = 2 * w + 12 * n
         rows.append({"kernel": "apply_bf16_learned", "n": n, "us": ms * 1e3, "bytes": byts,
                      "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak})
-    top = rows[-1]
-    line = {"metric": "HBM roofline fraction of SpMV and BF16 learned H-apply (algorithmic bytes / time)",
-            "value": top["frac"], "unit": f"fraction of {peak_kind} HBM {hbm_peak:.0f} GB/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": top["us"] / 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "SpMV 256^3 and 4096^2 (rho = 1), apply N = 2^20..2^22 leaf 64 rank 16 with "
-                                   "random BF16 factors", "l2": "inputs larger than L2"},
-            "rows": rows}
-    print(json.dumps(line), flush=True)
+        del pk, r, z
+    del ctx
+    torch.cuda.synchronize()
+    return rows
 
 
 def _count_kernel_nodes(torch, fn):
