@@ -370,9 +370,10 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
       if (it != tuned.end()) { bn = it->second; have = true; }
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(st, &cs);
+    const bool query_ok = cudaStreamIsCapturing(st, &cs) == cudaSuccess;
+    if (!query_ok) cudaGetLastError();
     const bool in_place = g.ep.resid && g.ep.resid == g.ep.out32;
-    if (!have && cs == cudaStreamCaptureStatusNone && !in_place && g.ksplit <= 1 && g.N % 128 == 0) {
+    if (!have && query_ok && cs == cudaStreamCaptureStatusNone && !in_place && g.ksplit <= 1 && g.N % 128 == 0) {
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
