@@ -43,6 +43,35 @@ HM_INLINE double warp_sum(double v) {
   return v;
 }
 
+// ------------------------------------------------------------------ float-float sums
+// An unevaluated pair hi + lo of FP32 numbers carries about 48 significant bits.  The product
+// of two FP32 numbers is exact as such a pair (Dekker's two-product, with an FMA for the error),
+// and Knuth's two-sum yields the exact rounding error of an addition; so dot products of FP32
+// vectors reach FP64-class accuracy on the FP32 pipes, which matters where FP64 issues at a
+// small fraction of the FP32 rate.  The _rn intrinsics keep the compiler from contracting or
+// reassociating the error-free steps.
+HM_INLINE void ff_add(float& hi, float& lo, float bh, float bl) {
+  const float s = __fadd_rn(hi, bh);
+  const float v = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(bh, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(bl, e));
+}
+HM_INLINE void ff_fma(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  ff_add(hi, lo, p, __fmaf_rn(a, b, -p));
+}
+// Sum over the warp (fixed butterfly); the result is taken from lane 0.
+HM_INLINE double ff_warp_sum(float hi, float lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, bh, bl);
+  }
+  return (double)hi + (double)lo;
+}
+
 // ------------------------------------------------------------------ element loads
 template <class T> HM_INLINE float to_f(T v);
 template <> HM_INLINE float to_f<float>(float v) { return v; }

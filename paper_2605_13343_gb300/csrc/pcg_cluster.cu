@@ -479,28 +479,25 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   auto gf = [&](float* base, int o, int l) -> float { return o == (int)me ? base[l] : *remote(base + l, o); };
   auto gd = [&](double* base, int o, int l) -> double { return o == (int)me ? base[l] : *remote(base + l, o); };
 
-  // FP64 is scarce on this part: per-thread FP64 partials are reduced by one warp, and the
-  // PCG scalars are computed by thread 0 and broadcast through shared memory.
-  __shared__ double red512[kCThreads];
+  // FP64 is scarce on this part (a warp instruction every ~16 cycles per SM).  Dot products of
+  // the FP32 vectors accumulate per thread and per warp as float-float pairs (exact products,
+  // error-free sums); FP64 starts at the per-warp sums, which one warp adds in a fixed tree.  The
+  // PCG scalars are computed by thread 0 and broadcast through shared memory.  Each slot q has
+  // its own per-warp array: between two uses of a slot lie several CTA barriers, so the
+  // reduction needs one barrier, not two.
+  __shared__ double redw[8][kCThreads / 32];
   __shared__ double scal[4];
   __shared__ int iscal[2];
-  auto cta_part = [&](double v, int q) {
-    __syncthreads();
-    red512[tid] = v;
+  auto cta_finish = [&](double w, int q) {   // w: this warp's sum, valid in lane 0
+    if ((tid & 31) == 0) redw[q][tid >> 5] = w;
     __syncthreads();
     if (tid < 32) {
-      // fixed pairwise tree: 16 values per lane, then the warp
-      double a[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) a[k] = (tid + 32 * k < (int)blockDim.x) ? red512[tid + 32 * k] : 0.0;
-#pragma unroll
-      for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-        for (int k = 0; k < w; ++k) a[k] += a[k + w];
-      const double s = warp_sum(a[0]);
+      const double s = warp_sum(tid < (int)(blockDim.x >> 5) ? redw[q][tid] : 0.0);
       if (tid == 0) part[q] = s;
     }
   };
+  auto cta_part = [&](double v, int q) { cta_finish(warp_sum(v), q); };   // FP64 terms
+  auto cta_part_ff = [&](float hi, float lo, int q) { cta_finish(ff_warp_sum(hi, lo), q); };
 
   // ---------------- init: x = 0, r = b, p = 0, z = M r
   double acc = 0.0;
@@ -528,16 +525,16 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     prolong();
   }
   __syncthreads();
-  acc = 0.0;
+  float ah = 0.f, al = 0.f;
   for (int i = tid; i < npc; i += blockDim.x) {
     const float ri = rv[i];
     float zi;
     if (PRE == CPRE_JACOBI) { zi = ri / coef[4 * i]; zv[i] = zi; }
     else if (PRE == CPRE_NONE) { zi = ri; zv[i] = zi; }
     else zi = zv[i];
-    acc = fma((double)ri, (double)zi, acc);
+    ff_fma(ah, al, ri, zi);
   }
-  cta_part(acc, 1);
+  cta_part_ff(ah, al, 1);
   cluster_sync();
   if (tid == 0) {
     const double rz0 = cl_total(1);
@@ -558,16 +555,16 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     const float bf = (float)beta;
     float* pc = pbuf[cur];
     float* pn = pbuf[cur ^ 1];
-    acc = 0.0;
+    ah = 0.f, al = 0.f;
     for (int i = tid; i < npc; i += blockDim.x) {
       const int g = n0 + i;
       const float pi = fmaf(bf, pc[i], zv[i]);
       pn[i] = pi;
       const float qi = row32(i, pi, [&](int o, int l) { return fmaf(bf, gf(pc, o, l), gf(zv, o, l)); });
       qv[i] = qi;
-      acc = fma((double)pi, (double)qi, acc);
+      ff_fma(ah, al, pi, qi);
     }
-    cta_part(acc, 2 + (it & 1));   // alternate slots: no reader of the previous value remains
+    cta_part_ff(ah, al, 2 + (it & 1));   // alternate slots: no reader of the previous value remains
     ++it;
     cluster_sync();
     if (tid == 0) {
@@ -581,7 +578,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     const double alpha = scal[2];
     const float af = (float)alpha;
     const bool replace = (P.recompute > 0 && (it % P.recompute) == 0) || rr <= near_thr;
-    double arr = 0.0, arz = 0.0;
+    float rrh = 0.f, rrl = 0.f, rzh = 0.f, rzl = 0.f;
     // x is updated in place after every CTA has read the old neighbour values it needs
     double xnew[4];
     int nl = 0;
@@ -594,21 +591,23 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
         const double ax = row64(g, xn, [&](int o, int l) { return fma(alpha, (double)gf(pn, o, l), gd(xs, o, l)); });
         const double rd = bs[i] - ax;
         ri = (float)rd;
-        arr = fma(rd, rd, arr);
+        const double sq = rd * rd;   // the FP64 square, carried as a float-float pair
+        const float sh = (float)sq;
+        ff_add(rrh, rrl, sh, (float)(sq - (double)sh));
       } else {
         ri = fmaf(-af, qv[i], rv[i]);
-        arr = fma((double)ri, (double)ri, arr);
+        ff_fma(rrh, rrl, ri, ri);
       }
       rv[i] = ri;
-      if (PRE == CPRE_JACOBI) { const float zi = ri / coef[4 * i]; zv[i] = zi; arz = fma((double)ri, (double)zi, arz); }
-      if (PRE == CPRE_NONE) { zv[i] = ri; arz = fma((double)ri, (double)ri, arz); }
+      if (PRE == CPRE_JACOBI) { const float zi = ri / coef[4 * i]; zv[i] = zi; ff_fma(rzh, rzl, ri, zi); }
+      if (PRE == CPRE_NONE) { zv[i] = ri; ff_fma(rzh, rzl, ri, ri); }
     }
     if (replace) cluster_sync();       // every CTA has read the old x of its neighbours
     nl = 0;
     for (int i = tid; i < npc; i += blockDim.x, ++nl) xs[i] = xnew[nl];
-    cta_part(arr, 4);
+    cta_part_ff(rrh, rrl, 4);
     if (PRE != CPRE_HMAT) {
-      cta_part(arz, 5);
+      cta_part_ff(rzh, rzl, 5);
     } else {
       __syncthreads();
       if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
@@ -636,9 +635,9 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       cluster_sync();
       prolong();
       __syncthreads();
-      arz = 0.0;
-      for (int i = tid; i < npc; i += blockDim.x) arz = fma((double)rv[i], (double)zv[i], arz);
-      cta_part(arz, 5);
+      rzh = 0.f, rzl = 0.f;
+      for (int i = tid; i < npc; i += blockDim.x) ff_fma(rzh, rzl, rv[i], zv[i]);
+      cta_part_ff(rzh, rzl, 5);
       cluster_sync();
       if (tid == 0) {
         const double rzn = cl_total(5);

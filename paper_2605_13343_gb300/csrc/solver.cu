@@ -312,9 +312,21 @@ struct PcgParams {
   int chunk;       // nodes owned per work unit (multiple of L for the H-matrix apply)
 };
 
-// FP64 is scarce on this part (about 2 FP64 FMA per clock per SM): every thread keeps its
-// own FP64 partial, one warp reduces the CTA's partials, one warp reduces the grid's, and
-// thread 0 computes alpha, beta and the stop test and broadcasts them.
+// FP64 is scarce on this part (about 2 FP64 FMA per clock per SM): dot products of the FP32
+// vectors accumulate per thread and per warp as float-float pairs (exact products, error-free
+// sums); FP64 starts at the per-warp sums.  One warp reduces the CTA's partials, one warp the
+// grid's, and thread 0 computes alpha, beta and the stop test and broadcasts them.
+HM_INLINE void cta_part_ff(float hi, float lo, double* red, double* dst) {
+  const double w = ff_warp_sum(hi, lo);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const double s = warp_sum(threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0);
+    if (threadIdx.x == 0) *dst = s;
+  }
+}
+// FP64 terms (||b||^2 and the final true residual, once per solve)
 HM_INLINE void cta_part(double v, double* red, double* dst) {
   __syncthreads();
   red[threadIdx.x] = v;
@@ -387,16 +399,16 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     if (!gs.sync(1)) return;
     OWN_LEAVES(k) phase_prolong<T>(F, k, W.tcoup, W.ydiag, W.z, sm);
   }
-  acc = 0.0;
+  float ah = 0.f, al = 0.f;
   OWN_NODES(i) {
     float zi;
     const float ri = W.r[i];
     if (PRE == PRE_JACOBI) { zi = ri / S.diag32[i]; W.z[i] = zi; }
     else if (PRE == PRE_NONE) { zi = ri; W.z[i] = zi; }
     else zi = W.z[i];
-    acc = fma((double)ri, (double)zi, acc);
+    ff_fma(ah, al, ri, zi);
   }
-  cta_part(acc, red, part_rz + blockIdx.x);
+  cta_part_ff(ah, al, red, part_rz + blockIdx.x);
   if (!gs.sync(2)) return;
   {
     const double rz0 = grid_sum0(part_rz);
@@ -421,16 +433,16 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
   while (status == HMPCG_NOT_CONVERGED && it < P.max_iter) {
     // ---- p = z + beta p, q = A p, p.q
     const float bf = (float)beta;
-    acc = 0.0;
+    ah = 0.f, al = 0.f;
     OWN_NODES(i) {
       const float pi = fmaf(bf, pcur[i], W.z[i]);
       pnext[i] = pi;
       const float qi = spmv_row32(S, (unsigned)i, pi,
                                   [&](int j) { return fmaf(bf, __ldcg(pcur + j), __ldcg(W.z + j)); });
       W.q[i] = qi;
-      acc = fma((double)pi, (double)qi, acc);
+      ff_fma(ah, al, pi, qi);
     }
-    cta_part(acc, red, part_pq + blockIdx.x);
+    cta_part_ff(ah, al, red, part_pq + blockIdx.x);
     ++it;
     if (!gs.sync(3)) return;
     {
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     // within 4x of the target, so that the stop test is always taken on b - A x in FP64
     const bool replace = (P.recompute > 0 && (it % P.recompute) == 0) || rr <= near_thr;
     // ---- x += alpha p, r -= alpha q (or r = b - A x), ||r||^2, z = M r (local part)
-    double arr = 0.0, arz = 0.0;
+    float rrh = 0.f, rrl = 0.f, rzh = 0.f, rzl = 0.f;
     OWN_NODES(i) {
       const double xn = fma(alpha, (double)pnext[i], xcur[i]);
       xnext[i] = xn;
@@ -460,18 +472,20 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
         });
         const double rd = P.b[i] - ax;
         ri = (float)rd;
-        arr = fma(rd, rd, arr);
+        const double sq = rd * rd;   // the FP64 square, carried as a float-float pair
+        const float sh = (float)sq;
+        ff_add(rrh, rrl, sh, (float)(sq - (double)sh));
       } else {
         ri = fmaf(-af, W.q[i], W.r[i]);
-        arr = fma((double)ri, (double)ri, arr);
+        ff_fma(rrh, rrl, ri, ri);
       }
       W.r[i] = ri;
-      if (PRE == PRE_JACOBI) { const float zi = ri / S.diag32[i]; W.z[i] = zi; arz = fma((double)ri, (double)zi, arz); }
-      if (PRE == PRE_NONE) { W.z[i] = ri; arz = fma((double)ri, (double)ri, arz); }
+      if (PRE == PRE_JACOBI) { const float zi = ri / S.diag32[i]; W.z[i] = zi; ff_fma(rzh, rzl, ri, zi); }
+      if (PRE == PRE_NONE) { W.z[i] = ri; ff_fma(rzh, rzl, ri, ri); }
     }
-    cta_part(arr, red, part_rr + blockIdx.x);
+    cta_part_ff(rrh, rrl, red, part_rr + blockIdx.x);
     if (PRE != PRE_HMAT) {
-      cta_part(arz, red, part_rz + blockIdx.x);
+      cta_part_ff(rzh, rzl, red, part_rz + blockIdx.x);
     } else {
       __syncthreads();
       OWN_LEAVES(k) phase_restrict<T>(F, k, W.r, W.ydiag, W.uhat, sm);
@@ -498,10 +512,10 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const PcgParams<T> P) {
     if (PRE == PRE_HMAT) {
       for (int m = blockIdx.x; m < F.K - 1; m += G) phase_tile<T>(F, m, W.uhat, W.tcoup, sm);
       if (!gs.sync(5)) return;
-      arz = 0.0;
+      rzh = 0.f, rzl = 0.f;
       OWN_LEAVES(k) phase_prolong<T>(F, k, W.tcoup, W.ydiag, W.z, sm);
-      OWN_NODES(i) arz = fma((double)W.r[i], (double)W.z[i], arz);
-      cta_part(arz, red, part_rz + blockIdx.x);
+      OWN_NODES(i) ff_fma(rzh, rzl, W.r[i], W.z[i]);
+      cta_part_ff(rzh, rzl, red, part_rz + blockIdx.x);
       if (!gs.sync(6)) return;
       const double rzn = grid_sum0(part_rz);
       if (tid == 0) {
