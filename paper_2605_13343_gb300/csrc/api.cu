@@ -32,7 +32,7 @@ using namespace hm;
 constexpr int kMaxBatchSystems = 256;   // systems per hmpcg_solve_batch call
 
 static bool valid_grid(int32_t ndim, const int32_t* dims) {
-  if (ndim < 1 || ndim > 3 || !dims) return false;
+  if (ndim < 2 || ndim > 3 || !dims) return false;   // 2-D or 3-D grids only
   int64_t n = 1;
   for (int a = 0; a < ndim; ++a) {
     if (dims[a] < 1 || (dims[a] & (dims[a] - 1))) return false;
