@@ -126,6 +126,37 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def frame_seeds(rank, nframes):
+    """Seeds of one rank's frames.  Replicas process disjoint frames (weak scaling), so no
+    frame is timed twice across ranks and no data-path collective is needed."""
+    if not 0 <= nframes <= 100000:
+        raise ValueError("at most 100000 frames per rank")
+    return [rank * 100000 + k for k in range(nframes)]
+
+
+def whole_job_ms_per_unit(dist, device, step_ms, units_per_step=1):
+    """Whole-job value of a time-like metric over replicas.
+
+    Every rank times the same number of steps.  The job's time is the slowest rank's total
+    (a MAX all-reduce when a process group is up; `device` is where the reduced tensor lives:
+    cuda for NCCL, cpu for gloo), and the job processed world x steps x units_per_step units.
+    Returns (job ms per unit, slowest rank's ms per step).  With one process both equal the
+    mean step time divided by units_per_step, resp. the mean step time.
+    """
+    steps = len(step_ms)
+    if steps == 0:
+        raise ValueError("no timed steps")
+    total = float(sum(step_ms))
+    world = 1
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total / (world * steps * units_per_step), total / steps
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,7 +208,7 @@ def main():
     ctx = h.Context(max_n=n, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
                     max_batch=1, weights=w)
     nfr = args.warmup + args.steps
-    seeds = [rank * 100000 + k for k in range(nfr)]
+    seeds = frame_seeds(rank, nfr)
     frames = [inputs.frame(FAMILY, s) for s in seeds]
     systems, bs = [], []
     for fr in frames:
@@ -256,11 +287,9 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = clk.stop()
-    ms = statistics.mean(t_learned)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    # value: the job's ms per frame (slowest rank's time over all ranks' frames);
+    # ms_per_step: the slowest rank's ms per frame
+    value_ms, ms = whole_job_ms_per_unit(dist if world > 1 else None, "cuda", t_learned)
 
     # iteration counts and accuracy of the learned frames; Jacobi on the same frames
     it_l, it_j, res_l, ms_inf, ms_sol = [], [], [], [], []
@@ -298,6 +327,7 @@ def main():
     for k in range(args.warmup):
         frame_e2e(k)
     t_e2e = timed(frame_e2e, ks)
+    e2e_ms, _ = whole_job_ms_per_unit(dist if world > 1 else None, "cuda", t_e2e)
 
     # launches per frame: capture one frame's calls into a CUDA graph with the driver API and
     # count its kernel nodes (every kernel of a frame is ours: assembly, inference, solve)
@@ -332,9 +362,8 @@ def main():
         except Exception as e:  # pragma: no cover - reported, not fatal
             cpu = {"error": str(e)}
 
-    e2e_ms = statistics.mean(t_e2e)
     line = {
-        "metric": METRIC, "value": ms * 1.0, "unit": "ms/frame", "n_gpus": world, "steps": len(ks),
+        "metric": METRIC, "value": value_ms, "unit": "ms/frame", "n_gpus": world, "steps": len(ks),
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "learned-H PCG (infer + solve), 3D 32x16x16 spheres 1:100, N=8192, "
