@@ -7,8 +7,9 @@ preconditioner), so importing it on either side couples nothing but the data.
 
 Workload shapes follow the multiphase Poisson benchmark of Supp. D (density
 contrast between a light phase rho=1 and heavy inclusions, b ~ N(0, I) projected
-to zero mean), instantiated with discs (2D) and spheres (3D) instead of the
-paper's rectangular barriers.
+to zero mean).  The benchmark configurations use discs (2D) and spheres (3D); the
+paper's own rectangular-barrier generator is ``density_barriers`` (frame
+families ``barriers2d_<N>``).
 """
 from __future__ import annotations
 
@@ -16,7 +17,8 @@ import math
 import numpy as np
 
 __all__ = [
-    "grid_centres", "density_discs", "density_spheres", "rhs", "frame",
+    "grid_centres", "density_discs", "density_spheres", "barrier_mask", "density_barriers",
+    "BARRIER_GAPS", "rhs", "frame",
     "FRAMES", "batch_mixed_dims", "density_for_dims", "network_layout", "network_blob",
 ]
 
@@ -77,6 +79,66 @@ def density_spheres(seed, dims=(32, 16, 16), n_range=(5, 12), r=(2.0, 6.0),
     return rho
 
 
+BARRIER_GAPS = ("top", "bottom", "middle_hole", "closed")
+
+
+def barrier_mask(dims, vertical, centre, thickness, gap_kind, gap=0.2):
+    """Cells covered by one rectangular barrier of the 2D benchmark (Supp. D, "Density field").
+
+    Coordinates are normalised cell centres u = (i + 1/2) / W, v = (j + 1/2) / H.  A vertical
+    barrier covers the band |u - centre| <= thickness / 2 over the full height except its gap;
+    a horizontal one swaps the axes.  The gap is a window of normalised length ``gap`` along the
+    barrier: at its high end ("top"), its low end ("bottom"), centred ("middle_hole"), or absent
+    ("closed").  Returns a boolean mask in lexicographic order (x fastest).
+    """
+    cx, cy = grid_centres(dims)
+    u, v = cx / dims[0], cy / dims[1]
+    across, along = (u, v) if vertical else (v, u)
+    band = np.abs(across - centre) <= 0.5 * thickness
+    if gap_kind == "top":
+        hole = along > 1.0 - gap
+    elif gap_kind == "bottom":
+        hole = along < gap
+    elif gap_kind == "middle_hole":
+        hole = np.abs(along - 0.5) < 0.5 * gap
+    elif gap_kind == "closed":
+        hole = np.zeros_like(band)
+    else:
+        raise ValueError(gap_kind)
+    return band & ~hole
+
+
+def density_barriers(seed, dims=(32, 32), rho_range=(5.0, 100.0), jitter=0.05, gap=0.2,
+                     return_params=False):
+    """2D density of the paper's benchmark generator (Supp. D, "Density field").
+
+    rho_heavy is log-uniform in ``rho_range``; light cells have density 1.  One to three
+    barriers (uniform count), each with an equiprobable orientation, a centre U[0.2, 0.8] on
+    the cross axis, a thickness U[0.05, 0.20] and a gap kind uniform over ``BARRIER_GAPS``
+    (see ``barrier_mask``).  A cell is heavy iff any barrier covers it.  Every cell's density
+    is then multiplied by 1 + N(0, jitter^2).
+    """
+    if len(dims) != 2:
+        raise ValueError("the barrier generator is 2D")
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA55]))
+    rho_heavy = float(math.exp(rng.uniform(math.log(rho_range[0]), math.log(rho_range[1]))))
+    nb = int(rng.integers(1, 4))
+    params = []
+    heavy = np.zeros(dims[0] * dims[1], dtype=bool)
+    for _ in range(nb):
+        vertical = bool(rng.integers(0, 2))
+        centre = float(rng.uniform(0.2, 0.8))
+        thickness = float(rng.uniform(0.05, 0.20))
+        kind = BARRIER_GAPS[int(rng.integers(0, len(BARRIER_GAPS)))]
+        params.append(dict(vertical=vertical, centre=centre, thickness=thickness, gap_kind=kind))
+        heavy |= barrier_mask(dims, vertical, centre, thickness, kind, gap)
+    rho = np.where(heavy, rho_heavy, 1.0)
+    rho = rho * (1.0 + jitter * rng.standard_normal(rho.shape))
+    if return_params:
+        return rho, dict(rho_heavy=rho_heavy, barriers=params, heavy=heavy)
+    return rho
+
+
 def rhs(seed, n):
     """b ~ N(0, I) of length n, projected onto the complement of the constant
     vector (Supp. D, right-hand side).  Drawn directly in solver order."""
@@ -102,15 +164,25 @@ FRAMES = {
                           gen=lambda s: density_discs(s, (128, 128), 20, (2.0, 8.0),
                                                       100.0, centre_margin=False)),
 }
+# the paper's own benchmark distribution (Supp. D): 1-3 barriers, contrast log-uniform in
+# [5, 100], 5 % jitter, zero-flux boundaries, w = 2 rho_i rho_j / (rho_i + rho_j), rtol 1e-8;
+# N from 1024 to 16384 on square-as-possible power-of-two grids
+for _n, _d in ((1024, (32, 32)), (2048, (64, 32)), (4096, (64, 64)), (8192, (128, 64)),
+               (16384, (128, 128))):
+    FRAMES[f"barriers2d_{_n}"] = dict(dims=_d, leaf=64, rank=16, bc="neumann", face="rho", rtol=1e-8,
+                                      gen=(lambda d: (lambda s: density_barriers(s, d)))(_d))
+del _n, _d
 
 
 def frame(family, seed):
-    """Return dict(dims, rho, b, leaf, rank) for one seeded frame of ``family``."""
+    """Return dict(dims, rho, b, leaf, rank, bc, face, rtol) for one seeded frame of
+    ``family`` (bc, face and rtol default to Dirichlet, 2/(rho_i+rho_j) and 1e-6)."""
     f = FRAMES[family]
     rho = f["gen"](seed)
     n = int(np.prod(f["dims"]))
     return dict(dims=tuple(f["dims"]), rho=rho, b=rhs(seed, n),
-                leaf=f["leaf"], rank=f["rank"])
+                leaf=f["leaf"], rank=f["rank"], bc=f.get("bc", "dirichlet"),
+                face=f.get("face", "inv_rho"), rtol=f.get("rtol", 1e-6))
 
 
 _MIXED_2D = {1024: (32, 32), 2048: (64, 32), 4096: (64, 64), 8192: (128, 64),

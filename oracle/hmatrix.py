@@ -173,22 +173,38 @@ def apply(f, r):
 
 
 # ----------------------------------------------------------------- SVD-H (plain method)
-def svdh_factors(a_dense, leaf, rank, leaves="block_inverse"):
+def pseudo_inverse(a_dense, rel_tol=1e-12):
+    """Moore-Penrose pseudo-inverse of a symmetric positive semi-definite matrix from its
+    eigendecomposition (LAPACK syevd): eigenvalues at or below rel_tol * lambda_max count as
+    the null space.  With zero-flux boundaries A 1 = 0 (Supp. D, "Operator assembly"), so A
+    has no inverse; A^+ is the inverse on the complement of the constants, where CG works for
+    a consistent right-hand side."""
+    w, v = np.linalg.eigh(a_dense)
+    keep = w > rel_tol * w.max()
+    p = (v[:, keep] / w[keep]) @ v[:, keep].T
+    return 0.5 * (p + p.T)
+
+
+def svdh_factors(a_dense, leaf, rank, leaves="block_inverse", inverse="cholesky"):
     """The plain H-matrix preconditioner built from the exact inverse.
 
     Leaves: ``"block_inverse"`` stores (A_kk)^-1, the exact inverse of A's
     diagonal block; ``"inverse_block"`` stores (A^-1)_kk.  Tiles: the rank-r
     truncated SVD X_r = U_r Sigma_r V_r^T of the exact block X = A^-1[R, C]
     (LAPACK gesdd), with r = min(rank, S L).  A^-1 comes from a Cholesky
-    factorisation (LAPACK potrf/potrs).
+    factorisation (LAPACK potrf/potrs), or, with ``inverse="pseudo"`` for a singular
+    zero-flux operator, is the pseudo-inverse A^+ (``pseudo_inverse``).
     """
     import scipy.linalg as sl
     n = a_dense.shape[0]
     k = n // leaf
     levels = int(round(math.log2(k)))
-    cf = sl.cho_factor(a_dense, lower=True)
-    ainv = sl.cho_solve(cf, np.eye(n))
-    ainv = 0.5 * (ainv + ainv.T)
+    if inverse == "pseudo":
+        ainv = pseudo_inverse(a_dense)
+    else:
+        cf = sl.cho_factor(a_dense, lower=True)
+        ainv = sl.cho_solve(cf, np.eye(n))
+        ainv = 0.5 * (ainv + ainv.T)
     f = dict(layout="svdh", n=n, leaf=leaf, rank=rank, K=k)
     f["leafblk"] = np.zeros((k, leaf, leaf))
     for b in range(k):
