@@ -18,6 +18,7 @@ and cites the passage it implements.  Modules:
 * ``network``  the hierarchical transformer forward pass (Sec. 4, Supp. B)
 * ``adamw``    AdamW with global-norm clipping (Supp. C)
 * ``train``    batch loss and its gradient by autograd through ``network`` (Sec. 6, Supp. C)
+* ``diagnostics`` spectrum of M A and the off-diagonal rank audit (Fig. 1, Fig. 3)
 
 Pins for every function live in ``tests/test_oracle_*.py``.
 """
