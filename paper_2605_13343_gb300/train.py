@@ -6,7 +6,9 @@ training contexts of Sec. 6.3 / Supp. D): 16^3 boxes with contrast log-uniform i
 random batch from one pool (every `--big-every`-th step from the larger grid),
 16 Rademacher probes per system, AdamW with global-norm clipping (inside the
 step) and a reduce-on-plateau learning-rate schedule (factor 0.5, patience 5 log
-steps, relative threshold 5e-3; Supp. C).  Every `--eval-every` steps the PCG
+steps, relative threshold 5e-3, floor max(lr * 1e-3, 1e-6); Supp. C).  With
+`--auto-stop` training ends once the rate is at its floor and the loss has not
+improved for 10 log steps (Supp. C, "Auto-stop").  Every `--eval-every` steps the PCG
 iteration count on held-out 32x16x16 frames is measured (inference + PCG, BF16
 factors, rtol 1e-6) next to Jacobi PCG; the best checkpoint by mean iterations
 is written to `--out` as a flat float32 file in the weight-blob order.
@@ -35,9 +37,12 @@ CFG = dict(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16)
 
 
 class Plateau:
-    """Reduce-on-plateau on a minimised quantity (relative threshold)."""
+    """Reduce-on-plateau on a minimised quantity (relative threshold), Supp. C: factor 0.5,
+    patience 5 log steps, threshold 5e-3, floor max(lr0 * 1e-3, 1e-6)."""
 
-    def __init__(self, lr, factor=0.5, patience=5, threshold=5e-3, min_lr=1e-6):
+    def __init__(self, lr, factor=0.5, patience=5, threshold=5e-3, min_lr=None):
+        if min_lr is None:
+            min_lr = max(lr * 1e-3, 1e-6)
         self.lr, self.factor, self.patience, self.threshold, self.min_lr = lr, factor, patience, threshold, min_lr
         self.best = float("inf")
         self.bad = 0
@@ -52,6 +57,25 @@ class Plateau:
                 self.lr = max(self.min_lr, self.lr * self.factor)
                 self.bad = 0
         return self.lr
+
+
+class AutoStop:
+    """Early termination of Supp. C: stop once the learning rate sits at its floor and the loss
+    has not improved by the relative threshold for ``patience`` consecutive log steps (twice
+    the scheduler's patience)."""
+
+    def __init__(self, patience=10, threshold=5e-3):
+        self.patience, self.threshold = patience, threshold
+        self.best = float("inf")
+        self.bad = 0
+
+    def step(self, value, lr, min_lr):
+        if value < self.best * (1.0 - self.threshold):
+            self.best = value
+            self.bad = 0
+        else:
+            self.bad += 1
+        return lr <= min_lr and self.bad >= self.patience
 
 
 def make_pool(family, seeds):
@@ -84,7 +108,9 @@ def evaluate(ctx, frames, rtol=1e-6):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=3000, help="step limit (the paper's is 1e5, with --auto-stop)")
+    ap.add_argument("--auto-stop", action="store_true",
+                    help="stop early once the learning rate is at its floor and the loss has stalled")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--probes", type=int, default=16)
     ap.add_argument("--lr", type=float, default=3e-4)
@@ -107,6 +133,7 @@ def main():
     held = make_pool("spheres3d_8192", range(20000, 20008))
     rng = np.random.default_rng(args.seed)
     sched = Plateau(args.lr)
+    stopper = AutoStop() if args.auto_stop else None
     lr = args.lr
     logf = open(args.log, "w") if args.log else None
     best = float("inf")
@@ -124,14 +151,16 @@ def main():
             batch = [small[i][0] for i in pick]
         want = step % args.log_every == 0
         loss = h.train_step(ctx, batch, args.probes, lr, int(rng.integers(1 << 62)), want_loss=want)
+        stop = False
         if want:
             window.append(loss)
             lr = sched.step(float(np.mean(window[-1:])))
+            stop = stopper is not None and stopper.step(loss, lr, sched.min_lr)
             rec = dict(step=step, loss=loss, lr=lr, t=time.time() - t0)
             if logf:
                 logf.write(json.dumps(rec) + "\n")
                 logf.flush()
-        if step % args.eval_every == 0 or step == args.steps:
+        if step % args.eval_every == 0 or step == args.steps or stop:
             it_l, it_j, ok = evaluate(ctx, held)
             rec = dict(step=step, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, loss=window[-1] if window else None,
                        t=time.time() - t0)
@@ -143,6 +172,9 @@ def main():
                 best = it_l
                 os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
                 h.get_weights(ctx, w0.size).tofile(args.out)
+        if stop:
+            print(json.dumps(dict(auto_stop=step, lr=lr)), flush=True)
+            break
     print(json.dumps(dict(done=True, best_iters=best, seconds=time.time() - t0)), flush=True)
 
 
