@@ -145,3 +145,48 @@ def test_status_strings_are_distinct():
     assert len(set(texts)) == len(codes)
     assert all("unknown" not in t for t in texts)
     assert "unknown" in h.status_string(42)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "hmpcg.h"
+int main(void) {
+  int32_t dims[3] = {32, 16, 16};
+  hmpcg_system sys;
+  hmpcg_config cfg = {0};
+  cfg.max_n = 8192; cfg.max_batch = 1; cfg.max_nrhs = 1; cfg.leaf = 64; cfg.rank = 16;
+  cfg.d_model = 128; cfg.n_layers = 4; cfg.n_heads = 4; cfg.d_mlp = 512;
+  printf("%lld %lld %lld %d %s\n",
+         (long long)hmpcg_packed_width(8192, 64, 16, HMPCG_PRE_LEARNED),
+         (long long)hmpcg_system_bytes(3, dims),
+         (long long)hmpcg_weight_count(&cfg),
+         hmpcg_system_layout(3, dims, (void*)(uintptr_t)4096, &sys),
+         hmpcg_status_string(HMPCG_E_BREAKDOWN));
+  return (int)(sys.n != 8192);
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    import os
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(h.LIB_PATH)
+    include = os.path.join(os.path.dirname(libdir), "include")
+    exe = tmp_path / "abi"
+    cc = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", include, str(src),
+                         "-L", libdir, "-lhmpcg", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                        capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr
+    width, nbytes, nweights, rc, text = run.stdout.split(" ", 4)
+    assert int(width) == h.packed_width(8192, 64, 16, h.PRE_LEARNED)
+    assert int(nbytes) == h.lib().hmpcg_system_bytes(3, _dims((32, 16, 16)))
+    assert int(nweights) == sum(math.prod(s) for _, s in inputs.network_layout())
+    assert int(rc) == h.OK and "breakdown" in text.lower()
