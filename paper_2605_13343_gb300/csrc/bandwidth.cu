@@ -772,13 +772,13 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
   }
   const int grid = std::max(1, std::min((f.K + kRWarps - 1) / kRWarps, c->num_sms * 3));
   const size_t smem = (size_t)kRWarps * 16384 + 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [&] {
     cudaFuncSetAttribute(apply_warp_restrict_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(apply_warp_restrict_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(apply_warp_restrict_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+    return true;
+  });
   switch (f.r) {
     case 8: apply_warp_restrict_kernel<8><<<grid, 32 * kRWarps, smem, st>>>(fmap, f, r, ydiag, uhat); break;
     case 16: apply_warp_restrict_kernel<16><<<grid, 32 * kRWarps, smem, st>>>(fmap, f, r, ydiag, uhat); break;
@@ -797,12 +797,12 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
     while ((1 << jnb) < nb) ++jnb;
     const int parts = std::max(1, std::min(16, nb / 16));     // CTAs sharing the tiles above the blocks
     auto smem_up = [&](int items) { return (size_t)2 * (2 * items - 1) * f.r * 4 + (size_t)(items - 1) * f.r * f.r * 2; };
-    static bool attr_up = false;
-    if (!attr_up) {
+    static std::atomic<unsigned long long> attr_up{0};
+    once_per_device(attr_up, [] {
       cudaFuncSetAttribute(block_up_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(block_up_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_up = true;
-    }
+      return true;
+    });
     if (f.r == 8) {
       block_up_kernel<8><<<nb, 1024, smem_up(kBlk), st>>>(f, uhat, f.K, kBlkLog, 0, bsum, tcoup);
       block_up_kernel<8><<<dim3(1, parts), 1024, smem_up(nb), st>>>(f, bsum, nb, jnb, kBlkLog, nullptr, tcoup);

@@ -5,11 +5,31 @@
 #include <cuda_fp8.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/hmpcg.h"
 
 #define HM_INLINE __device__ __forceinline__
 
 namespace hm {
+
+// Host: run `apply` (returns true on success) once per device in this process.  Kernel
+// attributes such as the dynamic shared-memory limit are per device, and several host threads
+// may reach a launcher for the first time together; `done` holds one bit per device ordinal.
+template <class Apply>
+inline bool once_per_device(std::atomic<unsigned long long>& done, Apply&& apply) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return true;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.load(std::memory_order_relaxed) & bit) return true;
+  if (!apply()) return false;
+  done.fetch_or(bit, std::memory_order_release);
+  return true;
+}
 
 // ------------------------------------------------------------------ status
 struct DevStatus {

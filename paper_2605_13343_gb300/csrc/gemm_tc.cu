@@ -308,13 +308,12 @@ template <int BN>
 static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) {
   constexpr int STAGES = 3;
   const size_t smem = STAGES * (128 * 64 * 2 + BN * 64 * 2) + 1024;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return HMPCG_E_CUDA;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  if (!once_per_device(attr_set, [&] {
+        return cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+               cudaSuccess;
+      }))
+    return HMPCG_E_CUDA;
   CUtensorMap mb;
   if (!make_map(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
   dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, std::max(1, g.ksplit));
@@ -351,13 +350,10 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
     // candidate width (warm-up + 3 timed runs each, CUDA events) and keeps the fastest; calls
     // during capture, GEMMs that add into their own output, and split-K use the rule below
     bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
-    static int sms = 0;
-    if (!sms) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (sms <= 0) sms = 1;
-    }
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+      sms = 1;
     const int64_t tiles128 = ((int64_t)(g.M + 127) / 128) * ((g.N + 127) / 128) * std::max(1, g.ksplit);
     if (bn == 128 && tiles128 < sms) bn = 64;   // rule: fewer 128-wide tiles than SMs -> narrower tiles
     static std::map<std::tuple<int, int, int, int, int>, int> tuned;
