@@ -370,7 +370,8 @@ def main():
                                "leaf 64, rank 16, d128 4 layers 4 heads MLP 512, BF16 factors, rtol 1e-6",
                    "weights": wsrc, "l2": "flushed (256 MiB write) before every frame, outside the timing",
                    "parallelism": f"replicas x{world}"},
-        "breakdown": {"infer_ms": statistics.mean(ms_inf), "solve_ms": sol_ms,
+        "breakdown": {"ms_per_frame_std": statistics.pstdev(t_learned), "e2e_ms_std": statistics.pstdev(t_e2e),
+                      "infer_ms": statistics.mean(ms_inf), "solve_ms": sol_ms,
                       "iters_learned": iters_mean, "true_rel_res_max": max(res_l),
                       "jacobi_ms_per_frame": statistics.mean(t_jac), "iters_jacobi": statistics.mean(it_j),
                       "jacobi_speedup": statistics.mean(t_jac) / ms},
