@@ -1,6 +1,6 @@
 """bench.py's multi-GPU path is replicas only: each rank solves its own frames, and the one
 collective is the MAX over ranks of the timed region.  Checked here with two gloo ranks on the
-CPU (the GPU machine has one GPU).
+CPU.
 """
 import json
 import os
