@@ -7,7 +7,7 @@ preconditioner), so importing it on either side couples nothing but the data.
 
 Workload shapes follow the multiphase Poisson benchmark of Supp. D (density
 contrast between a light phase rho=1 and heavy inclusions, b ~ N(0, I) projected
-to zero mean).  The benchmark configurations use discs (2D) and spheres (3D); the
+to zero mean).  Most frame families use discs (2D) and spheres (3D); the
 paper's own rectangular-barrier generator is ``density_barriers`` (frame
 families ``barriers2d_<N>``).
 """

@@ -132,7 +132,7 @@ def test_spmv_matches_dense():
 
 
 def test_density_generator_membership_brute_force():
-    # cfg1 disc: count heavy cells by an explicit double loop
+    # the 32x32 one-disc frame: count heavy cells by an explicit double loop
     rho = inputs.density_discs(7, (32, 32), 1, (8.0, 8.0), 10.0)
     rng = np.random.default_rng(7)
     px = rng.uniform(8.0, 24.0)
