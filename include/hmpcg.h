@@ -256,6 +256,16 @@ int hmpcg_get_grads(void* ctx, float* grads, int64_t count);
 /* Copy the context's FP32 master weights to `weights` (host, count floats). */
 int hmpcg_get_weights(void* ctx, float* weights, int64_t count);
 
+/* Self-test of the bounded-wait error path; the paper has no counterpart.
+ * One device thread polls *flag (device int32, acquire loads) at most
+ * max_iters times (1 <= max_iters <= 2^24, ~0.3 us apart) and writes
+ * HMPCG_OK to *status (device int32) once the flag is non-zero, else
+ * HMPCG_E_TIMEOUT -- the path every bounded wait of the library takes when
+ * it runs out.  Asynchronous on `stream`; the caller reads *status after it.
+ * Returns HMPCG_E_INVALID for NULL or misaligned pointers or max_iters out of
+ * range (before any device work), HMPCG_E_CUDA if the launch fails. */
+int hmpcg_selftest_wait(const int32_t* flag, int32_t* status, int64_t max_iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ EXPORTS = {
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "hmpcg_get_grads": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "hmpcg_apply_noalloc": (C.c_int, [C.POINTER(Factors), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hmpcg_selftest_wait": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "hmpcg_gemm_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                   C.c_void_p, C.c_int32, C.c_void_p]),
     "hmpcg_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.POINTER(Factors),
@@ -352,6 +353,13 @@ def get_weights(ctx, count):
     w = np.empty(count, dtype=np.float32)
     _check(lib().hmpcg_get_weights(ctx.h, w.ctypes.data_as(C.c_void_p), count), "get_weights")
     return w
+
+
+def selftest_wait(flag, status, max_iters, stream=None):
+    """hmpcg_selftest_wait: bounded wait on a device int32 flag; status (device int32) receives
+    OK once the flag is set, else E_TIMEOUT after max_iters polls."""
+    assert flag.dtype == torch.int32 and status.dtype == torch.int32
+    _check(lib().hmpcg_selftest_wait(_ptr(flag), _ptr(status), int(max_iters), _stream(stream)), "selftest_wait")
 
 
 def gemm_bf16(a, b, bias=None, act=0, out=None, stream=None):

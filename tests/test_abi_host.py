@@ -190,3 +190,13 @@ def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
     assert int(nbytes) == h.lib().hmpcg_system_bytes(3, _dims((32, 16, 16)))
     assert int(nweights) == sum(math.prod(s) for _, s in inputs.network_layout())
     assert int(rc) == h.OK and "breakdown" in text.lower()
+
+
+def test_selftest_wait_rejects_bad_arguments_before_any_device_work():
+    lib = h.lib()
+    p = C.c_void_p(FAKE_BASE)
+    assert lib.hmpcg_selftest_wait(None, p, 16, None) == h.E_INVALID
+    assert lib.hmpcg_selftest_wait(p, None, 16, None) == h.E_INVALID
+    assert lib.hmpcg_selftest_wait(p, p, 0, None) == h.E_INVALID                # at least one poll
+    assert lib.hmpcg_selftest_wait(p, p, (1 << 24) + 1, None) == h.E_INVALID    # bounded by 2^24
+    assert lib.hmpcg_selftest_wait(C.c_void_p(FAKE_BASE + 2), p, 16, None) == h.E_INVALID   # int32 alignment
