@@ -165,3 +165,25 @@ def test_pcg_reaches_rtol_1e8_on_barrier_frames(seed):
         err = np.linalg.norm(x - x_star) / np.linalg.norm(x_star)
         assert err <= 1.01 * kappa * out["rel_res"] + 1e-12, (name, err, kappa)
     assert runs["svdh"]["iters"] < runs["jacobi"]["iters"] < runs["cg"]["iters"]
+
+
+def test_papers_model_size_runs_on_a_barrier_frame():
+    # the paper's default model (Sec. 7.3): d = 128, 3 layers, 8 heads, leaf 128, L_s = 32
+    import torch
+    from oracle import network
+    cfg = dict(d=128, n_layers=3, n_heads=8, d_mlp=512, leaf=128, rank=32)
+    fr = inputs.frame("barriers2d_1024", 5)
+    s = grid.assemble(fr["rho"], fr["dims"], bc=fr["bc"], face=fr["face"])
+    p = network.unflatten(inputs.network_blob(0, **cfg).astype(np.float64), inputs.network_layout(**cfg))
+    with torch.no_grad():
+        f = network.to_numpy_factors(network.forward(p, s, cfg))
+    k = s["n"] // 128
+    assert f["leafblk"].shape == (k, 128, 128) and f["core"].shape == (k - 1, 32, 32)
+    assert all(np.isfinite(f[key]).all() for key in ("leafblk", "U", "V", "core", "g"))
+    # at initialisation the learned M is Jacobi up to the small factor heads (their F F^T term
+    # sums 128 products per entry at this leaf size, hence a few 1e-3)
+    m = hmatrix.dense_m(f)
+    assert np.allclose(np.diag(m) * s["diag"], 1.0, atol=1e-2)
+    asp = grid.sparse_matrix(s)
+    out = pcg.pcg(lambda v: asp @ v, lambda v: hmatrix.apply(f, v), fr["b"], rtol=fr["rtol"])
+    assert out["status"] == pcg.OK and out["rel_res"] <= fr["rtol"]
