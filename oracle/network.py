@@ -269,6 +269,21 @@ def highways(yd, yo, n, leaf, rank):
     return ud, uo
 
 
+def pool_tokens(h, n, leaf, rank):
+    """Pooled inputs of the off-diagonal tokens (Sec. 4.2; Supp. B "Off-diagonal tokens").
+
+    Row a of tile m (in heap order, M_H * L_s rows in all) is [mean of h over row
+    chunk a of R_m ; mean of h over column chunk a of C_m], a chunk being the
+    S L / L_s consecutive nodes starting at r0 + a * chunk (resp. c0 + a * chunk).
+    """
+    pooled = []
+    for (lev, s, r0, c0, ch) in tile_geometry(n, leaf, rank):
+        pr = h[r0:r0 + rank * ch].reshape(rank, ch, -1).mean(1)
+        pc = h[c0:c0 + rank * ch].reshape(rank, ch, -1).mean(1)
+        pooled.append(torch.cat([pr, pc], dim=1))
+    return torch.cat(pooled)
+
+
 def ffn(p, prefix, x, u):
     return x + linear(p, prefix + "ffn2", gelu(linear(p, prefix + "ffn1", u)))
 
@@ -290,12 +305,7 @@ def forward(p, sys, cfg, geom=None, highway=True):
     h = linear(p, "enc2", gelu(linear(p, "enc1", x)))
     for g in range(2):
         h = h + gelu(linear(p, f"gcn{g}", apply_p(geom["P"], h)))
-    pooled = []
-    for (lev, s, r0, c0, ch) in tile_geometry(n, leaf, rank):
-        pr = h[r0:r0 + rank * ch].reshape(rank, ch, -1).mean(1)
-        pc = h[c0:c0 + rank * ch].reshape(rank, ch, -1).mean(1)
-        pooled.append(torch.cat([pr, pc], dim=1))
-    xo = linear(p, "pool", torch.cat(pooled))
+    xo = linear(p, "pool", pool_tokens(h, n, leaf, rank))
     xd = h
     ed = torch.as_tensor(geom["edge_leaf"], dtype=TD)
     eo = torch.as_tensor(geom["edge_tile"], dtype=TD)
