@@ -350,14 +350,21 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
     // candidate width (warm-up + 3 timed runs each, CUDA events) and keeps the fastest; calls
     // during capture, GEMMs that add into their own output, and split-K use the rule below
     bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
-    // SM count per device, queried on the first call (before any capture) and cached
-    static std::atomic<int> sm_count[64];
+    // SM count per device, queried on the first call (before any capture) and cached only when
+    // the query succeeds; devices past the table, or a failed query, fall back to 148 SMs (the
+    // rule below then errs towards wide tiles)
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> sm_count[kMaxDev];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    int sms = sm_count[dev & 63].load(std::memory_order_relaxed);
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    int sms = (dev >= 0 && dev < kMaxDev) ? sm_count[dev].load(std::memory_order_relaxed) : 0;
     if (sms <= 0) {
-      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-      sm_count[dev & 63].store(sms, std::memory_order_relaxed);
+      if (dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+        if (dev < kMaxDev) sm_count[dev].store(sms, std::memory_order_relaxed);
+      } else {
+        cudaGetLastError();
+        sms = 148;
+      }
     }
     const int64_t tiles128 = ((int64_t)(g.M + 127) / 128) * ((g.N + 127) / 128) * std::max(1, g.ksplit);
     if (bn == 128 && tiles128 < sms) bn = 64;   // rule: fewer 128-wide tiles than SMs -> narrower tiles
