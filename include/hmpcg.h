@@ -210,6 +210,16 @@ int hmpcg_infer_factors(void* ctx, const hmpcg_system* systems, int32_t nsys,
 
 int64_t hmpcg_packed_width(int64_t n, int32_t leaf, int32_t rank, int32_t kind);
 
+/* Which kernels hmpcg_infer_factors runs (the function computed is the same, Sec. 4;
+ * Supp. B).  HMPCG_INFER_FUSED (default): three tensor-core launches per layer over both
+ * stacks when the network is d 128 / 4 heads / MLP 512 with leaf 64, rank 16 and
+ * n <= 16384, else the layered kernels.  HMPCG_INFER_LAYERED: always the layered
+ * kernels (one launch per LayerNorm, GEMM, attention and highway step; the same kernels
+ * the training step's forward uses).  Returns HMPCG_E_INVALID for a NULL context or
+ * another mode. */
+enum { HMPCG_INFER_LAYERED = 0, HMPCG_INFER_FUSED = 1 };
+int hmpcg_set_infer_mode(void* ctx, int32_t mode);
+
 /* One optimiser step of the cosine-Hutchinson objective (Sec. 6.1 Eq. 7;
  * Supp. C): n_probes Rademacher probes per system drawn from SplitMix64 keyed
  * by (step_seed, system); W = A Z; Y = M W; loss = mean over systems of

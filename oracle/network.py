@@ -339,6 +339,8 @@ def forward(p, sys, cfg, geom=None, highway=True):
     u = offh[:, :rank].reshape(k - 1, rank, rank)
     v = offh[:, rank:].reshape(k - 1, rank, rank)
     out["core"] = u @ v.transpose(1, 2)
+    # |U_m| |V_m|^T: the scale of each core entry's dot product (a bound for its rounding error)
+    out["core_scale"] = u.abs() @ v.abs().transpose(1, 2)
     return out
 
 
@@ -349,8 +351,9 @@ def geometry(sys, leaf, rank):
 
 def to_numpy_factors(f):
     g = dict(f)
-    for key in ("leafblk", "U", "V", "g", "core"):
-        g[key] = f[key].detach().numpy()
+    for key in ("leafblk", "U", "V", "g", "core", "core_scale"):
+        if key in f:
+            g[key] = f[key].detach().numpy()
     return g
 
 

@@ -72,6 +72,7 @@ EXPORTS = {
     "hmpcg_infer_factors": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_void_p, C.c_int32,
                                       C.c_void_p, C.c_void_p]),
     "hmpcg_packed_width": (C.c_int64, [C.c_int64, C.c_int32, C.c_int32, C.c_int32]),
+    "hmpcg_set_infer_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "hmpcg_train_step": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_int32, C.c_float,
                                    C.c_uint64, C.POINTER(C.c_float), C.c_void_p]),
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -330,6 +331,14 @@ def infer_factors(ctx, systems, packed, scales=None, stream=None):
     _check(lib().hmpcg_infer_factors(ctx.h, arr, len(systems), _ptr(packed), _DT[packed.dtype],
                                      _ptr(scales), _stream(stream)), "infer_factors")
     return packed
+
+
+INFER_LAYERED, INFER_FUSED = 0, 1
+
+
+def set_infer_mode(ctx, mode):
+    """hmpcg_set_infer_mode: INFER_FUSED (default) or INFER_LAYERED kernels for infer_factors."""
+    _check(lib().hmpcg_set_infer_mode(ctx.h, int(mode)), "set_infer_mode")
 
 
 def train_step(ctx, systems, n_probes, lr, step_seed, want_loss=True, stream=None):

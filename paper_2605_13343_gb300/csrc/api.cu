@@ -21,6 +21,7 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
 int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int n_probes, float lr,
                    uint64_t seed, float* loss_out, cudaStream_t st);
 int net_get_weights(Ctx* c, float* w, int64_t count);
+void net_set_fused(Net* N, bool on);
 int net_get_grads(Ctx* c, float* g, int64_t count);
 int solve_batch_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* const* b,
                          double* const* x, int nsys, const hmpcg_solve_opts* o, const int* csize, cudaStream_t st);
@@ -345,6 +346,14 @@ int hmpcg_infer_factors(void* ctx, const hmpcg_system* systems, int32_t nsys, vo
   Ctx* c = static_cast<Ctx*>(ctx);
   if (!c->net) return HMPCG_E_INVALID;
   return net_infer(c, systems, nsys, packed, dtype, scales, (cudaStream_t)stream);
+}
+
+int hmpcg_set_infer_mode(void* ctx, int32_t mode) {
+  if (!ctx || (mode != HMPCG_INFER_LAYERED && mode != HMPCG_INFER_FUSED)) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net) return HMPCG_E_INVALID;
+  net_set_fused(c->net, mode == HMPCG_INFER_FUSED);
+  return HMPCG_OK;
 }
 
 int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys, int32_t n_probes,

@@ -18,91 +18,9 @@
 #include <algorithm>
 #include "ctx.cuh"
 #include "net.cuh"
+#include "tc.cuh"
 
 namespace hm {
-
-namespace tc {
-
-HM_INLINE uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-HM_INLINE void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-HM_INLINE void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-HM_INLINE bool mbar_wait(uint32_t bar, uint32_t parity, long limit = (1l << 22)) {
-  for (long i = 0; i < limit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-HM_INLINE void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 B,
-// 8-row core groups 1024 B apart.
-HM_INLINE uint64_t sw128_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
-  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                          // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-HM_INLINE void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-
-HM_INLINE void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-HM_INLINE void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-HM_INLINE float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-
-}  // namespace tc
 
 template <int BN>
 __global__ void __launch_bounds__(128)
@@ -291,9 +209,9 @@ static bool encode_fn() {
 }
 
 // Row-major BF16 matrix (rows x cols, leading dimension ld elements), box 64 x box_rows.
-static bool make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+bool tma_map_bf16(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
   if (!encode_fn()) return false;
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || box_rows < 1 || box_rows > 256) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
@@ -315,7 +233,7 @@ static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) 
       }))
     return HMPCG_E_CUDA;
   CUtensorMap mb;
-  if (!make_map(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
+  if (!tma_map_bf16(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
   dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, std::max(1, g.ksplit));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
@@ -343,7 +261,7 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
   if (g.ksplit > 1 && (g.ep.out16 || g.ep.out16T || g.ep.pre16 || g.ep.resid || g.ep.bias || g.ep.act))
     return HMPCG_E_INVALID;   // split-K writes raw FP32 partials only
   CUtensorMap ma;
-  if (!make_map(&ma, g.A, g.M, g.K, g.lda, 128)) return HMPCG_E_INVALID;
+  if (!tma_map_bf16(&ma, g.A, g.M, g.K, g.lda, 128)) return HMPCG_E_INVALID;
   int bn = g.bn;
   if (bn == 0) {
     // tile-width autotuner: the first call of a shape outside stream capture times every

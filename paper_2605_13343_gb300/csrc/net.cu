@@ -193,6 +193,14 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
   N->gmean = (float*)alloc(4 * B * d);
   N->gpart = (double*)alloc(8 * B * ((n + 63) / 64 + (MH * r + 63) / 64) * d);
   N->etable = (float*)alloc(4 * h * L * L);
+  if (d == 128 && h == 4 && dm == 512 && L == 64 && r == 16 && cf.n_layers <= kEdgeMaxLayersNet) {
+    for (int l = 0; l < cf.n_layers; ++l) {
+      N->ftable[l] = (float*)alloc(4 * h * L * L);
+      N->fnbr[l] = (float*)alloc(4 * Td * 6 * h);
+    }
+    N->gp16 = (float*)alloc(4 * ((Td + To) / 16 + 1) * d);
+    N->fused_alloc = true;
+  }
   N->err = (int*)alloc(256);
   for (int i = 0; i < 2 && ok; ++i) ok = cudaStreamCreateWithFlags(&N->side[i], cudaStreamNonBlocking) == cudaSuccess;
   for (int i = 0; i < 32 && ok; ++i) ok = cudaEventCreateWithFlags(&N->ev[i], cudaEventDisableTiming) == cudaSuccess;
@@ -233,6 +241,8 @@ void net_destroy(Ctx* c) {
   delete c->net;
   c->net = nullptr;
 }
+
+void net_set_fused(Net* N, bool on) { N->use_fused = on ? 1 : 0; }
 
 int net_get_weights(Ctx* c, float* w, int64_t count) {
   Net* N = c->net;
@@ -472,13 +482,134 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
+// Forward pass with the fused layer kernels (net_fused.cu): the same encoder, pooling and heads
+// as net_forward; each layer is three launches over both stacks instead of ~20, and the edge
+// biases of all layers come from one launch (tables of zero-coupling pairs and stencil-neighbour
+// entries for the diagonal windows, whole 16 x 16 blocks for the tiles).
+static int net_forward_fused(Net* N, const SysBatch& sb, cudaStream_t st) {
+  const hmpcg_config& cf = N->cfg;
+  const WeightOff& o = N->off;
+  const int B = sb.B, n = sb.n, d = cf.d_model, h = cf.n_heads;
+  const int L = sb.L, r = sb.r, MH = sb.MH;
+  const int Td = B * n, To = B * MH * r;
+  const float* W = N->w32;
+  const bf16* W16 = N->w16;
+  GemmEpi e;
+  e.err = N->err;
+  int evi = 0;
+  auto fork = [&](cudaStream_t from, cudaStream_t to) -> int {
+    if (evi >= 32) return HMPCG_E_INVALID;
+    if (cudaEventRecord(N->ev[evi], from) != cudaSuccess) return HMPCG_E_CUDA;
+    if (cudaStreamWaitEvent(to, N->ev[evi], 0) != cudaSuccess) return HMPCG_E_CUDA;
+    ++evi;
+    return HMPCG_OK;
+  };
+  cudaStream_t sE = N->side[0];
+  // ---- edge biases of every layer (side stream, overlapping the encoder)
+  NET_TRY(fork(st, sE));
+  pdl_launch(edge_desc_off_kernel, dim3((B * MH * r * r + 7) / 8), dim3(256), 0, sE, sb, N->edesc_off);
+  {
+    EdgePrep E;
+    std::memset(&E, 0, sizeof(E));
+    for (int l = 0; l < cf.n_layers; ++l) {
+      for (int s = 0; s < 2; ++s) {
+        const BlockOff& bo = o.blk[s][l];
+        E.e1w[s][l] = W + bo.e1w; E.e1b[s][l] = W + bo.e1b; E.e2w[s][l] = W + bo.e2w; E.e2b[s][l] = W + bo.e2b;
+      }
+      E.table[l] = N->ftable[l];
+      E.nbr[l] = N->fnbr[l];
+      E.dense[l] = N->act[1][l].bias;
+    }
+    const int nt = (L * L + 255) / 256, nn = (Td * 2 * sb.ndim + 255) / 256, no = (B * MH * r * r + 255) / 256;
+    pdl_launch(edge_prep_kernel, dim3(nt + nn + no, cf.n_layers), dim3(256), 0, sE, sb, E, N->edesc_off, h, nt, nn);
+  }
+  // ---- features, encoder, GCN, pooled tile tokens (as in net_forward)
+  pdl_launch(global_stats_kernel, dim3(B), dim3(1024), 0, st, sb, N->gstat);
+  pdl_launch(encoder1_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->gstat, W + o.enc1w, W + o.enc1b, d, N->feat, N->h1, N->h1pre);
+  {
+    GemmEpi ep = e; ep.bias = W + o.enc2b; ep.out32 = N->xg[0]; ep.ld32 = d;
+    NET_TRY(gemm(N->h1, d, W16 + o.map16(o.enc2w), Td, d, d, ep, st));
+  }
+  for (int g = 0; g < 2; ++g) {
+    pdl_launch(prop_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->xg[g], d, N->pm[g]);
+    GemmEpi ep = e; ep.bias = W + o.gcnb[g]; ep.act = 1; ep.resid = N->xg[g]; ep.ldr = d;
+    ep.out32 = N->xg[g + 1]; ep.ld32 = d;
+    NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
+  }
+  const int tj0 = 31 - __builtin_clz((unsigned)(L / r)), tj1 = tj0 + sb.levels - 1;
+  chunk_trees(N, N->xg[2], nullptr, Td, d, tj0, tj1, st);
+  pdl_launch(pool_kernel, dim3(To), dim3(128), 0, st, sb, N->tree_a, tj0, d, N->pooled);
+  {
+    GemmEpi ep = e; ep.bias = W + o.poolb; ep.out32 = N->act[1][0].x_in; ep.ld32 = d;
+    NET_TRY(gemm(N->pooled, 2 * d, W16 + o.map16(o.poolw), To, d, 2 * d, ep, st));
+  }
+  NET_TRY(fork(sE, st));   // edge biases ready
+  // ---- layers
+  const float* xin[2] = {N->xg[2], N->act[1][0].x_in};
+  for (int l = 0; l < cf.n_layers; ++l) {
+    FusedStack fs[2];
+    FusedWeights fw[2];
+    for (int s = 0; s < 2; ++s) {
+      StackAct& a = N->act[s][l];
+      const BlockOff& bo = o.blk[s][l];
+      FusedStack& f = fs[s];
+      f.x_in = xin[s];
+      f.x_mid = a.x_mid;
+      f.y32 = a.y2f;
+      f.u = a.u;
+      f.ldu = 4 * d;
+      f.x_out = (l + 1 < cf.n_layers) ? N->act[s][l + 1].x_in : N->x_final[s];
+      f.gp16 = nullptr;
+      f.ln1g = W + bo.ln1g; f.ln1b = W + bo.ln1b; f.ln2g = W + bo.ln2g; f.ln2b = W + bo.ln2b;
+      f.qkvb = W + bo.qkvb; f.outb = W + bo.outb; f.f1b = W + bo.f1b; f.f2b = W + bo.f2b;
+      f.table = N->ftable[l];
+      f.nbrb = N->fnbr[l];
+      f.dense = a.bias;
+      f.T = s == 0 ? Td : To;
+      f.per_sys = s == 0 ? n : MH * r;
+      fw[s].wqkv = W16 + o.map16(bo.qkvw);
+      fw[s].wout = W16 + o.map16(bo.outw);
+      fw[s].w1 = W16 + o.map16(bo.f1w);
+      fw[s].w2 = W16 + o.map16(bo.f2w);
+      xin[s] = f.x_out;
+    }
+    NET_TRY(fused_layer(sb, fs, fw, N->gp16, N->gp16 + (size_t)(Td / 16) * d, N->gmean, N->err, st));
+  }
+  // ---- final norms and heads (as in net_forward)
+  for (int s = 0; s < 2; ++s) {
+    const int T = s == 0 ? Td : To;
+    pdl_launch(layernorm_kernel, dim3((T + 7) / 8), dim3(256), 0, st, N->x_final[s], W + o.lnfg[s], W + o.lnfb[s], T, d, N->yf[s],
+               (float*)nullptr, N->muf[s], N->rsf[s], 0);
+  }
+  {
+    GemmEpi ep = e; ep.bias = W + o.leaf1b; ep.act = 1; ep.out16 = N->leafh; ep.ld16 = d;
+    NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.leaf1w), Td, d, d, ep, st));
+  }
+  {
+    GemmEpi ep = e; ep.bias = W + o.leaf2b; ep.out32 = N->frow; ep.ld32 = L;
+    NET_TRY(gemm(N->leafh, d, W16 + o.map16(o.leaf2w), Td, L, d, ep, st));
+  }
+  {
+    GemmEpi ep = e; ep.bias = W + o.nodeb; ep.out32 = N->nodeo; ep.ld32 = 2 * r;
+    NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.nodew), Td, 2 * r, d, ep, st));
+  }
+  pdl_launch(gate_logit_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, N->yf[0], W + o.nodew + (int64_t)2 * r * d, W + o.nodeb + 2 * r, Td, d,
+             N->gate_logit);
+  {
+    GemmEpi ep = e; ep.bias = W + o.offb; ep.out32 = N->offo; ep.ld32 = 2 * r;
+    NET_TRY(gemm(N->yf[1], d, W16 + o.map16(o.offw), To, 2 * r, d, ep, st));
+  }
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
 int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int dtype, float* scales, cudaStream_t st) {
   Net* N = c->net;
   SysBatch sb;
   NET_TRY(make_batch(N->cfg, systems, nsys, sb));
   if (dtype != HMPCG_F32 && dtype != HMPCG_BF16) return HMPCG_E_INVALID;
   (void)scales;
-  NET_TRY(net_forward(N, sb, st));
+  if (N->use_fused && N->fused_alloc && fused_supported(N->cfg, sb)) NET_TRY(net_forward_fused(N, sb, st));
+  else NET_TRY(net_forward(N, sb, st));
   const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
   const int Td = sb.B * sb.n;
   const int Tt = sb.B * sb.MH;

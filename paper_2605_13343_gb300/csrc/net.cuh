@@ -80,6 +80,8 @@ struct StackAct {
   float* bias;      // edge bias [nwin][h][W][W]
 };
 
+constexpr int kEdgeMaxLayersNet = 16;
+
 struct Net {
   hmpcg_config cfg;
   WeightOff off;
@@ -124,6 +126,13 @@ struct Net {
   bf16* w16t;
   struct Train* tr;  // training buffers, allocated on the first train step
   int num_sms = 148;
+  // fused inference: per-layer bias tables [h][L][L] and stencil-neighbour biases [Td][6][h],
+  // 16-token column sums of LN2 (both stacks); allocated when the shape allows the fused path
+  float* ftable[kEdgeMaxLayersNet] = {};
+  float* fnbr[kEdgeMaxLayersNet] = {};
+  float* gp16 = nullptr;
+  bool fused_alloc = false;
+  int use_fused = 1;
   // scratch for the backward pass and training
   std::vector<void*> allocs;
 };
@@ -144,6 +153,42 @@ struct SysBatch {
 };
 
 int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, SysBatch& sb);
+
+// ---- fused inference layers (net_fused.cu): one stack's buffers and parameters of one layer
+struct FusedStack {
+  const float* x_in;      // residual stream entering the layer [T][d]
+  float* x_mid;           // after the attention residual [T][d]
+  float* y32;             // LN2 output, FP32 [T][d]
+  bf16* u;                // FFN input [T][ldu] BF16: y | r_hw (or row-chunk mean) | c_hw (or column-chunk mean)
+  int ldu;
+  float* x_out;           // residual stream leaving the layer [T][d]
+  float* gp16;            // 16-token column sums of y [T / 16][d]
+  const float *ln1g, *ln1b, *ln2g, *ln2b, *qkvb, *outb, *f1b, *f2b;
+  const float* table;     // diagonal stack: zero-coupling bias table [h][L][L]
+  const float* nbrb;      // diagonal stack: stencil-neighbour biases [T][2 ndim][h]
+  const float* dense;     // tile stack: biases [nwin][h][r][r]
+  int T;                  // tokens of this stack (all systems)
+  int per_sys;            // tokens per system
+};
+struct FusedWeights {
+  const bf16 *wqkv, *wout, *w1, *w2;   // BF16 [out][in] row-major (padded layout, 128-byte aligned)
+};
+// d = 128, 4 heads of 32, d_mlp = 512, leaf 64, rank 16, n a multiple of 128 and at most 16384
+bool fused_supported(const hmpcg_config& c, const SysBatch& sb);
+int fused_hw_block(int n, int L, int r);
+int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], float* gp16d, float* gp16o, float* g32,
+                int* err, cudaStream_t s);
+
+constexpr int kEdgeMaxLayers = 16;
+struct EdgePrep {
+  const float* e1w[2][kEdgeMaxLayers];
+  const float* e1b[2][kEdgeMaxLayers];
+  const float* e2w[2][kEdgeMaxLayers];
+  const float* e2b[2][kEdgeMaxLayers];
+  float* table[kEdgeMaxLayers];
+  float* nbr[kEdgeMaxLayers];
+  float* dense[kEdgeMaxLayers];
+};
 int net_forward(Net* N, const SysBatch& sb, cudaStream_t st);
 int net_pack_f32(Net* N, const SysBatch& sb, float* packed, cudaStream_t st);
 void net_train_release(Net* N);

@@ -1,0 +1,864 @@
+// Fused inference layers of the hierarchical transformer (Sec. 4.2, Sec. 4.3; Supp. B) on the
+// 5th-generation tensor cores.
+//
+// A layer is three launches over both stacks (diagonal windows of L = 64 tokens, tile windows of
+// L_s = 16 tokens); every CTA owns 128 consecutive tokens of one stack, one per TMEM lane:
+//
+//   fused_attn_kernel  x -> LN1 -> QKV (tcgen05, N = 384) -> per head S = Q K^T (tcgen05,
+//                      128 x 128 over the CTA's tokens, the window's diagonal block kept) + edge
+//                      bias -> softmax -> O = P V (tcgen05) -> output projection (tcgen05)
+//                      + residual -> LN2; writes x_mid, y = LN2 (FP32 for the highways, BF16 as
+//                      the FFN input's first block) and 16-token column sums of y.
+//   fused_hw_kernel    r_hw / c_hw of the diagonal tokens, the chunk means of the tile tokens
+//                      (Sec. 4.3) and the global token g from the 16-token sums.
+//   fused_ffn_kernel   [y, r_hw, c_hw, g] (TMA) -> FFN1 (tcgen05, 128 x 512 x 512) -> GELU ->
+//                      FFN2 (tcgen05) + residual.
+//
+// Weights reach shared memory by TMA with the 128-byte swizzle; activations written by threads
+// use the same swizzled K-major layout, so every operand is read by the tensor cores straight
+// from shared memory.  The edge bias of a diagonal window is the layer's table of zero-coupling
+// pairs (in-leaf positions only) with the stencil-neighbour entries overridden per token; a tile
+// window's bias is read whole (16 x 16 per head).  Every wait is bounded: on a timeout the CTA
+// records HMPCG_E_TIMEOUT, still waits (bounded) for its own MMAs and frees its TMEM.
+#include <cuda.h>
+#include <algorithm>
+#include "net.cuh"
+#include "tc.cuh"
+
+namespace hm {
+namespace {
+using namespace tc;
+
+constexpr int kTok = 128;   // tokens per CTA
+constexpr int kD = 128;     // model width
+constexpr int kDM = 512;    // FFN hidden width
+constexpr long kWaitLong = 1l << 24;
+constexpr int kMaxHwBlock = 512;   // nodes per highway block: 2 x 512 x 33 floats of shared memory
+
+// ----------------------------------------------------------------------------- attention block
+// 256 threads: two per token row (row = tid % 128 = TMEM lane; half = tid / 128 takes one half of
+// every row's columns).  Shared-memory map (bytes from the 1024-aligned base):
+constexpr int kAT = 256;
+constexpr uint32_t kA_Q = 0;           // LN1(x), then Q: [128 tok][128] BF16, 2 chunks of 16 KB
+constexpr uint32_t kA_WQ = 32768;      // Wqkv [384][128]: 2 chunks of 48 KB
+constexpr uint32_t kA_K = 32768;       // after the QKV MMAs: K [128 tok][128]
+constexpr uint32_t kA_O = 32768;       // after the S MMAs: O [128 tok][128]
+constexpr uint32_t kA_YS = 32768;      // after the output projection: LN2 rows [128][129] FP32
+constexpr uint32_t kA_VT = 65536;      // V^T [128 dims][128 tok]
+constexpr uint32_t kA_P = 98304;       // P [128 q][128 keys]
+constexpr uint32_t kA_WO = 131072;     // Wout [128][128]
+constexpr uint32_t kA_RB = 163840;     // bias rows [128][65] FP32
+constexpr uint32_t kA_PAR = kA_RB + 128 * 65 * 4;   // ln1 g/b, ln2 g/b, qkv bias, out bias: 1024 FP32
+constexpr uint32_t kA_XCH = kA_PAR + 1024 * 4;      // per-row exchange between the two halves
+constexpr uint32_t kA_SMEM = kA_XCH + 1536 * 4 + 1024;
+// parameter offsets (floats) inside kA_PAR
+constexpr int kP_LN1G = 0, kP_LN1B = 128, kP_LN2G = 256, kP_LN2B = 384, kP_QKVB = 512, kP_OUTB = 896;
+// exchange offsets (floats) inside kA_XCH: two [2][128] scratch pairs, lsum [2][4][128]
+constexpr int kX_A = 0, kX_B = 256, kX_L = 512;
+
+// TMEM columns: QKV 0..383, then S double buffer at 0 / 128, O at 384 + 32 h, projection at 256.
+struct AttnArgs {
+  FusedStack st[2];
+  Morton mo;
+  int n, nd2, nblk_d;
+  float scale;
+  int* err;
+};
+
+HM_INLINE void issue_s(uint8_t* sm, uint32_t dst, int hd) {
+  const uint32_t idesc = idesc_bf16(128, 128);
+  const uint64_t aq = sw128_desc(smem_u32(sm + kA_Q + (hd >> 1) * 16384));
+  const uint64_t bk = sw128_desc(smem_u32(sm + kA_K + (hd >> 1) * 16384));
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const uint64_t adv = (uint64_t)(((hd & 1) * 64 + j * 32) >> 4);   // byte offset inside the 128-byte row
+    mma_bf16(dst, aq + adv, bk + adv, idesc, j ? 1u : 0u);
+  }
+}
+
+// Bias block of head hd for the CTA's windows, fetched into registers one head ahead (4 float4
+// per thread): diagonal stack the table [64][64] of the layer, tile stack the 8 windows' [16][16].
+HM_INLINE void bias_fetch(const FusedStack& S, int sidx, int row0, int hd, int tid, float4 (&pf)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = tid + kAT * k;
+    pf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sidx == 0) {
+      pf[k] = reinterpret_cast<const float4*>(S.table + (size_t)hd * 4096)[q];
+    } else if (k < 2) {
+      const int w = q >> 6, e4 = q & 63;   // window of the CTA, float4 inside its 16 x 16 block
+      const int win = (row0 >> 4) + w;
+      if (win * 16 < S.T) pf[k] = reinterpret_cast<const float4*>(S.dense + ((size_t)win * 4 + hd) * 256)[e4];
+    }
+  }
+}
+HM_INLINE void bias_store(float* rb, int sidx, int tid, const float4 (&pf)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int q = tid + kAT * k;
+    if (sidx == 0) {
+      const int a = q >> 4, c = (q & 15) * 4;   // table row a goes to both windows' rows a and a + 64
+      float* r0 = rb + a * 65 + c;
+      float* r1 = rb + (a + 64) * 65 + c;
+      r0[0] = pf[k].x; r0[1] = pf[k].y; r0[2] = pf[k].z; r0[3] = pf[k].w;
+      r1[0] = pf[k].x; r1[1] = pf[k].y; r1[2] = pf[k].z; r1[3] = pf[k].w;
+    } else if (k < 2) {
+      const int w = q >> 6, e = (q & 63) * 4;   // row w * 16 + e / 16, key columns e % 16 ..
+      float* r = rb + (w * 16 + (e >> 4)) * 65 + (e & 15);
+      r[0] = pf[k].x; r[1] = pf[k].y; r[2] = pf[k].z; r[3] = pf[k].w;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kAT, 1)
+    fused_attn_kernel(const __grid_constant__ CUtensorMap mq0, const __grid_constant__ CUtensorMap mq1,
+                      const __grid_constant__ CUtensorMap mo0, const __grid_constant__ CUtensorMap mo1,
+                      const __grid_constant__ AttnArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t bar_w, bar_qkv, bar_s[2], bar_pv, bar_o, bar_end;
+  __shared__ uint32_t tmem_s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127, half = tid >> 7;
+  const int sidx = blockIdx.x < a.nblk_d ? 0 : 1;
+  const FusedStack& S = a.st[sidx];
+  const int row0 = (sidx ? blockIdx.x - a.nblk_d : blockIdx.x) * kTok;
+  const int grow = row0 + row;
+  const bool valid = grow < S.T;
+  float* par = reinterpret_cast<float*>(sm + kA_PAR);
+  float* xch = reinterpret_cast<float*>(sm + kA_XCH);
+  float* rb = reinterpret_cast<float*>(sm + kA_RB);
+  bool ok = true;
+
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar_w), 1);
+    mbar_init(smem_u32(&bar_qkv), 1);
+    mbar_init(smem_u32(&bar_s[0]), 1);
+    mbar_init(smem_u32(&bar_s[1]), 1);
+    mbar_init(smem_u32(&bar_pv), 1);
+    mbar_init(smem_u32(&bar_o), 1);
+    mbar_init(smem_u32(&bar_end), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    // the layer's weights do not depend on the previous kernel: fetch them before its end
+    const CUtensorMap* mq = sidx ? &mq1 : &mq0;
+    const CUtensorMap* mw = sidx ? &mo1 : &mo0;
+    const uint32_t bw = smem_u32(&bar_w);
+    mbar_expect_tx(bw, 3 * 2 * 16384 + 2 * 16384);
+    for (int kc = 0; kc < 2; ++kc)
+      for (int rb_ = 0; rb_ < 3; ++rb_) tma_load_2d(smem_u32(sm + kA_WQ + kc * 49152 + rb_ * 16384), mq, kc * 64, rb_ * 128, bw);
+    for (int kc = 0; kc < 2; ++kc) tma_load_2d(smem_u32(sm + kA_WO + kc * 16384), mw, kc * 64, 0, bw);
+  }
+  // layer parameters into shared memory (also weights: independent of the previous kernel)
+  for (int q = tid; q < 1024; q += kAT) {
+    float v;
+    if (q < 128) v = S.ln1g[q];
+    else if (q < 256) v = S.ln1b[q - 128];
+    else if (q < 384) v = S.ln2g[q - 256];
+    else if (q < 512) v = S.ln2b[q - 384];
+    else if (q < 896) v = S.qkvb[q - 512];
+    else v = S.outb[q - 896];
+    par[q] = v;
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_s)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's 32 lanes = its 32 rows
+  pdl_entry();
+  float4 pf[4];
+  bias_fetch(S, sidx, row0, 0, tid, pf);   // written by an earlier kernel: after the dependency wait
+  float nbv[6][4];                          // stencil-neighbour biases of this row, all heads
+  if (sidx == 0 && valid) {
+    for (int dir = 0; dir < a.nd2; ++dir) {
+      const float4 f = reinterpret_cast<const float4*>(S.nbrb)[(size_t)grow * a.nd2 + dir];
+      nbv[dir][0] = f.x; nbv[dir][1] = f.y; nbv[dir][2] = f.z; nbv[dir][3] = f.w;
+    }
+  }
+
+  // ---- LN1 of the row -> A operand (swizzled K-major BF16); each thread one 64-column half
+  {
+    float v[64];
+    if (valid) {
+      const float4* xp = reinterpret_cast<const float4*>(S.x_in + (size_t)grow * kD + 64 * half);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float4 f = xp[q];
+        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 64; ++c) v[c] = 0.f;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) s += v[c];
+    xch[kX_A + half * 128 + row] = s;
+    __syncthreads();
+    const float mean = (xch[kX_A + row] + xch[kX_A + 128 + row]) * (1.f / kD);
+    float ss = 0.f;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) { const float u = v[c] - mean; ss = fmaf(u, u, ss); }
+    xch[kX_B + half * 128 + row] = ss;
+    __syncthreads();
+    const float rstd = rsqrtf((xch[kX_B + row] + xch[kX_B + 128 + row]) * (1.f / kD) + 1e-5f);
+    const float* g = par + kP_LN1G + 64 * half;
+    const float* b = par + kP_LN1B + 64 * half;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) v[c] = valid ? (v[c] - mean) * rstd * g[c] + b[c] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) st_unit_bf16(sm + kA_Q + half * 16384 + sw128(row, u), v + u * 8);
+  }
+  fence_async_smem();
+  __syncthreads();
+
+  // ---- QKV = LN1(x) Wqkv^T: N = 256 (Q, K) and N = 128 (V) over K = 128
+  if (tid == 0) {
+    if (!mbar_wait(smem_u32(&bar_w), 0, kWaitLong)) ok = false;
+    tc_fence_after();
+    const uint32_t id256 = idesc_bf16(128, 256), id128 = idesc_bf16(128, 128);
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      const uint64_t ad = sw128_desc(smem_u32(sm + kA_Q + kc * 16384));
+      const uint64_t b0 = sw128_desc(smem_u32(sm + kA_WQ + kc * 49152));
+      const uint64_t b1 = sw128_desc(smem_u32(sm + kA_WQ + kc * 49152 + 32768));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t acc = (kc | k) ? 1u : 0u;
+        mma_bf16(tmem, ad + 2 * k, b0 + 2 * k, id256, acc);
+        mma_bf16(tmem + 256, ad + 2 * k, b1 + 2 * k, id128, acc);
+      }
+    }
+    mma_commit(smem_u32(&bar_qkv));
+  }
+  if (!mbar_wait(smem_u32(&bar_qkv), 0, kWaitLong)) ok = false;
+  __syncwarp();   // tcgen05.ld is warp-collective: reconverge after the issue branch and the wait
+  tc_fence_after();
+  // 12 column chunks of 32: half 0 takes Q (0-3) and V (8-9), half 1 K (4-7) and V (10-11)
+#pragma unroll 1
+  for (int e = 0; e < 6; ++e) {
+    const int c32 = half == 0 ? (e < 4 ? e : 4 + e) : (e < 4 ? 4 + e : 6 + e);
+    float v[32];
+    tmem_ld32(tl + c32 * 32, v);
+    const float* bq = par + kP_QKVB + c32 * 32;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] += bq[j];
+    if (c32 < 8) {
+      uint8_t* base = sm + (c32 < 4 ? kA_Q : kA_K) + ((c32 & 3) >> 1) * 16384;
+#pragma unroll
+      for (int u4 = 0; u4 < 4; ++u4) st_unit_bf16(base + sw128(row, (c32 & 1) * 4 + u4), v + 8 * u4);
+    } else {
+      // V transposed: element (dim, token) at row dim of the chunk holding the token
+      uint8_t* base = sm + kA_VT + (row >> 6) * 16384;
+      const int unit = (row & 63) >> 3, sub = (row & 7) * 2;
+      const int d0 = (c32 - 8) * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) *reinterpret_cast<bf16*>(base + sw128(d0 + j, unit) + sub) = __float2bfloat16_rn(v[j]);
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+
+  // ---- attention, one head at a time; S of head h + 2 is issued as soon as S of head h is read
+  if (tid == 0) {
+    tc_fence_after();
+    issue_s(sm, tmem, 0);
+    mma_commit(smem_u32(&bar_s[0]));
+    issue_s(sm, tmem + 128, 1);
+    mma_commit(smem_u32(&bar_s[1]));
+  }
+  const int i_sys = grow % a.n;          // diagonal stack: node index within its system
+  float* myrb = rb + row * 65;
+  const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+  for (int hd = 0; hd < 4; ++hd) {
+    bias_store(rb, sidx, tid, pf);
+    __syncthreads();
+    if (hd < 3) bias_fetch(S, sidx, row0, hd + 1, tid, pf);
+    uint8_t* pb = sm + kA_P;
+    if (!mbar_wait(smem_u32(&bar_s[hd & 1]), (hd >> 1) & 1, kWaitLong)) ok = false;
+    __syncwarp();
+    tc_fence_after();
+    const uint32_t scol = (uint32_t)((hd & 1) * 128);
+    if (sidx == 0) {
+      // a row's 64 keys are the CTA's key columns [64 (row / 64), +64): this thread takes half
+      const int wbase = (row >> 6) * 64 + 32 * half;
+      float s[32];
+      tmem_ld32(tl + scol + wbase, s);
+      if (valid) {
+        // stencil neighbours inside the leaf carry their own coupling: override their entries
+        for (int dir = 0; dir < a.nd2; ++dir) {
+          const int j = (dir & 1) ? a.mo.minus((unsigned)i_sys, dir >> 1) : a.mo.plus((unsigned)i_sys, dir >> 1);
+          if (j >= 0 && (j >> 6) == (i_sys >> 6) && ((j >> 5) & 1) == half) myrb[j & 63] = nbv[dir][hd];
+        }
+      }
+      float m = -3e38f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { s[j] = fmaf(s[j], a.scale, myrb[32 * half + j]); m = fmaxf(m, s[j]); }
+      xch[kX_A + half * 128 + row] = m;
+      __syncthreads();
+      m = fmaxf(xch[kX_A + row], xch[kX_A + 128 + row]);
+      float l = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { s[j] = __expf(s[j] - m); l += s[j]; }
+      xch[kX_L + (half * 4 + hd) * 128 + row] = l;
+      if (hd > 0 && !mbar_wait(smem_u32(&bar_pv), (hd - 1) & 1, kWaitLong)) ok = false;
+      const int wc = row >> 6;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        st_unit_bf16(pb + wc * 16384 + sw128(row, 4 * half + u), s + 8 * u);
+        st_unit_bf16(pb + (1 - wc) * 16384 + sw128(row, 4 * half + u), zero8);
+      }
+    } else {
+      // windows of 16: the warp's 32 rows hold two windows, keys [32 (warp % 4), +32); both
+      // threads of a row compute its 16-key softmax, each writes one chunk of the P row
+      float s32[32];
+      tmem_ld32(tl + scol + (warp & 3) * 32, s32);
+      const bool hi = (row >> 4) & 1;
+      float s[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) s[j] = hi ? s32[16 + j] : s32[j];
+      float m = -3e38f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) { s[j] = fmaf(s[j], a.scale, myrb[j]); m = fmaxf(m, s[j]); }
+      float l = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) { s[j] = __expf(s[j] - m); l += s[j]; }
+      xch[kX_L + (half * 4 + hd) * 128 + row] = half ? 0.f : l;
+      if (hd > 0 && !mbar_wait(smem_u32(&bar_pv), (hd - 1) & 1, kWaitLong)) ok = false;
+      // keys of this row's window: [16 (row / 16), +16) = chunk row / 64, units 2 ((row / 16) % 4) + {0, 1}
+      const int wc = row >> 6, wu = ((row >> 4) & 3) * 2;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool in = half == wc && (u == wu || u == wu + 1);
+        st_unit_bf16(pb + half * 16384 + sw128(row, u), in ? (u == wu ? s : s + 8) : zero8);
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t idesc = idesc_bf16(128, 32);
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc) {
+        const uint64_t ad = sw128_desc(smem_u32(pb + kc * 16384));
+        const uint64_t bd = sw128_desc(smem_u32(sm + kA_VT + kc * 16384 + hd * 4096));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mma_bf16(tmem + 384 + 32 * hd, ad + 2 * k, bd + 2 * k, idesc, (kc | k) ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&bar_pv));
+      if (hd + 2 < 4) {
+        issue_s(sm, tmem + scol, hd + 2);
+        mma_commit(smem_u32(&bar_s[hd & 1]));
+      }
+    }
+  }
+  if (!mbar_wait(smem_u32(&bar_pv), 1, kWaitLong)) ok = false;   // P V of head 3 (4th completion)
+  __syncwarp();
+  tc_fence_after();
+  // ---- O / l -> BF16 tile (half 0: heads 0, 1; half 1: heads 2, 3), then the output projection
+#pragma unroll 1
+  for (int e = 0; e < 2; ++e) {
+    const int hd = 2 * half + e;
+    float v[32];
+    tmem_ld32(tl + 384 + hd * 32, v);
+    const float inv = 1.f / (xch[kX_L + hd * 128 + row] + xch[kX_L + (4 + hd) * 128 + row]);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] *= inv;
+#pragma unroll
+    for (int u4 = 0; u4 < 4; ++u4) st_unit_bf16(sm + kA_O + half * 16384 + sw128(row, e * 4 + u4), v + 8 * u4);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc_fence_after();
+    const uint32_t idesc = idesc_bf16(128, 128);
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      const uint64_t ad = sw128_desc(smem_u32(sm + kA_O + kc * 16384));
+      const uint64_t bd = sw128_desc(smem_u32(sm + kA_WO + kc * 16384));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mma_bf16(tmem + 256, ad + 2 * k, bd + 2 * k, idesc, (kc | k) ? 1u : 0u);
+    }
+    mma_commit(smem_u32(&bar_o));
+  }
+  if (!mbar_wait(smem_u32(&bar_o), 0, kWaitLong)) ok = false;
+  __syncwarp();
+  tc_fence_after();
+  // ---- + bias + residual -> x_mid; LN2 -> y (FP32 and BF16); 16-token column sums of y
+  {
+    float v[64];
+    tmem_ld32(tl + 256 + 64 * half, v);
+    tmem_ld32(tl + 256 + 64 * half + 32, v + 32);
+    const float* ob = par + kP_OUTB + 64 * half;
+    if (valid) {
+      const float4* xp = reinterpret_cast<const float4*>(S.x_in + (size_t)grow * kD + 64 * half);
+      float4* xm = reinterpret_cast<float4*>(S.x_mid + (size_t)grow * kD + 64 * half);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float4 f = xp[q];
+        v[4 * q] += ob[4 * q] + f.x; v[4 * q + 1] += ob[4 * q + 1] + f.y;
+        v[4 * q + 2] += ob[4 * q + 2] + f.z; v[4 * q + 3] += ob[4 * q + 3] + f.w;
+        xm[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) s += v[c];
+    xch[kX_A + half * 128 + row] = s;
+    __syncthreads();
+    const float mean = (xch[kX_A + row] + xch[kX_A + 128 + row]) * (1.f / kD);
+    float ss = 0.f;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) { const float u = v[c] - mean; ss = fmaf(u, u, ss); }
+    xch[kX_B + half * 128 + row] = ss;
+    __syncthreads();
+    const float rstd = rsqrtf((xch[kX_B + row] + xch[kX_B + 128 + row]) * (1.f / kD) + 1e-5f);
+    const float* g = par + kP_LN2G + 64 * half;
+    const float* b = par + kP_LN2B + 64 * half;
+    float* ys = reinterpret_cast<float*>(sm + kA_YS) + row * 129 + 64 * half;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) {
+      v[c] = valid ? (v[c] - mean) * rstd * g[c] + b[c] : 0.f;
+      ys[c] = v[c];
+    }
+    if (valid) {
+      float4* yp = reinterpret_cast<float4*>(S.y32 + (size_t)grow * kD + 64 * half);
+      uint4* up = reinterpret_cast<uint4*>(S.u + (size_t)grow * S.ldu + 64 * half);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint4 pk;
+        pk.x = pack_bf16x2(v[8 * q], v[8 * q + 1]); pk.y = pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
+        pk.z = pack_bf16x2(v[8 * q + 4], v[8 * q + 5]); pk.w = pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
+        up[q] = pk;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const float* ys = reinterpret_cast<const float*>(sm + kA_YS);
+    const int c = row;
+#pragma unroll 1
+    for (int grp = 4 * half; grp < 4 * half + 4; ++grp) {
+      if (row0 + grp * 16 >= S.T) break;   // T is a multiple of 16: groups are whole
+      float s = 0.f;
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) s += ys[(grp * 16 + rr) * 129 + c];
+      S.gp16[(size_t)(row0 / 16 + grp) * kD + c] = s;
+    }
+  }
+  // ---- teardown: every MMA of this CTA has completed before TMEM is freed
+  if (tid == 0) mma_commit(smem_u32(&bar_end));
+  if (!mbar_wait(smem_u32(&bar_end), 0, kWaitLong)) ok = false;
+  if (!ok && a.err) atomicExch(a.err, (int)HMPCG_E_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// ----------------------------------------------------------------------------- highways
+struct HwArgs {
+  const float* yd;
+  const float* yo;        // LN2 outputs (FP32) of both stacks
+  bf16* ud;
+  bf16* uo;               // FFN inputs: columns [d, 2d) = r_hw part, [2d, 3d) = c_hw part
+  int ldu;
+  const float* gpd;
+  const float* gpo;       // 16-token column sums of y
+  float* g32;             // [B][d] global token
+  int B, n, L, r, K, MH, levels, NB, nblk;
+};
+
+// Blocks x < nblk: NB consecutive diagonal tokens x 32 channels: r_hw and c_hw (mean over the
+// tokens covering the node's row / column: itself and, per level, the tile token whose row
+// (column) chunk holds it), then an in-place pairwise tree over the block whose level j holds
+// the sums of aligned 2^j-node chunks: every tile token whose chunk lies in the block takes its
+// mean from there.  Blocks x >= nblk: 8 channels of the global token of one system (mean of y
+// over both stacks), from the 16-token sums.
+__global__ void __launch_bounds__(256) fused_hw_kernel(const __grid_constant__ HwArgs a) {
+  extern __shared__ float hs[];
+  pdl_entry();
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.y * 32;
+  if ((int)blockIdx.x >= a.nblk) {
+    __shared__ float red[32][9];
+    const int q = blockIdx.x - a.nblk;
+    const int b = q >> 2, cs8 = c0 + (q & 3) * 8;
+    const int c = tid & 7, part = tid >> 3;   // 32 parts
+    const int ngd = a.n / 16, ngo = a.MH * a.r / 16;
+    float acc0 = 0.f, acc1 = 0.f;
+    int g = part;
+    for (; g + 32 < ngd; g += 64) {
+      acc0 += a.gpd[((size_t)b * ngd + g) * kD + cs8 + c];
+      acc1 += a.gpd[((size_t)b * ngd + g + 32) * kD + cs8 + c];
+    }
+    for (; g < ngd; g += 32) acc0 += a.gpd[((size_t)b * ngd + g) * kD + cs8 + c];
+    for (g = part; g < ngo; g += 32) acc1 += a.gpo[((size_t)b * ngo + g) * kD + cs8 + c];
+    red[part][c] = acc0 + acc1;
+    __syncthreads();
+    if (part == 0) {
+      float s = 0.f;
+#pragma unroll
+      for (int p = 0; p < 32; ++p) s += red[p][c];
+      a.g32[(size_t)b * kD + cs8 + c] = s / (float)(a.n + a.MH * a.r);
+    }
+    return;
+  }
+  const int NB = a.NB;
+  float* rs = hs;
+  float* cs = hs + NB * 33;
+  const int t0 = blockIdx.x * NB;
+  const int b = t0 / a.n, ib0 = t0 % a.n;
+  const int lgL = 31 - __clz(a.L), lgr = 31 - __clz(a.r);
+  for (int q = tid; q < NB * 8; q += blockDim.x) {
+    const int node = q >> 3, cg = (q & 7) * 4;
+    const int i = ib0 + node, t = t0 + node;
+    const int k = i >> lgL;
+    float4 rsum = *reinterpret_cast<const float4*>(a.yd + (size_t)t * kD + c0 + cg);
+    float4 csum = rsum;
+    int nr = 1, nc = 1;
+    for (int lev = 1; lev <= a.levels; ++lev) {
+      const int lgS = a.levels - lev;
+      const int cl = k >> lgS;
+      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+      const int at = (i - (cl << (lgS + lgL))) >> (lgS + lgL - lgr);
+      const float4 v = *reinterpret_cast<const float4*>(a.yo + ((size_t)(b * a.MH + m) * a.r + at) * kD + c0 + cg);
+      if (cl & 1) { csum.x += v.x; csum.y += v.y; csum.z += v.z; csum.w += v.w; ++nc; }
+      else { rsum.x += v.x; rsum.y += v.y; rsum.z += v.z; rsum.w += v.w; ++nr; }
+    }
+    const float ir = 1.f / (float)nr, ic = 1.f / (float)nc;
+    rsum.x *= ir; rsum.y *= ir; rsum.z *= ir; rsum.w *= ir;
+    csum.x *= ic; csum.y *= ic; csum.z *= ic; csum.w *= ic;
+    float* rr = rs + node * 33 + cg;
+    float* cc = cs + node * 33 + cg;
+    rr[0] = rsum.x; rr[1] = rsum.y; rr[2] = rsum.z; rr[3] = rsum.w;
+    cc[0] = csum.x; cc[1] = csum.y; cc[2] = csum.z; cc[3] = csum.w;
+    bf16* u = a.ud + (size_t)t * a.ldu;
+    *reinterpret_cast<uint2*>(u + kD + c0 + cg) = make_uint2(pack_bf16x2(rsum.x, rsum.y), pack_bf16x2(rsum.z, rsum.w));
+    *reinterpret_cast<uint2*>(u + 2 * kD + c0 + cg) = make_uint2(pack_bf16x2(csum.x, csum.y), pack_bf16x2(csum.z, csum.w));
+  }
+  __syncthreads();
+  const int jmin = lgL - lgr;            // chunk of the deepest level: L / r nodes
+  const int lgNB = 31 - __clz(NB);
+  for (int j = 1; j <= lgNB; ++j) {
+    const int cnt = NB >> j;
+    for (int q = tid; q < cnt * 64; q += blockDim.x) {
+      float* buf = q < cnt * 32 ? rs : cs;
+      const int qq = q < cnt * 32 ? q : q - cnt * 32;
+      const int g = qq >> 5, c = qq & 31;
+      buf[(g << j) * 33 + c] += buf[((g << j) + (1 << (j - 1))) * 33 + c];
+    }
+    __syncthreads();
+    const int lev = a.levels - (j - jmin);   // the level whose chunks hold 2^j nodes
+    if (j >= jmin && lev >= 1 && lev <= a.levels) {
+      const int lgS = a.levels - lev;
+      const float inv = 1.f / (float)(1 << j);
+      for (int q = tid; q < cnt * 32; q += blockDim.x) {
+        const int g = q >> 5, c = q & 31;
+        const int start = ib0 + (g << j);
+        const int cl = (start >> lgL) >> lgS;
+        const int side = cl & 1;
+        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+        const int at = (start - (cl << (lgS + lgL))) >> j;
+        const float* src = side ? cs : rs;
+        a.uo[((size_t)(b * a.MH + m) * a.r + at) * a.ldu + kD + side * kD + c0 + c] =
+            __float2bfloat16_rn(src[(g << j) * 33 + c] * inv);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- FFN
+// 320 threads: warps 0-7 two per token row (the global-token columns of the input, the GELU
+// epilogue into H, the output epilogue), warp 8 the TMA producer (input tile, then 16 stages of
+// W1 and 8 of W2 through a 3-stage ring), warp 9 the MMA issuer.  TMEM: FFN1 in all 512 columns,
+// FFN2 in columns 0..127 once H has been read out.
+constexpr int kFT = 320;
+constexpr int kFStages = 3;
+constexpr uint32_t kF_U = 0;           // FFN input [128][512] BF16 (8 chunks); then the hidden H
+constexpr uint32_t kF_RING = 131072;   // weight ring: 3 stages of 32 KB
+constexpr uint32_t kF_SMEM = kF_RING + kFStages * 32768 + 1024;
+
+struct FfnArgs {
+  FusedStack st[2];
+  const float* g32;
+  int nblk_d;
+  int* err;
+};
+
+__global__ void __launch_bounds__(kFT, 1)
+    fused_ffn_kernel(const __grid_constant__ CUtensorMap mu0, const __grid_constant__ CUtensorMap mu1,
+                     const __grid_constant__ CUtensorMap m10, const __grid_constant__ CUtensorMap m11,
+                     const __grid_constant__ CUtensorMap m20, const __grid_constant__ CUtensorMap m21,
+                     const __grid_constant__ FfnArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t bar_u, full[kFStages], empty[kFStages], bar_f1, bar_f2;
+  __shared__ uint32_t tmem_s;
+  __shared__ int fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sidx = blockIdx.x < a.nblk_d ? 0 : 1;
+  const FusedStack& S = a.st[sidx];
+  const int row0 = (sidx ? blockIdx.x - a.nblk_d : blockIdx.x) * kTok;
+  bool ok = true;
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar_u), 1);
+    for (int s = 0; s < kFStages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_f1), 1);
+    mbar_init(smem_u32(&bar_f2), 1);
+    fail_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_s)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      const CUtensorMap* mu = sidx ? &mu1 : &mu0;
+      const CUtensorMap* m1 = sidx ? &m11 : &m10;
+      const CUtensorMap* m2 = sidx ? &m21 : &m20;
+      for (int i = 0; i < 24; ++i) {
+        const int st = i % kFStages;
+        if (i >= kFStages && !mbar_wait(smem_u32(&empty[st]), ((i / kFStages) - 1) & 1, kWaitLong)) { ok = false; break; }
+        const uint32_t fb = smem_u32(&full[st]);
+        if (i < 16) {
+          mbar_expect_tx(fb, 32768);
+          tma_load_2d(smem_u32(sm + kF_RING + st * 32768), m1, (i & 7) * 64, (i >> 3) * 256, fb);
+        } else {
+          mbar_expect_tx(fb, 16384);
+          tma_load_2d(smem_u32(sm + kF_RING + st * 32768), m2, (i - 16) * 64, 0, fb);
+        }
+        if (i == kFStages - 1) {
+          // the input tile is the previous kernels' output: wait for them, then fetch it
+          pdl_entry();
+          const uint32_t ub = smem_u32(&bar_u);
+          mbar_expect_tx(ub, 6 * 16384);
+          for (int kc = 0; kc < 6; ++kc) tma_load_2d(smem_u32(sm + kF_U + kc * 16384), mu, kc * 64, row0, ub);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 9) {
+    pdl_entry();
+    named_sync(1, 288);   // the global-token columns are in shared memory
+    if (lane == 0) {
+      if (!mbar_wait(smem_u32(&bar_u), 0, kWaitLong)) ok = false;
+      tc_fence_after();
+      const uint32_t id256 = idesc_bf16(128, 256);
+      for (int i = 0; i < 16; ++i) {
+        const int st = i % kFStages;
+        if (!mbar_wait(smem_u32(&full[st]), (i / kFStages) & 1, kWaitLong)) { ok = false; }
+        tc_fence_after();
+        const int nh = i >> 3, kc = i & 7;
+        const uint64_t ad = sw128_desc(smem_u32(sm + kF_U + kc * 16384));
+        const uint64_t bd = sw128_desc(smem_u32(sm + kF_RING + st * 32768));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mma_bf16(tmem + nh * 256, ad + 2 * k, bd + 2 * k, id256, (kc | k) ? 1u : 0u);
+        mma_commit(smem_u32(&empty[st]));
+      }
+      mma_commit(smem_u32(&bar_f1));
+    }
+    __syncwarp();
+    named_sync(2, 288);   // H is in shared memory and FFN1's accumulators have been read
+    if (lane == 0) {
+      tc_fence_after();
+      const uint32_t id128 = idesc_bf16(128, 128);
+      for (int j = 0; j < 8; ++j) {
+        const int i = 16 + j, st = i % kFStages;
+        if (!mbar_wait(smem_u32(&full[st]), (i / kFStages) & 1, kWaitLong)) { ok = false; }
+        tc_fence_after();
+        const uint64_t ad = sw128_desc(smem_u32(sm + kF_U + j * 16384));
+        const uint64_t bd = sw128_desc(smem_u32(sm + kF_RING + st * 32768));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mma_bf16(tmem, ad + 2 * k, bd + 2 * k, id128, (j | k) ? 1u : 0u);
+        mma_commit(smem_u32(&empty[st]));
+      }
+      mma_commit(smem_u32(&bar_f2));
+    }
+    __syncwarp();
+  } else {
+    // warps 0-7: row = tid % 128 (TMEM lane), half = tid / 128
+    pdl_entry();
+    const int row = tid & 127, half = tid >> 7;
+    const int grow = row0 + row;
+    const bool valid = grow < S.T;
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    {
+      float gv[64];
+      if (valid) {
+        const float4* gp = reinterpret_cast<const float4*>(a.g32 + (size_t)(grow / S.per_sys) * kD + 64 * half);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const float4 f = gp[q];
+          gv[4 * q] = f.x; gv[4 * q + 1] = f.y; gv[4 * q + 2] = f.z; gv[4 * q + 3] = f.w;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) gv[c] = 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) st_unit_bf16(sm + kF_U + (6 + half) * 16384 + sw128(row, u), gv + u * 8);
+    }
+    fence_async_smem();
+    named_sync(1, 288);
+    if (!mbar_wait(smem_u32(&bar_f1), 0, kWaitLong)) ok = false;
+    __syncwarp();
+    tc_fence_after();
+#pragma unroll 1
+    for (int e = 0; e < 8; ++e) {
+      const int c32 = half * 8 + e;
+      float v[32];
+      tmem_ld32(tl + c32 * 32, v);
+      const float4* bp = reinterpret_cast<const float4*>(S.f1b + c32 * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 bb = __ldg(bp + q);
+        v[4 * q] = gelu_f(v[4 * q] + bb.x); v[4 * q + 1] = gelu_f(v[4 * q + 1] + bb.y);
+        v[4 * q + 2] = gelu_f(v[4 * q + 2] + bb.z); v[4 * q + 3] = gelu_f(v[4 * q + 3] + bb.w);
+      }
+#pragma unroll
+      for (int u4 = 0; u4 < 4; ++u4) st_unit_bf16(sm + kF_U + (c32 >> 1) * 16384 + sw128(row, (c32 & 1) * 4 + u4), v + 8 * u4);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    named_sync(2, 288);
+    if (!mbar_wait(smem_u32(&bar_f2), 0, kWaitLong)) ok = false;
+    __syncwarp();
+    tc_fence_after();
+#pragma unroll 1
+    for (int e = 0; e < 2; ++e) {
+      const int c32 = half * 2 + e;
+      float v[32];
+      tmem_ld32(tl + c32 * 32, v);
+      if (valid) {
+        const float4* xm = reinterpret_cast<const float4*>(S.x_mid + (size_t)grow * kD + c32 * 32);
+        const float4* bp = reinterpret_cast<const float4*>(S.f2b + c32 * 32);
+        float4* xo = reinterpret_cast<float4*>(S.x_out + (size_t)grow * kD + c32 * 32);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 f = xm[q];
+          const float4 bb = __ldg(bp + q);
+          xo[q] = make_float4(v[4 * q] + bb.x + f.x, v[4 * q + 1] + bb.y + f.y, v[4 * q + 2] + bb.z + f.z,
+                              v[4 * q + 3] + bb.w + f.w);
+        }
+      }
+    }
+  }
+  if (!ok) fail_s = 1;
+  tc_fence_before();
+  __syncthreads();
+  if (fail_s && tid == 0 && a.err) atomicExch(a.err, (int)HMPCG_E_TIMEOUT);
+  __syncwarp();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+template <class... KArgs, class... Args>
+int launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...) == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+}  // namespace
+
+bool fused_supported(const hmpcg_config& c, const SysBatch& sb) {
+  if (c.d_model != kD || c.n_heads != 4 || c.d_mlp != kDM || sb.L != 64 || sb.r != 16) return false;
+  if (sb.n % kTok || sb.K < 2) return false;
+  const int nb = fused_hw_block(sb.n, sb.L, sb.r);
+  return nb > 0 && nb <= kMaxHwBlock;
+}
+
+int fused_hw_block(int n, int L, int r) {
+  // NB consecutive nodes hold every chunk that starts among them: the largest chunk is a
+  // level-1 one, (K / 2) L / r = n / (2 r) nodes; NB divides n (all are powers of two)
+  (void)L;
+  const int big = n / (2 * r);
+  return std::min(std::max(256, big), n);
+}
+
+int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], float* gp16d, float* gp16o, float* g32,
+                int* err, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr{0};
+  if (!once_per_device(attr, [] {
+        return cudaFuncSetAttribute(fused_attn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kA_SMEM) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(fused_ffn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kF_SMEM) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(fused_hw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxHwBlock * 33 * 4) ==
+                   cudaSuccess;
+      }))
+    return HMPCG_E_CUDA;
+  CUtensorMap mq[2], mo[2], mu[2], m1[2], m2[2];
+  for (int i = 0; i < 2; ++i) {
+    if (!tma_map_bf16(&mq[i], w[i].wqkv, 3 * kD, kD, kD, 128) || !tma_map_bf16(&mo[i], w[i].wout, kD, kD, kD, 128) ||
+        !tma_map_bf16(&m1[i], w[i].w1, kDM, 4 * kD, 4 * kD, 256) || !tma_map_bf16(&m2[i], w[i].w2, kD, kDM, kDM, 128) ||
+        !tma_map_bf16(&mu[i], st[i].u, st[i].T, 3 * kD, st[i].ldu, 128))
+      return HMPCG_E_INVALID;
+  }
+  st[0].gp16 = gp16d;
+  st[1].gp16 = gp16o;
+  const int nblk_d = st[0].T / kTok, nblk_o = (st[1].T + kTok - 1) / kTok;
+  AttnArgs aa;
+  aa.st[0] = st[0];
+  aa.st[1] = st[1];
+  aa.mo = sb.mo;
+  aa.n = sb.n;
+  aa.nd2 = 2 * sb.ndim;
+  aa.nblk_d = nblk_d;
+  aa.scale = 0.17677669529663688f;   // 1 / sqrt(32)
+  aa.err = err;
+  int rc = launch_pdl(fused_attn_kernel, dim3(nblk_d + nblk_o), dim3(kAT), kA_SMEM, s, mq[0], mq[1], mo[0], mo[1], aa);
+  if (rc) return rc;
+  HwArgs ha;
+  ha.yd = st[0].y32; ha.yo = st[1].y32;
+  ha.ud = st[0].u; ha.uo = st[1].u; ha.ldu = st[0].ldu;
+  ha.gpd = gp16d; ha.gpo = gp16o; ha.g32 = g32;
+  ha.B = sb.B; ha.n = sb.n; ha.L = sb.L; ha.r = sb.r; ha.K = sb.K; ha.MH = sb.MH; ha.levels = sb.levels;
+  ha.NB = fused_hw_block(sb.n, sb.L, sb.r);
+  ha.nblk = sb.B * sb.n / ha.NB;
+  if (st[1].ldu != ha.ldu) return HMPCG_E_INVALID;
+  rc = launch_pdl(fused_hw_kernel, dim3(ha.nblk + 4 * sb.B, kD / 32), dim3(256), (size_t)2 * ha.NB * 33 * 4, s, ha);
+  if (rc) return rc;
+  FfnArgs fa;
+  fa.st[0] = st[0];
+  fa.st[1] = st[1];
+  fa.g32 = g32;
+  fa.nblk_d = nblk_d;
+  fa.err = err;
+  rc = launch_pdl(fused_ffn_kernel, dim3(nblk_d + nblk_o), dim3(kFT), kF_SMEM, s, mu[0], mu[1], m1[0], m1[1], m2[0], m2[1], fa);
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+}  // namespace hm

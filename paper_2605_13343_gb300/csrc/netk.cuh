@@ -402,6 +402,50 @@ __global__ void edge_bias_off_kernel(const SysBatch sb, const float* __restrict_
   for (int hh = 0; hh < h; ++hh) bias[(((size_t)win * h + hh) * r + a) * r + bb] = out[hh];
 }
 
+// Edge biases of every layer for the fused attention, one launch (blockIdx.y = layer).  Blocks
+// [0, nt): the diagonal table of zero-coupling pairs [h][L][L]; [nt, nt + nn): the stencil-
+// neighbour biases [T][2 ndim][h] (entries whose neighbour lies outside the leaf are unused);
+// the rest: the tile biases [nwin][h][r][r] from the tile descriptors.
+__global__ void edge_prep_kernel(const SysBatch sb, const EdgePrep E, const float* __restrict__ edesc, int h, int nt,
+                                 int nn) {
+  pdl_entry();
+  __shared__ EdgeMlp s;
+  const int l = blockIdx.y, bx = blockIdx.x;
+  const int role = bx < nt ? 0 : (bx < nt + nn ? 1 : 2);
+  const int st = role == 2 ? 1 : 0;
+  load_edge_mlp(s, E.e1w[st][l], E.e1b[st][l], E.e2w[st][l], E.e2b[st][l], h);
+  const int L = sb.L;
+  float e[4], out[8];
+  if (role == 0) {
+    const int idx = bx * blockDim.x + threadIdx.x;
+    if (idx >= L * L) return;
+    const int bb = idx % L, a = idx / L;
+    for (int ax = 0; ax < 3; ++ax)
+      e[ax] = ax < sb.ndim ? ((float)compact(bb, sb.mo.mask[ax]) - (float)compact(a, sb.mo.mask[ax])) / sb.leaf_side : 0.f;
+    e[3] = a == bb ? 1.f : 0.f;
+    edge_mlp(s, e, h, out);
+    for (int hh = 0; hh < h; ++hh) E.table[l][((size_t)hh * L + a) * L + bb] = out[hh];
+  } else if (role == 1) {
+    const int nd = 2 * sb.ndim;
+    const int idx = (bx - nt) * blockDim.x + threadIdx.x;
+    if (idx >= sb.B * sb.n * nd) return;
+    const int dir = idx % nd, t = idx / nd;
+    const int bsys = t / sb.n, i = t % sb.n, k = i / L;
+    const int j = (dir & 1) ? sb.mo.minus(i, dir >> 1) : sb.mo.plus(i, dir >> 1);
+    if (j < 0 || j / L != k) return;
+    leaf_desc(sb, bsys, k, i - k * L, j - k * L, e);
+    edge_mlp(s, e, h, out);
+    for (int hh = 0; hh < h; ++hh) E.nbr[l][(size_t)idx * h + hh] = out[hh];
+  } else {
+    const int r = sb.r;
+    const int idx = (bx - nt - nn) * blockDim.x + threadIdx.x;
+    if (idx >= sb.B * sb.MH * r * r) return;
+    const int bb = idx % r, a = (idx / r) % r, win = idx / (r * r);
+    edge_mlp(s, edesc + (size_t)idx * 4, h, out);
+    for (int hh = 0; hh < h; ++hh) E.dense[l][(((size_t)win * h + hh) * r + a) * r + bb] = out[hh];
+  }
+}
+
 // LayerNorm over d (warp per token), eps = 1e-5.  Writes BF16 (leading dim ld16) and/or FP32.
 __global__ void layernorm_kernel(const float* __restrict__ x, const float* __restrict__ gam,
                                  const float* __restrict__ bet, int T, int d, bf16* __restrict__ out16,
