@@ -34,6 +34,7 @@ constexpr int kD = 128;     // model width
 constexpr int kDM = 512;    // FFN hidden width
 constexpr long kWaitLong = 1l << 24;
 constexpr int kMaxHwBlock = 512;   // nodes per highway block: 2 x 512 x 33 floats of shared memory
+constexpr int kMaxLevels = 9;      // tree levels of the fused path (K <= 512 leaves)
 
 // ----------------------------------------------------------------------------- attention block
 // 256 threads: two per token row (row = tid % 128 = TMEM lane; half = tid / 128 takes one half of
@@ -43,7 +44,8 @@ constexpr uint32_t kA_Q = 0;           // LN1(x), then Q: [128 tok][128] BF16, 2
 constexpr uint32_t kA_WQ = 32768;      // Wqkv [384][128]: 2 chunks of 48 KB
 constexpr uint32_t kA_K = 32768;       // after the QKV MMAs: K [128 tok][128]
 constexpr uint32_t kA_O = 32768;       // after the S MMAs: O [128 tok][128]
-constexpr uint32_t kA_YS = 32768;      // after the output projection: LN2 rows [128][129] FP32
+constexpr uint32_t kA_XS = 0;          // after the output projection: projected rows [128][132] FP32
+constexpr int kXS = 132;               // row stride (floats) of the staged rows: conflict-free float4 access
 constexpr uint32_t kA_VT = 65536;      // V^T [128 dims][128 tok]
 constexpr uint32_t kA_P = 98304;       // P [128 q][128 keys]
 constexpr uint32_t kA_WO = 131072;     // Wout [128][128]
@@ -53,8 +55,8 @@ constexpr uint32_t kA_XCH = kA_PAR + 1024 * 4;      // per-row exchange between 
 constexpr uint32_t kA_SMEM = kA_XCH + 1536 * 4 + 1024;
 // parameter offsets (floats) inside kA_PAR
 constexpr int kP_LN1G = 0, kP_LN1B = 128, kP_LN2G = 256, kP_LN2B = 384, kP_QKVB = 512, kP_OUTB = 896;
-// exchange offsets (floats) inside kA_XCH: two [2][128] scratch pairs, lsum [2][4][128]
-constexpr int kX_A = 0, kX_B = 256, kX_L = 512;
+// exchange offsets (floats) inside kA_XCH: the row maxima [2][128], lsum [2][4][128]
+constexpr int kX_A = 0, kX_L = 512;
 
 // TMEM columns: QKV 0..383, then S double buffer at 0 / 128, O at 384 + 32 h, projection at 256.
 struct AttnArgs {
@@ -173,46 +175,51 @@ __global__ void __launch_bounds__(kAT, 1)
   pdl_entry();
   float4 pf[4];
   bias_fetch(S, sidx, row0, 0, tid, pf);   // written by an earlier kernel: after the dependency wait
-  float nbv[6][4];                          // stencil-neighbour biases of this row, all heads
-  if (sidx == 0 && valid) {
-    for (int dir = 0; dir < a.nd2; ++dir) {
-      const float4 f = reinterpret_cast<const float4*>(S.nbrb)[(size_t)grow * a.nd2 + dir];
-      nbv[dir][0] = f.x; nbv[dir][1] = f.y; nbv[dir][2] = f.z; nbv[dir][3] = f.w;
+  // stencil neighbours inside the leaf whose key falls in this thread's half: in-leaf column and
+  // bias per head (the other entries of the row come from the table)
+  float4 nbv[6];
+  int nbj[6];
+  const int i_sys = grow % a.n;          // diagonal stack: node index within its system
+#pragma unroll
+  for (int dir = 0; dir < 6; ++dir) {
+    nbj[dir] = -1;
+    if (sidx == 0 && valid && dir < a.nd2) {
+      const int j = (dir & 1) ? a.mo.minus((unsigned)i_sys, dir >> 1) : a.mo.plus((unsigned)i_sys, dir >> 1);
+      if (j >= 0 && (j >> 6) == (i_sys >> 6) && ((j >> 5) & 1) == half) {
+        nbj[dir] = j & 63;
+        nbv[dir] = reinterpret_cast<const float4*>(S.nbrb)[(size_t)grow * a.nd2 + dir];
+      }
     }
   }
 
-  // ---- LN1 of the row -> A operand (swizzled K-major BF16); each thread one 64-column half
+  // ---- LN1 -> A operand (swizzled K-major BF16): warp w normalises rows 16 w .. 16 w + 15, a lane
+  // holds columns 4 lane .. 4 lane + 3 (coalesced 512-byte row reads)
   {
-    float v[64];
-    if (valid) {
-      const float4* xp = reinterpret_cast<const float4*>(S.x_in + (size_t)grow * kD + 64 * half);
+    const float4 g4 = reinterpret_cast<const float4*>(par + kP_LN1G)[lane_id()];
+    const float4 b4 = reinterpret_cast<const float4*>(par + kP_LN1B)[lane_id()];
+    float4 xr[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float4 f = xp[q];
-        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 64; ++c) v[c] = 0.f;
+    for (int k = 0; k < 16; ++k) {
+      const int r = 16 * warp + k;
+      xr[k] = (row0 + r < S.T) ? reinterpret_cast<const float4*>(S.x_in + (size_t)(row0 + r) * kD)[lane_id()]
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < 64; ++c) s += v[c];
-    xch[kX_A + half * 128 + row] = s;
-    __syncthreads();
-    const float mean = (xch[kX_A + row] + xch[kX_A + 128 + row]) * (1.f / kD);
-    float ss = 0.f;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) { const float u = v[c] - mean; ss = fmaf(u, u, ss); }
-    xch[kX_B + half * 128 + row] = ss;
-    __syncthreads();
-    const float rstd = rsqrtf((xch[kX_B + row] + xch[kX_B + 128 + row]) * (1.f / kD) + 1e-5f);
-    const float* g = par + kP_LN1G + 64 * half;
-    const float* b = par + kP_LN1B + 64 * half;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) v[c] = valid ? (v[c] - mean) * rstd * g[c] + b[c] : 0.f;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) st_unit_bf16(sm + kA_Q + half * 16384 + sw128(row, u), v + u * 8);
+    for (int k = 0; k < 16; ++k) {
+      const int r = 16 * warp + k;
+      const float4 x = xr[k];
+      const float mean = warp_sum((x.x + x.y) + (x.z + x.w)) * (1.f / kD);
+      const float dx = x.x - mean, dy = x.y - mean, dz = x.z - mean, dw = x.w - mean;
+      const float var = warp_sum((dx * dx + dy * dy) + (dz * dz + dw * dw)) * (1.f / kD);
+      const float rstd = rsqrtf(var + 1e-5f);
+      const bool ok_r = row0 + r < S.T;
+      const float y0 = ok_r ? dx * rstd * g4.x + b4.x : 0.f, y1 = ok_r ? dy * rstd * g4.y + b4.y : 0.f;
+      const float y2 = ok_r ? dz * rstd * g4.z + b4.z : 0.f, y3 = ok_r ? dw * rstd * g4.w + b4.w : 0.f;
+      // columns 4 lane .. +3: chunk lane / 16, unit (lane % 16) / 2, bytes 8 (lane % 2)
+      const int c = 4 * lane_id();
+      *reinterpret_cast<uint2*>(sm + kA_Q + (c >> 6) * 16384 + sw128(r, (c & 63) >> 3) + (c & 4) * 2) =
+          make_uint2(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3));
+    }
   }
   fence_async_smem();
   __syncthreads();
@@ -273,7 +280,6 @@ __global__ void __launch_bounds__(kAT, 1)
     issue_s(sm, tmem + 128, 1);
     mma_commit(smem_u32(&bar_s[1]));
   }
-  const int i_sys = grow % a.n;          // diagonal stack: node index within its system
   float* myrb = rb + row * 65;
   const float zero8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
@@ -291,13 +297,10 @@ __global__ void __launch_bounds__(kAT, 1)
       const int wbase = (row >> 6) * 64 + 32 * half;
       float s[32];
       tmem_ld32(tl + scol + wbase, s);
-      if (valid) {
-        // stencil neighbours inside the leaf carry their own coupling: override their entries
-        for (int dir = 0; dir < a.nd2; ++dir) {
-          const int j = (dir & 1) ? a.mo.minus((unsigned)i_sys, dir >> 1) : a.mo.plus((unsigned)i_sys, dir >> 1);
-          if (j >= 0 && (j >> 6) == (i_sys >> 6) && ((j >> 5) & 1) == half) myrb[j & 63] = nbv[dir][hd];
-        }
-      }
+      // stencil neighbours inside the leaf carry their own coupling: override their entries
+#pragma unroll
+      for (int dir = 0; dir < 6; ++dir)
+        if (nbj[dir] >= 0) myrb[nbj[dir]] = hd == 0 ? nbv[dir].x : hd == 1 ? nbv[dir].y : hd == 2 ? nbv[dir].z : nbv[dir].w;
       float m = -3e38f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) { s[j] = fmaf(s[j], a.scale, myrb[32 * half + j]); m = fmaxf(m, s[j]); }
@@ -393,69 +396,53 @@ __global__ void __launch_bounds__(kAT, 1)
   if (!mbar_wait(smem_u32(&bar_o), 0, kWaitLong)) ok = false;
   __syncwarp();
   tc_fence_after();
-  // ---- + bias + residual -> x_mid; LN2 -> y (FP32 and BF16); 16-token column sums of y
+  // ---- projection + bias -> shared rows; then warp w takes rows 16 w .. 16 w + 15 (one 16-token
+  // group): + residual -> x_mid, LN2 -> y (FP32 and BF16), the group's column sums of y
   {
+    float* xs = reinterpret_cast<float*>(sm + kA_XS);
     float v[64];
     tmem_ld32(tl + 256 + 64 * half, v);
     tmem_ld32(tl + 256 + 64 * half + 32, v + 32);
     const float* ob = par + kP_OUTB + 64 * half;
-    if (valid) {
-      const float4* xp = reinterpret_cast<const float4*>(S.x_in + (size_t)grow * kD + 64 * half);
-      float4* xm = reinterpret_cast<float4*>(S.x_mid + (size_t)grow * kD + 64 * half);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float4 f = xp[q];
-        v[4 * q] += ob[4 * q] + f.x; v[4 * q + 1] += ob[4 * q + 1] + f.y;
-        v[4 * q + 2] += ob[4 * q + 2] + f.z; v[4 * q + 3] += ob[4 * q + 3] + f.w;
-        xm[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
-    }
-    float s = 0.f;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) s += v[c];
-    xch[kX_A + half * 128 + row] = s;
-    __syncthreads();
-    const float mean = (xch[kX_A + row] + xch[kX_A + 128 + row]) * (1.f / kD);
-    float ss = 0.f;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) { const float u = v[c] - mean; ss = fmaf(u, u, ss); }
-    xch[kX_B + half * 128 + row] = ss;
-    __syncthreads();
-    const float rstd = rsqrtf((xch[kX_B + row] + xch[kX_B + 128 + row]) * (1.f / kD) + 1e-5f);
-    const float* g = par + kP_LN2G + 64 * half;
-    const float* b = par + kP_LN2B + 64 * half;
-    float* ys = reinterpret_cast<float*>(sm + kA_YS) + row * 129 + 64 * half;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) {
-      v[c] = valid ? (v[c] - mean) * rstd * g[c] + b[c] : 0.f;
-      ys[c] = v[c];
-    }
-    if (valid) {
-      float4* yp = reinterpret_cast<float4*>(S.y32 + (size_t)grow * kD + 64 * half);
-      uint4* up = reinterpret_cast<uint4*>(S.u + (size_t)grow * S.ldu + 64 * half);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        uint4 pk;
-        pk.x = pack_bf16x2(v[8 * q], v[8 * q + 1]); pk.y = pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
-        pk.z = pack_bf16x2(v[8 * q + 4], v[8 * q + 5]); pk.w = pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
-        up[q] = pk;
-      }
-    }
+    for (int q = 0; q < 16; ++q)
+      *reinterpret_cast<float4*>(xs + row * kXS + 64 * half + 4 * q) =
+          make_float4(v[4 * q] + ob[4 * q], v[4 * q + 1] + ob[4 * q + 1], v[4 * q + 2] + ob[4 * q + 2], v[4 * q + 3] + ob[4 * q + 3]);
   }
   __syncthreads();
   {
-    const float* ys = reinterpret_cast<const float*>(sm + kA_YS);
-    const int c = row;
-#pragma unroll 1
-    for (int grp = 4 * half; grp < 4 * half + 4; ++grp) {
-      if (row0 + grp * 16 >= S.T) break;   // T is a multiple of 16: groups are whole
-      float s = 0.f;
+    const float* xs = reinterpret_cast<const float*>(sm + kA_XS);
+    const int lane = lane_id();
+    const float4 g4 = reinterpret_cast<const float4*>(par + kP_LN2G)[lane];
+    const float4 b4 = reinterpret_cast<const float4*>(par + kP_LN2B)[lane];
+    float4 xr[16];
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr) s += ys[(grp * 16 + rr) * 129 + c];
-      S.gp16[(size_t)(row0 / 16 + grp) * kD + c] = s;
+    for (int k = 0; k < 16; ++k) {
+      const int r = 16 * warp + k;
+      xr[k] = (row0 + r < S.T) ? reinterpret_cast<const float4*>(S.x_in + (size_t)(row0 + r) * kD)[lane]
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = 16 * warp + k;
+      if (row0 + r >= S.T) break;   // uniform across the warp
+      const size_t gr = (size_t)(row0 + r);
+      const float4 p = *reinterpret_cast<const float4*>(xs + r * kXS + 4 * lane);
+      const float4 x = make_float4(p.x + xr[k].x, p.y + xr[k].y, p.z + xr[k].z, p.w + xr[k].w);
+      reinterpret_cast<float4*>(S.x_mid + gr * kD)[lane] = x;
+      const float mean = warp_sum((x.x + x.y) + (x.z + x.w)) * (1.f / kD);
+      const float dx = x.x - mean, dy = x.y - mean, dz = x.z - mean, dw = x.w - mean;
+      const float var = warp_sum((dx * dx + dy * dy) + (dz * dz + dw * dw)) * (1.f / kD);
+      const float rstd = rsqrtf(var + 1e-5f);
+      const float4 y = make_float4(dx * rstd * g4.x + b4.x, dy * rstd * g4.y + b4.y, dz * rstd * g4.z + b4.z,
+                                   dw * rstd * g4.w + b4.w);
+      reinterpret_cast<float4*>(S.y32 + gr * kD)[lane] = y;
+      *reinterpret_cast<uint2*>(S.u + gr * S.ldu + 4 * lane) = make_uint2(pack_bf16x2(y.x, y.y), pack_bf16x2(y.z, y.w));
+      cs.x += y.x; cs.y += y.y; cs.z += y.z; cs.w += y.w;
+    }
+    if (row0 + 16 * warp < S.T)   // T is a multiple of 16: a group is whole or absent
+      reinterpret_cast<float4*>(S.gp16 + (size_t)(row0 / 16 + warp) * kD)[lane] = cs;
   }
   // ---- teardown: every MMA of this CTA has completed before TMEM is freed
   if (tid == 0) mma_commit(smem_u32(&bar_end));
@@ -486,31 +473,41 @@ struct HwArgs {
 // the sums of aligned 2^j-node chunks: every tile token whose chunk lies in the block takes its
 // mean from there.  Blocks x >= nblk: 8 channels of the global token of one system (mean of y
 // over both stacks), from the 16-token sums.
-__global__ void __launch_bounds__(256) fused_hw_kernel(const __grid_constant__ HwArgs a) {
+constexpr int kHT = 1024;
+__global__ void __launch_bounds__(kHT) fused_hw_kernel(const __grid_constant__ HwArgs a) {
   extern __shared__ float hs[];
   pdl_entry();
   const int tid = threadIdx.x;
   const int c0 = blockIdx.y * 32;
   if ((int)blockIdx.x >= a.nblk) {
-    __shared__ float red[32][9];
+    __shared__ float red[kHT / 8][9];
+    __shared__ float red8[8][9];
     const int q = blockIdx.x - a.nblk;
     const int b = q >> 2, cs8 = c0 + (q & 3) * 8;
-    const int c = tid & 7, part = tid >> 3;   // 32 parts
+    const int c = tid & 7, part = tid >> 3;   // kHT / 8 parts
+    constexpr int NP = kHT / 8;
     const int ngd = a.n / 16, ngo = a.MH * a.r / 16;
     float acc0 = 0.f, acc1 = 0.f;
     int g = part;
-    for (; g + 32 < ngd; g += 64) {
+    for (; g + NP < ngd; g += 2 * NP) {
       acc0 += a.gpd[((size_t)b * ngd + g) * kD + cs8 + c];
-      acc1 += a.gpd[((size_t)b * ngd + g + 32) * kD + cs8 + c];
+      acc1 += a.gpd[((size_t)b * ngd + g + NP) * kD + cs8 + c];
     }
-    for (; g < ngd; g += 32) acc0 += a.gpd[((size_t)b * ngd + g) * kD + cs8 + c];
-    for (g = part; g < ngo; g += 32) acc1 += a.gpo[((size_t)b * ngo + g) * kD + cs8 + c];
+    for (; g < ngd; g += NP) acc0 += a.gpd[((size_t)b * ngd + g) * kD + cs8 + c];
+    for (g = part; g < ngo; g += NP) acc1 += a.gpo[((size_t)b * ngo + g) * kD + cs8 + c];
     red[part][c] = acc0 + acc1;
+    __syncthreads();
+    if (part < 8) {   // 8 partial chains of 16, then one
+      float s = 0.f;
+#pragma unroll
+      for (int p = 0; p < NP / 8; ++p) s += red[part * (NP / 8) + p][c];
+      red8[part][c] = s;
+    }
     __syncthreads();
     if (part == 0) {
       float s = 0.f;
 #pragma unroll
-      for (int p = 0; p < 32; ++p) s += red[p][c];
+      for (int p = 0; p < 8; ++p) s += red8[p][c];
       a.g32[(size_t)b * kD + cs8 + c] = s / (float)(a.n + a.MH * a.r);
     }
     return;
@@ -521,20 +518,34 @@ __global__ void __launch_bounds__(256) fused_hw_kernel(const __grid_constant__ H
   const int t0 = blockIdx.x * NB;
   const int b = t0 / a.n, ib0 = t0 % a.n;
   const int lgL = 31 - __clz(a.L), lgr = 31 - __clz(a.r);
+  const float* __restrict__ yd = a.yd;
+  const float* __restrict__ yo = a.yo;
+  bf16* __restrict__ ud = a.ud;
   for (int q = tid; q < NB * 8; q += blockDim.x) {
     const int node = q >> 3, cg = (q & 7) * 4;
     const int i = ib0 + node, t = t0 + node;
     const int k = i >> lgL;
-    float4 rsum = *reinterpret_cast<const float4*>(a.yd + (size_t)t * kD + c0 + cg);
+    float4 rsum = *reinterpret_cast<const float4*>(yd + (size_t)t * kD + c0 + cg);
     float4 csum = rsum;
     int nr = 1, nc = 1;
-    for (int lev = 1; lev <= a.levels; ++lev) {
-      const int lgS = a.levels - lev;
-      const int cl = k >> lgS;
-      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-      const int at = (i - (cl << (lgS + lgL))) >> (lgS + lgL - lgr);
-      const float4 v = *reinterpret_cast<const float4*>(a.yo + ((size_t)(b * a.MH + m) * a.r + at) * kD + c0 + cg);
-      if (cl & 1) { csum.x += v.x; csum.y += v.y; csum.z += v.z; csum.w += v.w; ++nc; }
+    // every level's token row is requested before the first sum (levels <= kMaxLevels)
+    float4 vl[kMaxLevels];
+#pragma unroll
+    for (int lev = 1; lev <= kMaxLevels; ++lev) {
+      vl[lev - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lev <= a.levels) {
+        const int lgS = a.levels - lev;
+        const int cl = k >> lgS;
+        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+        const int at = (i - (cl << (lgS + lgL))) >> (lgS + lgL - lgr);
+        vl[lev - 1] = *reinterpret_cast<const float4*>(yo + ((size_t)(b * a.MH + m) * a.r + at) * kD + c0 + cg);
+      }
+    }
+#pragma unroll
+    for (int lev = 1; lev <= kMaxLevels; ++lev) {
+      if (lev > a.levels) break;
+      const float4 v = vl[lev - 1];
+      if ((k >> (a.levels - lev)) & 1) { csum.x += v.x; csum.y += v.y; csum.z += v.z; csum.w += v.w; ++nc; }
       else { rsum.x += v.x; rsum.y += v.y; rsum.z += v.z; rsum.w += v.w; ++nr; }
     }
     const float ir = 1.f / (float)nr, ic = 1.f / (float)nc;
@@ -544,7 +555,7 @@ __global__ void __launch_bounds__(256) fused_hw_kernel(const __grid_constant__ H
     float* cc = cs + node * 33 + cg;
     rr[0] = rsum.x; rr[1] = rsum.y; rr[2] = rsum.z; rr[3] = rsum.w;
     cc[0] = csum.x; cc[1] = csum.y; cc[2] = csum.z; cc[3] = csum.w;
-    bf16* u = a.ud + (size_t)t * a.ldu;
+    bf16* u = ud + (size_t)t * a.ldu;
     *reinterpret_cast<uint2*>(u + kD + c0 + cg) = make_uint2(pack_bf16x2(rsum.x, rsum.y), pack_bf16x2(rsum.z, rsum.w));
     *reinterpret_cast<uint2*>(u + 2 * kD + c0 + cg) = make_uint2(pack_bf16x2(csum.x, csum.y), pack_bf16x2(csum.z, csum.w));
   }
@@ -581,11 +592,13 @@ __global__ void __launch_bounds__(256) fused_hw_kernel(const __grid_constant__ H
 }
 
 // ----------------------------------------------------------------------------- FFN
-// 320 threads: warps 0-7 two per token row (the global-token columns of the input, the GELU
-// epilogue into H, the output epilogue), warp 8 the TMA producer (input tile, then 16 stages of
-// W1 and 8 of W2 through a 3-stage ring), warp 9 the MMA issuer.  TMEM: FFN1 in all 512 columns,
-// FFN2 in columns 0..127 once H has been read out.
-constexpr int kFT = 320;
+// 576 threads: warps 0-15 four per token row (warp w reads TMEM lanes 32 (w % 4) and takes the
+// column quarter w / 4: the global-token columns of the input, the GELU epilogue into H, the
+// output epilogue), warp 16 the TMA producer (input tile, then 16 stages of W1 and 8 of W2
+// through a 3-stage ring), warp 17 the MMA issuer.  TMEM: FFN1 in all 512 columns, FFN2 in
+// columns 0..127 once H has been read out.
+constexpr int kFMath = 512;
+constexpr int kFT = kFMath + 64;
 constexpr int kFStages = 3;
 constexpr uint32_t kF_U = 0;           // FFN input [128][512] BF16 (8 chunks); then the hidden H
 constexpr uint32_t kF_RING = 131072;   // weight ring: 3 stages of 32 KB
@@ -635,7 +648,7 @@ __global__ void __launch_bounds__(kFT, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_s;
 
-  if (warp == 8) {
+  if (warp == kFMath / 32) {
     if (lane == 0) {
       const CUtensorMap* mu = sidx ? &mu1 : &mu0;
       const CUtensorMap* m1 = sidx ? &m11 : &m10;
@@ -661,9 +674,9 @@ __global__ void __launch_bounds__(kFT, 1)
       }
     }
     __syncwarp();
-  } else if (warp == 9) {
+  } else if (warp == kFMath / 32 + 1) {
     pdl_entry();
-    named_sync(1, 288);   // the global-token columns are in shared memory
+    named_sync(1, kFMath + 32);   // the global-token columns are in shared memory
     if (lane == 0) {
       if (!mbar_wait(smem_u32(&bar_u), 0, kWaitLong)) ok = false;
       tc_fence_after();
@@ -682,7 +695,7 @@ __global__ void __launch_bounds__(kFT, 1)
       mma_commit(smem_u32(&bar_f1));
     }
     __syncwarp();
-    named_sync(2, 288);   // H is in shared memory and FFN1's accumulators have been read
+    named_sync(2, kFMath + 32);   // H is in shared memory and FFN1's accumulators have been read
     if (lane == 0) {
       tc_fence_after();
       const uint32_t id128 = idesc_bf16(128, 128);
@@ -700,70 +713,81 @@ __global__ void __launch_bounds__(kFT, 1)
     }
     __syncwarp();
   } else {
-    // warps 0-7: row = tid % 128 (TMEM lane), half = tid / 128
+    // warps 0-15: row = 32 (warp % 4) + lane (TMEM lane), column quarter cq = warp / 4
     pdl_entry();
-    const int row = tid & 127, half = tid >> 7;
+    const int row = 32 * (warp & 3) + lane, cq = warp >> 2;
     const int grow = row0 + row;
     const bool valid = grow < S.T;
     const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     {
-      float gv[64];
+      // global-token columns 384 + 32 cq .. +32 of this row
+      float gv[32];
       if (valid) {
-        const float4* gp = reinterpret_cast<const float4*>(a.g32 + (size_t)(grow / S.per_sys) * kD + 64 * half);
+        const float4* gp = reinterpret_cast<const float4*>(a.g32 + (size_t)(grow / S.per_sys) * kD + 32 * cq);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < 8; ++q) {
           const float4 f = gp[q];
           gv[4 * q] = f.x; gv[4 * q + 1] = f.y; gv[4 * q + 2] = f.z; gv[4 * q + 3] = f.w;
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < 64; ++c) gv[c] = 0.f;
+        for (int c = 0; c < 32; ++c) gv[c] = 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) st_unit_bf16(sm + kF_U + (6 + half) * 16384 + sw128(row, u), gv + u * 8);
+      for (int u = 0; u < 4; ++u) st_unit_bf16(sm + kF_U + (6 + (cq >> 1)) * 16384 + sw128(row, (cq & 1) * 4 + u), gv + u * 8);
     }
     fence_async_smem();
-    named_sync(1, 288);
+    named_sync(1, kFMath + 32);
     if (!mbar_wait(smem_u32(&bar_f1), 0, kWaitLong)) ok = false;
     __syncwarp();
     tc_fence_after();
 #pragma unroll 1
-    for (int e = 0; e < 8; ++e) {
-      const int c32 = half * 8 + e;
+    for (int e = 0; e < 4; ++e) {
+      const int c32 = cq * 4 + e;
       float v[32];
       tmem_ld32(tl + c32 * 32, v);
       const float4* bp = reinterpret_cast<const float4*>(S.f1b + c32 * 32);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const float4 bb = __ldg(bp + q);
-        v[4 * q] = gelu_f(v[4 * q] + bb.x); v[4 * q + 1] = gelu_f(v[4 * q + 1] + bb.y);
-        v[4 * q + 2] = gelu_f(v[4 * q + 2] + bb.z); v[4 * q + 3] = gelu_f(v[4 * q + 3] + bb.w);
+        v[4 * q] = gelu_as(v[4 * q] + bb.x); v[4 * q + 1] = gelu_as(v[4 * q + 1] + bb.y);
+        v[4 * q + 2] = gelu_as(v[4 * q + 2] + bb.z); v[4 * q + 3] = gelu_as(v[4 * q + 3] + bb.w);
       }
 #pragma unroll
       for (int u4 = 0; u4 < 4; ++u4) st_unit_bf16(sm + kF_U + (c32 >> 1) * 16384 + sw128(row, (c32 & 1) * 4 + u4), v + 8 * u4);
     }
     fence_async_smem();
     tc_fence_before();
-    named_sync(2, 288);
+    named_sync(2, kFMath + 32);
+    // the residual rows of this warp's output rows are fetched while FFN2 runs: math warp w
+    // writes rows 8 w .. 8 w + 7 (coalesced), lane = columns 4 lane .. +3
+    float4 xr[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int r = 8 * warp + k;
+      xr[k] = (row0 + r < S.T) ? reinterpret_cast<const float4*>(S.x_mid + (size_t)(row0 + r) * kD)[lane]
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     if (!mbar_wait(smem_u32(&bar_f2), 0, kWaitLong)) ok = false;
     __syncwarp();
     tc_fence_after();
-#pragma unroll 1
-    for (int e = 0; e < 2; ++e) {
-      const int c32 = half * 2 + e;
+    float* xs = reinterpret_cast<float*>(sm + kF_U);   // H is dead once FFN2 has completed
+    {
       float v[32];
-      tmem_ld32(tl + c32 * 32, v);
-      if (valid) {
-        const float4* xm = reinterpret_cast<const float4*>(S.x_mid + (size_t)grow * kD + c32 * 32);
-        const float4* bp = reinterpret_cast<const float4*>(S.f2b + c32 * 32);
-        float4* xo = reinterpret_cast<float4*>(S.x_out + (size_t)grow * kD + c32 * 32);
+      tmem_ld32(tl + cq * 32, v);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 f = xm[q];
-          const float4 bb = __ldg(bp + q);
-          xo[q] = make_float4(v[4 * q] + bb.x + f.x, v[4 * q + 1] + bb.y + f.y, v[4 * q + 2] + bb.z + f.z,
-                              v[4 * q + 3] + bb.w + f.w);
-        }
+      for (int q = 0; q < 8; ++q) *reinterpret_cast<float4*>(xs + row * kXS + cq * 32 + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    named_sync(3, kFMath);
+    {
+      const float4 b4 = __ldg(reinterpret_cast<const float4*>(S.f2b) + lane);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = 8 * warp + k;
+        if (row0 + r >= S.T) break;
+        const float4 p = *reinterpret_cast<const float4*>(xs + r * kXS + 4 * lane);
+        reinterpret_cast<float4*>(S.x_out + (size_t)(row0 + r) * kD)[lane] =
+            make_float4(p.x + b4.x + xr[k].x, p.y + b4.y + xr[k].y, p.z + b4.z + xr[k].z, p.w + b4.w + xr[k].w);
       }
     }
   }
@@ -848,7 +872,7 @@ int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], f
   ha.NB = fused_hw_block(sb.n, sb.L, sb.r);
   ha.nblk = sb.B * sb.n / ha.NB;
   if (st[1].ldu != ha.ldu) return HMPCG_E_INVALID;
-  rc = launch_pdl(fused_hw_kernel, dim3(ha.nblk + 4 * sb.B, kD / 32), dim3(256), (size_t)2 * ha.NB * 33 * 4, s, ha);
+  rc = launch_pdl(fused_hw_kernel, dim3(ha.nblk + 4 * sb.B, kD / 32), dim3(kHT), (size_t)2 * ha.NB * 33 * 4, s, ha);
   if (rc) return rc;
   FfnArgs fa;
   fa.st[0] = st[0];

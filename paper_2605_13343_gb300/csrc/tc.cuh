@@ -86,6 +86,24 @@ HM_INLINE void tmem_ld16(uint32_t taddr, float* v) {
 
 HM_INLINE float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26:
+// erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2), t = 1 / (1 + p x), x >= 0,
+// |error| <= 1.5e-7; odd in x.  Two MUFU operations (reciprocal, exponential) and ten FMA-pipe
+// instructions, for the GELU epilogues whose result is rounded to BF16 (unit roundoff 3.9e-3).
+HM_INLINE float erf_as(float x) {
+  const float ax = fabsf(x);
+  const float t = __fdividef(1.f, fmaf(0.3275911f, ax, 1.f));
+  float p = fmaf(1.061405429f, t, -1.453152027f);
+  p = fmaf(p, t, 1.421413741f);
+  p = fmaf(p, t, -0.284496736f);
+  p = fmaf(p, t, 0.254829592f);
+  p *= t;
+  const float e = 1.f - p * __expf(-ax * ax);
+  return copysignf(e, x);
+}
+HM_INLINE float gelu_as(float x) { return 0.5f * x * (1.f + erf_as(x * 0.70710678118654752f)); }
+HM_INLINE int lane_id() { return (int)(threadIdx.x & 31); }
+
 // Shared-memory byte offset of 16-byte unit `unit` (8 BF16 values) of row `row` in a K-major
 // tile of 64-element (128-byte) rows under the 128-byte swizzle: the unit index is XORed with
 // the row's position in its 8-row atom.  Tiles start on 1024-byte boundaries.
