@@ -231,6 +231,16 @@ int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys,
                      int32_t n_probes, float lr, uint64_t step_seed,
                      float* loss_out, void* stream);
 
+/* Probes of the following hmpcg_train_step calls.  HMPCG_PROBES_RADEMACHER
+ * (default): +-1 entries (the benchmark configuration).  HMPCG_PROBES_GAUSSIAN_SMOOTHED:
+ * the paper's probes (Sec. 6.2 Eq. 8; Supp. C): standard normal entries (Box-Muller on
+ * two SplitMix64 outputs of the same stream), then `steps` sweeps
+ * z <- z - omega D^-1 A z (the paper: omega 0.6, 2 sweeps).  Returns HMPCG_E_INVALID for
+ * a context without a network, another kind, omega outside (0, 1] or steps outside
+ * 0..8. */
+enum { HMPCG_PROBES_RADEMACHER = 0, HMPCG_PROBES_GAUSSIAN_SMOOTHED = 1 };
+int hmpcg_set_train_probes(void* ctx, int32_t kind, float omega, int32_t steps);
+
 /* z = M r exactly as hmpcg_apply with nrhs = 1, but without a context and
  * without allocating anything.  The paper has no counterpart: this is for
  * callers that cannot call cudaMalloc, such as code inside a custom device

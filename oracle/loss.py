@@ -42,6 +42,16 @@ def rademacher_probes(step_seed, system, n, kz):
     return np.array(rng.rademacher(step_seed, system, n, kz), dtype=np.float64)
 
 
+def gaussian_probes(step_seed, system, n, kz):
+    """Gaussian probes drawn from the counter-based SplitMix64 stream (Box-Muller)."""
+    return np.array(rng.gaussian(step_seed, system, n, kz), dtype=np.float64)
+
+
+def smoothed_gaussian_probes(step_seed, system, n, kz, matvec, diag, omega=0.6, steps=2):
+    """The paper's training probes: Gaussian, then `steps` damped-Jacobi sweeps (Eq. 8)."""
+    return jacobi_smooth(gaussian_probes(step_seed, system, n, kz), matvec, diag, omega, steps)
+
+
 def jacobi_smooth(z, matvec, diag, omega=0.6, steps=2):
     """Damped-Jacobi low-pass on probes, z <- z - omega D^-1 A z (Eq. 8)."""
     z = np.array(z, dtype=np.float64, copy=True)

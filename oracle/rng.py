@@ -50,3 +50,27 @@ def rademacher(step_seed, system, n, kz):
         for j in range(kz):
             z[i][j] = -1.0 if (at(key, i * kz + j) >> 63) else 1.0
     return z
+
+
+def uniform53(x):
+    """A 64-bit output as a uniform in [0, 1): its top 53 bits over 2^53."""
+    return (x >> 11) * (1.0 / 9007199254740992.0)
+
+
+def gaussian(step_seed, system, n, kz):
+    """Standard normal probe matrix Z (n x kz) of one system (Box & Muller 1958).
+
+    Element (i, j) takes outputs 2e and 2e + 1 (e = i * kz + j) of the system's
+    stream as uniforms u1, u2 and returns sqrt(-2 ln(1 - u1)) cos(2 pi u2); 1 - u1
+    is never 0.
+    """
+    import math
+    key = probe_key(step_seed, system)
+    z = [[0.0] * kz for _ in range(n)]
+    for i in range(n):
+        for j in range(kz):
+            e = i * kz + j
+            u1 = uniform53(at(key, 2 * e))
+            u2 = uniform53(at(key, 2 * e + 1))
+            z[i][j] = math.sqrt(-2.0 * math.log1p(-u1)) * math.cos(2.0 * math.pi * u2)
+    return z

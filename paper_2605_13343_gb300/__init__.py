@@ -73,6 +73,7 @@ EXPORTS = {
                                       C.c_void_p, C.c_void_p]),
     "hmpcg_packed_width": (C.c_int64, [C.c_int64, C.c_int32, C.c_int32, C.c_int32]),
     "hmpcg_set_infer_mode": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hmpcg_set_train_probes": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int32]),
     "hmpcg_train_step": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_int32, C.c_float,
                                    C.c_uint64, C.POINTER(C.c_float), C.c_void_p]),
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -339,6 +340,14 @@ INFER_LAYERED, INFER_FUSED = 0, 1
 def set_infer_mode(ctx, mode):
     """hmpcg_set_infer_mode: INFER_FUSED (default) or INFER_LAYERED kernels for infer_factors."""
     _check(lib().hmpcg_set_infer_mode(ctx.h, int(mode)), "set_infer_mode")
+
+
+PROBES_RADEMACHER, PROBES_GAUSSIAN_SMOOTHED = 0, 1
+
+
+def set_train_probes(ctx, kind, omega=0.6, steps=2):
+    """hmpcg_set_train_probes: Rademacher, or the paper's smoothed Gaussian probes."""
+    _check(lib().hmpcg_set_train_probes(ctx.h, int(kind), float(omega), int(steps)), "set_train_probes")
 
 
 def train_step(ctx, systems, n_probes, lr, step_seed, want_loss=True, stream=None):

@@ -243,6 +243,11 @@ void net_destroy(Ctx* c) {
 }
 
 void net_set_fused(Net* N, bool on) { N->use_fused = on ? 1 : 0; }
+void net_set_probes(Net* N, int kind, float omega, int steps) {
+  N->probe_kind = kind;
+  N->probe_omega = omega;
+  N->probe_steps = steps;
+}
 
 int net_get_weights(Ctx* c, float* w, int64_t count) {
   Net* N = c->net;

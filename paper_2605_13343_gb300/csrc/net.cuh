@@ -133,6 +133,10 @@ struct Net {
   float* gp16 = nullptr;
   bool fused_alloc = false;
   int use_fused = 1;
+  // training probes: Rademacher, or Gaussian with probe_steps damped-Jacobi sweeps (weight omega)
+  int probe_kind = 0;
+  float probe_omega = 0.6f;
+  int probe_steps = 2;
   // scratch for the backward pass and training
   std::vector<void*> allocs;
 };

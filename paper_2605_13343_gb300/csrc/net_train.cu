@@ -192,7 +192,15 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
 
   // ---- probes and the fixed operand W = A Z
   const int64_t nzt = (int64_t)Td * nz;
-  probes_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, seed, nz, T->z);
+  if (N->probe_kind == HMPCG_PROBES_GAUSSIAN_SMOOTHED) {
+    probes_gauss_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, seed, nz, T->z);
+    for (int k = 0; k < N->probe_steps; ++k) {
+      spmv_multi_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->w);
+      probes_smooth_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, N->probe_omega, T->w, T->z);
+    }
+  } else {
+    probes_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, seed, nz, T->z);
+  }
   spmv_multi_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->w);
   // ---- forward, factors, Y = M W, loss
   TR_TRY(net_forward(N, sb, st));

@@ -51,6 +51,31 @@ __global__ void probes_kernel(const SysBatch sb, uint64_t step_seed, int nz, flo
   const uint64_t v = sm64_mix(key + (uint64_t)(e + 1) * 0x9E3779B97F4A7C15ull);
   z[idx] = (v >> 63) ? -1.f : 1.f;
 }
+// Gaussian probes (Box & Muller 1958) from outputs 2e and 2e + 1 of the same stream: uniforms
+// from their top 53 bits, z = sqrt(-2 ln(1 - u1)) cos(2 pi u2) with the transcendentals in FP32
+// (1 - u1 is exact in FP64 and never 0).
+__global__ void probes_gauss_kernel(const SysBatch sb, uint64_t step_seed, int nz, float* __restrict__ z) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)sb.B * sb.n * nz;
+  if (idx >= tot) return;
+  const int b = (int)(idx / ((int64_t)sb.n * nz));
+  const int64_t e = idx % ((int64_t)sb.n * nz);
+  const uint64_t key = sm64_mix(step_seed * 0x100000001B3ull + (uint64_t)b);
+  const uint64_t v1 = sm64_mix(key + (uint64_t)(2 * e + 1) * 0x9E3779B97F4A7C15ull);
+  const uint64_t v2 = sm64_mix(key + (uint64_t)(2 * e + 2) * 0x9E3779B97F4A7C15ull);
+  const double u1 = (double)(v1 >> 11) * (1.0 / 9007199254740992.0);
+  const double u2 = (double)(v2 >> 11) * (1.0 / 9007199254740992.0);
+  z[idx] = sqrtf(-2.f * logf((float)(1.0 - u1))) * cospif(2.f * (float)u2);
+}
+// One damped-Jacobi sweep on the probes (Sec. 6.2 Eq. 8): z <- z - omega D^-1 (A z), with A z in w.
+__global__ void probes_smooth_kernel(const SysBatch sb, int nz, float omega, const float* __restrict__ w,
+                                     float* __restrict__ z) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)sb.B * sb.n * nz) return;
+  const int64_t t = idx / nz;
+  const int b = (int)(t / sb.n), i = (int)(t % sb.n);
+  z[idx] = (float)((double)z[idx] - (double)omega * (double)w[idx] / sb.diag[b][i]);
+}
 // W = A Z with the FP64 operator (rounded to FP32), node-major [n][nz].
 __global__ void spmv_multi_kernel(const SysBatch sb, int nz, const float* __restrict__ z, float* __restrict__ w) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -2,8 +2,9 @@
 
 The GPU step runs the forward and every backward GEMM with BF16 operands and FP32
 accumulation; the clipped gradient is compared with the oracle's (torch autograd
-in FP64 on the same weights, systems and SplitMix64 probes) by cosine similarity
-and relative 2-norm error over the whole vector and over each large tensor.
+in FP64 on the same weights, systems and SplitMix64 probes, Rademacher or the
+paper's smoothed Gaussian ones) by relative 2-norm error over the whole vector
+and over each tensor that carries a share of it.
 """
 import numpy as np
 import pytest
@@ -47,32 +48,54 @@ def _systems(dims, seeds):
     return out_gpu, out_ref
 
 
-def _cos(a, b):
-    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+def _gpu_systems(dims, seeds):
+    """Device systems only (the held-out test needs no oracle copies)."""
+    out = []
+    for s in seeds:
+        rho = inputs.density_for_dims(s, dims, rho_heavy=float(np.exp(np.random.default_rng(s).uniform(0, np.log(100)))))
+        sg = h.System(dims)
+        h.assemble(torch.from_numpy(rho).cuda(), sg)
+        out.append(sg)
+    return out
 
 
-@pytest.mark.parametrize("cfg,dims,seeds,nz,tol_cos", [
-    (SMALL, (16, 16), [1, 2], 8, 0.995),
-    (CFG3, (16, 16, 16), [3, 4], 16, 0.98)])
-def test_train_step_gradient_parity(cfg, dims, seeds, nz, tol_cos):
+# Relative 2-norm bounds of the clipped gradient against the FP64 oracle.  The GPU rounds every GEMM
+# operand and stored activation to BF16 (unit roundoff u = 2^-9) on a path of about 60 roundings
+# (forward and backward through 4 layers); independent errors add in quadrature, sqrt(60) u ~ 0.015,
+# and the measured worst tensor on the GB300 was 0.023 (whole vector 0.018).  A tensor carrying at
+# least 1% of the gradient norm (or 0.1% if it has >= 4096 entries) must be within 0.05, the whole
+# vector within 0.04: a wrong sign, transposition or dropped term in any such tensor gives an error
+# of order 1.
+REL_TENSOR = 0.05
+REL_ALL = 0.04
+
+
+@pytest.mark.parametrize("cfg,dims,seeds,nz,probes", [
+    (SMALL, (16, 16), [1, 2], 8, "rademacher"),
+    (CFG3, (16, 16, 16), [3, 4], 16, "rademacher"),
+    (CFG3, (16, 16, 16), [5, 6], 16, "gaussian")])
+def test_train_step_gradient_parity(cfg, dims, seeds, nz, probes):
     w, lay = _blob(cfg, 5)
     n = int(np.prod(dims))
     ctx = _ctx(cfg, n, len(seeds), w)
+    if probes == "gaussian":
+        h.set_train_probes(ctx, h.PROBES_GAUSSIAN_SMOOTHED, 0.6, 2)
     sg, sr = _systems(dims, seeds)
     loss_gpu = h.train_step(ctx, sg, nz, 0.0, 1234)
     g_gpu = h.get_grads(ctx, w.size).astype(np.float64)
-    l_ref, g_ref, _ = train.batch_loss(w.astype(np.float64), lay, cfg, sr, 1234, nz)
+    l_ref, g_ref, _ = train.batch_loss(w.astype(np.float64), lay, cfg, sr, 1234, nz, probes=probes)
     g_ref = adamw.clip_global(g_ref, 1.0)
     assert abs(loss_gpu - l_ref) <= 2e-3 * max(1.0, abs(l_ref)), (loss_gpu, l_ref)
-    assert _cos(g_gpu, g_ref) >= tol_cos, _cos(g_gpu, g_ref)
-    # large tensors one by one
+    tot = np.linalg.norm(g_ref)
+    assert np.linalg.norm(g_gpu - g_ref) <= REL_ALL * tot, np.linalg.norm(g_gpu - g_ref) / tot
     off = 0
     for name, shp in lay:
         k = int(np.prod(shp))
         a, b = g_gpu[off:off + k], g_ref[off:off + k]
         off += k
-        if k >= 4096 and np.linalg.norm(b) > 1e-3 * np.linalg.norm(g_ref):
-            assert _cos(a, b) >= 0.95, (name, _cos(a, b))
+        nb = np.linalg.norm(b)
+        if nb >= 1e-2 * tot or (k >= 4096 and nb >= 1e-3 * tot):
+            assert np.linalg.norm(a - b) <= REL_TENSOR * nb, (name, np.linalg.norm(a - b) / nb)
     # lr = 0 left the weights untouched
     assert np.array_equal(h.get_weights(ctx, w.size), w)
     ctx.close()
@@ -90,16 +113,25 @@ def test_adamw_update_matches_oracle():
     ctx.close()
 
 
-def test_training_reduces_loss():
-    """AdamW steps on one fixed batch with fixed probes lower that batch's loss (measured by
-    steps with lr = 0, which leave the weights unchanged): the update follows the gradient."""
+def test_training_lowers_heldout_loss():
+    """Steps on fresh batches (new frames every step, new probes) lower the loss of a held-out
+    batch of other frames with fixed probes (evaluated with lr = 0, which changes nothing): what
+    the training learns carries over to systems it never saw."""
     w = inputs.network_blob(0, **CFG3)
     ctx = _ctx(CFG3, 4096, 4, w)
-    sg, _ = _systems((16, 16, 16), [9000 + q for q in range(4)])
-    before = h.train_step(ctx, sg, 16, 0.0, 12345)
-    for step in range(40):
-        h.train_step(ctx, sg, 16, 3e-4, 12345)
-    after = h.train_step(ctx, sg, 16, 0.0, 12345)
-    # the evaluation is deterministic: any drop well above rounding (1e-6) is descent
-    assert after < before - 5e-4, (before, after)
+    held = _gpu_systems((16, 16, 16), [9100 + q for q in range(4)])
+    before = h.train_step(ctx, held, 16, 0.0, 777)
+    for step in range(STEPS_HELDOUT):
+        sg = _gpu_systems((16, 16, 16), [20000 + 4 * step + q for q in range(4)])
+        h.train_step(ctx, sg, 16, LR_HELDOUT, 5000 + step, want_loss=False)
+    after = h.train_step(ctx, held, 16, 0.0, 777)
+    assert after < before * (1.0 - DROP_HELDOUT), (before, after)
     ctx.close()
+
+
+# 200 AdamW steps at the paper's learning rate 3e-4 (Supp. C) from the seeded initialisation; on
+# the GB300 the held-out loss fell monotonically at every 25-step check, 0.0727 -> 0.0700 (3.7 %),
+# so a 2 % drop is required.  (At 1e-3 the run is unstable: the loss first jumps to 0.116.)
+STEPS_HELDOUT = 200
+LR_HELDOUT = 3e-4
+DROP_HELDOUT = 0.02

@@ -168,3 +168,26 @@ def test_gaussian_hutchinson_and_smoothing():
 def test_probe_count():
     assert loss.probe_count(1024) == 64 and loss.probe_count(16384) == 128
     assert loss.probe_count(8192) == 91
+
+
+def test_gaussian_probes_are_standard_normal():
+    # Box-Muller normals from the SplitMix64 stream: moments and the normal CDF (Kolmogorov-Smirnov)
+    from scipy import stats
+    z = np.array(rng.gaussian(5, 3, 4096, 8)).ravel()
+    n = z.size
+    assert abs(z.mean()) <= 4.0 / np.sqrt(n)
+    assert abs(z.var() - 1.0) <= 4.0 * np.sqrt(2.0 / n)
+    assert abs(stats.skew(z)) <= 4.0 * np.sqrt(6.0 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # different systems and steps draw different (uncorrelated) probes
+    z2 = np.array(rng.gaussian(6, 3, 4096, 8)).ravel()
+    assert abs(np.corrcoef(z, z2)[0, 1]) <= 4.0 / np.sqrt(n)
+
+
+def test_smoothed_gaussian_probes_follow_eq8():
+    s, a = _sys((8, 8), 6)
+    d = s["diag"]
+    g = loss.gaussian_probes(2, 1, 64, 5)
+    z = loss.smoothed_gaussian_probes(2, 1, 64, 5, lambda v: a @ v, d)
+    smat = np.eye(64) - 0.6 * (a / d[:, None])
+    assert np.allclose(z, smat @ (smat @ g), atol=1e-12)
