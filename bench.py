@@ -779,23 +779,41 @@ def _cpu_baseline(weights):
         return pool.apply(_cpu_baseline_worker, (weights,))
 
 
-def _cpu_baseline_worker(weights):
+def _cpu_baseline_worker(weights, nframes=5):
+    """The oracle as it stands, timed on the host cores over `nframes` frames of the headline
+    workload (seeds 1000..): learned-H frame (FP64 network forward + FP64 PCG), its PCG alone,
+    and Jacobi PCG on the same frames."""
     import numpy as np
     import torch
     import inputs
     from oracle import grid, hmatrix, network, pcg
     torch.set_num_threads(os.cpu_count() or 1)
     p = network.unflatten(_weights_blob(weights, inputs), inputs.network_layout(**CFG))
-    fr = inputs.frame(FAMILY, 1000)
-    sys_ = grid.assemble(fr["rho"], fr["dims"])
-    a = grid.sparse_matrix(sys_)
-    t0 = time.perf_counter()
-    with torch.no_grad():
-        f = network.to_numpy_factors(network.forward(p, sys_, CFG))
-    out = pcg.pcg(lambda v: a @ v, lambda v: hmatrix.apply(f, v), fr["b"], rtol=1e-6)
-    ms = (time.perf_counter() - t0) * 1e3
-    return {"value": ms, "unit": "ms/frame", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"1 frame (seed 1000), oracle network forward + oracle PCG, {out['iters']} iterations"}
+    t_frame, t_solve, t_jac, it_l, it_j = [], [], [], [], []
+    for k in range(nframes):
+        fr = inputs.frame(FAMILY, 1000 + k)
+        sys_ = grid.assemble(fr["rho"], fr["dims"])
+        a = grid.sparse_matrix(sys_)
+        t0 = time.perf_counter()
+        with torch.no_grad():
+            f = network.to_numpy_factors(network.forward(p, sys_, CFG))
+        t1 = time.perf_counter()
+        out = pcg.pcg(lambda v: a @ v, lambda v: hmatrix.apply(f, v), fr["b"], rtol=1e-6)
+        t2 = time.perf_counter()
+        d = sys_["diag"]
+        outj = pcg.pcg(lambda v: a @ v, lambda v: v / d, fr["b"], rtol=1e-6)
+        t3 = time.perf_counter()
+        t_frame.append((t2 - t0) * 1e3)
+        t_solve.append((t2 - t1) * 1e3)
+        t_jac.append((t3 - t2) * 1e3)
+        it_l.append(out["iters"])
+        it_j.append(outj["iters"])
+    return {"value": statistics.mean(t_frame), "unit": "ms/frame", "cores": torch.get_num_threads(), "kind": "oracle",
+            "std": statistics.pstdev(t_frame),
+            "sample": f"{nframes} frames (seeds 1000..{1000 + nframes - 1}): oracle network forward (torch FP64, "
+                      f"{torch.get_num_threads()} threads) + oracle PCG (numpy/scipy FP64, one thread)",
+            "learned_solve_ms": statistics.mean(t_solve), "learned_iters": statistics.mean(it_l),
+            "jacobi_ms": statistics.mean(t_jac), "jacobi_iters": statistics.mean(it_j)}
 
 
 if __name__ == "__main__":

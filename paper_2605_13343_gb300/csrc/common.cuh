@@ -81,6 +81,28 @@ HM_INLINE void ff_fma(float& hi, float& lo, float a, float b) {
   const float p = __fmul_rn(a, b);
   ff_add(hi, lo, p, __fmaf_rn(a, b, -p));
 }
+// Sum of float-float pairs over the warp (fixed butterfly): every lane ends with the same pair.
+HM_INLINE void ff_warp_pair(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, bh, bl);
+  }
+}
+// a / b in FP64 by Newton-Raphson iteration on 1 / b from an FP32 seed (two steps take the seed's
+// 2^-23 relative error below FP64's unit roundoff), then one residual correction of the quotient.
+// FP64 division is a long instruction sequence on a part with a small FP64 rate; this is seven
+// dependent FP64 operations.  Operands outside FP32's normal range take the plain division.
+HM_INLINE double div_nr(double a, double b) {
+  const double ab = fabs(b);
+  if (!(ab > 1e-30 && ab < 1e30)) return a / b;
+  double y = (double)(1.0f / (float)b);
+  y = fma(y, fma(-b, y, 1.0), y);
+  y = fma(y, fma(-b, y, 1.0), y);
+  const double q = a * y;
+  return fma(y, fma(-b, q, a), q);
+}
 // Sum over the warp (fixed butterfly); the result is taken from lane 0.
 HM_INLINE double ff_warp_sum(float hi, float lo) {
 #pragma unroll

@@ -491,7 +491,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
 // as net_forward; each layer is three launches over both stacks instead of ~20, and the edge
 // biases of all layers come from one launch (tables of zero-coupling pairs and stencil-neighbour
 // entries for the diagonal windows, whole 16 x 16 blocks for the tiles).
-static int net_forward_fused(Net* N, const SysBatch& sb, cudaStream_t st) {
+static int net_forward_fused(Net* N, const SysBatch& sb, void* packed, int dtype, cudaStream_t st) {
   const hmpcg_config& cf = N->cfg;
   const WeightOff& o = N->off;
   const int B = sb.B, n = sb.n, d = cf.d_model, h = cf.n_heads;
@@ -580,30 +580,17 @@ static int net_forward_fused(Net* N, const SysBatch& sb, cudaStream_t st) {
     }
     NET_TRY(fused_layer(sb, fs, fw, N->gp16, N->gp16 + (size_t)(Td / 16) * d, N->gmean, N->err, st));
   }
-  // ---- final norms and heads (as in net_forward)
-  for (int s = 0; s < 2; ++s) {
-    const int T = s == 0 ? Td : To;
-    pdl_launch(layernorm_kernel, dim3((T + 7) / 8), dim3(256), 0, st, N->x_final[s], W + o.lnfg[s], W + o.lnfb[s], T, d, N->yf[s],
-               (float*)nullptr, N->muf[s], N->rsf[s], 0);
-  }
-  {
-    GemmEpi ep = e; ep.bias = W + o.leaf1b; ep.act = 1; ep.out16 = N->leafh; ep.ld16 = d;
-    NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.leaf1w), Td, d, d, ep, st));
-  }
-  {
-    GemmEpi ep = e; ep.bias = W + o.leaf2b; ep.out32 = N->frow; ep.ld32 = L;
-    NET_TRY(gemm(N->leafh, d, W16 + o.map16(o.leaf2w), Td, L, d, ep, st));
-  }
-  {
-    GemmEpi ep = e; ep.bias = W + o.nodeb; ep.out32 = N->nodeo; ep.ld32 = 2 * r;
-    NET_TRY(gemm(N->yf[0], d, W16 + o.map16(o.nodew), Td, 2 * r, d, ep, st));
-  }
-  pdl_launch(gate_logit_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, N->yf[0], W + o.nodew + (int64_t)2 * r * d, W + o.nodeb + 2 * r, Td, d,
-             N->gate_logit);
-  {
-    GemmEpi ep = e; ep.bias = W + o.offb; ep.out32 = N->offo; ep.ld32 = 2 * r;
-    NET_TRY(gemm(N->yf[1], d, W16 + o.map16(o.offw), To, 2 * r, d, ep, st));
-  }
+  // ---- final norms, heads, gate and the pack: one launch over both stacks
+  FusedHeads fh;
+  fh.xd = N->x_final[0];
+  fh.xo = N->x_final[1];
+  for (int s = 0; s < 2; ++s) { fh.lnfg[s] = W + o.lnfg[s]; fh.lnfb[s] = W + o.lnfb[s]; }
+  fh.leaf1w = W16 + o.map16(o.leaf1w); fh.leaf2w = W16 + o.map16(o.leaf2w);
+  fh.nodew = W16 + o.map16(o.nodew); fh.offw = W16 + o.map16(o.offw);
+  fh.leaf1b = W + o.leaf1b; fh.leaf2b = W + o.leaf2b; fh.nodeb = W + o.nodeb; fh.offb = W + o.offb;
+  fh.gate_w = W + o.nodew + (int64_t)2 * r * d;
+  fh.gate_b = W + o.nodeb + 2 * r;
+  NET_TRY(fused_heads(sb, fh, packed, dtype == HMPCG_BF16 ? 1 : 0, N->err, st));
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
@@ -613,8 +600,8 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
   NET_TRY(make_batch(N->cfg, systems, nsys, sb));
   if (dtype != HMPCG_F32 && dtype != HMPCG_BF16) return HMPCG_E_INVALID;
   (void)scales;
-  if (N->use_fused && N->fused_alloc && fused_supported(N->cfg, sb)) NET_TRY(net_forward_fused(N, sb, st));
-  else NET_TRY(net_forward(N, sb, st));
+  if (N->use_fused && N->fused_alloc && fused_supported(N->cfg, sb)) return net_forward_fused(N, sb, packed, dtype, st);
+  NET_TRY(net_forward(N, sb, st));
   const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
   const int Td = sb.B * sb.n;
   const int Tt = sb.B * sb.MH;

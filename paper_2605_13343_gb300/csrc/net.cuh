@@ -183,6 +183,19 @@ int fused_hw_block(int n, int L, int r);
 int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], float* gp16d, float* gp16o, float* g32,
                 int* err, cudaStream_t s);
 
+// Fused heads (net_fused.cu): LN_f of both stacks, leaf / node / tile heads, gate, pack.
+struct FusedHeads {
+  const float* xd;
+  const float* xo;
+  const float* lnfg[2];
+  const float* lnfb[2];
+  const bf16 *leaf1w, *leaf2w, *nodew, *offw;   // BF16 [out][in]
+  const float *leaf1b, *leaf2b, *nodeb, *offb;
+  const float* gate_w;                           // FP32 row 2 L_s of the node head
+  const float* gate_b;
+};
+int fused_heads(const SysBatch& sb, const FusedHeads& hw, void* packed, int bf16_out, int* err, cudaStream_t s);
+
 constexpr int kEdgeMaxLayers = 16;
 struct EdgePrep {
   const float* e1w[2][kEdgeMaxLayers];

@@ -22,6 +22,7 @@
 // records HMPCG_E_TIMEOUT, still waits (bounded) for its own MMAs and frees its TMEM.
 #include <cuda.h>
 #include <algorithm>
+#include <cstring>
 #include "net.cuh"
 #include "tc.cuh"
 
@@ -35,6 +36,8 @@ constexpr int kDM = 512;    // FFN hidden width
 constexpr long kWaitLong = 1l << 24;
 constexpr int kMaxHwBlock = 512;   // nodes per highway block: 2 x 512 x 33 floats of shared memory
 constexpr int kMaxLevels = 9;      // tree levels of the fused path (K <= 512 leaves)
+
+HM_INLINE float softplus_f(float x) { return x > 20.f ? x : log1pf(expf(x)); }
 
 // ----------------------------------------------------------------------------- attention block
 // 256 threads: two per token row (row = tid % 128 = TMEM lane; half = tid / 128 takes one half of
@@ -799,6 +802,263 @@ __global__ void __launch_bounds__(kFT, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
+// ----------------------------------------------------------------------------- heads (Sec. 4.4)
+// Diagonal CTAs (128 nodes = 2 leaves): LN_f -> leaf head d -> d (GELU) -> L and node head
+// d -> 2 L_s on tcgen05, the gate logit as an FP32 dot with the BF16-rounded LN_f row (as in the
+// layered path), then the packed rows scaled by diag(A)^-1/2 and the gate softplus / diag(A).
+// Tile CTAs (128 tokens = 8 tiles): LN_f -> off head d -> 2 L_s -> B_m = U_m V_m^T.  Every packed
+// row range a CTA owns is contiguous: staged in shared memory, written with whole-warp stores.
+constexpr uint32_t kH_A = 0;          // LN_f rows BF16 [128][128]
+constexpr uint32_t kH_W1 = 32768;     // leaf1 [128][128]
+constexpr uint32_t kH_WN = 65536;     // node head rows 0..47 [48][128] (rows past 2 L_s + 1 zero-filled)
+constexpr uint32_t kH_W2 = 77824;     // leaf2 [64][128]
+constexpr uint32_t kH_H = 94208;      // GELU(leaf1) BF16 [128][128]
+constexpr uint32_t kH_ST = 126976;    // staged outputs FP32: F rows [128][65] or U, V [128][33]
+constexpr uint32_t kH_G = kH_ST + 128 * 65 * 4;   // gate logits [128], diag^-1/2 [128]
+constexpr uint32_t kH_SMEM = kH_G + 256 * 4 + 1024;
+
+struct HeadArgs {
+  const float* x[2];            // x_final of both stacks
+  const float* lnfg[2];
+  const float* lnfb[2];
+  const float *leaf1b, *leaf2b, *nodeb, *offb;
+  const float* gate_w;          // row 2 L_s of the node head (FP32) and its bias
+  const float* gate_b;
+  const double* diag[kMaxSys];
+  void* packed;
+  int bf16_out;
+  int64_t P;
+  int n, K, MH, Td, To, nblk_d;
+  int* err;
+};
+
+template <class T>
+HM_INLINE void head_store(T* p, float v);
+template <> HM_INLINE void head_store<float>(float* p, float v) { *p = v; }
+template <> HM_INLINE void head_store<bf16>(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <class T>
+__device__ void heads_body(uint8_t* sm, const HeadArgs& a, uint32_t tmem, uint64_t* bars, int sidx, int row0) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & 127, half = tid >> 7;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const int ntok = sidx ? a.To : a.Td;
+  T* out = reinterpret_cast<T*>(a.packed);
+  float* gl = reinterpret_cast<float*>(sm + kH_G);
+  float* sinv = gl + 128;
+  bool ok = true;
+  // ---- LN_f (warp w: rows 16 w ..), BF16 rows into the A tile; the gate logit on the rounded row
+  {
+    const float4 g4 = reinterpret_cast<const float4*>(a.lnfg[sidx])[lane];
+    const float4 b4 = reinterpret_cast<const float4*>(a.lnfb[sidx])[lane];
+    const float4 wg = sidx == 0 ? reinterpret_cast<const float4*>(a.gate_w)[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 xr[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = 16 * warp + k;
+      xr[k] = (row0 + r < ntok) ? reinterpret_cast<const float4*>(a.x[sidx] + (size_t)(row0 + r) * kD)[lane]
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int r = 16 * warp + k;
+      const float4 x = xr[k];
+      const float mean = warp_sum((x.x + x.y) + (x.z + x.w)) * (1.f / kD);
+      const float dx = x.x - mean, dy = x.y - mean, dz = x.z - mean, dw = x.w - mean;
+      const float var = warp_sum((dx * dx + dy * dy) + (dz * dz + dw * dw)) * (1.f / kD);
+      const float rstd = rsqrtf(var + 1e-5f);
+      const bool ok_r = row0 + r < ntok;
+      const __nv_bfloat162 y01 = __floats2bfloat162_rn(ok_r ? dx * rstd * g4.x + b4.x : 0.f, ok_r ? dy * rstd * g4.y + b4.y : 0.f);
+      const __nv_bfloat162 y23 = __floats2bfloat162_rn(ok_r ? dz * rstd * g4.z + b4.z : 0.f, ok_r ? dw * rstd * g4.w + b4.w : 0.f);
+      const int c = 4 * lane;
+      *reinterpret_cast<uint2*>(sm + kH_A + (c >> 6) * 16384 + sw128(r, (c & 63) >> 3) + (c & 4) * 2) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&y01), *reinterpret_cast<const uint32_t*>(&y23));
+      if (sidx == 0) {
+        const float2 f01 = __bfloat1622float2(y01), f23 = __bfloat1622float2(y23);
+        float gs = fmaf(f01.x, wg.x, fmaf(f01.y, wg.y, fmaf(f23.x, wg.z, f23.y * wg.w)));
+        gs = warp_sum(gs);
+        if (lane == 0) {
+          gl[r] = gs + a.gate_b[0];
+          const int t = row0 + r;
+          sinv[r] = ok_r ? (float)(1.0 / sqrt(a.diag[t / a.n][t % a.n])) : 0.f;
+        }
+      }
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    if (!mbar_wait(smem_u32(&bars[0]), 0, kWaitLong)) ok = false;   // weights
+    tc_fence_after();
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      const uint64_t ad = sw128_desc(smem_u32(sm + kH_A + kc * 16384));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t acc = (kc | k) ? 1u : 0u;
+        if (sidx == 0) {
+          mma_bf16(tmem, ad + 2 * k, sw128_desc(smem_u32(sm + kH_W1 + kc * 16384)) + 2 * k, idesc_bf16(128, 128), acc);
+          mma_bf16(tmem + 128, ad + 2 * k, sw128_desc(smem_u32(sm + kH_WN + kc * 6144)) + 2 * k, idesc_bf16(128, 48), acc);
+        } else {
+          mma_bf16(tmem, ad + 2 * k, sw128_desc(smem_u32(sm + kH_WN + kc * 6144)) + 2 * k, idesc_bf16(128, 32), acc);
+        }
+      }
+    }
+    mma_commit(smem_u32(&bars[1]));
+  }
+  if (!mbar_wait(smem_u32(&bars[1]), 0, kWaitLong)) ok = false;
+  __syncwarp();
+  tc_fence_after();
+  float* st = reinterpret_cast<float*>(sm + kH_ST);
+  if (sidx == 0) {
+    // leaf1 + bias -> GELU -> BF16 H (this thread: 64 columns); U~, V~ (+ bias) x diag^-1/2 staged
+    {
+      float v[32];
+#pragma unroll 1
+      for (int e = 0; e < 2; ++e) {
+        const int c32 = 2 * half + e;
+        tmem_ld32(tl + c32 * 32, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = gelu_f(v[j] + a.leaf1b[c32 * 32 + j]);
+#pragma unroll
+        for (int u4 = 0; u4 < 4; ++u4) st_unit_bf16(sm + kH_H + half * 16384 + sw128(row, e * 4 + u4), v + 8 * u4);
+      }
+      tmem_ld32(tl + 128, v);   // node head columns 0..31 (both halves read them; half 0 stages)
+      if (half == 0) {
+        const float si = sinv[row];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) st[row * 33 + j] = (v[j] + a.nodeb[j]) * si;
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc) {
+        const uint64_t ad = sw128_desc(smem_u32(sm + kH_H + kc * 16384));
+        const uint64_t bd = sw128_desc(smem_u32(sm + kH_W2 + kc * 8192));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) mma_bf16(tmem + 192, ad + 2 * k, bd + 2 * k, idesc_bf16(128, 64), (kc | k) ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&bars[2]));
+    }
+    // U~, V~ rows (16 each) and the gate of the CTA's 128 nodes are contiguous in the packed vector
+    {
+      const int t0 = row0;
+      const int b = t0 / a.n, i0 = t0 % a.n;
+      T* base = out + (size_t)b * a.P;
+      const int64_t offU = (int64_t)a.K * 64 * 64 + (int64_t)a.MH * 16 * 16, offV = offU + (int64_t)a.n * 16,
+                    offG = offV + (int64_t)a.n * 16;
+      for (int q = tid; q < 128 * 16; q += blockDim.x) {
+        const int r = q >> 4, c = q & 15;
+        head_store<T>(base + offU + (int64_t)(i0 + r) * 16 + c, st[r * 33 + c]);
+        head_store<T>(base + offV + (int64_t)(i0 + r) * 16 + c, st[r * 33 + 16 + c]);
+      }
+      if (tid < 128) {
+        const int t = t0 + tid;
+        const double di = a.diag[b][t % a.n];
+        head_store<T>(base + offG + i0 + tid, (float)((double)softplus_f(gl[tid]) / di));
+      }
+    }
+    if (!mbar_wait(smem_u32(&bars[2]), 0, kWaitLong)) ok = false;
+    __syncwarp();
+    tc_fence_after();
+    __syncthreads();   // the U, V staging reads above are done: F rows reuse the buffer
+    {
+      float v[32];
+      tmem_ld32(tl + 192 + 32 * half, v);
+      const float si = sinv[row];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) st[row * 65 + 32 * half + j] = (v[j] + a.leaf2b[32 * half + j]) * si;
+    }
+    __syncthreads();
+    {
+      // F blocks of the CTA's two leaves: 2 x 64 x 64 contiguous values
+      const int b = row0 / a.n, i0 = row0 % a.n;
+      T* base = out + (size_t)b * a.P + (int64_t)(i0 / 64) * 64 * 64;
+      for (int q = tid; q < 128 * 64; q += blockDim.x) head_store<T>(base + q, st[(q >> 6) * 65 + (q & 63)]);
+    }
+  } else {
+    // off head: U_m rows (16) and V_m rows (16) of every token, then B_m = U_m V_m^T per tile
+    if (half == 0) {
+      float v[32];
+      tmem_ld32(tl, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) st[row * 33 + j] = v[j] + a.offb[j];
+    } else {
+      float v[32];
+      tmem_ld32(tl, v);   // warp-collective: both halves load, half 1 discards
+      (void)v;
+    }
+    __syncthreads();
+    for (int q = tid; q < 8 * 256; q += blockDim.x) {
+      const int w = q >> 8, ab = q & 255, aa = ab >> 4, cc = ab & 15;
+      const int t = row0 + 16 * w;      // first token of tile window w
+      if (t >= a.To) continue;
+      const int tile = t >> 4;          // (system, tile) index
+      const int b = tile / a.MH, m = tile % a.MH;
+      const float* U = st + (16 * w + aa) * 33;
+      const float* V = st + (16 * w + cc) * 33 + 16;
+      float acc = 0.f;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc = fmaf(U[e], V[e], acc);
+      head_store<T>(out + (size_t)b * a.P + (int64_t)a.K * 64 * 64 + (int64_t)m * 256 + ab, acc);
+    }
+  }
+  if (!ok && a.err) atomicExch(a.err, (int)HMPCG_E_TIMEOUT);
+}
+
+__global__ void __launch_bounds__(kAT, 1)
+    fused_heads_kernel(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap mn,
+                       const __grid_constant__ CUtensorMap m2, const __grid_constant__ CUtensorMap mo,
+                       const __grid_constant__ HeadArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tmem_s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int sidx = blockIdx.x < a.nblk_d ? 0 : 1;
+  const int row0 = (sidx ? blockIdx.x - a.nblk_d : blockIdx.x) * kTok;
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) mbar_init(smem_u32(&bars[q]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    const uint32_t bw = smem_u32(&bars[0]);
+    if (sidx == 0) {
+      mbar_expect_tx(bw, 2 * 16384 + 2 * 6144 + 2 * 8192);
+      for (int kc = 0; kc < 2; ++kc) {
+        tma_load_2d(smem_u32(sm + kH_W1 + kc * 16384), &m1, kc * 64, 0, bw);
+        tma_load_2d(smem_u32(sm + kH_WN + kc * 6144), &mn, kc * 64, 0, bw);
+        tma_load_2d(smem_u32(sm + kH_W2 + kc * 8192), &m2, kc * 64, 0, bw);
+      }
+    } else {
+      mbar_expect_tx(bw, 2 * 4096);
+      for (int kc = 0; kc < 2; ++kc) tma_load_2d(smem_u32(sm + kH_WN + kc * 6144), &mo, kc * 64, 0, bw);
+    }
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_s)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  pdl_entry();
+  if (a.bf16_out) heads_body<bf16>(sm, a, tmem, bars, sidx, row0);
+  else heads_body<float>(sm, a, tmem, bars, sidx, row0);
+  // every MMA of this CTA has completed (its last commit was waited on above) before TMEM is freed
+  if (tid == 0) mma_commit(smem_u32(&bars[3]));
+  mbar_wait(smem_u32(&bars[3]), 0, kWaitLong);
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
 template <class... KArgs, class... Args>
 int launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -881,6 +1141,37 @@ int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], f
   fa.nblk_d = nblk_d;
   fa.err = err;
   rc = launch_pdl(fused_ffn_kernel, dim3(nblk_d + nblk_o), dim3(kFT), kF_SMEM, s, mu[0], mu[1], m1[0], m1[1], m2[0], m2[1], fa);
+  if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+int fused_heads(const SysBatch& sb, const FusedHeads& hw, void* packed, int bf16_out, int* err, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr{0};
+  if (!once_per_device(attr, [] {
+        return cudaFuncSetAttribute(fused_heads_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH_SMEM) ==
+               cudaSuccess;
+      }))
+    return HMPCG_E_CUDA;
+  CUtensorMap m1, mn, m2, mo;
+  if (!tma_map_bf16(&m1, hw.leaf1w, kD, kD, kD, 128) || !tma_map_bf16(&mn, hw.nodew, 2 * sb.r + 1, kD, kD, 48) ||
+      !tma_map_bf16(&m2, hw.leaf2w, 64, kD, kD, 64) || !tma_map_bf16(&mo, hw.offw, 2 * sb.r, kD, kD, 32))
+    return HMPCG_E_INVALID;
+  HeadArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x[0] = hw.xd; a.x[1] = hw.xo;
+  for (int q = 0; q < 2; ++q) { a.lnfg[q] = hw.lnfg[q]; a.lnfb[q] = hw.lnfb[q]; }
+  a.leaf1b = hw.leaf1b; a.leaf2b = hw.leaf2b; a.nodeb = hw.nodeb; a.offb = hw.offb;
+  a.gate_w = hw.gate_w; a.gate_b = hw.gate_b;
+  for (int b = 0; b < sb.B; ++b) a.diag[b] = sb.diag[b];
+  a.packed = packed;
+  a.bf16_out = bf16_out;
+  a.P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
+  a.n = sb.n; a.K = sb.K; a.MH = sb.MH;
+  a.Td = sb.B * sb.n; a.To = sb.B * sb.MH * sb.r;
+  a.nblk_d = a.Td / kTok;
+  a.err = err;
+  const int nblk_o = (a.To + kTok - 1) / kTok;
+  const int rc = launch_pdl(fused_heads_kernel, dim3(a.nblk_d + nblk_o), dim3(kAT), kH_SMEM, s, m1, mn, m2, mo, a);
   if (rc) return rc;
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }

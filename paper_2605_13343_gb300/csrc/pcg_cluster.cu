@@ -65,12 +65,16 @@ struct CParams {
 
 // Shared-memory carve-up (byte offsets), identical in every CTA.
 struct CLayout {
-  size_t x, b, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tc, part, rs, ws, leaf, bridge, gate, core, total;
+  size_t x, b, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tv, part, partff, rs, ws, leaf, bridge, gate, core, total;
 };
+
+// Couplings a CTA's own leaves need: one per (level, cluster of the level) among its lpc leaves,
+// at most levels + 2 lpc of them (one per level while a cluster spans the CTA, then lpc / 2^j).
+__host__ __device__ inline int coupling_entries(int lpc, int levels) { return levels + 2 * lpc; }
 
 template <class T>
 __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, int nslot, bool learned, bool hmat,
-                                     bool fsm) {
+                                     bool fsm, int levels) {
   CLayout o;
   size_t p = 0;
   auto take = [&](size_t bytes) { size_t q = p; p = (p + bytes + 15) / 16 * 16; return q; };
@@ -86,14 +90,15 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
   o.nbr = take(24 * (size_t)npc);              // 6 neighbours: (owner << 16) | local index, -1 at the boundary
   o.wm = take(12 * (size_t)npc);               // w32 of the -a face of each owned node
   o.uh = take(hmat ? 4 * (size_t)nslot * (2 * lpc - 1) * R : 0);   // per slot: leaves, then aligned pair, quad, ... sums
-  o.tc = take(hmat ? 4 * (size_t)tpc * 2 * R : 0);
+  o.tv = take(hmat ? 4 * (size_t)coupling_entries(lpc, levels) * 2 * R : 0);   // strip sums, then couplings
   o.part = take(8 * 8);
+  o.partff = take(8 * 8);
   o.rs = take(hmat ? 4 * (size_t)lpc * L : 0);
   o.ws = take(hmat ? 4 * (size_t)lpc * (L > nslot * R ? L : nslot * R) : 0);
   o.leaf = take(hmat && fsm ? sizeof(T) * (size_t)lpc * L * (L + kLeafPad) : 0);
   o.bridge = take(hmat && fsm ? sizeof(T) * (size_t)nslot * npc * R : 0);
   o.gate = take(hmat && fsm && learned ? sizeof(T) * (size_t)npc : 0);
-  o.core = take(hmat && fsm ? sizeof(T) * (size_t)tpc * R * R : 0);
+  o.core = take(0);   // cores are read from the packed tensor (L2-resident)
   o.total = p;
   return o;
 }
@@ -111,7 +116,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   const int L = LC ? LC : F.L, R = RC ? RC : F.r;
   const bool hmat = PRE == CPRE_HMAT;
   const bool fsm = P.fsm != 0;
-  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, fsm);
+  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, fsm, F.levels);
   double* xs = reinterpret_cast<double*>(sm + lay.x);
   double* bs = reinterpret_cast<double*>(sm + lay.b);
   float* rv = reinterpret_cast<float*>(sm + lay.r);
@@ -123,14 +128,14 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   int* nbt = reinterpret_cast<int*>(sm + lay.nbr);
   float* wmv = reinterpret_cast<float*>(sm + lay.wm);
   float* uh = reinterpret_cast<float*>(sm + lay.uh);
-  float* tcp = reinterpret_cast<float*>(sm + lay.tc);
+  float* tvb = reinterpret_cast<float*>(sm + lay.tv);
   double* part = reinterpret_cast<double*>(sm + lay.part);
+  float2* partff = reinterpret_cast<float2*>(sm + lay.partff);
   float* rs = reinterpret_cast<float*>(sm + lay.rs);
   float* ws = reinterpret_cast<float*>(sm + lay.ws);
   T* sleaf = reinterpret_cast<T*>(sm + lay.leaf);
   T* sbr = reinterpret_cast<T*>(sm + lay.bridge);
   T* sgate = reinterpret_cast<T*>(sm + lay.gate);
-  T* score = reinterpret_cast<T*>(sm + lay.core);
   const int tid = threadIdx.x;
   const int n0 = me * npc;
   const int LP = L + kLeafPad;
@@ -140,7 +145,6 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   const T* brf = fsm ? sbr : (hmat ? F.bridge + (size_t)n0 * R : nullptr);
   const size_t brs = fsm ? (size_t)npc * R : (size_t)F.n * R;          // slot stride
   const T* gtf = fsm ? sgate : (hmat && F.learned ? F.gate + n0 : nullptr);
-  auto core_of = [&](int tl, int m) -> const T* { return fsm ? score + (size_t)tl * R * R : F.core + (size_t)m * R * R; };
 
   // value of node i of an owner-distributed array (local shared memory or DSMEM)
   auto ld_f = [&](float* base, int i) -> float {
@@ -188,11 +192,6 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
         sbr[(size_t)s * npc * R + e] = F.bridge[((size_t)s * F.n + n0) * R + e];
     if (F.learned)
       for (int e = tid; e < npc; e += blockDim.x) sgate[e] = F.gate[n0 + e];
-    for (int tl = 0; tl < P.tpc; ++tl) {
-      const int m = me + tl * C;
-      if (m >= F.K - 1) break;
-      for (int e = tid; e < R * R; e += blockDim.x) score[(size_t)tl * R * R + e] = F.core[(size_t)m * R * R + e];
-    }
   }
   __syncthreads();
 
@@ -337,69 +336,87 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       u[(P.lpc + node) * R + e] = acc;
     }
   };
-  // strip sums and coupling of the owned tiles: a strip of S <= lpc leaves is one tree node
-  // of one CTA, a longer strip is the sum of S / lpc whole-CTA roots (<= 16 remote loads)
-  auto tiles = [&]() {
+  // Coupling stage (Sec. 5) for this CTA's own leaves, computed here rather than by the tiles'
+  // owners: for each level and each cluster of that level holding owned leaves, the strip sum of
+  // the sibling cluster (one tree node of one CTA, or the sum of whole-CTA roots, <= 16 remote
+  // loads) and its product with the tile's core (t^r = B s^c for a row cluster, t^c = B^T s^r for a
+  // column cluster).  No cluster barrier is needed between the couplings and the prolongation.
+  // Entries: one per level while a cluster spans the CTA (levels 1..lv0), then 2, 4, ..., lpc.
+  const int k0 = n0 / L;
+  const int lgl = hmat ? 31 - __clz(P.lpc) : 0;
+  const int lv0 = hmat ? F.levels - lgl : 0;
+  const int NE = hmat ? lv0 + 2 * P.lpc - 2 : 0;
+  auto ent_level = [&](int ent, int& lev, int& j) {
+    if (ent < lv0) { lev = ent + 1; j = 0; return; }
+    int rel = ent - lv0, t = 0;
+    while (rel >= (2 << t)) { rel -= 2 << t; ++t; }
+    lev = lv0 + 1 + t;
+    j = rel;
+  };
+  auto tiles_local = [&]() {
     const int T1 = 2 * P.lpc - 1;
-    int lg = 0;
-    while ((1 << lg) < P.lpc) ++lg;
-    for (int q = tid; q < P.tpc * 2 * R; q += blockDim.x) {
-      const int tl = q / (2 * R), side = (q / R) & 1, e = q % R;
-      const int m = me + tl * C;
-      if (m >= F.K - 1) continue;
-      const int lev = 32 - __clz(m + 1);
-      const int t = m + 1 - (1 << (lev - 1));
+    float* ssum = tvb;                         // [NE][R] sibling strip sums
+    float* coup = tvb + (size_t)NE * R;        // [NE][R] couplings
+    for (int q = tid; q < NE * R; q += blockDim.x) {
+      const int ent = q / R, e = q % R;
+      int lev, j;
+      ent_level(ent, lev, j);
+      const int cl = (k0 >> (F.levels - lev)) + j;
+      const int sib = cl ^ 1;
+      const int slot = F.learned ? (sib & 1) : lev - 1;
       const int Sl = F.K >> lev;
-      const int k0 = side ? (2 * t + 1) * Sl : 2 * t * Sl;
-      const int slot = F.learned ? side : lev - 1;
+      const int kk0 = sib * Sl;
       float acc = 0.f;
       if (Sl <= P.lpc) {
-        int j = 0, base = 0, cnt = P.lpc;
-        while ((1 << j) < Sl) { base += cnt; cnt >>= 1; ++j; }
-        const int owner = k0 / P.lpc, g = (k0 % P.lpc) >> j;
-        acc = *remote(uh + ((size_t)slot * T1 + base + g) * R + e, owner);
+        int jj = 0, base = 0, cnt = P.lpc;
+        while ((1 << jj) < Sl) { base += cnt; cnt >>= 1; ++jj; }
+        const int owner = kk0 / P.lpc, g = (kk0 % P.lpc) >> jj;
+        float* src = uh + ((size_t)slot * T1 + base + g) * R + e;
+        acc = owner == (int)me ? *src : *remote(src, owner);
       } else {
         const int root = T1 - 1;
-        const int o0 = k0 / P.lpc, no = Sl / P.lpc;
+        const int o0 = kk0 / P.lpc, no = Sl / P.lpc;
         float v[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) v[c] = c < no ? *remote(uh + ((size_t)slot * T1 + root) * R + e, o0 + c) : 0.f;
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc += v[c];
       }
-      (void)lg;
-      ws[q] = acc;    // ws reused as [tile][side][e] strip sums (tpc 2 R <= lpc max(L, nslot R))
+      ssum[q] = acc;
     }
     __syncthreads();
-    for (int q = tid; q < P.tpc * 2 * R; q += blockDim.x) {
-      const int tl = q / (2 * R), side = (q / R) & 1, e = q % R;
-      const int m = me + tl * C;
-      if (m >= F.K - 1) continue;
-      const T* Bm = core_of(tl, m);
+    for (int q = tid; q < NE * R; q += blockDim.x) {
+      const int ent = q / R, e = q % R;
+      int lev, j;
+      ent_level(ent, lev, j);
+      const int cl = (k0 >> (F.levels - lev)) + j;
+      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+      const T* Bm = F.core + (size_t)m * R * R;
       const float sB = F.sc_core ? F.sc_core[m] : 1.f;
-      const float* srow = ws + (size_t)tl * 2 * R;        // s^r
-      const float* scol = srow + R;                        // s^c
+      const float* sv = ssum + (size_t)ent * R;
       float acc = 0.f;
-      if (side == 0) { for (int f = 0; f < R; ++f) acc = fmaf(tf<T>(Bm[e * R + f]), scol[f], acc); }   // t^r = B s^c
-      else { for (int f = 0; f < R; ++f) acc = fmaf(tf<T>(Bm[f * R + e]), srow[f], acc); }              // t^c = B^T s^r
-      tcp[(size_t)tl * 2 * R + side * R + e] = acc * sB;
+      if ((cl & 1) == 0) { for (int f = 0; f < R; ++f) acc = fmaf(tf<T>(Bm[e * R + f]), sv[f], acc); }   // t^r = B s^c
+      else { for (int f = 0; f < R; ++f) acc = fmaf(tf<T>(Bm[f * R + e]), sv[f], acc); }                // t^c = B^T s^r
+      coup[q] = acc * sB;
     }
+    __syncthreads();
   };
   // prolongation of every owned leaf: z = ydiag + sum_s W_s a_s
   auto prolong = [&]() {
     float* as = ws;   // [lpc][nslot][R]
-    const int lgC = 31 - __clz(C);   // C is a power of two
     for (int q = tid; q < P.lpc * R; q += blockDim.x) {
       const int kl = q / R, e = q % R;
       const int k = n0 / L + kl;
+      const float* coup = tvb + (size_t)NE * R;
       float tv[24];
 #pragma unroll
       for (int lev = 1; lev <= 24; ++lev) {
         tv[lev - 1] = 0.f;
         if (lev <= F.levels) {
-          const int cl = k >> (F.levels - lev);                  // cluster of leaf k at this level
-          const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-          tv[lev - 1] = *remote(tcp + (size_t)(m >> lgC) * 2 * R + (cl & 1) * R + e, m & (C - 1));
+          const int sh = F.levels - lev;
+          const int j = (k >> sh) - (k0 >> sh);                  // cluster of leaf k among the owned ones
+          const int ent = (lev <= lv0 + 1 ? lev - 1 : lv0 + (1 << (lev - lv0)) - 2) + j;
+          tv[lev - 1] = coup[(size_t)ent * R + e];
         }
       }
       if (F.learned) {
@@ -485,7 +502,12 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   // PCG scalars are computed by thread 0 and broadcast through shared memory.  Each slot q has
   // its own per-warp array: between two uses of a slot lie several CTA barriers, so the
   // reduction needs one barrier, not two.
+  // The dot products of the iteration stay float-float pairs through the CTA and the cluster
+  // reductions (FP32 instructions only, fixed order): warp sums, then warp 0 over the warps, then
+  // warp 0 over the CTAs' pairs (one remote load per lane); FP64 starts at hi + lo.  The scalars
+  // are formed by warp 0 and broadcast through shared memory.
   __shared__ double redw[8][kCThreads / 32];
+  __shared__ float2 redf[8][kCThreads / 32];
   __shared__ double scal[4];
   __shared__ int iscal[2];
   auto cta_finish = [&](double w, int q) {   // w: this warp's sum, valid in lane 0
@@ -496,8 +518,26 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       if (tid == 0) part[q] = s;
     }
   };
-  auto cta_part = [&](double v, int q) { cta_finish(warp_sum(v), q); };   // FP64 terms
-  auto cta_part_ff = [&](float hi, float lo, int q) { cta_finish(ff_warp_sum(hi, lo), q); };
+  auto cta_part = [&](double v, int q) { cta_finish(warp_sum(v), q); };   // FP64 terms (once per solve)
+  auto cta_part_ff = [&](float hi, float lo, int q) {
+    ff_warp_pair(hi, lo);
+    if ((tid & 31) == 0) redf[q][tid >> 5] = make_float2(hi, lo);
+    __syncthreads();
+    if (tid < 32) {
+      const float2 v = tid < (int)(blockDim.x >> 5) ? redf[q][tid] : make_float2(0.f, 0.f);
+      float h = v.x, l = v.y;
+      ff_warp_pair(h, l);
+      if (tid == 0) partff[q] = make_float2(h, l);
+    }
+  };
+  // cluster total of float-float slot q; called by all of warp 0 after a cluster barrier
+  auto cl_total_ff = [&](int q) -> double {
+    const int lane = tid & 31;
+    const float2 v = lane < C ? *remote(partff + q, lane) : make_float2(0.f, 0.f);
+    float h = v.x, l = v.y;
+    ff_warp_pair(h, l);
+    return (double)h + (double)l;
+  };
 
   // ---------------- init: x = 0, r = b, p = 0, z = M r
   double acc = 0.0;
@@ -520,8 +560,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   __syncthreads();
   const double bb = scal[0];
   if (hmat) {
-    tiles();
-    cluster_sync();
+    tiles_local();
     prolong();
   }
   __syncthreads();
@@ -536,11 +575,13 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   }
   cta_part_ff(ah, al, 1);
   cluster_sync();
-  if (tid == 0) {
-    const double rz0 = cl_total(1);
-    scal[1] = rz0;
-    iscal[0] = (bb == 0.0) ? HMPCG_OK
-             : (!(rz0 > 0.0) ? ((rz0 != rz0) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN) : HMPCG_NOT_CONVERGED);
+  if (tid < 32) {
+    const double rz0 = cl_total_ff(1);
+    if (tid == 0) {
+      scal[1] = rz0;
+      iscal[0] = (bb == 0.0) ? HMPCG_OK
+               : (!(rz0 > 0.0) ? ((rz0 != rz0) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN) : HMPCG_NOT_CONVERGED);
+    }
   }
   __syncthreads();
   double rz = scal[1];
@@ -567,10 +608,12 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     cta_part_ff(ah, al, 2 + (it & 1));   // alternate slots: no reader of the previous value remains
     ++it;
     cluster_sync();
-    if (tid == 0) {
-      const double pq = cl_total(2 + ((it - 1) & 1));
-      iscal[0] = (pq > 0.0) ? HMPCG_NOT_CONVERGED : ((pq != pq) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN);
-      scal[2] = rz / pq;
+    if (tid < 32) {
+      const double pq = cl_total_ff(2 + ((it - 1) & 1));
+      if (tid == 0) {
+        iscal[0] = (pq > 0.0) ? HMPCG_NOT_CONVERGED : ((pq != pq) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN);
+        scal[2] = div_nr(rz, pq);
+      }
     }
     __syncthreads();
     status = iscal[0];
@@ -616,14 +659,17 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     cur ^= 1;
     __syncthreads();
     cluster_sync();
-    if (tid == 0) {
-      const double rrn = cl_total(4);
-      scal[3] = rrn;
-      iscal[0] = (rrn != rrn) ? HMPCG_E_NAN : (rrn <= P.rtol * P.rtol * bb ? HMPCG_OK : HMPCG_NOT_CONVERGED);
-      if (PRE != CPRE_HMAT && iscal[0] == HMPCG_NOT_CONVERGED) {
-        const double rzn = cl_total(5);
-        if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
-        scal[1] = rzn;
+    if (tid < 32) {
+      const double rrn = cl_total_ff(4);
+      const double rzn = PRE != CPRE_HMAT ? cl_total_ff(5) : 0.0;
+      if (tid == 0) {
+        scal[3] = rrn;
+        iscal[0] = (rrn != rrn) ? HMPCG_E_NAN : (rrn <= P.rtol * P.rtol * bb ? HMPCG_OK : HMPCG_NOT_CONVERGED);
+        if (PRE != CPRE_HMAT && iscal[0] == HMPCG_NOT_CONVERGED) {
+          if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+          scal[1] = rzn;
+          scal[0] = div_nr(rzn, rz);   // beta
+        }
       }
     }
     __syncthreads();
@@ -631,25 +677,25 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
     status = iscal[0];
     if (status != HMPCG_NOT_CONVERGED) break;
     if (hmat) {
-      tiles();
-      cluster_sync();
+      tiles_local();
       prolong();
       __syncthreads();
       rzh = 0.f, rzl = 0.f;
       for (int i = tid; i < npc; i += blockDim.x) ff_fma(rzh, rzl, rv[i], zv[i]);
       cta_part_ff(rzh, rzl, 5);
       cluster_sync();
-      if (tid == 0) {
-        const double rzn = cl_total(5);
-        if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
-        scal[1] = rzn;
+      if (tid < 32) {
+        const double rzn = cl_total_ff(5);
+        if (tid == 0) {
+          if (!(rzn > 0.0)) iscal[0] = (rzn != rzn) ? HMPCG_E_NAN : HMPCG_E_BREAKDOWN;
+          scal[1] = rzn;
+          scal[0] = div_nr(rzn, rz);   // beta
+        }
       }
       __syncthreads();
       status = iscal[0];
       if (status != HMPCG_NOT_CONVERGED) break;
     }
-    if (tid == 0) scal[0] = scal[1] / rz;
-    __syncthreads();
     beta = scal[0];
     rz = scal[1];
     // part[5] is rewritten in the next iteration only after two more cluster barriers
@@ -745,8 +791,7 @@ static bool plan_cluster(const hmpcg_system* sys, const FactorView<T>* fv, int C
   if (hmat && (n / C) / L * C != fv->K) return false;
   const int tpc = hmat ? (fv->K - 1 + C - 1) / C : 0;
   const int R = hmat ? fv->r : 16, nslot = hmat ? fv->nslot : 1;
-  const CLayout lay = c_layout<T>(npc, lpc, tpc, L, R, nslot, hmat && fv->learned, hmat, fsm);
-  if (hmat && (size_t)tpc * 2 * R > (size_t)lpc * std::max(L, nslot * R)) return false;
+  const CLayout lay = c_layout<T>(npc, lpc, tpc, L, R, nslot, hmat && fv->learned, hmat, fsm, hmat ? fv->levels : 0);
   if (hmat && (size_t)lpc * nslot * R > (size_t)lpc * std::max(L, nslot * R)) return false;
   if (lay.total > 220 * 1024) return false;
   P.s = make_sysview(sys);

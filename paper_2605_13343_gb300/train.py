@@ -4,7 +4,8 @@ Systems are drawn from two seeded pools assembled on the device once (the cached
 training contexts of Sec. 6.3 / Supp. D): 16^3 boxes with contrast log-uniform in
 [1, 100] and 32x16x16 boxes with 5-12 spheres of contrast 100.  Each step takes a
 random batch from one pool (every `--big-every`-th step from the larger grid),
-16 Rademacher probes per system, AdamW with global-norm clipping (inside the
+16 probes per system (Rademacher, or with `--probe-kind gaussian` the paper's Gaussian
+probes smoothed by two damped-Jacobi sweeps, Sec. 6.2), AdamW with global-norm clipping (inside the
 step) and a reduce-on-plateau learning-rate schedule (factor 0.5, patience 5 log
 steps, relative threshold 5e-3, floor max(lr * 1e-3, 1e-6); Supp. C).  With
 `--auto-stop` training ends once the rate is at its floor and the loss has not
@@ -123,11 +124,16 @@ def main():
                                                   "hmpcg_d128_l4.f32"))
     ap.add_argument("--log", default=None)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--probe-kind", choices=["rademacher", "gaussian"], default="rademacher")
+    ap.add_argument("--omega", type=float, default=0.6)
+    ap.add_argument("--smooth-steps", type=int, default=2)
     args = ap.parse_args()
 
     w0 = np.fromfile(args.init, dtype=np.float32) if args.init else inputs.network_blob(args.seed, **CFG)
     ctx = h.Context(max_n=8192, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
                     max_batch=args.batch, weights=w0)
+    if args.probe_kind == "gaussian":
+        h.set_train_probes(ctx, h.PROBES_GAUSSIAN_SMOOTHED, args.omega, args.smooth_steps)
     small = make_pool("spheres3d_4096_lu", range(args.pool))
     big = make_pool("spheres3d_8192", range(10000, 10000 + args.pool // 2))
     held = make_pool("spheres3d_8192", range(20000, 20008))
