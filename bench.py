@@ -166,6 +166,7 @@ def main():
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2605_13343_gb300", "weights",
                                                       "hmpcg_d128_l4.f32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the training-step and batch measurements")
     ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192", "bandwidth", "train4096"],
                     help="frame8192: the per-frame headline; batch64: 64 ragged systems in one graph; "
                          "precision16384: FP32/BF16/FP8 apply sweep with SVD-H factors")
@@ -355,6 +356,28 @@ def main():
         except Exception as exc:  # reported, not fatal
             bw_rows = [{"error": str(exc)[:200]}]
 
+    # secondary workloads, after the timed region so that the frame numbers are unaffected: the
+    # training step and the 64-system ragged batch (their own --workload runs print full lines)
+    secondary = None
+    if rank == 0 and not args.no_secondary:
+        secondary = {}
+        small = argparse.Namespace(**vars(args))
+        small.steps, small.warmup = 5, 2
+        try:
+            t = bench_train(small, h, torch, np, inputs, bf16_peak, peak_kind, emit=False)
+            secondary["train4096"] = {"ms_per_step": t["value"], "steps": t["steps"], "workload": t["config"]["workload"]}
+        except Exception as exc:  # reported, not fatal
+            secondary["train4096"] = {"error": str(exc)[:200]}
+        try:
+            bt = bench_batch(small, h, torch, np, inputs, w, wsrc, emit=False)
+            secondary["batch64"] = {"solves_per_s": bt["value"], "ms_per_batch": bt["ms_per_step"],
+                                    "learned_converged": bt["learned_converged"],
+                                    "jacobi_fallbacks": bt["jacobi_fallbacks"], "iters_mean": bt["iters_mean"],
+                                    "jacobi": bt["jacobi"], "steps": bt["steps"]}
+        except Exception as exc:
+            secondary["batch64"] = {"error": str(exc)[:200]}
+        torch.cuda.synchronize()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -382,6 +405,7 @@ def main():
         "cuda_graph": graph is not None if graph_error is None else f"direct launches ({graph_error[:80]})",
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "secondary": secondary,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -520,7 +544,7 @@ def bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind, family="dis
     print(json.dumps(line), flush=True)
 
 
-def bench_batch(args, h, torch, np, inputs, w, wsrc):
+def bench_batch(args, h, torch, np, inputs, w, wsrc, emit=True):
     """64 ragged systems (N uniform over {1024 ... 16384}, 2D and 3D alternating, 1:100): learned-H
     inference per grid shape plus one hmpcg_solve_batch, captured as one CUDA graph; Jacobi batch
     beside it.  A step is one whole batch."""
@@ -624,6 +648,8 @@ def bench_batch(args, h, torch, np, inputs, w, wsrc):
             "iters_mean": {"learned": statistics.mean(a.iters for a in inf_l),
                            "jacobi": statistics.mean(j.iters for j in inf_j)},
             "clocks": clocks, "systems": per}
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -722,7 +748,7 @@ def _count_kernel_nodes(torch, fn):
         return None
 
 
-def bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind):
+def bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind, emit=True):
     """Training step of the cosine-Hutchinson objective: 32 systems 16^3 (density ratio
     log-uniform in [1, 100]), 16 Rademacher probes each, BF16 forward, hand-written backward,
     global-norm clip, AdamW (lr 3e-4).  A step is one hmpcg_train_step."""
@@ -759,6 +785,8 @@ def bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind):
                                    "batch 32, 16 Rademacher probes, d128 4 layers 4 heads MLP 512, seeded init",
                        "tokens_per_step": tokens, "l2": "working set (activations ~1 GB) larger than L2"},
             "loss_after": loss, "clocks": clocks}
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
 
 
