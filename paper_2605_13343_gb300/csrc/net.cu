@@ -199,6 +199,8 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
       N->fnbr[l] = (float*)alloc(4 * Td * 6 * h);
     }
     N->gp16 = (float*)alloc(4 * ((Td + To) / 16 + 1) * d);
+    N->spart1 = (double*)alloc(8 * B * 32 * 8);
+    N->spart2 = (double*)alloc(8 * B * 32 * 4);
     N->fused_alloc = true;
   }
   N->err = (int*)alloc(256);
@@ -528,18 +530,17 @@ static int net_forward_fused(Net* N, const SysBatch& sb, void* packed, int dtype
     const int nt = (L * L + 255) / 256, nn = (Td * 2 * sb.ndim + 255) / 256, no = (B * MH * r * r + 255) / 256;
     pdl_launch(edge_prep_kernel, dim3(nt + nn + no, cf.n_layers), dim3(256), 0, sE, sb, E, N->edesc_off, h, nt, nn);
   }
-  // ---- features, encoder, GCN, pooled tile tokens (as in net_forward)
-  pdl_launch(global_stats_kernel, dim3(B), dim3(1024), 0, st, sb, N->gstat);
-  pdl_launch(encoder1_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->gstat, W + o.enc1w, W + o.enc1b, d, N->feat, N->h1, N->h1pre);
+  // ---- global statistics, features, encoder and GCN layers (tensor-core kernels), pooled tile tokens
   {
-    GemmEpi ep = e; ep.bias = W + o.enc2b; ep.out32 = N->xg[0]; ep.ld32 = d;
-    NET_TRY(gemm(N->h1, d, W16 + o.map16(o.enc2w), Td, d, d, ep, st));
-  }
-  for (int g = 0; g < 2; ++g) {
-    pdl_launch(prop_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, N->xg[g], d, N->pm[g]);
-    GemmEpi ep = e; ep.bias = W + o.gcnb[g]; ep.act = 1; ep.resid = N->xg[g]; ep.ldr = d;
-    ep.out32 = N->xg[g + 1]; ep.ld32 = d;
-    NET_TRY(gemm(N->pm[g], d, W16 + o.map16(o.gcnw[g]), Td, d, d, ep, st));
+    FusedEncoder fe;
+    fe.enc1w = W + o.enc1w; fe.enc1b = W + o.enc1b; fe.enc2b = W + o.enc2b;
+    fe.enc2w = W16 + o.map16(o.enc2w);
+    for (int g = 0; g < 2; ++g) { fe.gcnb[g] = W + o.gcnb[g]; fe.gcnw[g] = W16 + o.map16(o.gcnw[g]); }
+    for (int g = 0; g < 3; ++g) fe.xg[g] = N->xg[g];
+    fe.part1 = N->spart1;
+    fe.part2 = N->spart2;
+    fe.err = N->err;
+    NET_TRY(fused_encoder(sb, fe, st));
   }
   const int tj0 = 31 - __builtin_clz((unsigned)(L / r)), tj1 = tj0 + sb.levels - 1;
   chunk_trees(N, N->xg[2], nullptr, Td, d, tj0, tj1, st);

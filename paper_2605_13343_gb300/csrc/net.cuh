@@ -131,6 +131,8 @@ struct Net {
   float* ftable[kEdgeMaxLayersNet] = {};
   float* fnbr[kEdgeMaxLayersNet] = {};
   float* gp16 = nullptr;
+  double* spart1 = nullptr;   // global-statistics partials of the fused encoder [B][32][8], [B][32][4]
+  double* spart2 = nullptr;
   bool fused_alloc = false;
   int use_fused = 1;
   // training probes: Rademacher, or Gaussian with probe_steps damped-Jacobi sweeps (weight omega)
@@ -182,6 +184,18 @@ bool fused_supported(const hmpcg_config& c, const SysBatch& sb);
 int fused_hw_block(int n, int L, int r);
 int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], float* gp16d, float* gp16o, float* g32,
                 int* err, cudaStream_t s);
+
+// Fused encoder (net_fused.cu): global statistics (two passes), features -> enc1 -> enc2, two GCN
+// layers; xg[0..2] receive the encoder output and the two GCN outputs.
+struct FusedEncoder {
+  const float *enc1w, *enc1b, *enc2b, *gcnb[2];
+  const bf16 *enc2w, *gcnw[2];
+  float* xg[3];
+  double* part1;   // [B][32][8]
+  double* part2;   // [B][32][4]
+  int* err;
+};
+int fused_encoder(const SysBatch& sb, const FusedEncoder& fe, cudaStream_t s);
 
 // Fused heads (net_fused.cu): LN_f of both stacks, leaf / node / tile heads, gate, pack.
 struct FusedHeads {

@@ -208,20 +208,31 @@ __global__ void __launch_bounds__(kAT, 1)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int r = 16 * warp + k;
-      const float4 x = xr[k];
-      const float mean = warp_sum((x.x + x.y) + (x.z + x.w)) * (1.f / kD);
-      const float dx = x.x - mean, dy = x.y - mean, dz = x.z - mean, dw = x.w - mean;
-      const float var = warp_sum((dx * dx + dy * dy) + (dz * dz + dw * dw)) * (1.f / kD);
-      const float rstd = rsqrtf(var + 1e-5f);
-      const bool ok_r = row0 + r < S.T;
-      const float y0 = ok_r ? dx * rstd * g4.x + b4.x : 0.f, y1 = ok_r ? dy * rstd * g4.y + b4.y : 0.f;
-      const float y2 = ok_r ? dz * rstd * g4.z + b4.z : 0.f, y3 = ok_r ? dw * rstd * g4.w + b4.w : 0.f;
-      // columns 4 lane .. +3: chunk lane / 16, unit (lane % 16) / 2, bytes 8 (lane % 2)
-      const int c = 4 * lane_id();
-      *reinterpret_cast<uint2*>(sm + kA_Q + (c >> 6) * 16384 + sw128(r, (c & 63) >> 3) + (c & 4) * 2) =
-          make_uint2(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3));
+    for (int k0 = 0; k0 < 16; k0 += 4) {   // four rows at a time: their shuffle chains interleave
+      float mean[4], rstd[4];
+      float4 dv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mean[k] = (xr[k0 + k].x + xr[k0 + k].y) + (xr[k0 + k].z + xr[k0 + k].w);
+      warp_sum4(mean);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        mean[k] *= 1.f / kD;
+        dv[k] = make_float4(xr[k0 + k].x - mean[k], xr[k0 + k].y - mean[k], xr[k0 + k].z - mean[k], xr[k0 + k].w - mean[k]);
+        rstd[k] = (dv[k].x * dv[k].x + dv[k].y * dv[k].y) + (dv[k].z * dv[k].z + dv[k].w * dv[k].w);
+      }
+      warp_sum4(rstd);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 16 * warp + k0 + k;
+        const float rs = rsqrtf(rstd[k] * (1.f / kD) + 1e-5f);
+        const bool ok_r = row0 + r < S.T;
+        const float y0 = ok_r ? dv[k].x * rs * g4.x + b4.x : 0.f, y1 = ok_r ? dv[k].y * rs * g4.y + b4.y : 0.f;
+        const float y2 = ok_r ? dv[k].z * rs * g4.z + b4.z : 0.f, y3 = ok_r ? dv[k].w * rs * g4.w + b4.w : 0.f;
+        // columns 4 lane .. +3: chunk lane / 16, unit (lane % 16) / 2, bytes 8 (lane % 2)
+        const int c = 4 * lane_id();
+        *reinterpret_cast<uint2*>(sm + kA_Q + (c >> 6) * 16384 + sw128(r, (c & 63) >> 3) + (c & 4) * 2) =
+            make_uint2(pack_bf16x2(y0, y1), pack_bf16x2(y2, y3));
+      }
     }
   }
   fence_async_smem();
@@ -426,26 +437,40 @@ __global__ void __launch_bounds__(kAT, 1)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float4 cs = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row0 + 16 * warp < S.T) {   // T is a multiple of 16: this warp's 16 rows are whole or absent
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int r = 16 * warp + k;
-      if (row0 + r >= S.T) break;   // uniform across the warp
-      const size_t gr = (size_t)(row0 + r);
-      const float4 p = *reinterpret_cast<const float4*>(xs + r * kXS + 4 * lane);
-      const float4 x = make_float4(p.x + xr[k].x, p.y + xr[k].y, p.z + xr[k].z, p.w + xr[k].w);
-      reinterpret_cast<float4*>(S.x_mid + gr * kD)[lane] = x;
-      const float mean = warp_sum((x.x + x.y) + (x.z + x.w)) * (1.f / kD);
-      const float dx = x.x - mean, dy = x.y - mean, dz = x.z - mean, dw = x.w - mean;
-      const float var = warp_sum((dx * dx + dy * dy) + (dz * dz + dw * dw)) * (1.f / kD);
-      const float rstd = rsqrtf(var + 1e-5f);
-      const float4 y = make_float4(dx * rstd * g4.x + b4.x, dy * rstd * g4.y + b4.y, dz * rstd * g4.z + b4.z,
-                                   dw * rstd * g4.w + b4.w);
-      reinterpret_cast<float4*>(S.y32 + gr * kD)[lane] = y;
-      *reinterpret_cast<uint2*>(S.u + gr * S.ldu + 4 * lane) = make_uint2(pack_bf16x2(y.x, y.y), pack_bf16x2(y.z, y.w));
-      cs.x += y.x; cs.y += y.y; cs.z += y.z; cs.w += y.w;
-    }
-    if (row0 + 16 * warp < S.T)   // T is a multiple of 16: a group is whole or absent
+      for (int k0 = 0; k0 < 16; k0 += 4) {   // four rows at a time: their shuffle chains interleave
+        float4 xv[4];
+        float mean[4], var[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = 16 * warp + k0 + k;
+          const float4 p = *reinterpret_cast<const float4*>(xs + r * kXS + 4 * lane);
+          xv[k] = make_float4(p.x + xr[k0 + k].x, p.y + xr[k0 + k].y, p.z + xr[k0 + k].z, p.w + xr[k0 + k].w);
+          reinterpret_cast<float4*>(S.x_mid + (size_t)(row0 + r) * kD)[lane] = xv[k];
+          mean[k] = (xv[k].x + xv[k].y) + (xv[k].z + xv[k].w);
+        }
+        warp_sum4(mean);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          mean[k] *= 1.f / kD;
+          xv[k] = make_float4(xv[k].x - mean[k], xv[k].y - mean[k], xv[k].z - mean[k], xv[k].w - mean[k]);
+          var[k] = (xv[k].x * xv[k].x + xv[k].y * xv[k].y) + (xv[k].z * xv[k].z + xv[k].w * xv[k].w);
+        }
+        warp_sum4(var);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const size_t gr = (size_t)(row0 + 16 * warp + k0 + k);
+          const float rs = rsqrtf(var[k] * (1.f / kD) + 1e-5f);
+          const float4 y = make_float4(xv[k].x * rs * g4.x + b4.x, xv[k].y * rs * g4.y + b4.y,
+                                       xv[k].z * rs * g4.z + b4.z, xv[k].w * rs * g4.w + b4.w);
+          reinterpret_cast<float4*>(S.y32 + gr * kD)[lane] = y;
+          *reinterpret_cast<uint2*>(S.u + gr * S.ldu + 4 * lane) = make_uint2(pack_bf16x2(y.x, y.y), pack_bf16x2(y.z, y.w));
+          cs.x += y.x; cs.y += y.y; cs.z += y.z; cs.w += y.w;
+        }
+      }
       reinterpret_cast<float4*>(S.gp16 + (size_t)(row0 / 16 + warp) * kD)[lane] = cs;
+    }
   }
   // ---- teardown: every MMA of this CTA has completed before TMEM is freed
   if (tid == 0) mma_commit(smem_u32(&bar_end));
@@ -880,7 +905,7 @@ __device__ void heads_body(uint8_t* sm, const HeadArgs& a, uint32_t tmem, uint64
         if (lane == 0) {
           gl[r] = gs + a.gate_b[0];
           const int t = row0 + r;
-          sinv[r] = ok_r ? (float)(1.0 / sqrt(a.diag[t / a.n][t % a.n])) : 0.f;
+          sinv[r] = ok_r ? rsqrtf((float)a.diag[t / a.n][t % a.n]) : 0.f;
         }
       }
     }
@@ -958,8 +983,8 @@ __device__ void heads_body(uint8_t* sm, const HeadArgs& a, uint32_t tmem, uint64
       }
       if (tid < 128) {
         const int t = t0 + tid;
-        const double di = a.diag[b][t % a.n];
-        head_store<T>(base + offG + i0 + tid, (float)((double)softplus_f(gl[tid]) / di));
+        const float di = (float)a.diag[b][t % a.n];
+        head_store<T>(base + offG + i0 + tid, softplus_f(gl[tid]) / di);
       }
     }
     if (!mbar_wait(smem_u32(&bars[2]), 0, kWaitLong)) ok = false;
@@ -1059,6 +1084,360 @@ __global__ void __launch_bounds__(kAT, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// ----------------------------------------------------------------------------- encoder (Sec. 4.1)
+// The 12 global statistics in two passes over all SMs (pass 1: per-CTA sums and extrema of
+// log rho and log diag and the boundary count; pass 2, with pass 1's means and heavy threshold:
+// squared deviations and the heavy count), folded in a fixed order by the encoder kernel.  Then
+// per 128 nodes: features -> enc1 (FP32, GELU) -> enc2 (tcgen05), and per GCN layer
+// (D^-1 A) h -> W (tcgen05) -> + b, GELU, + h.
+constexpr int kStatCTAs = 32;
+HM_INLINE unsigned morton_compact(unsigned v, unsigned mask) {
+  unsigned out = 0, bit = 0;
+  while (mask) {
+    const unsigned low = mask & (0u - mask);
+    if (v & low) out |= 1u << bit;
+    ++bit;
+    mask &= mask - 1u;
+  }
+  return out;
+}
+
+// fixed-order CTA reduction of up to 8 values per thread: kind 0 sum (FP32 in a warp, FP64 across
+// warps), 1 max, 2 min; thread 0 writes `out`
+HM_INLINE void cta_reduce8(const float (&v)[8], const int (&kind)[8], int nv, double* out) {
+  __shared__ float wv[8][8];
+  float r[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    r[q] = v[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const float u = __shfl_xor_sync(0xffffffffu, r[q], o);
+      r[q] = kind[q] == 0 ? r[q] + u : kind[q] == 1 ? fmaxf(r[q], u) : fminf(r[q], u);
+    }
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) wv[w][q] = r[q];
+  __syncthreads();
+  if ((int)threadIdx.x < nv) {   // one thread per value, in parallel
+    const int q = threadIdx.x, nw = blockDim.x >> 5;
+    double acc = kind[q] == 0 ? 0.0 : (double)wv[0][q];
+    for (int k = (kind[q] == 0 ? 0 : 1); k < nw; ++k)
+      acc = kind[q] == 0 ? acc + (double)wv[k][q] : kind[q] == 1 ? fmax(acc, (double)wv[k][q]) : fmin(acc, (double)wv[k][q]);
+    out[q] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) stats1_kernel(const __grid_constant__ SysBatch sb, double* __restrict__ part1) {
+  pdl_entry();
+  const int b = blockIdx.y, c = blockIdx.x, per = sb.n / kStatCTAs;
+  const double* rho = sb.rho[b];
+  const double* dg = sb.diag[b];
+  float v[8] = {0.f, 0.f, -3e38f, 3e38f, -3e38f, 3e38f, 0.f, 0.f};
+  for (int i = c * per + threadIdx.x; i < (c + 1) * per; i += blockDim.x) {
+    const float lr = logf((float)rho[i]), ld = logf((float)dg[i]);
+    v[0] += lr; v[1] += ld;
+    v[2] = fmaxf(v[2], lr); v[3] = fminf(v[3], lr); v[4] = fmaxf(v[4], ld); v[5] = fminf(v[5], ld);
+    bool bnd = false;
+    for (int a = 0; a < sb.ndim; ++a) {
+      const unsigned m = sb.mo.mask[a];
+      if ((i & m) == m || (i & m) == 0u) bnd = true;
+    }
+    v[6] += bnd ? 1.f : 0.f;
+  }
+  const int kind[8] = {0, 0, 1, 2, 1, 2, 0, 0};
+  cta_reduce8(v, kind, 7, part1 + ((size_t)b * kStatCTAs + c) * 8);
+}
+
+// Fold of the per-CTA partials of system b: warp w (< nq) reduces quantity w over the 32 partials
+// (lane = partial, fixed shuffle tree; kinds as in cta_reduce8) into out[w].  Needs nq warps.
+HM_INLINE void fold_partials(const double* part, int stride, int b, const int* kind, int nq, double* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < nq) {
+    double v = part[((size_t)b * kStatCTAs + lane) * stride + w];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = kind[w] == 0 ? v + u : kind[w] == 1 ? fmax(v, u) : fmin(v, u);
+    }
+    if (lane == 0) out[w] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) stats2_kernel(const __grid_constant__ SysBatch sb, const double* __restrict__ part1,
+                                                     double* __restrict__ part2) {
+  pdl_entry();
+  const int b = blockIdx.y, c = blockIdx.x, per = sb.n / kStatCTAs;
+  __shared__ double f1[8];
+  __shared__ float sh[3];
+  const int kind1[7] = {0, 0, 1, 2, 1, 2, 0};
+  fold_partials(part1, 8, b, kind1, 4, f1);   // sums of log rho, log diag; max, min of log rho
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double inv_n = 1.0 / sb.n;   // n is a power of two: exact
+    sh[0] = (float)(f1[0] * inv_n);
+    sh[1] = (float)(f1[1] * inv_n);
+    sh[2] = (float)(0.5 * (f1[2] + f1[3]));
+  }
+  __syncthreads();
+  const float mr = sh[0], md = sh[1], thr = sh[2];
+  const double* rho = sb.rho[b];
+  const double* dg = sb.diag[b];
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int i = c * per + threadIdx.x; i < (c + 1) * per; i += blockDim.x) {
+    const float lr = logf((float)rho[i]), ld = logf((float)dg[i]);
+    v[0] = fmaf(lr - mr, lr - mr, v[0]);
+    v[1] = fmaf(ld - md, ld - md, v[1]);
+    v[2] += lr > thr ? 1.f : 0.f;
+  }
+  const int kind[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  cta_reduce8(v, kind, 3, part2 + ((size_t)b * kStatCTAs + c) * 4);
+}
+
+// shared-memory map of the encoder / GCN kernels
+constexpr uint32_t kE_A = 0;            // A tile [128][128] BF16
+constexpr uint32_t kE_W = 32768;        // W [128][128] BF16 (TMA)
+constexpr uint32_t kE_ST = 65536;       // staged rows [128][132] FP32
+constexpr uint32_t kE_W1 = kE_ST + 128 * 132 * 4;   // enc1 weights [128][20], b1 [128], b2 [128] FP32
+constexpr uint32_t kE_G = kE_W1 + (128 * 20 + 256) * 4;   // global statistics [12] FP32
+constexpr uint32_t kE_NB = kE_G + 64;   // GCN: neighbour list per row: 6 x (index, coefficient)
+constexpr uint32_t kE_SMEM = kE_NB + 128 * 6 * 8 + 1024;
+
+struct EncArgs {
+  SysBatch sb;
+  const float* x;          // GCN input rows [T][d]
+  float* out;              // output rows [T][d]
+  const float* bias;       // enc2 / GCN bias
+  const float *w1, *b1;    // enc1 [d][20], [d]
+  const double* part1;
+  const double* part2;
+  int T;
+  int* err;
+};
+
+template <int MODE>   // 0: features -> enc1 -> enc2; 1: GCN layer
+__global__ void __launch_bounds__(256, 1) encoder_mma_kernel(const __grid_constant__ CUtensorMap mw, const __grid_constant__ EncArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t bar_w, bar_m;
+  __shared__ uint32_t tmem_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & 127, half = tid >> 7;
+  const int row0 = blockIdx.x * kTok;
+  const SysBatch& sb = a.sb;
+  float* st = reinterpret_cast<float*>(sm + kE_ST);
+  bool ok = true;
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar_w), 1);
+    mbar_init(smem_u32(&bar_m), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    mbar_expect_tx(smem_u32(&bar_w), 2 * 16384);
+    for (int kc = 0; kc < 2; ++kc) tma_load_2d(smem_u32(sm + kE_W + kc * 16384), &mw, kc * 64, 0, smem_u32(&bar_w));
+  }
+  float* w1s = reinterpret_cast<float*>(sm + kE_W1);
+  if (MODE == 0) {
+    for (int q = tid; q < 128 * 20 + 128; q += blockDim.x) w1s[q] = q < 128 * 20 ? a.w1[q] : a.b1[q - 128 * 20];
+  }
+  for (int q = tid; q < 128; q += blockDim.x) w1s[128 * 20 + 128 + q] = a.bias[q];
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tmem_s)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_s;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  pdl_entry();
+  const float* bias = w1s + 128 * 20 + 128;
+  if (MODE == 0) {
+    // ---- global statistics of this CTA's system (a CTA of 128 nodes never straddles systems)
+    float* gs = reinterpret_cast<float*>(sm + kE_G);
+    const int b = row0 / sb.n;
+    {
+      __shared__ double fv[10];
+      const int kind1[7] = {0, 0, 1, 2, 1, 2, 0};
+      const int kind2[3] = {0, 0, 0};
+      fold_partials(a.part1, 8, b, kind1, 7, fv);
+      if (warp == 7) {   // warp 7 folds the three sums of pass 2 (the shuffle tree needs whole warps)
+        for (int w2 = 0; w2 < 3; ++w2) {
+          double v = a.part2[((size_t)b * kStatCTAs + lane) * 4 + w2];
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) fv[7 + w2] = v;
+        }
+      }
+      (void)kind2;
+      __syncthreads();
+      if (tid < 12) {   // n is a power of two: 1 / n and log2 n are exact
+        const double inv_n = 1.0 / sb.n;
+        const int q = tid;
+        float g;
+        switch (q) {
+          case 0: g = (float)(31 - __clz(sb.n)) * (1.f / 16.f); break;
+          case 1: g = sb.ndim == 3 ? 1.f : 0.f; break;
+          case 2: g = (float)fv[2]; break;
+          case 3: g = (float)fv[3]; break;
+          case 4: g = (float)(fv[0] * inv_n); break;
+          case 5: g = sqrtf((float)(fv[7] * inv_n)); break;
+          case 6: g = (float)(fv[9] * inv_n); break;
+          case 7: g = (float)(fv[1] * inv_n); break;
+          case 8: g = sqrtf((float)(fv[8] * inv_n)); break;
+          case 9: g = (float)fv[4]; break;
+          case 10: g = (float)fv[5]; break;
+          default: g = (float)(fv[6] * inv_n); break;
+        }
+        gs[q] = g;
+      }
+      __syncthreads();
+    }
+    // ---- node features and enc1 (this thread: outputs 64 half .. +63), GELU -> A tile
+    {
+      const int t = row0 + row;
+      const bool valid = t < a.T;
+      float f[kFeat];
+#pragma unroll
+      for (int q = 0; q < kFeat; ++q) f[q] = 0.f;
+      if (valid) {
+        const int i = t % sb.n;
+        const double* rho = sb.rho[b];
+        const double ri = rho[i];
+        const float di = (float)sb.diag[b][i];
+        float off = 0.f, nb = 0.f, iface = 0.f;
+        for (int ax = 0; ax < sb.ndim; ++ax) {
+          const int jp = sb.mo.plus(i, ax);
+          if (jp >= 0) { off += (float)sb.w[b][ax][i]; if (rho[jp] != ri) iface = 1.f; } else nb += 1.f;
+          const int jm = sb.mo.minus(i, ax);
+          if (jm >= 0) { off += (float)sb.w[b][ax][jm]; if (rho[jm] != ri) iface = 1.f; } else nb += 1.f;
+        }
+        f[0] = logf((float)ri) - gs[4];
+        for (int ax = 0; ax < 3; ++ax)
+          f[1 + ax] = ax < sb.ndim ? ((float)morton_compact(i, sb.mo.mask[ax]) + 0.5f) / (float)sb.dims[ax] - 0.5f : 0.f;
+        f[4] = nb / (float)(2 * sb.ndim);
+        f[5] = logf(di) - gs[7];
+        f[6] = off / di;
+        f[7] = iface;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) f[8 + q] = gs[q];
+      }
+#pragma unroll 1
+      for (int u = 0; u < 8; ++u) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int j = 64 * half + 8 * u + e;
+          float acc = w1s[128 * 20 + j];
+#pragma unroll
+          for (int q = 0; q < kFeat; ++q) acc = fmaf(w1s[j * kFeat + q], f[q], acc);
+          v[e] = valid ? gelu_as(acc) : 0.f;
+        }
+        st_unit_bf16(sm + kE_A + half * 16384 + sw128(row, u), v);
+      }
+    }
+  } else {
+    // ---- (D^-1 A) h of row t: h_i - sum_j (w_ij / d_i) h_j; neighbour lists first (a thread per
+    // row), then warp w gathers rows 16 w .. 16 w + 15 four at a time (lane: columns 4 lane ..)
+    int* nbj = reinterpret_cast<int*>(sm + kE_NB);
+    float* nbc = reinterpret_cast<float*>(sm + kE_NB + 128 * 6 * 4);
+    if (half == 0) {
+      const int t = row0 + row;
+      int nj = 0;
+      if (t < a.T) {
+        const int b = t / sb.n, i = t % sb.n;
+        const size_t base = (size_t)b * sb.n;
+        const float di = (float)sb.diag[b][i];
+        for (int ax = 0; ax < sb.ndim; ++ax) {
+          const int jp = sb.mo.plus(i, ax);
+          if (jp >= 0) { nbj[row * 6 + nj] = (int)(base + jp); nbc[row * 6 + nj] = (float)sb.w[b][ax][i] / di; ++nj; }
+          const int jm = sb.mo.minus(i, ax);
+          if (jm >= 0) { nbj[row * 6 + nj] = (int)(base + jm); nbc[row * 6 + nj] = (float)sb.w[b][ax][jm] / di; ++nj; }
+        }
+      }
+      for (int q = nj; q < 6; ++q) { nbj[row * 6 + q] = -1; nbc[row * 6 + q] = 0.f; }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k0 = 0; k0 < 16; k0 += 4) {
+      float4 xv[4][7];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 16 * warp + k0 + k;
+        const int t = row0 + r;
+        xv[k][0] = t < a.T ? reinterpret_cast<const float4*>(a.x + (size_t)t * kD)[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const int j = nbj[r * 6 + q];
+          xv[k][1 + q] = j >= 0 ? reinterpret_cast<const float4*>(a.x + (size_t)j * kD)[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 16 * warp + k0 + k;
+        float4 v = xv[k][0];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const float c = nbc[r * 6 + q];
+          v.x = fmaf(-c, xv[k][1 + q].x, v.x); v.y = fmaf(-c, xv[k][1 + q].y, v.y);
+          v.z = fmaf(-c, xv[k][1 + q].z, v.z); v.w = fmaf(-c, xv[k][1 + q].w, v.w);
+        }
+        const int cc = 4 * lane;
+        *reinterpret_cast<uint2*>(sm + kE_A + (cc >> 6) * 16384 + sw128(r, (cc & 63) >> 3) + (cc & 4) * 2) =
+            make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+      }
+    }
+  }
+  fence_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    if (!mbar_wait(smem_u32(&bar_w), 0, kWaitLong)) ok = false;
+    tc_fence_after();
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      const uint64_t ad = sw128_desc(smem_u32(sm + kE_A + kc * 16384));
+      const uint64_t bd = sw128_desc(smem_u32(sm + kE_W + kc * 16384));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc_bf16(128, 128), (kc | k) ? 1u : 0u);
+    }
+    mma_commit(smem_u32(&bar_m));
+  }
+  if (!mbar_wait(smem_u32(&bar_m), 0, kWaitLong)) ok = false;
+  __syncwarp();
+  tc_fence_after();
+  {
+    float v[32];
+#pragma unroll 1
+    for (int e = 0; e < 2; ++e) {
+      const int c32 = 2 * half + e;
+      tmem_ld32(tl + c32 * 32, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<float4*>(st + row * 132 + c32 * 32 + 4 * q) =
+            make_float4(v[4 * q] + bias[c32 * 32 + 4 * q], v[4 * q + 1] + bias[c32 * 32 + 4 * q + 1],
+                        v[4 * q + 2] + bias[c32 * 32 + 4 * q + 2], v[4 * q + 3] + bias[c32 * 32 + 4 * q + 3]);
+    }
+  }
+  __syncthreads();
+  // ---- rows out (warp w: rows 16 w ..): enc2 -> h; GCN -> GELU(.) + h
+#pragma unroll 4
+  for (int k = 0; k < 16; ++k) {
+    const int r = 16 * warp + k;
+    const int t = row0 + r;
+    if (t >= a.T) break;
+    float4 v = *reinterpret_cast<const float4*>(st + r * 132 + 4 * lane);
+    if (MODE == 1) {
+      const float4 x = reinterpret_cast<const float4*>(a.x + (size_t)t * kD)[lane];
+      v = make_float4(gelu_as(v.x) + x.x, gelu_as(v.y) + x.y, gelu_as(v.z) + x.z, gelu_as(v.w) + x.w);
+    }
+    reinterpret_cast<float4*>(a.out + (size_t)t * kD)[lane] = v;
+  }
+  if (!ok && a.err) atomicExch(a.err, (int)HMPCG_E_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
 template <class... KArgs, class... Args>
 int launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -1142,6 +1521,42 @@ int fused_layer(const SysBatch& sb, FusedStack st[2], const FusedWeights w[2], f
   fa.err = err;
   rc = launch_pdl(fused_ffn_kernel, dim3(nblk_d + nblk_o), dim3(kFT), kF_SMEM, s, mu[0], mu[1], m1[0], m1[1], m2[0], m2[1], fa);
   if (rc) return rc;
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+int fused_encoder(const SysBatch& sb, const FusedEncoder& fe, cudaStream_t s) {
+  static std::atomic<unsigned long long> attr{0};
+  if (!once_per_device(attr, [] {
+        return cudaFuncSetAttribute(encoder_mma_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kE_SMEM) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(encoder_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kE_SMEM) ==
+                   cudaSuccess;
+      }))
+    return HMPCG_E_CUDA;
+  if (sb.n % kStatCTAs) return HMPCG_E_SHAPE;
+  CUtensorMap me, mg0, mg1;
+  if (!tma_map_bf16(&me, fe.enc2w, kD, kD, kD, 128) || !tma_map_bf16(&mg0, fe.gcnw[0], kD, kD, kD, 128) ||
+      !tma_map_bf16(&mg1, fe.gcnw[1], kD, kD, kD, 128))
+    return HMPCG_E_INVALID;
+  int rc = launch_pdl(stats1_kernel, dim3(kStatCTAs, sb.B), dim3(256), 0, s, sb, fe.part1);
+  if (rc) return rc;
+  rc = launch_pdl(stats2_kernel, dim3(kStatCTAs, sb.B), dim3(256), 0, s, sb, (const double*)fe.part1, fe.part2);
+  if (rc) return rc;
+  EncArgs a;
+  a.sb = sb;
+  a.T = sb.B * sb.n;
+  a.part1 = fe.part1;
+  a.part2 = fe.part2;
+  a.err = fe.err;
+  const int nblk = a.T / kTok;
+  a.x = nullptr; a.out = fe.xg[0]; a.bias = fe.enc2b; a.w1 = fe.enc1w; a.b1 = fe.enc1b;
+  rc = launch_pdl(encoder_mma_kernel<0>, dim3(nblk), dim3(256), kE_SMEM, s, me, a);
+  if (rc) return rc;
+  for (int g = 0; g < 2; ++g) {
+    a.x = fe.xg[g]; a.out = fe.xg[g + 1]; a.bias = fe.gcnb[g];
+    rc = launch_pdl(encoder_mma_kernel<1>, dim3(nblk), dim3(256), kE_SMEM, s, g ? mg1 : mg0, a);
+    if (rc) return rc;
+  }
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 

@@ -103,6 +103,14 @@ HM_INLINE float erf_as(float x) {
 }
 HM_INLINE float gelu_as(float x) { return 0.5f * x * (1.f + erf_as(x * 0.70710678118654752f)); }
 HM_INLINE int lane_id() { return (int)(threadIdx.x & 31); }
+// Four independent warp sums (fixed butterfly each), interleaved so that their shuffles overlap.
+HM_INLINE void warp_sum4(float (&v)[4]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+}
 
 // Shared-memory byte offset of 16-byte unit `unit` (8 BF16 values) of row `row` in a K-major
 // tile of 64-element (128-byte) rows under the 128-byte swizzle: the unit index is XORed with
