@@ -310,6 +310,46 @@ def main():
     for k in ks:
         it_j.append(h.solve(ctx, systems[k], jac, bs[k], x, rtol=1e-6).iters)
 
+    # the same frames with the factors emitted and applied in FP8-E4M3 (one scale per block),
+    # captured as a graph like the BF16 frame
+    K = n // 64
+    packed8 = torch.empty(P, dtype=torch.float8_e4m3fn, device="cuda")
+    sc8 = torch.empty(4 * K + K - 1, dtype=torch.float32, device="cuda")
+    fac8 = h.factors(h.PRE_LEARNED, packed8, n, 64, 16, sc8)
+
+    def body8():
+        h.assemble(slot_rho, slot_sys)
+        h.infer_factors(ctx, [slot_sys], packed8, scales=sc8)
+        h.solve(ctx, slot_sys, fac8, slot_b, x, rtol=1e-6, info=False)
+
+    slot_rho.copy_(rho_dev[0]); slot_b.copy_(bs[0]); body8()
+    torch.cuda.synchronize()
+    graph8 = None
+    try:
+        g8 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g8, capture_error_mode="relaxed"):
+            body8()
+        graph8 = g8
+    except Exception:
+        graph8 = None
+    torch.cuda.synchronize()
+
+    def frame_fp8(k):
+        slot_rho.copy_(rho_dev[k], non_blocking=True)
+        slot_b.copy_(bs[k], non_blocking=True)
+        if graph8 is not None:
+            graph8.replay()
+        else:
+            body8()
+
+    t_fp8 = timed(frame_fp8, ks)
+    it_8, res_8 = [], []
+    for k in ks:
+        h.infer_factors(ctx, [systems[k]], packed8, scales=sc8)
+        inf8 = h.solve(ctx, systems[k], fac8, bs[k], x, rtol=1e-6, allow=(h.OK, h.NOT_CONVERGED, h.E_BREAKDOWN))
+        it_8.append(inf8.iters)
+        res_8.append(inf8.rel_res_true)
+
     # end to end through the public API with host buffers: H2D of rho and b into the slot,
     # the captured frame, D2H of x
     rho_h = [torch.from_numpy(fr["rho"]).pin_memory() for fr in frames]
@@ -397,7 +437,9 @@ def main():
                       "infer_ms": statistics.mean(ms_inf), "solve_ms": sol_ms,
                       "iters_learned": iters_mean, "true_rel_res_max": max(res_l),
                       "jacobi_ms_per_frame": statistics.mean(t_jac), "iters_jacobi": statistics.mean(it_j),
-                      "jacobi_speedup": statistics.mean(t_jac) / ms},
+                      "jacobi_speedup": statistics.mean(t_jac) / ms,
+                      "fp8_factors": {"ms_per_frame": statistics.mean(t_fp8), "iters": statistics.mean(it_8),
+                                      "true_rel_res_max": max(res_8), "cuda_graph": graph8 is not None}},
         "roofline": roof,
         "roofline_bandwidth_kernels": bw_rows,
         "e2e": {"value": e2e_ms, "unit": "ms/frame", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n},

@@ -204,7 +204,10 @@ int hmpcg_autotune_batch(void* ctx, const hmpcg_system* systems,
  * diagonal and off-diagonal attention stacks with highways -> decoder heads ->
  * packed tensor.  `packed` holds nsys consecutive packed vectors of width
  * hmpcg_packed_width(n, leaf, rank, HMPCG_PRE_LEARNED), element type `dtype`;
- * all systems have the same grid. */
+ * all systems have the same grid.  dtype HMPCG_FP8E4M3 needs `scales` (device,
+ * nsys consecutive arrays of 4K + M_H floats in the hmpcg_factors order): each
+ * block is stored as RN_even(value / scale) with scale = max|block| / 448 (1 for
+ * an all-zero block); F32 and BF16 need scales == NULL (else HMPCG_E_INVALID). */
 int hmpcg_infer_factors(void* ctx, const hmpcg_system* systems, int32_t nsys,
                         void* packed, int32_t dtype, float* scales, void* stream);
 

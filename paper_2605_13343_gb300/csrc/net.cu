@@ -180,6 +180,7 @@ int net_create(Ctx* c, const float* weights, int64_t count, cudaStream_t st) {
   N->nodeo = (float*)alloc(4 * Td * 2 * r);
   N->gate_logit = (float*)alloc(4 * Td);
   N->offo = (float*)alloc(4 * To * 2 * r);
+  N->q32 = (float*)alloc(4 * B * (K * L * L + MH * r * r + 2 * n * r + n));
   N->rhw = (float*)alloc(4 * Td * d);
   N->chw = (float*)alloc(4 * Td * d);
   {
@@ -599,11 +600,19 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
   Net* N = c->net;
   SysBatch sb;
   NET_TRY(make_batch(N->cfg, systems, nsys, sb));
-  if (dtype != HMPCG_F32 && dtype != HMPCG_BF16) return HMPCG_E_INVALID;
-  (void)scales;
+  if (dtype != HMPCG_F32 && dtype != HMPCG_BF16 && dtype != HMPCG_FP8E4M3) return HMPCG_E_INVALID;
+  if ((dtype == HMPCG_FP8E4M3) != (scales != nullptr)) return HMPCG_E_INVALID;
+  const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
+  if (dtype == HMPCG_FP8E4M3) {
+    // FP32 factors into the staging buffer, then one FP32 scale per block (Supp. B layout)
+    NET_TRY(net_infer(c, systems, nsys, N->q32, HMPCG_F32, nullptr, st));
+    const int nblk = 4 * sb.K + sb.MH;
+    pdl_launch(quant_fp8_kernel, dim3(sb.B * nblk), dim3(256), 0, st, sb, (const float*)N->q32,
+               (__nv_fp8_e4m3*)packed, scales, P);
+    return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+  }
   if (N->use_fused && N->fused_alloc && fused_supported(N->cfg, sb)) return net_forward_fused(N, sb, packed, dtype, st);
   NET_TRY(net_forward(N, sb, st));
-  const int64_t P = (int64_t)sb.K * sb.L * sb.L + (int64_t)sb.MH * sb.r * sb.r + 2LL * sb.n * sb.r + sb.n;
   const int Td = sb.B * sb.n;
   const int Tt = sb.B * sb.MH;
   if (dtype == HMPCG_F32) {

@@ -114,6 +114,7 @@ struct Net {
   float* nodeo;      // [Td][2r]
   float* gate_logit; // [Td]
   float* offo;       // [To][2r]
+  float* q32;        // FP32 packed factors of the batch before FP8 quantisation [B][P]
   float* rhw; float* chw; float* gmean;   // highway buffers (FP32)
   float* tree_a; float* tree_b;           // chunk-sum trees ([levels][T >> j][d]) of the pooled arrays
   double* gpart;     // per-chunk column sums for the global token

@@ -789,5 +789,39 @@ __global__ void pack_tiles_kernel(const SysBatch sb, const float* __restrict__ o
   }
 }
 
+// FP8-E4M3 factors with one FP32 scale per block (scale = max |block| / 448, the largest finite
+// E4M3 value; stored = RN_even(value / scale), saturating).  Blocks in packed order, which is
+// also the scale order: K leaf blocks (L x L), M_H cores (r x r), K bridges U~ and K bridges
+// V~ (the L x r rows of one leaf each), K gate slices (L values).  One CTA per block.
+__global__ void quant_fp8_kernel(const SysBatch sb, const float* __restrict__ src, __nv_fp8_e4m3* __restrict__ dst,
+                                 float* __restrict__ scales, int64_t P) {
+  pdl_entry();
+  const int K = sb.K, MH = sb.MH, L = sb.L, r = sb.r;
+  const int nblk = 4 * K + MH;
+  const int b = blockIdx.x / nblk, j = blockIdx.x % nblk;
+  const int64_t offC = (int64_t)K * L * L, offU = offC + (int64_t)MH * r * r;
+  const int64_t offV = offU + (int64_t)sb.n * r, offG = offV + (int64_t)sb.n * r;
+  int64_t off;
+  int len;
+  if (j < K) { off = (int64_t)j * L * L; len = L * L; }
+  else if (j < K + MH) { off = offC + (int64_t)(j - K) * r * r; len = r * r; }
+  else if (j < 2 * K + MH) { off = offU + (int64_t)(j - K - MH) * L * r; len = L * r; }
+  else if (j < 3 * K + MH) { off = offV + (int64_t)(j - 2 * K - MH) * L * r; len = L * r; }
+  else { off = offG + (int64_t)(j - 3 * K - MH) * L; len = L; }
+  const float* s = src + (size_t)b * P + off;
+  __nv_fp8_e4m3* o = dst + (size_t)b * P + off;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) m = fmaxf(m, fabsf(s[i]));
+  for (int q = 16; q; q >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, q));
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+  const float sc = m > 0.f ? m / 448.f : 1.f;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) o[i] = __nv_fp8_e4m3(s[i] / sc);
+  if (threadIdx.x == 0) scales[(size_t)b * nblk + j] = sc;
+}
+
 }  // namespace
 }  // namespace hm

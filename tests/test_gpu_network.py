@@ -181,3 +181,81 @@ def test_fused_inference_matches_layered(family, seeds):
             if key != "core":
                 assert _elem(fu[key], la[key]) <= ELEM_TOL, (key, _elem(fu[key], la[key]))
     ctx.close()
+
+
+def test_fp8_inference_quantises_each_block():
+    """FP8 factors from hmpcg_infer_factors: every block is the FP32 inference rounded to E4M3
+    with scale max|block| / 448; the dequantised factors stay within the element bound of the
+    FP64 oracle forward, and learned PCG on them matches the FP64 oracle PCG on the same
+    (dequantised) preconditioner."""
+    w, lay = _blob(3, scale_heads=10.0)
+    fr = inputs.frame("spheres3d_8192", 6)
+    n, L, r = 8192, 64, 16
+    K = n // L
+    ctx = _ctx(n, w)
+    s = _gpu_system(fr)
+    P = h.packed_width(n, L, r, h.PRE_LEARNED)
+    p32 = torch.empty(P, dtype=torch.float32, device="cuda")
+    h.infer_factors(ctx, [s], p32)
+    p8 = torch.empty(P, dtype=torch.float8_e4m3fn, device="cuda")
+    sc = torch.empty(4 * K + K - 1, dtype=torch.float32, device="cuda")
+    h.infer_factors(ctx, [s], p8, scales=sc)
+    torch.cuda.synchronize()
+    f32 = p32.cpu().double().numpy()
+    q = p8.cpu().float().double().numpy()
+    scn = sc.cpu().double().numpy()
+    # block boundaries in packed order (the scale order)
+    offs, lens = [], []
+    o = 0
+    for cnt, ln in ((K, L * L), (K - 1, r * r), (K, L * r), (K, L * r), (K, L)):
+        for _ in range(cnt):
+            offs.append(o); lens.append(ln); o += ln
+    assert o == P
+    deq = np.empty(P)
+    for j, (o, ln) in enumerate(zip(offs, lens)):
+        blk = f32[o:o + ln]
+        amax = np.abs(blk).max()
+        assert abs(scn[j] - amax / 448.0) <= 1e-6 * amax / 448.0, j
+        deq[o:o + ln] = q[o:o + ln] * scn[j]
+        # E4M3: 3 mantissa bits, so rounding moves a normal value by <= 2^-4 of itself and a
+        # subnormal one (|v| < 2^-6 scale) by <= 2^-10 scale; two FP32 runs of the network may
+        # differ in the last bits, which can move a value to the neighbouring code: allow 2^-3
+        assert np.all(np.abs(deq[o:o + ln] - blk) <= 2.0 ** -3 * np.abs(blk) + 2.0 ** -9 * scn[j]), j
+    got = hmatrix.unpack(deq, n, L, r, "learned")
+    ref = grid.assemble(fr["rho"], fr["dims"])
+    p = network.unflatten(w, lay)
+    with torch.no_grad():
+        f = network.to_numpy_factors(network.forward(p, ref, CFG))
+    for key in ("leafblk", "U", "V"):
+        assert _elem(got[key], f[key]) <= ELEM_TOL, (key, _elem(got[key], f[key]))
+    ce = float((np.abs(got["core"] - f["core"]) / np.maximum(f["core_scale"], 1e-300)).max())
+    assert ce <= ELEM_TOL, ce
+    assert _elem(got["g"], f["g"]) <= ELEM_TOL
+    a = grid.sparse_matrix(ref)
+    out = pcg.pcg(lambda v: a @ v, lambda v: hmatrix.apply(got, v), fr["b"], rtol=1e-6)
+    assert out["status"] == pcg.OK
+    b = torch.from_numpy(fr["b"]).cuda()
+    x = torch.empty_like(b)
+    info = h.solve(ctx, s, h.factors(h.PRE_LEARNED, p8, n, L, r, sc), b, x, rtol=1e-6)
+    assert info.status == h.OK
+    rel = np.linalg.norm(fr["b"] - a @ x.cpu().numpy()) / np.linalg.norm(fr["b"])
+    assert rel <= 1e-6
+    assert abs(info.iters - out["iters"]) <= max(2, 0.05 * out["iters"]), (info.iters, out["iters"])
+    ctx.close()
+
+
+def test_fp8_inference_argument_checks():
+    w, _ = _blob(3)
+    ctx = _ctx(4096, w)
+    fr = inputs.frame("spheres3d_4096_lu", 0)
+    s = _gpu_system(fr)
+    P = h.packed_width(4096, 64, 16, h.PRE_LEARNED)
+    p8 = torch.empty(P, dtype=torch.float8_e4m3fn, device="cuda")
+    p32 = torch.empty(P, dtype=torch.float32, device="cuda")
+    sc = torch.empty(4 * 64 + 63, dtype=torch.float32, device="cuda")
+    arr = h.systems_array([s])
+    lib = h.lib()
+    assert lib.hmpcg_infer_factors(ctx.h, arr, 1, h.C.c_void_p(p8.data_ptr()), h.FP8E4M3, None, None) == h.E_INVALID
+    assert lib.hmpcg_infer_factors(ctx.h, arr, 1, h.C.c_void_p(p32.data_ptr()), h.F32,
+                                   h.C.c_void_p(sc.data_ptr()), None) == h.E_INVALID
+    ctx.close()
