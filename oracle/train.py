@@ -17,9 +17,23 @@ import torch
 from . import grid, loss, network
 
 
+def sai_scale(sys):
+    """||A|| of the SAI loss: the Gershgorin bound 2 max_i A_ii, which bounds lambda_max(A) from
+    above for these diagonally dominant operators (the off-diagonal magnitudes of a row sum to at
+    most A_ii) and meets it up to a few per cent where the coefficient is locally constant."""
+    return 2.0 * float(np.max(sys["diag"]))
+
+
 def batch_loss(blob, layout, cfg, systems, step_seed, n_probes, geoms=None, grad=True, probes="rademacher",
-               omega=0.6, smooth_steps=2):
-    """Mean cosine loss of a batch and (optionally) its gradient w.r.t. the weights."""
+               omega=0.6, smooth_steps=2, loss_kind="cosine", highway=True):
+    """Mean loss of a batch and (optionally) its gradient w.r.t. the weights.
+
+    loss_kind "cosine" is Eq. 7; "sai" is the SAI ablation of Sec. 6.1 on the same operand,
+    || Y / ||A|| - Z ||_F^2 / ||Z||_F^2 with Y = M A Z.  The paper writes A M Z; for symmetric A
+    and M both orders have the same probe expectation ||M A / ||A|| - I||_F^2 (the two matrices
+    are transposes of each other), and the division by ||Z||_F^2 makes the value a mean per
+    probe entry.  ``highway=False`` runs the network with its highway channels held at zero
+    (the ablation of Sec. 7.3)."""
     flat = torch.as_tensor(np.asarray(blob, dtype=np.float64)).clone().requires_grad_(grad)
     p = {}
     off = 0
@@ -38,10 +52,14 @@ def batch_loss(blob, layout, cfg, systems, step_seed, n_probes, geoms=None, grad
             z = loss.rademacher_probes(step_seed, b, sys["n"], n_probes)
         w = torch.as_tensor(a @ z)
         geom = geoms[b] if geoms is not None else None
-        f = network.forward(p, sys, cfg, geom=geom)
+        f = network.forward(p, sys, cfg, geom=geom, highway=highway)
         y = network.apply_torch(f, w)
         zt = torch.as_tensor(z)
-        lb = 1.0 - (zt * y).sum() / (zt.norm() * y.norm())
+        if loss_kind == "sai":
+            c = sai_scale(sys)
+            lb = ((y / c - zt) ** 2).sum() / (zt * zt).sum()
+        else:
+            lb = 1.0 - (zt * y).sum() / (zt.norm() * y.norm())
         losses.append(float(lb))
         total = total + lb
     total = total / len(systems)
