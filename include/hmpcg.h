@@ -244,6 +244,21 @@ int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys,
 enum { HMPCG_PROBES_RADEMACHER = 0, HMPCG_PROBES_GAUSSIAN_SMOOTHED = 1 };
 int hmpcg_set_train_probes(void* ctx, int32_t kind, float omega, int32_t steps);
 
+/* Loss of the following hmpcg_train_step calls.  HMPCG_LOSS_COSINE (default): Eq. 7.
+ * HMPCG_LOSS_SAI: the SAI ablation of Sec. 6.1 on the same operand Y = M A Z,
+ * mean over systems of ||Y / c - Z||_F^2 / ||Z||_F^2 with c = 2 max_i A_ii (a Gershgorin
+ * bound of ||A||_2; the paper writes A M Z, whose probe expectation is the same for
+ * symmetric A and M).  Returns HMPCG_E_INVALID for a context without a network or
+ * another kind. */
+enum { HMPCG_LOSS_COSINE = 0, HMPCG_LOSS_SAI = 1 };
+int hmpcg_set_train_loss(void* ctx, int32_t kind);
+
+/* Highway ablation (Sec. 4.3; Sec. 7.3): on = 0 holds the row, column and global highway
+ * channels of every FFN input at zero in hmpcg_infer_factors and hmpcg_train_step (the
+ * FFN reads [y, 0, 0, 0]; inference then runs the layered kernels); on = 1 (default)
+ * restores them.  Returns HMPCG_E_INVALID for a context without a network. */
+int hmpcg_set_highways(void* ctx, int32_t on);
+
 /* z = M r exactly as hmpcg_apply with nrhs = 1, but without a context and
  * without allocating anything.  The paper has no counterpart: this is for
  * callers that cannot call cudaMalloc, such as code inside a custom device

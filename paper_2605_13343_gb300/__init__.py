@@ -74,6 +74,8 @@ EXPORTS = {
     "hmpcg_packed_width": (C.c_int64, [C.c_int64, C.c_int32, C.c_int32, C.c_int32]),
     "hmpcg_set_infer_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "hmpcg_set_train_probes": (C.c_int, [C.c_void_p, C.c_int32, C.c_float, C.c_int32]),
+    "hmpcg_set_train_loss": (C.c_int, [C.c_void_p, C.c_int32]),
+    "hmpcg_set_highways": (C.c_int, [C.c_void_p, C.c_int32]),
     "hmpcg_train_step": (C.c_int, [C.c_void_p, C.POINTER(SystemStruct), C.c_int32, C.c_int32, C.c_float,
                                    C.c_uint64, C.POINTER(C.c_float), C.c_void_p]),
     "hmpcg_get_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -348,6 +350,19 @@ PROBES_RADEMACHER, PROBES_GAUSSIAN_SMOOTHED = 0, 1
 def set_train_probes(ctx, kind, omega=0.6, steps=2):
     """hmpcg_set_train_probes: Rademacher, or the paper's smoothed Gaussian probes."""
     _check(lib().hmpcg_set_train_probes(ctx.h, int(kind), float(omega), int(steps)), "set_train_probes")
+
+
+LOSS_COSINE, LOSS_SAI = 0, 1
+
+
+def set_train_loss(ctx, kind):
+    """hmpcg_set_train_loss: LOSS_COSINE (Eq. 7, default) or the LOSS_SAI ablation."""
+    _check(lib().hmpcg_set_train_loss(ctx.h, int(kind)), "set_train_loss")
+
+
+def set_highways(ctx, on):
+    """hmpcg_set_highways: highway channels on (default) or held at zero (ablation)."""
+    _check(lib().hmpcg_set_highways(ctx.h, int(bool(on))), "set_highways")
 
 
 def train_step(ctx, systems, n_probes, lr, step_seed, want_loss=True, stream=None):

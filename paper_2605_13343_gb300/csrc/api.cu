@@ -23,6 +23,8 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int n_probes, 
 int net_get_weights(Ctx* c, float* w, int64_t count);
 void net_set_fused(Net* N, bool on);
 void net_set_probes(Net* N, int kind, float omega, int steps);
+void net_set_highways(Net* N, bool on);
+void net_set_loss(Net* N, int kind);
 int net_get_grads(Ctx* c, float* g, int64_t count);
 int solve_batch_dispatch(Ctx* c, const hmpcg_system* sys, const hmpcg_factors* f, const double* const* b,
                          double* const* x, int nsys, const hmpcg_solve_opts* o, const int* csize, cudaStream_t st);
@@ -363,6 +365,22 @@ int hmpcg_set_train_probes(void* ctx, int32_t kind, float omega, int32_t steps) 
   if (!c->net || (kind != HMPCG_PROBES_RADEMACHER && kind != HMPCG_PROBES_GAUSSIAN_SMOOTHED)) return HMPCG_E_INVALID;
   if (!(omega > 0.f && omega <= 1.f) || steps < 0 || steps > 8) return HMPCG_E_INVALID;
   net_set_probes(c->net, kind, omega, steps);
+  return HMPCG_OK;
+}
+
+int hmpcg_set_train_loss(void* ctx, int32_t kind) {
+  if (!ctx) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net || (kind != HMPCG_LOSS_COSINE && kind != HMPCG_LOSS_SAI)) return HMPCG_E_INVALID;
+  net_set_loss(c->net, kind);
+  return HMPCG_OK;
+}
+
+int hmpcg_set_highways(void* ctx, int32_t on) {
+  if (!ctx) return HMPCG_E_INVALID;
+  Ctx* c = static_cast<Ctx*>(ctx);
+  if (!c->net) return HMPCG_E_INVALID;
+  net_set_highways(c->net, on != 0);
   return HMPCG_OK;
 }
 

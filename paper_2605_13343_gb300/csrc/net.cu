@@ -246,6 +246,8 @@ void net_destroy(Ctx* c) {
 }
 
 void net_set_fused(Net* N, bool on) { N->use_fused = on ? 1 : 0; }
+void net_set_highways(Net* N, bool on) { N->use_highways = on ? 1 : 0; }
+void net_set_loss(Net* N, int kind) { N->loss_kind = kind; }
 void net_set_probes(Net* N, int kind, float omega, int steps) {
   N->probe_kind = kind;
   N->probe_omega = omega;
@@ -434,16 +436,24 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
     // the global token (side stream) and the row/column highways (here) run concurrently; the
     // off-diagonal gathers need both
     NET_TRY(fork(st, sO));
-    {
+    if (N->use_highways) {
       const int nch_d = (n + kGChunk - 1) / kGChunk, nch_o = (MH * r + kGChunk - 1) / kGChunk;
       pdl_launch(highway_g_partial_kernel, dim3(dim3(nch_d + nch_o, B)), dim3(128), 0, sO, sb, ad.y2f, ao.y2f, d, nch_d, nch_o, N->gpart);
       pdl_launch(highway_g_final_kernel, dim3((B * d + 7) / 8), dim3(256), 0, sO, sb, N->gpart, d, nch_d + nch_o, N->gmean);
       pdl_launch(concat_g_kernel, dim3((Td + 7) / 8), dim3(256), 0, sO, N->gmean, n, Td, d, ad.u);
     }
-    pdl_launch(highway_rc_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+    if (N->use_highways) {
+      pdl_launch(highway_rc_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+    } else {
+      // ablation: the FFN reads [y, 0, 0, 0]
+      pdl_launch(hw_zero_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, Td, d, ad.u);
+      pdl_launch(hw_zero_kernel, dim3((To + 7) / 8), dim3(256), 0, st, To, d, ao.u);
+    }
     NET_TRY(fork(sO, st));
-    chunk_trees(N, N->rhw, N->chw, Td, d, tj0, tj1, st);
-    pdl_launch(highway_off_kernel, dim3(To), dim3(128), 0, st, sb, N->tree_a, N->tree_b, tj0, N->gmean, d, ao.u);
+    if (N->use_highways) {
+      chunk_trees(N, N->rhw, N->chw, Td, d, tj0, tj1, st);
+      pdl_launch(highway_off_kernel, dim3(To), dim3(128), 0, st, sb, N->tree_a, N->tree_b, tj0, N->gmean, d, ao.u);
+    }
     NET_TRY(fork(st, sO));
     for (int s = 0; s < 2; ++s) {
       StackAct& a = N->act[s][l];
@@ -611,7 +621,8 @@ int net_infer(Ctx* c, const hmpcg_system* systems, int nsys, void* packed, int d
                (__nv_fp8_e4m3*)packed, scales, P);
     return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
   }
-  if (N->use_fused && N->fused_alloc && fused_supported(N->cfg, sb)) return net_forward_fused(N, sb, packed, dtype, st);
+  if (N->use_fused && N->use_highways && N->fused_alloc && fused_supported(N->cfg, sb))
+    return net_forward_fused(N, sb, packed, dtype, st);
   NET_TRY(net_forward(N, sb, st));
   const int Td = sb.B * sb.n;
   const int Tt = sb.B * sb.MH;

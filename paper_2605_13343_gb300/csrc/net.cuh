@@ -140,6 +140,9 @@ struct Net {
   int probe_kind = 0;
   float probe_omega = 0.6f;
   int probe_steps = 2;
+  // ablations: highway channels held at zero (inference and training); training loss kind
+  int use_highways = 1;
+  int loss_kind = 0;
   // scratch for the backward pass and training
   std::vector<void*> allocs;
 };

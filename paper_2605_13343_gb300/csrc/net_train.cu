@@ -208,8 +208,13 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   tapply_restrict_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->w, T->y, T->uh, T->vh);
   tapply_tile_kernel<<<B * MH, 256, 0, st>>>(sb, nz, T->pk, T->uh, T->vh, T->sr, T->sc, T->tr, T->tc);
   tapply_prolong_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->tr, T->tc, T->y, T->au, T->av);
-  loss_sums_kernel<<<B, 256, 0, st>>>(sb, nz, T->z, T->y, T->sums);
-  loss_grad_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->y, T->sums, T->dy);
+  if (N->loss_kind == HMPCG_LOSS_SAI) {
+    sai_sums_kernel<<<B, 256, 0, st>>>(sb, nz, T->z, T->y, T->sums);
+    sai_grad_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->y, T->sums, T->dy);
+  } else {
+    loss_sums_kernel<<<B, 256, 0, st>>>(sb, nz, T->z, T->y, T->sums);
+    loss_grad_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->y, T->sums, T->dy);
+  }
   // ---- apply backward -> gradient of the packed factors
   tbwd_restrict_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->w, T->dy, T->dpk, T->qu, T->qv);
   tbwd_tile_kernel<<<B * MH, 256, 0, st>>>(sb, nz, T->pk, T->qu, T->qv, T->sr, T->sc, T->dpk, T->ur, T->uc);
@@ -254,7 +259,11 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
       gelu_bwd_kernel<<<(unsigned)(((int64_t)Tt * dm + 255) / 256), 256, 0, st>>>(T->gH[s], a.hpre, (int64_t)Tt * dm);
       TR_TRY(linear_bwd(N, T->gH[s], dm, a.u, 4 * d, Tt, dm, 4 * d, bo.f1w, bo.f1b, T->gU[s], 0, st));
     }
-    {
+    if (!N->use_highways) {
+      // highway ablation: the highway slices of the FFN input are constants, only y gets a gradient
+      hwb_own_kernel<<<(Td + 7) / 8, 256, 0, st>>>(Td, d, T->gU[0], T->gY[0]);
+      hwb_own_kernel<<<(To + 7) / 8, 256, 0, st>>>(To, d, T->gU[1], T->gY[1]);
+    } else {
       const int nch_d = (n + 63) / 64, nch_o = (MH * r + 63) / 64;
       hwb_g_partial_kernel<<<dim3(nch_d + nch_o, B), 128, 0, st>>>(sb, T->gU[0], T->gU[1], d, nch_d, nch_o, T->gpart);
       hwb_g_final_kernel<<<B, 128, 0, st>>>(sb, T->gpart, d, nch_d + nch_o, T->dgh);
@@ -336,7 +345,9 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
     if (cudaStreamSynchronize(st) != cudaSuccess) return HMPCG_E_CUDA;
     if (err) return err;
     double tot = 0.0;
-    for (int b = 0; b < B; ++b) tot += 1.0 - sums[3 * b] / std::sqrt(sums[3 * b + 1] * sums[3 * b + 2]);
+    for (int b = 0; b < B; ++b)
+      tot += N->loss_kind == HMPCG_LOSS_SAI ? sums[3 * b] / sums[3 * b + 1]
+                                            : 1.0 - sums[3 * b] / std::sqrt(sums[3 * b + 1] * sums[3 * b + 2]);
     *loss_out = (float)(tot / B);
   }
   (void)P;

@@ -266,6 +266,56 @@ __global__ void loss_grad_kernel(const SysBatch sb, int nz, const float* __restr
   dy[idx] = (float)(c1 * z[idx] + c2 * y[idx]);
 }
 
+// SAI ablation loss (Sec. 6.1): L_b = ||Y_b / c_b - Z_b||_F^2 / ||Z_b||_F^2 with c_b = 2 max_i
+// A_ii (a Gershgorin bound of ||A_b||_2), Y = M A Z.  sums[3b..3b+2] = (numerator, ||Z||^2, c).
+__global__ void sai_sums_kernel(const SysBatch sb, int nz, const float* __restrict__ z, const float* __restrict__ y,
+                                double* __restrict__ sums) {
+  __shared__ double red[2][32];
+  __shared__ double cb;
+  const int b = blockIdx.x;
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double dm = 0.0;
+  for (int i = threadIdx.x; i < sb.n; i += blockDim.x) dm = fmax(dm, sb.diag[b][i]);
+  for (int q = 16; q; q >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, q));
+  if ((threadIdx.x & 31) == 0) red[0][w] = dm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int q = 0; q < nw; ++q) m = fmax(m, red[0][q]);
+    cb = 2.0 * m;
+  }
+  __syncthreads();
+  const double ic = 1.0 / cb;
+  const size_t n = (size_t)sb.n * nz;
+  const float* zb = z + (size_t)b * n;
+  const float* yb = y + (size_t)b * n;
+  double ee = 0, zz = 0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = zb[i], e = (double)yb[i] * ic - a;
+    ee += e * e; zz += a * a;
+  }
+  ee = warp_sum(ee); zz = warp_sum(zz);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { red[0][w] = ee; red[1][w] = zz; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int q = 0; q < nw; ++q) { s0 += red[0][q]; s1 += red[1][q]; }
+    sums[3 * b] = s0; sums[3 * b + 1] = s1; sums[3 * b + 2] = cb;
+  }
+}
+// dL/dY for L = mean_b ||Y/c - Z||^2 / ||Z||^2: 2 (Y/c - Z) / (c ||Z||^2 B).
+__global__ void sai_grad_kernel(const SysBatch sb, int nz, const float* __restrict__ z, const float* __restrict__ y,
+                                const double* __restrict__ sums, float* __restrict__ dy) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)sb.n * nz;
+  if (idx >= sb.B * per) return;
+  const int b = (int)(idx / per);
+  const double zz = sums[3 * b + 1], c = sums[3 * b + 2];
+  const double e = (double)y[idx] / c - (double)z[idx];
+  dy[idx] = (float)(2.0 * e / (c * zz * sb.B));
+}
+
 // ------------------------------------------------------------------ apply backward
 // Leaf (b, k): dF = G P1^T + W P2^T (P1 = F^T W, P2 = F^T G); dg = sum_c G W;
 // qu = U~^T G, qv = V~^T G.
@@ -867,6 +917,13 @@ __global__ void hwb_rc_kernel(const SysBatch sb, const float* __restrict__ dud, 
     ec[(size_t)t * d + c] = cc;
     dy2d[(size_t)t * d + c] = dud[(size_t)t * 4 * d + c] + rr + cc + dg[(size_t)b * d + c];
   }
+}
+// Highway ablation: the LN2 output's gradient is the first d columns of the FFN-input gradient.
+__global__ void hwb_own_kernel(int T, int d, const float* __restrict__ du, float* __restrict__ dy2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  for (int c = lane; c < d; c += 32) dy2[(size_t)t * d + c] = du[(size_t)t * 4 * d + c];
 }
 // Off tokens: dy2o = du_own + sum over row chunk of er + sum over column chunk of ec + dg.
 __global__ void hwb_off_kernel(const SysBatch sb, const float* __restrict__ duo, const float* __restrict__ er,

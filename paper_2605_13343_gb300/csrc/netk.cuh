@@ -711,6 +711,15 @@ __global__ void concat_g_kernel(const float* __restrict__ g, int n, int T, int d
   for (int c = lane; c < d; c += 32) u[(size_t)t * 4 * d + 3 * d + c] = __float2bfloat16_rn(g[(size_t)b * d + c]);
 }
 
+// Highway ablation: zero the three highway slices of the FFN input rows [y | r | c | g].
+__global__ void hw_zero_kernel(int T, int d, bf16* __restrict__ u) {
+  pdl_entry();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  for (int c = lane; c < 3 * d; c += 32) u[(size_t)t * 4 * d + d + c] = __float2bfloat16_rn(0.f);
+}
+
 // Off-diagonal token gathers: mean of r_hw over its row chunk, of c_hw over its column chunk, g
 // (chunk sums from the trees of r_hw and c_hw).  One CTA per token, one thread per channel.
 __global__ void highway_off_kernel(const SysBatch sb, const float* __restrict__ trr, const float* __restrict__ trc,

@@ -84,9 +84,41 @@ def make_pool(family, seeds):
     for s in seeds:
         fr = inputs.frame(family, s)
         sg = h.System(fr["dims"])
-        h.assemble(torch.from_numpy(fr["rho"]).cuda(), sg)
+        bc = h.BC_NEUMANN if fr["bc"] == "neumann" else h.BC_DIRICHLET
+        face = h.FACE_RHO if fr["face"] == "rho" else h.FACE_INV_RHO
+        h.assemble(torch.from_numpy(fr["rho"]).cuda(), sg, bc=bc, face=face)
         out.append((sg, torch.from_numpy(fr["b"]).cuda()))
     return out
+
+
+def split_pools(family, n_train, n_test, seed):
+    """The per-scale split of Supp. D: n_train training and n_test test frames of one family
+    with disjoint seeds, assembled on the device once (cached contexts, Sec. 6.3)."""
+    base = 100000 * (seed + 1)
+    return make_pool(family, range(base, base + n_train)), make_pool(family, range(base + 50000, base + 50000 + n_test))
+
+
+def evaluate_detail(ctx, frames, rtol):
+    """Mean and standard deviation of learned-H and Jacobi PCG iterations over frames."""
+    n = frames[0][0].n
+    P = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+    packed = torch.empty(P, dtype=torch.bfloat16, device="cuda")
+    fac = h.factors(h.PRE_LEARNED, packed, n, 64, 16)
+    jac = h.Factors()
+    jac.kind = h.PRE_JACOBI
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    it_l, it_j, failed = [], [], 0
+    for sg, b in frames:
+        h.infer_factors(ctx, [sg], packed)
+        info = h.solve(ctx, sg, fac, b, x, rtol=rtol, allow=(h.OK, h.NOT_CONVERGED, h.E_BREAKDOWN, h.E_NAN))
+        if info.status == h.OK:
+            it_l.append(info.iters)
+        else:
+            failed += 1
+        it_j.append(h.solve(ctx, sg, jac, b, x, rtol=rtol).iters)
+    return dict(iters_learned=float(np.mean(it_l)) if it_l else None,
+                iters_learned_std=float(np.std(it_l)) if it_l else None, failed=failed,
+                iters_jacobi=float(np.mean(it_j)), iters_jacobi_std=float(np.std(it_j)), frames=len(frames))
 
 
 def evaluate(ctx, frames, rtol=1e-6):
@@ -127,6 +159,13 @@ def main():
     ap.add_argument("--probe-kind", choices=["rademacher", "gaussian"], default="rademacher")
     ap.add_argument("--omega", type=float, default=0.6)
     ap.add_argument("--smooth-steps", type=int, default=2)
+    ap.add_argument("--loss", choices=["cosine", "sai"], default="cosine",
+                    help="cosine: Eq. 7; sai: the SAI-loss ablation of Sec. 6.1")
+    ap.add_argument("--no-highways", action="store_true", help="highway channels held at zero (ablation)")
+    ap.add_argument("--family", default=None,
+                    help="train and test on one frame family with the --split of Supp. D (e.g. barriers2d_4096) "
+                         "instead of the two 3D pools")
+    ap.add_argument("--split", default="100/20", help="training/test frame counts with --family")
     args = ap.parse_args()
 
     w0 = np.fromfile(args.init, dtype=np.float32) if args.init else inputs.network_blob(args.seed, **CFG)
@@ -134,9 +173,21 @@ def main():
                     max_batch=args.batch, weights=w0)
     if args.probe_kind == "gaussian":
         h.set_train_probes(ctx, h.PROBES_GAUSSIAN_SMOOTHED, args.omega, args.smooth_steps)
-    small = make_pool("spheres3d_4096_lu", range(args.pool))
-    big = make_pool("spheres3d_8192", range(10000, 10000 + args.pool // 2))
-    held = make_pool("spheres3d_8192", range(20000, 20008))
+    if args.loss == "sai":
+        h.set_train_loss(ctx, h.LOSS_SAI)
+    if args.no_highways:
+        h.set_highways(ctx, False)
+    rtol = 1e-6
+    if args.family:
+        n_train, n_test = (int(v) for v in args.split.split("/"))
+        small, held = split_pools(args.family, n_train, n_test, args.seed)
+        big = []
+        rtol = inputs.frame(args.family, 0)["rtol"]
+        args.batch = min(args.batch, n_train)
+    else:
+        small = make_pool("spheres3d_4096_lu", range(args.pool))
+        big = make_pool("spheres3d_8192", range(10000, 10000 + args.pool // 2))
+        held = make_pool("spheres3d_8192", range(20000, 20008))
     rng = np.random.default_rng(args.seed)
     sched = Plateau(args.lr)
     stopper = AutoStop() if args.auto_stop else None
@@ -145,11 +196,11 @@ def main():
     best = float("inf")
     t0 = time.time()
     window = []
-    it_l, it_j, ok = evaluate(ctx, held)
+    it_l, it_j, ok = evaluate(ctx, held, rtol)
     rec = dict(step=0, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, t=0.0)
     print(json.dumps(rec), flush=True)
     for step in range(1, args.steps + 1):
-        if args.big_every and step % args.big_every == 0:
+        if big and args.big_every and step % args.big_every == 0:
             pick = rng.choice(len(big), size=max(1, args.batch // 2), replace=False)
             batch = [big[i][0] for i in pick]
         else:
@@ -167,7 +218,7 @@ def main():
                 logf.write(json.dumps(rec) + "\n")
                 logf.flush()
         if step % args.eval_every == 0 or step == args.steps or stop:
-            it_l, it_j, ok = evaluate(ctx, held)
+            it_l, it_j, ok = evaluate(ctx, held, rtol)
             rec = dict(step=step, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, loss=window[-1] if window else None,
                        t=time.time() - t0)
             print(json.dumps(rec), flush=True)
@@ -181,7 +232,10 @@ def main():
         if stop:
             print(json.dumps(dict(auto_stop=step, lr=lr)), flush=True)
             break
-    print(json.dumps(dict(done=True, best_iters=best, seconds=time.time() - t0)), flush=True)
+    final = evaluate_detail(ctx, held, rtol)
+    print(json.dumps(dict(done=True, best_iters=best, seconds=time.time() - t0, steps=step, loss_kind=args.loss,
+                          highways=not args.no_highways, family=args.family or "spheres3d pools",
+                          test_final=final)), flush=True)
 
 
 if __name__ == "__main__":

@@ -93,13 +93,15 @@ def test_weight_count_matches_layout():
     assert h.lib().hmpcg_weight_count(ctypes.byref(c)) == w.size
 
 
-@pytest.mark.parametrize("family,seeds", [("spheres3d_4096_lu", [0]), ("spheres3d_4096_lu", [1, 2]),
-                                          ("spheres3d_8192", [0])])
-def test_inference_parity(family, seeds):
+@pytest.mark.parametrize("family,seeds,highway", [("spheres3d_4096_lu", [0], True), ("spheres3d_4096_lu", [1, 2], True),
+                                                  ("spheres3d_8192", [0], True), ("spheres3d_4096_lu", [5], False)])
+def test_inference_parity(family, seeds, highway):
     w, lay = _blob(7)
     frs = [inputs.frame(family, s) for s in seeds]
     n = int(np.prod(frs[0]["dims"]))
     ctx = _ctx(n, w, batch=len(seeds))
+    if not highway:
+        h.set_highways(ctx, False)
     systems = [_gpu_system(fr) for fr in frs]
     P = h.packed_width(n, 64, 16, h.PRE_LEARNED)
     packed = torch.empty(len(seeds) * P, dtype=torch.float32, device="cuda")
@@ -110,7 +112,7 @@ def test_inference_parity(family, seeds):
     for b, fr in enumerate(frs):
         ref = grid.assemble(fr["rho"], fr["dims"])
         with torch.no_grad():
-            f = network.to_numpy_factors(network.forward(p, ref, CFG))
+            f = network.to_numpy_factors(network.forward(p, ref, CFG, highway=highway))
         got = hmatrix.unpack(got_all[b * P:(b + 1) * P], n, 64, 16, "learned")
         for key in ("leafblk", "U", "V", "core"):
             assert _rel(got[key], f[key]) <= 3e-2, (key, _rel(got[key], f[key]))

@@ -65,25 +65,36 @@ def _gpu_systems(dims, seeds):
 # and the measured worst tensor on the GB300 was 0.023 (whole vector 0.018).  A tensor carrying at
 # least 1% of the gradient norm (or 0.1% if it has >= 4096 entries) must be within 0.05, the whole
 # vector within 0.04: a wrong sign, transposition or dropped term in any such tensor gives an error
-# of order 1.
+# of order 1.  The bounds hold where the per-system loss is not small: near the minimum of Eq. 7
+# dL/dY is a difference of two nearly equal terms and amplifies the BF16 error of Y by about
+# 1 / L (on systems 7 and 8, with losses 0.14 and 0.08, the off-diagonal stack's tensors measured
+# 0.03-0.09 on the GB300), so every case runs on systems whose loss at this initialisation is
+# far from zero; the SAI and highway-off cases reuse systems 3 and 4 of the measured budget.
 REL_TENSOR = 0.05
 REL_ALL = 0.04
 
 
-@pytest.mark.parametrize("cfg,dims,seeds,nz,probes", [
-    (SMALL, (16, 16), [1, 2], 8, "rademacher"),
-    (CFG3, (16, 16, 16), [3, 4], 16, "rademacher"),
-    (CFG3, (16, 16, 16), [5, 6], 16, "gaussian")])
-def test_train_step_gradient_parity(cfg, dims, seeds, nz, probes):
+@pytest.mark.parametrize("cfg,dims,seeds,nz,probes,loss_kind,highway", [
+    (SMALL, (16, 16), [1, 2], 8, "rademacher", "cosine", True),
+    (CFG3, (16, 16, 16), [3, 4], 16, "rademacher", "cosine", True),
+    (CFG3, (16, 16, 16), [5, 6], 16, "gaussian", "cosine", True),
+    (CFG3, (16, 16, 16), [3, 4], 16, "rademacher", "sai", True),
+    (CFG3, (16, 16, 16), [3, 4], 16, "rademacher", "cosine", False)])
+def test_train_step_gradient_parity(cfg, dims, seeds, nz, probes, loss_kind, highway):
     w, lay = _blob(cfg, 5)
     n = int(np.prod(dims))
     ctx = _ctx(cfg, n, len(seeds), w)
     if probes == "gaussian":
         h.set_train_probes(ctx, h.PROBES_GAUSSIAN_SMOOTHED, 0.6, 2)
+    if loss_kind == "sai":
+        h.set_train_loss(ctx, h.LOSS_SAI)
+    if not highway:
+        h.set_highways(ctx, False)
     sg, sr = _systems(dims, seeds)
     loss_gpu = h.train_step(ctx, sg, nz, 0.0, 1234)
     g_gpu = h.get_grads(ctx, w.size).astype(np.float64)
-    l_ref, g_ref, _ = train.batch_loss(w.astype(np.float64), lay, cfg, sr, 1234, nz, probes=probes)
+    l_ref, g_ref, _ = train.batch_loss(w.astype(np.float64), lay, cfg, sr, 1234, nz, probes=probes,
+                                       loss_kind=loss_kind, highway=highway)
     g_ref = adamw.clip_global(g_ref, 1.0)
     assert abs(loss_gpu - l_ref) <= 2e-3 * max(1.0, abs(l_ref)), (loss_gpu, l_ref)
     tot = np.linalg.norm(g_ref)
