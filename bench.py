@@ -167,7 +167,8 @@ def main():
                                                       "hmpcg_d128_l4.f32"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the training-step and batch measurements")
-    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192", "bandwidth", "train4096"],
+    ap.add_argument("--workload", default="frame8192", choices=["frame8192", "batch64", "precision16384", "svdh8192", "bandwidth", "train4096",
+                             "barriers"],
                     help="frame8192: the per-frame headline; batch64: 64 ragged systems in one graph; "
                          "precision16384: FP32/BF16/FP8 apply sweep with SVD-H factors")
     args = ap.parse_args()
@@ -201,6 +202,8 @@ def main():
         return bench_train(args, h, torch, np, inputs, bf16_peak, peak_kind)
     if args.workload == "bandwidth":
         return bench_bandwidth(args, h, torch, np, hbm_peak, peak_kind)
+    if args.workload == "barriers":
+        return bench_barriers(args, h, torch, np, inputs)
     if args.workload == "svdh8192":
         return bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind, family=FAMILY)
     if args.workload == "batch64":
@@ -416,6 +419,11 @@ def main():
                                     "jacobi": bt["jacobi"], "steps": bt["steps"]}
         except Exception as exc:
             secondary["batch64"] = {"error": str(exc)[:200]}
+        try:
+            br = bench_barriers(small, h, torch, np, inputs, emit=False)
+            secondary["barriers_rtol1e-8"] = {"weights": br["config"]["weights"], "sizes": br["sizes"]}
+        except Exception as exc:
+            secondary["barriers_rtol1e-8"] = {"error": str(exc)[:200]}
         torch.cuda.synchronize()
 
     cpu = None
@@ -584,6 +592,104 @@ def bench_precision(args, h, torch, np, inputs, hbm_peak, peak_kind, family="dis
                        "svdh_build_seconds": build_s},
             "sweep": out}
     print(json.dumps(line), flush=True)
+
+
+BARRIER_SIZES = (1024, 2048, 4096, 8192, 16384)
+BARRIER_WEIGHTS = os.path.join(ROOT, "paper_2605_13343_gb300", "weights", "hmpcg_d128_l4_barriers.f32")
+
+
+def bench_barriers(args, h, torch, np, inputs, emit=True, frames_per_size=20):
+    """The paper's benchmark distribution (Supp. D): 2D barrier frames with zero-flux boundaries,
+    face rule 2 rho_i rho_j / (rho_i + rho_j), PCG to rtol 1e-8, at N = 1024 ... 16384; the 20 test
+    frames of each scale from the disjoint-seed split (seed 1) the barrier checkpoint was trained
+    on.  Per size: learned-H frame (assemble + infer + solve, one CUDA graph per size) and Jacobi
+    PCG frame (assemble + solve), CUDA events per frame, L2 flushed between frames.  A step is
+    one frame."""
+    wsrc = os.path.basename(BARRIER_WEIGHTS) if os.path.exists(BARRIER_WEIGHTS) else "seeded init"
+    w = np.fromfile(BARRIER_WEIGHTS, dtype=np.float32) if os.path.exists(BARRIER_WEIGHTS) else \
+        inputs.network_blob(0, **CFG)
+    ctx = h.Context(max_n=max(BARRIER_SIZES), leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
+                    max_batch=1, weights=w)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    _, test_seeds = inputs.split_seeds(1, 100, frames_per_size)
+    jac = h.Factors()
+    jac.kind = h.PRE_JACOBI
+    rows = {}
+    for n in BARRIER_SIZES:
+        fam = f"barriers2d_{n}"
+        frs = [inputs.frame(fam, s) for s in test_seeds]
+        rtol = frs[0]["rtol"]
+        rho_dev = [torch.from_numpy(fr["rho"]).cuda() for fr in frs]
+        b_dev = [torch.from_numpy(fr["b"]).cuda() for fr in frs]
+        slot_rho = torch.empty(n, dtype=torch.float64, device="cuda")
+        slot_b = torch.empty(n, dtype=torch.float64, device="cuda")
+        slot = h.System(frs[0]["dims"])
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        packed = torch.empty(h.packed_width(n, 64, 16, h.PRE_LEARNED), dtype=torch.bfloat16, device="cuda")
+        fac = h.factors(h.PRE_LEARNED, packed, n, 64, 16)
+
+        def asm():
+            h.assemble(slot_rho, slot, bc=h.BC_NEUMANN, face=h.FACE_RHO)
+
+        def body_l():
+            asm()
+            h.infer_factors(ctx, [slot], packed)
+            h.solve(ctx, slot, fac, slot_b, x, rtol=rtol, info=False)
+
+        def body_j():
+            asm()
+            h.solve(ctx, slot, jac, slot_b, x, rtol=rtol, info=False)
+
+        graphs = {}
+        for name, body in (("learned", body_l), ("jacobi", body_j)):
+            slot_rho.copy_(rho_dev[0]); slot_b.copy_(b_dev[0])
+            body(); body()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                body()
+            graphs[name] = g
+        torch.cuda.synchronize()
+        out = {}
+        for name in ("learned", "jacobi"):
+            ts, its, fails = [], [], 0
+            for k in range(len(frs)):
+                slot_rho.copy_(rho_dev[k]); slot_b.copy_(b_dev[k])
+                flush.fill_(k & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                graphs[name].replay()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                # iterations and status of the same frame through the public calls
+                f = fac if name == "learned" else jac
+                if name == "learned":
+                    h.infer_factors(ctx, [slot], packed)
+                inf = h.solve(ctx, slot, f, slot_b, x, rtol=rtol, allow=(h.OK, h.NOT_CONVERGED, h.E_BREAKDOWN, h.E_NAN))
+                if inf.status != h.OK:
+                    fails += 1
+                its.append(inf.iters)
+            out[name] = {"ms_per_frame": statistics.mean(ts), "ms_std": statistics.pstdev(ts),
+                         "iters": statistics.mean(its), "iters_std": statistics.pstdev(its), "not_ok": fails}
+        out["speedup_vs_jacobi"] = out["jacobi"]["ms_per_frame"] / out["learned"]["ms_per_frame"]
+        rows[str(n)] = out
+        del graphs
+        torch.cuda.synchronize()
+    line = {"metric": "ms/frame to rtol 1e-8 on the paper's barrier distribution (learned-H vs Jacobi PCG)",
+            "value": rows["8192"]["learned"]["ms_per_frame"], "unit": "ms/frame", "n_gpus": 1,
+            "steps": frames_per_size, "warmup": 2, "ms_per_step": rows["8192"]["learned"]["ms_per_frame"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "barriers2d_N (Supp. D generator: 1-3 barriers, contrast log-uniform [5,100], "
+                                   "5% jitter, zero-flux), N=1024..16384, 20 test frames each (split seed 1), "
+                                   "leaf 64 rank 16 d128 4 layers, BF16 factors, rtol 1e-8",
+                       "weights": wsrc, "l2": "flushed (256 MiB write) before every frame, outside the timing"},
+            "sizes": rows}
+    ctx.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def bench_batch(args, h, torch, np, inputs, w, wsrc, emit=True):

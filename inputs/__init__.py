@@ -174,6 +174,13 @@ for _n, _d in ((1024, (32, 32)), (2048, (64, 32)), (4096, (64, 64)), (8192, (128
 del _n, _d
 
 
+def split_seeds(seed, n_train, n_test):
+    """Disjoint frame seeds of one training/test split (Supp. D: 100 training and 20 test frames
+    per scale): training seeds start at 100000 (seed + 1), test seeds 50000 above them."""
+    base = 100000 * (seed + 1)
+    return list(range(base, base + n_train)), list(range(base + 50000, base + 50000 + n_test))
+
+
 def frame(family, seed):
     """Return dict(dims, rho, b, leaf, rank, bc, face, rtol) for one seeded frame of
     ``family`` (bc, face and rtol default to Dirichlet, 2/(rho_i+rho_j) and 1e-6)."""

@@ -72,11 +72,16 @@ int64_t net_weight_count(const hmpcg_config* c) {
   return weight_offsets(*c).total;
 }
 
+// Inference takes head dims 16 and 32 and windows of 16 ... 128 tokens (the paper's L = 128,
+// L_s = 32, 8 heads of 16 among them); training the benchmark shapes (head dim 32, leaf <= 64).
 static bool net_shape_ok(const hmpcg_config& c) {
-  return c.d_model % 64 == 0 && c.d_model >= 64 && c.n_heads > 0 && c.d_model / c.n_heads == 32 &&
-         c.d_mlp % 64 == 0 && c.n_layers >= 1 && c.leaf >= 16 && c.leaf <= 64 && (c.leaf & (c.leaf - 1)) == 0 &&
-         c.rank % 16 == 0 && c.leaf % c.rank == 0 && c.rank <= 32 && c.max_batch >= 1 && c.max_batch <= kMaxSys;
+  return c.d_model % 64 == 0 && c.d_model >= 64 && c.n_heads > 0 && c.n_heads <= 8 && c.d_model % c.n_heads == 0 &&
+         (c.d_model / c.n_heads == 32 || c.d_model / c.n_heads == 16) && c.d_mlp % 64 == 0 && c.n_layers >= 1 &&
+         c.leaf >= 16 && c.leaf <= 128 && (c.leaf & (c.leaf - 1)) == 0 && c.rank % 16 == 0 && c.leaf % c.rank == 0 &&
+         c.rank <= 32 && c.max_batch >= 1 && c.max_batch <= kMaxSys;
 }
+bool net_train_shape_ok(const hmpcg_config& c) { return c.d_model / c.n_heads == 32 && c.leaf <= 64; }
+
 
 // One CTA per weight tensor: FP32 master (dense) -> BF16 copy (padded layout).
 __global__ void cast_bf16_kernel(const float* __restrict__ a, bf16* __restrict__ b, const int64_t* __restrict__ segs,
@@ -307,6 +312,23 @@ static void pdl_launch(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStrea
   cudaLaunchKernelEx(&cfg, k, std::forward<Args>(a)...);
 }
 
+// Window attention launch: W tokens per window, head dim hd.
+static int launch_attention(int W, int hd, int T, int d, int h, const bf16* qkv, const float* bias, bf16* o, float* lse,
+                            cudaStream_t s) {
+  const int nwh = (T / W) * h;
+  auto grid = [&](int hpc) { return dim3((nwh + hpc - 1) / hpc); };
+#define HM_ATT(WW, HH)                                                                                           \
+  if (W == WW && hd == HH) {                                                                                    \
+    constexpr int nw = WW / 16 > 4 ? WW / 16 : 4;                                                                \
+    pdl_launch(attention_kernel<WW, HH>, grid(nw / (WW / 16)), dim3(32 * nw), 0, s, qkv, bias, T, d, h, o, lse); \
+    return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;                                          \
+  }
+  HM_ATT(128, 32) HM_ATT(64, 32) HM_ATT(32, 32) HM_ATT(16, 32)
+  HM_ATT(128, 16) HM_ATT(64, 16) HM_ATT(32, 16) HM_ATT(16, 16)
+#undef HM_ATT
+  return HMPCG_E_SHAPE;
+}
+
 // Chunk-sum trees of x0 (and x1) for chunk sizes 2^j0 .. 2^j1 rows.
 static void chunk_trees(Net* N, const float* x0, const float* x1, int T, int d, int j0, int j1, cudaStream_t st) {
   const int nsrc = x1 ? 2 : 1;
@@ -417,10 +439,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
         NET_TRY(gemm(a.y1, d, W16 + o.map16(bo.qkvw), T, 3 * d, d, ep, ss));
       }
       {
-        const int nwh = (T / Wn) * h;   // window-heads; a CTA takes 64 / Wn of them
-        if (Wn == 64) pdl_launch(attention_kernel<64>, dim3(nwh), dim3(128), 0, ss, a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else if (Wn == 32) pdl_launch(attention_kernel<32>, dim3((nwh + 1) / 2), dim3(128), 0, ss, a.qkv, a.bias, T, d, h, a.o, a.lse);
-        else pdl_launch(attention_kernel<16>, dim3((nwh + 3) / 4), dim3(128), 0, ss, a.qkv, a.bias, T, d, h, a.o, a.lse);
+        NET_TRY(launch_attention(Wn, d / h, T, d, h, a.qkv, a.bias, a.o, a.lse, ss));
       }
       {
         GemmEpi ep = e; ep.bias = W + bo.outb; ep.resid = a.x_in; ep.ldr = d; ep.out32 = a.x_mid; ep.ld32 = d;

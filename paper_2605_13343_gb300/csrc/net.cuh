@@ -163,6 +163,7 @@ struct SysBatch {
 };
 
 int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, SysBatch& sb);
+bool net_train_shape_ok(const hmpcg_config& c);
 
 // ---- fused inference layers (net_fused.cu): one stack's buffers and parameters of one layer
 struct FusedStack {

@@ -180,7 +180,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   Net* N = c->net;
   SysBatch sb;
   TR_TRY(make_batch(N->cfg, systems, nsys, sb));
-  if (nz < 1 || nz > 32) return HMPCG_E_SHAPE;
+  if (nz < 1 || nz > 32 || !net_train_shape_ok(N->cfg)) return HMPCG_E_SHAPE;
   N->num_sms = c->num_sms;
   TR_TRY(train_alloc(N, nz));
   Train* T = N->tr;

@@ -499,27 +499,39 @@ HM_INLINE void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p) {
                : "=r"(r0), "=r"(r1) : "r"((uint32_t)__cvta_generic_to_shared(p)));
 }
 
-template <int W>
-__global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__ qkv, const float* __restrict__ bias,
-                                                        int T, int d, int h, bf16* __restrict__ out,
-                                                        float* __restrict__ lse) {
+// Windowed attention of one stack (Sec. 4.2): softmax(Q K^T / sqrt(HD) + bias) V per window of W
+// tokens and head of HD channels, on mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  A
+// warp owns 16 query rows of one window-head; a CTA of NW = max(4, W / 16) warps takes NW / (W / 16)
+// window-heads, their K and V rows staged in shared memory.  lse = log-sum-exp per (token, head)
+// for the backward.
+template <int W, int HD>
+__global__ void __launch_bounds__(32 * (W / 16 > 4 ? W / 16 : 4)) attention_kernel(
+    const bf16* __restrict__ qkv, const float* __restrict__ bias, int T, int d, int h, bf16* __restrict__ out,
+    float* __restrict__ lse) {
   pdl_entry();
-  constexpr int WPH = W / 16;      // warps per window-head
-  constexpr int HPC = 4 / WPH;     // window-heads per CTA
-  constexpr int RS = 40;           // shared row stride in BF16 elements (80 bytes)
+  static_assert(HD == 16 || HD == 32, "head dims of the tensor-core fragments");
+  constexpr int WPH = W / 16;                // warps per window-head
+  constexpr int NW = WPH > 4 ? WPH : 4;      // warps per CTA
+  constexpr int HPC = NW / WPH;              // window-heads per CTA
+  constexpr int RS = HD + 8;                 // shared row stride in BF16 elements (conflict-free ldmatrix)
+  constexpr int PPR = HD / 8;                // 16-byte parts per K (or V) row
+  constexpr int KS = HD / 16;                // k-steps of Q K^T
+  constexpr int NT = HD / 8;                 // n-tiles of P V
   __shared__ __align__(16) bf16 ks[HPC][W][RS];
   __shared__ __align__(16) bf16 vs[HPC][W][RS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwh = (T / W) * h;
   const size_t ld = 3 * (size_t)d;
-  for (int q = threadIdx.x; q < HPC * W * 8; q += blockDim.x) {   // 8 x 16 bytes per key row
-    const int slot = q / (W * 8), rem = q % (W * 8), row = rem >> 3, part = rem & 7;
+  for (int q = threadIdx.x; q < HPC * W * 2 * PPR; q += blockDim.x) {
+    const int slot = q / (W * 2 * PPR), rem = q % (W * 2 * PPR), row = rem / (2 * PPR), part = rem % (2 * PPR);
     const int wh = blockIdx.x * HPC + slot;
     if (wh >= nwh) continue;
     const int win = wh / h, head = wh % h;
     const size_t t = (size_t)win * W + row;
-    const bf16* src = qkv + t * ld + (part < 4 ? d : 2 * d) + head * 32 + (part & 3) * 8;
-    bf16* dst = (part < 4 ? &ks[slot][row][0] : &vs[slot][row][0]) + (part & 3) * 8;
+    const bool isk = part < PPR;
+    const int pp = isk ? part : part - PPR;
+    const bf16* src = qkv + t * ld + (isk ? d : 2 * d) + head * HD + pp * 8;
+    bf16* dst = (isk ? &ks[slot][row][0] : &vs[slot][row][0]) + pp * 8;
     *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(src);
   }
   __syncthreads();
@@ -529,12 +541,13 @@ __global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__
   const int win = wh / h, head = wh % h;
   const int a0 = rb * 16 + (lane >> 2), a1 = a0 + 8;      // this thread's two query rows
   const size_t t0 = (size_t)win * W + a0, t1 = t0 + 8;
+  (void)a1;
   const int cq = 2 * (lane & 3);
-  uint32_t qa[2][4];
+  uint32_t qa[KS][4];
 #pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-    const bf16* q0 = qkv + t0 * ld + head * 32 + 16 * kk + cq;
-    const bf16* q1 = qkv + t1 * ld + head * 32 + 16 * kk + cq;
+  for (int kk = 0; kk < KS; ++kk) {
+    const bf16* q0 = qkv + t0 * ld + head * HD + 16 * kk + cq;
+    const bf16* q1 = qkv + t1 * ld + head * HD + 16 * kk + cq;
     qa[kk][0] = *reinterpret_cast<const uint32_t*>(q0);
     qa[kk][1] = *reinterpret_cast<const uint32_t*>(q1);
     qa[kk][2] = *reinterpret_cast<const uint32_t*>(q0 + 8);
@@ -545,13 +558,13 @@ __global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__
   for (int j = 0; j < W / 8; ++j) {
     s[j][0] = s[j][1] = s[j][2] = s[j][3] = 0.f;
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
+    for (int kk = 0; kk < KS; ++kk) {
       uint32_t b0, b1;
       ldsm_x2(b0, b1, &ks[slot][8 * j + (lane & 7)][16 * kk + ((lane >> 3) & 1) * 8]);
       mma_bf16(s[j], qa[kk], b0, b1);
     }
   }
-  const float scale = 0.17677669529663688f;   // 1 / sqrt(32)
+  const float scale = HD == 32 ? 0.17677669529663688f : 0.25f;   // 1 / sqrt(HD)
   const float* bp0 = bias + (((size_t)win * h + head) * W + a0) * W;
   const float* bp1 = bp0 + 8 * (size_t)W;
   float m0 = -3e38f, m1 = -3e38f;
@@ -582,25 +595,25 @@ __global__ void __launch_bounds__(128) attention_kernel(const bf16* __restrict__
     l0 += __shfl_xor_sync(0xffffffffu, l0, o);
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
   }
-  float oc[4][4];
+  float oc[NT][4];
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) oc[nt][0] = oc[nt][1] = oc[nt][2] = oc[nt][3] = 0.f;
+  for (int nt = 0; nt < NT; ++nt) oc[nt][0] = oc[nt][1] = oc[nt][2] = oc[nt][3] = 0.f;
 #pragma unroll
   for (int kk = 0; kk < W / 16; ++kk) {
     const uint32_t pa[4] = {pack_bf16(s[2 * kk][0], s[2 * kk][1]), pack_bf16(s[2 * kk][2], s[2 * kk][3]),
                             pack_bf16(s[2 * kk + 1][0], s[2 * kk + 1][1]), pack_bf16(s[2 * kk + 1][2], s[2 * kk + 1][3])};
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
+    for (int nt = 0; nt < NT; ++nt) {
       uint32_t b0, b1;
       ldsm_x2_t(b0, b1, &vs[slot][16 * kk + (lane & 15)][8 * nt]);
       mma_bf16(oc[nt], pa, b0, b1);
     }
   }
   const float i0 = 1.f / l0, i1 = 1.f / l1;
-  bf16* o0 = out + t0 * d + head * 32 + cq;
-  bf16* o1 = out + t1 * d + head * 32 + cq;
+  bf16* o0 = out + t0 * d + head * HD + cq;
+  bf16* o1 = out + t1 * d + head * HD + cq;
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
+  for (int nt = 0; nt < NT; ++nt) {
     *reinterpret_cast<__nv_bfloat162*>(o0 + 8 * nt) = __floats2bfloat162_rn(oc[nt][0] * i0, oc[nt][1] * i0);
     *reinterpret_cast<__nv_bfloat162*>(o1 + 8 * nt) = __floats2bfloat162_rn(oc[nt][2] * i1, oc[nt][3] * i1);
   }

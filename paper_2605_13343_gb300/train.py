@@ -94,8 +94,8 @@ def make_pool(family, seeds):
 def split_pools(family, n_train, n_test, seed):
     """The per-scale split of Supp. D: n_train training and n_test test frames of one family
     with disjoint seeds, assembled on the device once (cached contexts, Sec. 6.3)."""
-    base = 100000 * (seed + 1)
-    return make_pool(family, range(base, base + n_train)), make_pool(family, range(base + 50000, base + 50000 + n_test))
+    tr, te = inputs.split_seeds(seed, n_train, n_test)
+    return make_pool(family, tr), make_pool(family, te)
 
 
 def evaluate_detail(ctx, frames, rtol):
@@ -163,13 +163,17 @@ def main():
                     help="cosine: Eq. 7; sai: the SAI-loss ablation of Sec. 6.1")
     ap.add_argument("--no-highways", action="store_true", help="highway channels held at zero (ablation)")
     ap.add_argument("--family", default=None,
-                    help="train and test on one frame family with the --split of Supp. D (e.g. barriers2d_4096) "
-                         "instead of the two 3D pools")
+                    help="train and test on frame families (comma-separated, e.g. barriers2d_1024,barriers2d_4096) "
+                         "with the --split of Supp. D instead of the two 3D pools; steps cycle through the "
+                         "families, a family of N > 4096 takes a batch of --batch * 4096 / N systems")
     ap.add_argument("--split", default="100/20", help="training/test frame counts with --family")
     args = ap.parse_args()
 
     w0 = np.fromfile(args.init, dtype=np.float32) if args.init else inputs.network_blob(args.seed, **CFG)
-    ctx = h.Context(max_n=8192, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
+    max_n = 8192
+    if args.family:
+        max_n = max(max_n, max(int(np.prod(inputs.frame(f, 0)["dims"])) for f in args.family.split(",")))
+    ctx = h.Context(max_n=max_n, leaf=64, rank=16, d_model=128, n_layers=4, n_heads=4, d_mlp=512,
                     max_batch=args.batch, weights=w0)
     if args.probe_kind == "gaussian":
         h.set_train_probes(ctx, h.PROBES_GAUSSIAN_SMOOTHED, args.omega, args.smooth_steps)
@@ -178,12 +182,18 @@ def main():
     if args.no_highways:
         h.set_highways(ctx, False)
     rtol = 1e-6
+    fam_pools = None
     if args.family:
         n_train, n_test = (int(v) for v in args.split.split("/"))
-        small, held = split_pools(args.family, n_train, n_test, args.seed)
-        big = []
-        rtol = inputs.frame(args.family, 0)["rtol"]
-        args.batch = min(args.batch, n_train)
+        fams = args.family.split(",")
+        fam_pools = []
+        for fam in fams:
+            tr, te = split_pools(fam, n_train, n_test, args.seed)
+            nb = max(1, min(n_train, args.batch * 4096 // max(4096, tr[0][0].n)))
+            fam_pools.append((fam, tr, te, nb))
+        rtol = inputs.frame(fams[0], 0)["rtol"]
+        # held-out evaluation during training: the largest family's test frames
+        small, held, big = fam_pools[-1][1], fam_pools[-1][2], []
     else:
         small = make_pool("spheres3d_4096_lu", range(args.pool))
         big = make_pool("spheres3d_8192", range(10000, 10000 + args.pool // 2))
@@ -196,22 +206,36 @@ def main():
     best = float("inf")
     t0 = time.time()
     window = []
+    cycle = []
+    nfam = len(fam_pools) if fam_pools is not None else 1
     it_l, it_j, ok = evaluate(ctx, held, rtol)
     rec = dict(step=0, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, t=0.0)
     print(json.dumps(rec), flush=True)
     for step in range(1, args.steps + 1):
-        if big and args.big_every and step % args.big_every == 0:
+        if fam_pools is not None:
+            _, pool, _, nb = fam_pools[step % len(fam_pools)]
+            pick = rng.choice(len(pool), size=nb, replace=False)
+            batch = [pool[i][0] for i in pick]
+        elif big and args.big_every and step % args.big_every == 0:
             pick = rng.choice(len(big), size=max(1, args.batch // 2), replace=False)
             batch = [big[i][0] for i in pick]
         else:
             pick = rng.choice(len(small), size=args.batch, replace=False)
             batch = [small[i][0] for i in pick]
-        want = step % args.log_every == 0
+        # the logged loss: the mean over the last nfam steps of each log cycle, one batch of every
+        # scale when training cycles through several (one scale's batch alone would make the
+        # plateau rule react to the scale, not to progress)
+        into_cycle = (-step) % args.log_every
+        want = into_cycle < nfam
         loss = h.train_step(ctx, batch, args.probes, lr, int(rng.integers(1 << 62)), want_loss=want)
         stop = False
         if want:
+            cycle.append(loss)
+        if step % args.log_every == 0:
+            loss = float(np.mean(cycle))
+            cycle = []
             window.append(loss)
-            lr = sched.step(float(np.mean(window[-1:])))
+            lr = sched.step(loss)
             stop = stopper is not None and stopper.step(loss, lr, sched.min_lr)
             rec = dict(step=step, loss=loss, lr=lr, t=time.time() - t0)
             if logf:
@@ -232,7 +256,8 @@ def main():
         if stop:
             print(json.dumps(dict(auto_stop=step, lr=lr)), flush=True)
             break
-    final = evaluate_detail(ctx, held, rtol)
+    final = ({fam: evaluate_detail(ctx, te, rtol) for fam, _, te, _ in fam_pools} if fam_pools is not None
+             else evaluate_detail(ctx, held, rtol))
     print(json.dumps(dict(done=True, best_iters=best, seconds=time.time() - t0, steps=step, loss_kind=args.loss,
                           highways=not args.no_highways, family=args.family or "spheres3d pools",
                           test_final=final)), flush=True)

@@ -99,3 +99,52 @@ def test_learned_pcg_rtol_1e8(path, seed):
     info = h.solve(ctx, s, h.factors(h.PRE_LEARNED, packed, 1024, 64, 16), b, x, rtol=fr["rtol"])
     _check(info, out, a, fr, x.cpu().numpy())
     ctx.close()
+
+
+PAPER_CFG = dict(d=128, n_layers=3, n_heads=8, d_mlp=512, leaf=128, rank=32)
+
+
+@pytest.mark.parametrize("n,seed", [(4096, 4), (8192, 5)])
+def test_paper_size_network_on_barrier_frames(n, seed):
+    """The paper's model size (Sec. 7.3: d 128, 3 layers, 8 heads of 16, leaf 128, rank 32;
+    128-token diagonal windows, 32-token tile windows) on its own frames: GPU factors against the
+    FP64 oracle forward element by element, then PCG to rtol 1e-8 on them against the FP64
+    oracle PCG on the same packed factors."""
+    from oracle import network
+    cfg = PAPER_CFG
+    lay = inputs.network_layout(**cfg)
+    w = inputs.network_blob(22, **cfg)
+    off = 0
+    for name, shp in lay:
+        k = int(np.prod(shp))
+        if name in ("leaf2.w", "node.w", "off.w"):
+            w[off:off + k] *= 10.0
+        off += k
+    fr, ref, s = _frame(n, seed)
+    L, r = cfg["leaf"], cfg["rank"]
+    ctx = h.Context(max_n=n, leaf=L, rank=r, d_model=cfg["d"], n_layers=cfg["n_layers"], n_heads=cfg["n_heads"],
+                    d_mlp=cfg["d_mlp"], weights=w)
+    P = h.packed_width(n, L, r, h.PRE_LEARNED)
+    packed = torch.empty(P, dtype=torch.float32, device="cuda")
+    h.infer_factors(ctx, [s], packed)
+    torch.cuda.synchronize()
+    got = hmatrix.unpack(packed.cpu().numpy().astype(np.float64), n, L, r, "learned")
+    p = network.unflatten(w.astype(np.float64), lay)
+    with torch.no_grad():
+        f = network.to_numpy_factors(network.forward(p, ref, cfg))
+    for key in ("leafblk", "U", "V"):
+        g2 = got[key].reshape(got[key].shape[0], -1)
+        r2 = f[key].reshape(f[key].shape[0], -1)
+        sc = np.maximum(np.abs(r2).max(axis=1, keepdims=True), 1e-300)
+        e = float((np.abs(g2 - r2) / sc).max())
+        assert e <= 0.1, (key, e)
+    ce = float((np.abs(got["core"] - f["core"]) / np.maximum(f["core_scale"], 1e-300)).max())
+    assert ce <= 0.1, ce
+    assert float(np.abs(got["g"] - f["g"]).max() / np.abs(f["g"]).max()) <= 0.1
+    a = grid.sparse_matrix(ref)
+    out = pcg.pcg(lambda v: a @ v, lambda v: hmatrix.apply(got, v), fr["b"], rtol=fr["rtol"])
+    b = torch.from_numpy(fr["b"]).cuda()
+    x = torch.empty_like(b)
+    info = h.solve(ctx, s, h.factors(h.PRE_LEARNED, packed, n, L, r), b, x, rtol=fr["rtol"])
+    _check(info, out, a, fr, x.cpu().numpy())
+    ctx.close()

@@ -31,3 +31,12 @@ def test_network_blob_and_batch_shapes_are_reproducible():
     assert {int(np.prod(d)) for d in d1} <= {1024, 2048, 4096, 8192, 16384}
     assert all(len(d) == (2 if i % 2 == 0 else 3) for i, d in enumerate(d1))
     assert np.array_equal(inputs.rhs(9, 100), inputs.rhs(9, 100))
+
+
+def test_split_seeds_are_disjoint():
+    for seed in (0, 1, 5):
+        tr, te = inputs.split_seeds(seed, 100, 20)
+        assert len(tr) == 100 and len(te) == 20 and not set(tr) & set(te)
+    a = set(sum(inputs.split_seeds(0, 100, 20), []))
+    b = set(sum(inputs.split_seeds(1, 100, 20), []))
+    assert not a & b
