@@ -10,6 +10,7 @@
 // position c ^ (i & 7), which makes both the column pass (lane = column pair) and the
 // row pass (lane = row, 16-byte reads) free of bank conflicts.
 #include <algorithm>
+#include <utility>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include "ctx.cuh"
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(32 * kRWarps) apply_warp_restrict_kernel(const
                                                                            float* __restrict__ ydiag,
                                                                            float* __restrict__ uhat) {
   extern __shared__ uint8_t sraw[];
+  pdl_entry();
   __shared__ __align__(8) uint64_t bars[kRWarps][2];
   __shared__ __align__(16) float rstage[kRWarps][64], wstage[kRWarps][64];
   uint8_t* sal = sraw + ((1024u - (s32(sraw) & 1023u)) & 1023u);
@@ -320,12 +322,47 @@ __global__ void __launch_bounds__(32 * kWarps) apply_warp_prolong_kernel(FactorV
                                                                          const float* __restrict__ acoup,
                                                                          const float* __restrict__ ydiag,
                                                                          float* __restrict__ z) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t pol = pol_evict_first();
   for (int kk = blockIdx.x * kWarps + warp; kk < f.K; kk += gridDim.x * kWarps) {
     const int k = f.K - 1 - kk;
     float y0 = ydiag[(size_t)k * 64 + lane], y1 = ydiag[(size_t)k * 64 + 32 + lane];
-    if (acoup && f.nslot == 2) {
+    if (!acoup && f.learned && f.nslot == 2) {
+      // learned factors: both bridges' loads first, then this leaf's coupling inputs gathered
+      // from the tile outputs level by level (the leaf is on one side of each level's tile),
+      // summed in level order
+      const uint4* w0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane) * R);
+      const uint4* w1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane + 32) * R);
+      const uint4* v0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane) * R);
+      const uint4* v1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane + 32) * R);
+      uint4 p0[R / 8], q0[R / 8], p1[R / 8], q1[R / 8];
+#pragma unroll
+      for (int c = 0; c < R / 8; ++c) {
+        p0[c] = ld_hint(w0 + c, pol);
+        q0[c] = ld_hint(w1 + c, pol);
+        p1[c] = ld_hint(v0 + c, pol);
+        q1[c] = ld_hint(v1 + c, pol);
+      }
+      float tv[24];
+#pragma unroll
+      for (int lev = 1; lev <= 24; ++lev) {
+        tv[lev - 1] = 0.f;
+        if (lev <= f.levels && lane < R) {
+          const int cl = k >> (f.levels - lev);
+          const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+          tv[lev - 1] = __ldg(tcoup + ((size_t)m * 2 + (cl & 1)) * R + lane);
+        }
+      }
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int lev = 1; lev <= 24; ++lev)
+        if (lev <= f.levels) {
+          if ((k >> (f.levels - lev)) & 1) a1 += tv[lev - 1]; else a0 += tv[lev - 1];
+        }
+      prolong_rows<R>(p0, q0, a0, y0, y1);
+      prolong_rows<R>(p1, q1, a1, y0, y1);
+    } else if (acoup && f.nslot == 2) {
       const uint4* w0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane) * R);
       const uint4* w1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane + 32) * R);
       const uint4* v0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane) * R);
@@ -551,14 +588,15 @@ __global__ void __launch_bounds__(256) leaf_coupling_kernel(FactorView<__nv_bflo
 }
 
 // ---------------------------------------------------------------- blocked strip sums (learned)
-// The coupling stage for learned factors (bridge slot = side) in three passes over blocks of
+// The coupling stage for learned factors (bridge slot = side) in two passes over blocks of
 // up to 256 consecutive items (leaves, or block totals one level up):
 //   block_up:   per block, the sums of aligned groups of 2^j items (slot 0 and slot 1) in shared
 //               memory, then the couplings t^r = B s^c, t^c = B^T s^r of every tile whose two
-//               clusters lie inside the block; optionally the block's totals per slot.
-//   (block_up again on the block totals, one CTA, for the tiles above the blocks)
-//   block_down: per leaf, a[s] = sum over the levels where the leaf is on side s of that
-//               tile's coupling output (row side t^r, column side t^c).
+//               clusters lie inside the block (cores read from global memory); optionally the
+//               block's totals per slot.
+//   (block_up again on the block totals, for the tiles above the blocks)
+// The prolongation then gathers, per leaf, a[s] = the sum over the levels where the leaf is on
+// side s of that tile's coupling output (row side t^r, column side t^c).
 constexpr int kBlk = 256;           // items per block
 constexpr int kBlkLog = 8;
 HM_INLINE int node_off(int n, int j) { return 2 * n - 2 * (n >> j); }   // level j of an n-item tree
@@ -600,21 +638,14 @@ __global__ void __launch_bounds__(1024) block_up_kernel(FactorView<__nv_bfloat16
                                                         float* __restrict__ tcoup) {
   static_assert(R <= 16, "one output pair per lane of a half-warp");
   constexpr int Q = R / 4, LQ = ilog2(Q);          // float4 per node
-  constexpr int C = R * R / 8, LC = ilog2(C);      // 16-byte chunks per core
   extern __shared__ __align__(16) uint8_t smraw[];
+  pdl_entry();
   const int nb = 1 << jl, nodes = 2 * nb - 1;
   float4* sums4 = reinterpret_cast<float4*>(smraw);                                 // [2][nodes][Q]
-  __nv_bfloat16* cores = reinterpret_cast<__nv_bfloat16*>(sums4 + 2 * nodes * Q);
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int blk = blockIdx.x, i0 = blk * nb;
   const int part = blockIdx.y, nparts = gridDim.y;
   const int ntile = (nb - 1 - part + nparts - 1) / nparts;    // tiles of this CTA
-  stage_batched<8>(reinterpret_cast<uint4*>(cores), ntile * C, tid, nthr, [&](int q) {
-    int j, tl;
-    tile_level(jl, part + (q >> LC) * nparts, j, tl);
-    const int m = (1 << (f.levels - jbase - j - 1)) - 1 + (i0 >> (j + 1)) + tl;
-    return reinterpret_cast<const uint4*>(f.core) + (size_t)m * C + (q & (C - 1));
-  });
 #pragma unroll
   for (int s = 0; s < 2; ++s)
     stage_batched<2>(sums4 + s * nodes * Q, nb * Q, tid, nthr, [&](int q) {
@@ -645,14 +676,16 @@ __global__ void __launch_bounds__(1024) block_up_kernel(FactorView<__nv_bfloat16
     const int m = (1 << (f.levels - jbase - j - 1)) - 1 + (i0 >> (j + 1)) + tl;
     const float* sr = sums + (0 * nodes + node_off(nb, j) + 2 * tl) * R;       // row cluster, slot 0
     const float* sc = sums + (1 * nodes + node_off(nb, j) + 2 * tl + 1) * R;   // column cluster, slot 1
-    const __nv_bfloat16* Bs = cores + (size_t)it * R * R;
+    // the core straight from global memory (row e by 16-byte loads, column e through L1): without
+    // a staged copy the CTA needs only the sums and three CTAs fit an SM
+    const __nv_bfloat16* Bs = f.core + (size_t)m * R * R;
     const uint4* row = reinterpret_cast<const uint4*>(Bs + e * R);
     const float4* sc4 = reinterpret_cast<const float4*>(sc);
     const float4* sr4 = reinterpret_cast<const float4*>(sr);
     float2 a2 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int c = 0; c < R / 8; ++c) {
-      const uint4 u = row[c];
+      const uint4 u = __ldg(row + c);
       const float4 s0 = sc4[2 * c], s1 = sc4[2 * c + 1];
       a2 = __ffma2_rn(bf2(u.x), make_float2(s0.x, s0.y), a2);
       a2 = __ffma2_rn(bf2(u.y), make_float2(s0.z, s0.w), a2);
@@ -663,62 +696,13 @@ __global__ void __launch_bounds__(1024) block_up_kernel(FactorView<__nv_bfloat16
 #pragma unroll
     for (int q4 = 0; q4 < Q; ++q4) {
       const float4 v = sr4[q4];
-      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 0) * R + e]), v.x, tc);
-      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 1) * R + e]), v.y, tc);
-      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 2) * R + e]), v.z, tc);
-      tc = fmaf(__bfloat162float(Bs[(4 * q4 + 3) * R + e]), v.w, tc);
+      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 0) * R + e)), v.x, tc);
+      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 1) * R + e)), v.y, tc);
+      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 2) * R + e)), v.z, tc);
+      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 3) * R + e)), v.w, tc);
     }
     tcoup[(size_t)m * 2 * R + e] = a2.x + a2.y;
     tcoup[(size_t)m * 2 * R + R + e] = tc;
-  }
-}
-
-// Per-leaf coupling inputs for one block of kBlk leaves: levels inside the block from the
-// staged tile outputs, levels above it from global memory.  Sums run from the top level down.
-template <int R>
-__global__ void __launch_bounds__(1024) block_down_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ tcoup,
-                                                          float* __restrict__ acoup) {
-  constexpr int Q = R / 4, LQ = ilog2(Q);
-  constexpr int H = 2 * Q, LH = ilog2(H);            // float4 per tile ([t^r | t^c])
-  __shared__ __align__(16) float4 st[(kBlk - 1) * H];  // local tiles, level-major
-  __shared__ __align__(16) float4 top[2 * Q];
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int blk = gridDim.x - 1 - blockIdx.x, k0 = blk * kBlk;
-  stage_batched<4>(st, (kBlk - 1) * H, tid, nthr, [&](int q) {
-    int j, tl;
-    tile_level(kBlkLog, q >> LH, j, tl);
-    const int m = (1 << (f.levels - j - 1)) - 1 + (k0 >> (j + 1)) + tl;
-    return reinterpret_cast<const float4*>(tcoup + (size_t)m * 2 * R) + (q & (H - 1));
-  });
-  if (tid < 2 * R) {
-    const int s = tid / R, e = tid % R;
-    float tv[24];
-#pragma unroll
-    for (int lev = 1; lev <= 24; ++lev) {
-      tv[lev - 1] = 0.f;
-      if (lev <= f.levels - kBlkLog) {
-        const int cl = k0 >> (f.levels - lev);
-        const int side = cl & 1;
-        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-        if (side == s) tv[lev - 1] = tcoup[((size_t)m * 2 + side) * R + e];
-      }
-    }
-    float a = 0.f;
-#pragma unroll
-    for (int lev = 0; lev < 24; ++lev) a += tv[lev];
-    reinterpret_cast<float*>(top)[tid] = a;
-  }
-  __syncthreads();
-  float4* out4 = reinterpret_cast<float4*>(acoup);
-  for (int q = tid; q < 2 * kBlk * Q; q += nthr) {
-    const int s = q >> (kBlkLog + LQ), g = (q >> LQ) & (kBlk - 1), e4 = q & (Q - 1);
-    float4 a = top[s * Q + e4];
-#pragma unroll
-    for (int j = kBlkLog - 1; j >= 0; --j) {
-      const int cl = g >> j;
-      if ((cl & 1) == s) a = add4(a, st[((kBlk - (kBlk >> j)) + (cl >> 1)) * H + s * Q + e4]);
-    }
-    out4[((size_t)s * f.K + k0 + g) * Q + e4] = a;
   }
 }
 
@@ -726,6 +710,24 @@ __global__ void __launch_bounds__(1024) block_down_kernel(FactorView<__nv_bfloat
 
 // ============================================================================ launchers
 SysView make_sysview(const hmpcg_system* s);
+
+// Launch with programmatic stream serialisation: the kernel's launch overlaps the tail of the
+// previous kernel in the stream; every kernel launched so waits (griddepcontrol.wait) before
+// its first global access.
+template <class... KArgs, class... Args>
+static void launch_pdl_bw(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(a)...);
+}
 
 // Cube SpMV when every axis has at least two cells; returns 1 when not applicable.
 int spmv_cube_launch(const hmpcg_system* sys, const float* x, float* y, cudaStream_t st) {
@@ -780,39 +782,40 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
     return true;
   });
   switch (f.r) {
-    case 8: apply_warp_restrict_kernel<8><<<grid, 32 * kRWarps, smem, st>>>(fmap, f, r, ydiag, uhat); break;
-    case 16: apply_warp_restrict_kernel<16><<<grid, 32 * kRWarps, smem, st>>>(fmap, f, r, ydiag, uhat); break;
-    default: apply_warp_restrict_kernel<32><<<grid, 32 * kRWarps, smem, st>>>(fmap, f, r, ydiag, uhat); break;
+    case 8: launch_pdl_bw(apply_warp_restrict_kernel<8>, dim3(grid), dim3(32 * kRWarps), smem, st, fmap, f, r, ydiag, uhat); break;
+    case 16: launch_pdl_bw(apply_warp_restrict_kernel<16>, dim3(grid), dim3(32 * kRWarps), smem, st, fmap, f, r, ydiag, uhat); break;
+    default: launch_pdl_bw(apply_warp_restrict_kernel<32>, dim3(grid), dim3(32 * kRWarps), smem, st, fmap, f, r, ydiag, uhat); break;
   }
   const int gridp = std::max(1, std::min((f.K + kWarps - 1) / kWarps, c->num_sms * 8));
   const float* acoup = nullptr;
   const bool blocked = f.learned && f.nslot == 2 && f.r <= 16 && f.K >= 2 * kBlk && f.K <= kBlk * kBlk && c->tree &&
                        4LL * f.K * f.r <= c->tree_cap;
   if (blocked) {
-    // learned factors: blocked strip sums, tile couplings and per-leaf inputs in three passes
+    // learned factors: blocked strip sums and tile couplings in two passes; the prolongation
+    // gathers each leaf's coupling inputs from the tile outputs itself
     const int nb = f.K / kBlk;
-    float* a_out = c->tree;                              // [2][K][R]
     float* bsum = c->tree + 2LL * f.K * f.r;             // [2][nb][R]
     int jnb = 0;
     while ((1 << jnb) < nb) ++jnb;
     const int parts = std::max(1, std::min(16, nb / 16));     // CTAs sharing the tiles above the blocks
-    auto smem_up = [&](int items) { return (size_t)2 * (2 * items - 1) * f.r * 4 + (size_t)(items - 1) * f.r * f.r * 2; };
+    auto smem_up = [&](int items) { return (size_t)2 * (2 * items - 1) * f.r * 4; };
     static std::atomic<unsigned long long> attr_up{0};
     once_per_device(attr_up, [] {
       cudaFuncSetAttribute(block_up_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       cudaFuncSetAttribute(block_up_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       return true;
     });
+    float* nobsum = nullptr;
+    const float* up_in = uhat;
+    const float* top_in = bsum;
     if (f.r == 8) {
-      block_up_kernel<8><<<nb, 1024, smem_up(kBlk), st>>>(f, uhat, f.K, kBlkLog, 0, bsum, tcoup);
-      block_up_kernel<8><<<dim3(1, parts), 1024, smem_up(nb), st>>>(f, bsum, nb, jnb, kBlkLog, nullptr, tcoup);
-      block_down_kernel<8><<<nb, 1024, 0, st>>>(f, tcoup, a_out);
+      launch_pdl_bw(block_up_kernel<8>, dim3(nb), dim3(1024), smem_up(kBlk), st, f, up_in, (int)f.K, kBlkLog, 0, bsum, tcoup);
+      launch_pdl_bw(block_up_kernel<8>, dim3(1, parts), dim3(1024), smem_up(nb), st, f, top_in, nb, jnb, kBlkLog, nobsum, tcoup);
     } else {
-      block_up_kernel<16><<<nb, 1024, smem_up(kBlk), st>>>(f, uhat, f.K, kBlkLog, 0, bsum, tcoup);
-      block_up_kernel<16><<<dim3(1, parts), 1024, smem_up(nb), st>>>(f, bsum, nb, jnb, kBlkLog, nullptr, tcoup);
-      block_down_kernel<16><<<nb, 1024, 0, st>>>(f, tcoup, a_out);
+      launch_pdl_bw(block_up_kernel<16>, dim3(nb), dim3(1024), smem_up(kBlk), st, f, up_in, (int)f.K, kBlkLog, 0, bsum, tcoup);
+      launch_pdl_bw(block_up_kernel<16>, dim3(1, parts), dim3(1024), smem_up(nb), st, f, top_in, nb, jnb, kBlkLog, nobsum, tcoup);
     }
-    acoup = a_out;
+    acoup = nullptr;
   } else if (f.K >= 512 && c->tree && (int64_t)f.nslot * 2 * f.K * f.r <= c->tree_cap) {
     // cluster sums by a tree: every tile reads two precomputed sums; then one pass gathers each
     // leaf's coupling input into the tree buffer, which is free again by then
@@ -837,10 +840,12 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
   } else {
     tile_launch(f, uhat, tcoup, c->num_sms, st);
   }
+  const float* tc_in = tcoup;
+  const float* yd_in = ydiag;
   switch (f.r) {
-    case 8: apply_warp_prolong_kernel<8><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, acoup, ydiag, z); break;
-    case 16: apply_warp_prolong_kernel<16><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, acoup, ydiag, z); break;
-    default: apply_warp_prolong_kernel<32><<<gridp, 32 * kWarps, 0, st>>>(f, tcoup, acoup, ydiag, z); break;
+    case 8: launch_pdl_bw(apply_warp_prolong_kernel<8>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
+    case 16: launch_pdl_bw(apply_warp_prolong_kernel<16>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
+    default: launch_pdl_bw(apply_warp_prolong_kernel<32>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
   }
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
