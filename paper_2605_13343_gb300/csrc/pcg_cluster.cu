@@ -26,6 +26,10 @@ namespace {
 
 constexpr int kCThreads = 512;
 constexpr int kLeafPad = 8;   // row padding of leaf blocks in shared memory (16-byte rows, bank spread)
+// neighbour table entries: (owning CTA << 11) | local index (at most 2048 nodes per CTA, 16 CTAs)
+constexpr int kNbrShift = 11;
+constexpr int kNbrMask = (1 << kNbrShift) - 1;
+constexpr uint16_t kNoNbr = 0xFFFF;
 
 // Generic pointer to the same shared-memory object in CTA `rank` of the cluster: plain
 // loads through it are ordinary memory operations that the compiler may batch.
@@ -59,13 +63,13 @@ struct CParams {
   double rtol;
   int max_iter, recompute;
   int C, npc, lpc, tpc;   // CTAs, nodes / leaves / tiles per CTA
-  int fsm;                // 1: the CTA's factor share is copied to shared memory; 0: read from L2
+  int fsm;                // 1: the CTA's factor share in shared memory; 2: its leaf blocks only; 0: all from L2
   int fallback;           // batched H-matrix solves: re-solve with Jacobi after a breakdown
 };
 
 // Shared-memory carve-up (byte offsets), identical in every CTA.
 struct CLayout {
-  size_t x, b, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tv, part, partff, rs, ws, leaf, bridge, gate, core, total;
+  size_t x, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tv, part, partff, rs, ws, leaf, bridge, gate, core, total;
 };
 
 // Couplings a CTA's own leaves need: one per (level, cluster of the level) among its lpc leaves,
@@ -74,12 +78,11 @@ __host__ __device__ inline int coupling_entries(int lpc, int levels) { return le
 
 template <class T>
 __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, int nslot, bool learned, bool hmat,
-                                     bool fsm, int levels) {
+                                     int fsm, int levels) {
   CLayout o;
   size_t p = 0;
   auto take = [&](size_t bytes) { size_t q = p; p = (p + bytes + 15) / 16 * 16; return q; };
   o.x = take(8 * (size_t)npc);
-  o.b = take(8 * (size_t)npc);
   o.r = take(4 * (size_t)npc);
   o.z = take(4 * (size_t)npc);
   o.q = take(4 * (size_t)npc);
@@ -87,7 +90,7 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
   o.p1 = take(4 * (size_t)npc);
   o.yd = take(4 * (size_t)npc);
   o.coef = take(16 * (size_t)npc);             // diag32, w32[0..2] of owned nodes
-  o.nbr = take(24 * (size_t)npc);              // 6 neighbours: (owner << 16) | local index, -1 at the boundary
+  o.nbr = take(12 * (size_t)npc);              // 6 neighbours: (owner << 11) | local index, 0xFFFF at the boundary
   o.wm = take(12 * (size_t)npc);               // w32 of the -a face of each owned node
   o.uh = take(hmat ? 4 * (size_t)nslot * (2 * lpc - 1) * R : 0);   // per slot: leaves, then aligned pair, quad, ... sums
   o.tv = take(hmat ? 4 * (size_t)coupling_entries(lpc, levels) * 2 * R : 0);   // strip sums, then couplings
@@ -95,9 +98,11 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
   o.partff = take(8 * 8);
   o.rs = take(hmat ? 4 * (size_t)lpc * L : 0);
   o.ws = take(hmat ? 4 * (size_t)lpc * (L > nslot * R ? L : nslot * R) : 0);
-  o.leaf = take(hmat && fsm ? sizeof(T) * (size_t)lpc * L * (L + kLeafPad) : 0);
-  o.bridge = take(hmat && fsm ? sizeof(T) * (size_t)nslot * npc * R : 0);
-  o.gate = take(hmat && fsm && learned ? sizeof(T) * (size_t)npc : 0);
+  // fsm 1: leaves (padded rows), bridges and gates in shared memory; 2: leaves only, rows
+  // unpadded with the 16-byte chunks XOR-swizzled by row; 0: everything read from L2
+  o.leaf = take(hmat && fsm ? sizeof(T) * (size_t)lpc * L * (fsm == 2 ? L : L + kLeafPad) : 0);
+  o.bridge = take(hmat && fsm == 1 ? sizeof(T) * (size_t)nslot * npc * R : 0);
+  o.gate = take(hmat && fsm == 1 && learned ? sizeof(T) * (size_t)npc : 0);
   o.core = take(0);   // cores are read from the packed tensor (L2-resident)
   o.total = p;
   return o;
@@ -115,17 +120,17 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   const int C = P.C, npc = P.npc;
   const int L = LC ? LC : F.L, R = RC ? RC : F.r;
   const bool hmat = PRE == CPRE_HMAT;
-  const bool fsm = P.fsm != 0;
-  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, fsm, F.levels);
+  const bool fsm = P.fsm == 1;          // leaves, bridges and gates in shared memory
+  const bool fleaf = P.fsm != 0;        // leaves in shared memory (padded rows, or swizzled with fsm 2)
+  const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, P.fsm, F.levels);
   double* xs = reinterpret_cast<double*>(sm + lay.x);
-  double* bs = reinterpret_cast<double*>(sm + lay.b);
   float* rv = reinterpret_cast<float*>(sm + lay.r);
   float* zv = reinterpret_cast<float*>(sm + lay.z);
   float* qv = reinterpret_cast<float*>(sm + lay.q);
   float* pbuf[2] = {reinterpret_cast<float*>(sm + lay.p0), reinterpret_cast<float*>(sm + lay.p1)};
   float* ydv = reinterpret_cast<float*>(sm + lay.yd);
   float* coef = reinterpret_cast<float*>(sm + lay.coef);
-  int* nbt = reinterpret_cast<int*>(sm + lay.nbr);
+  uint16_t* nbt = reinterpret_cast<uint16_t*>(sm + lay.nbr);
   float* wmv = reinterpret_cast<float*>(sm + lay.wm);
   float* uh = reinterpret_cast<float*>(sm + lay.uh);
   float* tvb = reinterpret_cast<float*>(sm + lay.tv);
@@ -138,10 +143,10 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   T* sgate = reinterpret_cast<T*>(sm + lay.gate);
   const int tid = threadIdx.x;
   const int n0 = me * npc;
-  const int LP = L + kLeafPad;
+  const int LP = P.fsm == 2 ? L : L + kLeafPad;
   // factor share: shared-memory copies (fsm) or the packed tensor itself (L2-resident)
-  const int LPs = fsm ? LP : L;
-  const T* lf = fsm ? sleaf : (hmat ? F.leaf + (size_t)(n0 / L) * L * L : nullptr);
+  const int LPs = fleaf ? LP : L;
+  const T* lf = fleaf ? sleaf : (hmat ? F.leaf + (size_t)(n0 / L) * L * L : nullptr);
   const T* brf = fsm ? sbr : (hmat ? F.bridge + (size_t)n0 * R : nullptr);
   const size_t brs = fsm ? (size_t)npc * R : (size_t)F.n * R;          // slot stride
   const T* gtf = fsm ? sgate : (hmat && F.learned ? F.gate + n0 : nullptr);
@@ -170,15 +175,24 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   // ---------------- load: owned b, coefficients, factor share
   for (int i = tid; i < npc; i += blockDim.x) {
     const int g = n0 + i;
-    bs[i] = P.b[g];
     coef[4 * i] = S.diag32[g];
     for (int a = 0; a < 3; ++a) {
       coef[4 * i + 1 + a] = a < S.mo.ndim ? S.w32[a][g] : 0.f;
       const int jp = a < S.mo.ndim ? S.mo.plus(g, a) : -1;
       const int jm = a < S.mo.ndim ? S.mo.minus(g, a) : -1;
-      nbt[6 * i + 2 * a] = jp < 0 ? -1 : (((jp / npc) << 16) | (jp % npc));
-      nbt[6 * i + 2 * a + 1] = jm < 0 ? -1 : (((jm / npc) << 16) | (jm % npc));
+      nbt[6 * i + 2 * a] = jp < 0 ? kNoNbr : (uint16_t)(((jp / npc) << kNbrShift) | (jp % npc));
+      nbt[6 * i + 2 * a + 1] = jm < 0 ? kNoNbr : (uint16_t)(((jm / npc) << kNbrShift) | (jm % npc));
       wmv[3 * i + a] = jm < 0 ? 0.f : S.w32[a][jm];
+    }
+  }
+  if (hmat && P.fsm == 2) {
+    // leaf rows of 64 BF16 = 8 chunks of 16 bytes; chunk c of row i is stored at c ^ (i & 7)
+    const int k0 = n0 / L;
+    const uint4* src = reinterpret_cast<const uint4*>(F.leaf + (size_t)k0 * L * L);
+    uint4* dst = reinterpret_cast<uint4*>(sleaf);
+    for (int e = tid; e < P.lpc * L * (L / 8); e += blockDim.x) {
+      const int row = e / (L / 8), c = e % (L / 8);   // row over all owned leaves
+      dst[row * (L / 8) + (c ^ (row & 7))] = src[e];
     }
   }
   if (hmat && fsm) {
@@ -268,6 +282,96 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       const float sg = F.sc_gate ? F.sc_gate[k] : 1.f;
       const float r_i = rs[kl * L + gl];
       ydv[kl * L + gl] = fmaf(tf<T>(gtf[kl * L + gl]) * sg, r_i, (acc.x + acc.y) * sc_leaf(k));
+    }
+  };
+  // Leaf-only shared-memory mode (fsm 2: 16 leaves per CTA, one warp each): the leaf block is
+  // unpadded with its 16-byte chunks XOR-swizzled by row (conflict-free down a column and along
+  // a row); bridges and gates come from L2.  Per warp: w = F^T r (lane = column pair), the
+  // restriction of both bridges (lane = (slot, chunk, row group), partial sums over 8 rows, a
+  // butterfly over the row groups), then y = F w + g r (lane = rows lane, lane + 32).
+  auto restrict_leaves_vec32 = [&]() {
+    if (grp < P.lpc) {
+      float* r_l = rs + grp * L;
+      for (int i = gl; i < L; i += G) r_l[i] = rv[grp * L + i];
+    }
+    __syncthreads();
+    if (grp < P.lpc) {
+      const int kl = grp, k = n0 / L + kl;
+      const T* blk = lf + (size_t)kl * L * L;
+      const float4* r4 = reinterpret_cast<const float4*>(rs + kl * L);
+      float* w_l = ws + kl * max(L, F.nslot * R);
+      {                                                  // w = F^T r, columns 2 gl, 2 gl + 1
+        float2 acc = make_float2(0.f, 0.f);
+        const int cc = gl >> 2, off = (2 * gl) & 7;
+#pragma unroll 4
+        for (int i4 = 0; i4 < 16; ++i4) {
+          const float4 rr = r4[i4];
+          const float rv4[4] = {rr.x, rr.y, rr.z, rr.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = 4 * i4 + u;
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(blk + i * 64 + ((cc ^ (i & 7)) << 3) + off));
+            acc = __ffma2_rn(f, make_float2(rv4[u], rv4[u]), acc);
+          }
+        }
+        const float sb = sc_leaf(k);
+        w_l[2 * gl] = acc.x * sb;
+        w_l[2 * gl + 1] = acc.y * sb;
+      }
+      {                                                  // restriction of both bridges
+        const int combo = gl & 3, rg = gl >> 2;          // combo = (slot, 8-wide chunk of the row)
+        const int sl = combo >> 1, ch = combo & 1;
+        const uint4* W = reinterpret_cast<const uint4*>(brf + (size_t)sl * brs + (size_t)kl * L * R);
+        float part[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        uint4 wv[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) wv[m] = __ldg(W + (size_t)(rg + 8 * m) * 2 + ch);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const float ri = rs[kl * L + rg + 8 * m];
+          const uint32_t uu[4] = {wv[m].x, wv[m].y, wv[m].z, wv[m].w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&uu[q]));
+            part[2 * q] = fmaf(f.x, ri, part[2 * q]);
+            part[2 * q + 1] = fmaf(f.y, ri, part[2 * q + 1]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          part[q] += __shfl_xor_sync(0xffffffffu, part[q], 4);
+          part[q] += __shfl_xor_sync(0xffffffffu, part[q], 8);
+          part[q] += __shfl_xor_sync(0xffffffffu, part[q], 16);
+        }
+        if (rg == 0) {
+          const float sc = sc_br(sl, k);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) uh[((size_t)sl * (2 * P.lpc - 1) + kl) * R + ch * 8 + q] = part[q] * sc;
+        }
+      }
+    }
+    __syncthreads();
+    if (grp < P.lpc) {                                   // y = F w + g r, rows gl and gl + 32
+      const int kl = grp, k = n0 / L + kl;
+      const float4* w4 = reinterpret_cast<const float4*>(ws + kl * max(L, F.nslot * R));
+      const float sg = F.sc_gate ? F.sc_gate[k] : 1.f;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int row = gl + 32 * hh;
+        const uint4* rowp = reinterpret_cast<const uint4*>(lf + (size_t)kl * L * L + (size_t)row * 64);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint4 u = rowp[c ^ (row & 7)];
+          const float4 wa = w4[2 * c], wb = w4[2 * c + 1];
+          acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x)), make_float2(wa.x, wa.y), acc);
+          acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y)), make_float2(wa.z, wa.w), acc);
+          acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.z)), make_float2(wb.x, wb.y), acc);
+          acc = __ffma2_rn(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.w)), make_float2(wb.z, wb.w), acc);
+        }
+        const float r_i = rs[kl * L + row];
+        ydv[kl * L + row] = fmaf(tf<T>(gtf[kl * L + row]) * sg, r_i, (acc.x + acc.y) * sc_leaf(k));
+      }
     }
   };
   auto restrict_leaves = [&]() {
@@ -473,8 +577,8 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ep = nbt[6 * il + 2 * a], em = nbt[6 * il + 2 * a + 1];
-      if (ep >= 0) acc = fmaf(-coef[4 * il + 1 + a], get(ep >> 16, ep & 0xFFFF), acc);
-      if (em >= 0) acc = fmaf(-wmv[3 * il + a], get(em >> 16, em & 0xFFFF), acc);
+      if (ep != kNoNbr) acc = fmaf(-coef[4 * il + 1 + a], get(ep >> kNbrShift, ep & kNbrMask), acc);
+      if (em != kNoNbr) acc = fmaf(-wmv[3 * il + a], get(em >> kNbrShift, em & kNbrMask), acc);
     }
     return acc;
   };
@@ -484,9 +588,9 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int ep = nbt[6 * il + 2 * a], em = nbt[6 * il + 2 * a + 1];
-      if (ep >= 0) acc = fma(-S.w[a][i], get(ep >> 16, ep & 0xFFFF), acc);
-      if (em >= 0) {
-        const int o = em >> 16, l = em & 0xFFFF;
+      if (ep != kNoNbr) acc = fma(-S.w[a][i], get(ep >> kNbrShift, ep & kNbrMask), acc);
+      if (em != kNoNbr) {
+        const int o = em >> kNbrShift, l = em & kNbrMask;
         acc = fma(-S.w[a][o * npc + l], get(o, l), acc);
       }
     }
@@ -542,7 +646,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   // ---------------- init: x = 0, r = b, p = 0, z = M r
   double acc = 0.0;
   for (int i = tid; i < npc; i += blockDim.x) {
-    const double bi = bs[i];
+    const double bi = P.b[n0 + i];
     xs[i] = 0.0;
     rv[i] = (float)bi;
     pbuf[0][i] = 0.f;
@@ -551,7 +655,8 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   cta_part(acc, 0);
   if (hmat) {
     __syncthreads();
-    if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
+    if (kVec && P.fsm == 2) restrict_leaves_vec32();
+      else if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
     build_tree();
   }
   __syncthreads();
@@ -632,7 +737,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       float ri;
       if (replace) {
         const double ax = row64(g, xn, [&](int o, int l) { return fma(alpha, (double)gf(pn, o, l), gd(xs, o, l)); });
-        const double rd = bs[i] - ax;
+        const double rd = P.b[g] - ax;
         ri = (float)rd;
         const double sq = rd * rd;   // the FP64 square, carried as a float-float pair
         const float sh = (float)sq;
@@ -653,7 +758,8 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       cta_part_ff(rzh, rzl, 5);
     } else {
       __syncthreads();
-      if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
+      if (kVec && P.fsm == 2) restrict_leaves_vec32();
+      else if (kVec && fsm && F.learned && G == 64) restrict_leaves_vec(); else restrict_leaves();
       build_tree();
     }
     cur ^= 1;
@@ -707,7 +813,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   for (int i = tid; i < npc; i += blockDim.x) {
     const int g = n0 + i;
     const double ax = row64(g, xs[i], [&](int o, int l) { return gd(xs, o, l); });
-    const double rd = bs[i] - ax;
+    const double rd = P.b[g] - ax;
     acc = fma(rd, rd, acc);
     P.x[g] = xs[i];
   }
@@ -777,7 +883,7 @@ SysView make_sysview(const hmpcg_system* s);
 // Parameters and shared-memory bytes of one system on a cluster of C CTAs with the factor share
 // in shared memory (fsm) or read from L2; false when the system does not fit that shape.
 template <class T, int PRE>
-static bool plan_cluster(const hmpcg_system* sys, const FactorView<T>* fv, int C, bool fsm, CParams<T>& P,
+static bool plan_cluster(const hmpcg_system* sys, const FactorView<T>* fv, int C, int fsm, CParams<T>& P,
                          size_t& smem) {
   const int n = (int)sys->n;
   const bool hmat = PRE == CPRE_HMAT;
@@ -793,10 +899,15 @@ static bool plan_cluster(const hmpcg_system* sys, const FactorView<T>* fv, int C
   const int R = hmat ? fv->r : 16, nslot = hmat ? fv->nslot : 1;
   const CLayout lay = c_layout<T>(npc, lpc, tpc, L, R, nslot, hmat && fv->learned, hmat, fsm, hmat ? fv->levels : 0);
   if (hmat && (size_t)lpc * nslot * R > (size_t)lpc * std::max(L, nslot * R)) return false;
+  // the leaf-only mode runs the 32-thread vector restriction: BF16 learned factors, leaf 64,
+  // rank 16, 16 leaves per CTA
+  if (fsm == 2 && !(hmat && std::is_same<T, __nv_bfloat16>::value && fv->learned && L == 64 && R == 16 &&
+                    nslot == 2 && lpc * 32 == kCThreads))
+    return false;
   if (lay.total > 220 * 1024) return false;
   P.s = make_sysview(sys);
   if (fv) P.f = *fv; else memset(&P.f, 0, sizeof(P.f));
-  P.C = C; P.npc = npc; P.lpc = lpc; P.tpc = tpc; P.fsm = fsm ? 1 : 0;
+  P.C = C; P.npc = npc; P.lpc = lpc; P.tpc = tpc; P.fsm = hmat ? fsm : 0;
   smem = lay.total;
   return true;
 }
@@ -848,12 +959,12 @@ static int cluster_capacity(const void* kern, int C, size_t smem) {
 template <class T, int PRE>
 static int try_cluster(Ctx* c, const hmpcg_system* sys, const FactorView<T>* fv, const double* b, double* x,
                        const hmpcg_solve_opts* o, cudaStream_t st) {
-  for (int fsm = 1; fsm >= 0; --fsm) {
-    if (!fsm && PRE != CPRE_HMAT) break;
+  for (int fsm : {1, 2, 0}) {
+    if (fsm != 1 && PRE != CPRE_HMAT) break;
     for (int C : {16, 8}) {
       CParams<T> P;
       size_t smem = 0;
-      if (!plan_cluster<T, PRE>(sys, fv, C, fsm != 0, P, smem)) continue;
+      if (!plan_cluster<T, PRE>(sys, fv, C, fsm, P, smem)) continue;
       P.fallback = 0;
       const bool spec = PRE == CPRE_HMAT && fv->L == 64 && fv->r == 16;
       auto kern = spec ? pcg_cluster_kernel<T, PRE, 64, 16> : pcg_cluster_kernel<T, PRE, 0, 0>;
@@ -933,8 +1044,9 @@ static int run_batch_typed(Ctx* c, const hmpcg_system* sys, const hmpcg_factors*
   for (int i = 0; i < nsys; ++i) {
     const int C = csize[i];
     size_t sm = 0;
-    bool ok = plan_cluster<T, PRE>(&sys[i], PRE == CPRE_HMAT ? &fv[i] : nullptr, C, true, plan[i], sm);
-    if (!ok && PRE == CPRE_HMAT) ok = plan_cluster<T, PRE>(&sys[i], &fv[i], C, false, plan[i], sm);
+    bool ok = plan_cluster<T, PRE>(&sys[i], PRE == CPRE_HMAT ? &fv[i] : nullptr, C, 1, plan[i], sm);
+    if (!ok && PRE == CPRE_HMAT) ok = plan_cluster<T, PRE>(&sys[i], &fv[i], C, 2, plan[i], sm);
+    if (!ok && PRE == CPRE_HMAT) ok = plan_cluster<T, PRE>(&sys[i], &fv[i], C, 0, plan[i], sm);
     if (!ok) return HMPCG_E_SHAPE;
     plan[i].b = b[i]; plan[i].x = x[i]; plan[i].st = c->bst + i;
     plan[i].fallback = (PRE == CPRE_HMAT && o && o->fallback) ? 1 : 0;

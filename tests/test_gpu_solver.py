@@ -342,3 +342,30 @@ def test_pcg_learned_layout_random_spd(ctx, path, dtype):
     assert info.status == h.OK
     assert abs(info.iters - out["iters"]) <= max(2, 0.02 * out["iters"])
     assert _true_rel(a, fr["b"], x.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_pcg_learned_layout_n16384(ctx, path, dtype):
+    """N = 16384 on one cluster: 16 leaves per CTA, so the BF16 leaf blocks live in shared memory
+    without the bridges (swizzled rows, one warp per leaf) and the FP32 ones are read from L2."""
+    fr = inputs.frame("discs2d_16384", 1)
+    ref = grid.assemble(fr["rho"], fr["dims"])
+    n = ref["n"]
+    f = _learned_random(n, 64, 16, seed=9)
+    dinv = 1.0 / ref["diag"]
+    f["g"] = dinv
+    for k in range(n // 64):
+        f["leafblk"][k] *= 0.02 * np.sqrt(dinv[k * 64:(k + 1) * 64])[:, None]
+    f["U"] *= 0.3 * np.sqrt(dinv / n)[:, None]
+    f["V"] *= 0.3 * np.sqrt(dinv / n)[:, None]
+    f["core"] *= 0.3
+    packed, sc, deq = _upload(f, torch.float32 if dtype == "f32" else torch.bfloat16)
+    out, a = _oracle_solve(ref, fr["b"], lambda v: hmatrix.apply(deq, v))
+    assert out["status"] == pcg.OK
+    s = _gpu_system(fr["dims"], fr["rho"])
+    b = torch.from_numpy(fr["b"]).cuda()
+    x = torch.empty_like(b)
+    info = h.solve(ctx, s, h.factors(h.PRE_LEARNED, packed, n, 64, 16, sc), b, x, rtol=1e-6)
+    assert info.status == h.OK
+    assert abs(info.iters - out["iters"]) <= max(2, 0.02 * out["iters"])
+    assert _true_rel(a, fr["b"], x.cpu().numpy()) <= 1e-6
