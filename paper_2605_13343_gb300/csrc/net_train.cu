@@ -278,13 +278,15 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
       ln_bwd(N, T->gY[s], d, a.x_mid, a.mu2, a.rs2, bo.ln2g, bo.ln2b, Tt, T->gx[s], 1, st);
       TR_TRY(linear_bwd(N, T->gx[s], d, a.o, d, Tt, d, d, bo.outw, bo.outb, T->gO[s], 0, st));
       {
-        const dim3 ag((Tt + 63) / 64, h);
+        const int nwh = (Tt / Wn) * h;   // window-heads; a CTA of 4 warps takes 64 / Wn of them
+        const int hpc = 64 / Wn;
+        const dim3 ag((nwh + hpc - 1) / hpc);
         if (Wn == 64)
-          attention_bwd_kernel<64><<<ag, 64, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
+          attention_bwd_mma_kernel<64><<<ag, 128, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
         else if (Wn == 32)
-          attention_bwd_kernel<32><<<ag, 64, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
+          attention_bwd_mma_kernel<32><<<ag, 128, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
         else
-          attention_bwd_kernel<16><<<ag, 64, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
+          attention_bwd_mma_kernel<16><<<ag, 128, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
       }
       {
         const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;

@@ -2,6 +2,7 @@
 // backward, the cosine loss, and the backward of every network layer.
 #pragma once
 #include "net.cuh"
+#include "mma_sync.cuh"
 
 namespace hm {
 namespace {
@@ -621,80 +622,179 @@ __global__ void layernorm_bwd_kernel(const float* __restrict__ dy, int ldy, cons
 }
 
 // ------------------------------------------------------------------ attention backward
-// Two passes per (64-token block, head): pass 1 (thread = query) gives dQ and dbias,
-// pass 2 (thread = key) gives dK and dV; both recompute P from Q, K, bias and lse.
+// Backward of the windowed attention on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
+// accumulators), head dim 32.  Per window-head, with Q scaled by 1/sqrt(32):
+//   pass 1, a warp per 16 query rows:  S = Q K^T + bias, P = exp(S - lse), dP = dO V^T,
+//     D = rowsum(P o dP), dS = P o (dP - D) -> dbias; dQ = dS K / sqrt(32);
+//   pass 2, a warp per 16 key rows (transposed products, P^T recomputed):  dV = P^T dO,
+//     dK = dS^T Q.
+// P, dS and dO are rounded to BF16 as operands of the second products.
 template <int W>
-__global__ void __launch_bounds__(64) attention_bwd_kernel(const bf16* __restrict__ qkv, const float* __restrict__ bias,
-                                                            const float* __restrict__ lse, const float* __restrict__ dout,
-                                                            int T, int d, int h, float* __restrict__ dqkv,
-                                                            float* __restrict__ dbias) {
-  __shared__ float qs[64][33], ks[64][33], vs[64][33], dos[64][33];
-  __shared__ float lses[64], dd[64];
-  const int head = blockIdx.y;
-  const int t0 = blockIdx.x * 64;
-  const int tl = threadIdx.x;
-  const int t = t0 + tl;
-  const int ld = 3 * d;
-  const float scale = 0.17677669529663688f;
-  if (t < T) {
-    for (int c = 0; c < 32; ++c) {
-      qs[tl][c] = __bfloat162float(qkv[(size_t)t * ld + head * 32 + c]) * scale;
-      ks[tl][c] = __bfloat162float(qkv[(size_t)t * ld + d + head * 32 + c]);
-      vs[tl][c] = __bfloat162float(qkv[(size_t)t * ld + 2 * d + head * 32 + c]);
-      dos[tl][c] = dout[(size_t)t * d + head * 32 + c];
+__global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __restrict__ qkv,
+                                                                const float* __restrict__ bias,
+                                                                const float* __restrict__ lse,
+                                                                const float* __restrict__ dout, int T, int d, int h,
+                                                                float* __restrict__ dqkv, float* __restrict__ dbias) {
+  constexpr int WPH = W / 16;                // warps per window-head
+  constexpr int HPC = 4 / WPH;               // window-heads per CTA (4 warps)
+  constexpr int RS = 40;                     // shared row stride in BF16 elements (80 bytes)
+  __shared__ __align__(16) bf16 qs[HPC][W][RS], ks[HPC][W][RS], vs[HPC][W][RS], os[HPC][W][RS];
+  __shared__ float lses[HPC][W], dds[HPC][W];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwh = (T / W) * h;
+  const size_t ld = 3 * (size_t)d;
+  const float scale = 0.17677669529663688f;   // 1 / sqrt(32)
+  // stage Q (scaled), K, V and dO of the CTA's window-heads: 16 parts of 8 values per row
+  for (int q = threadIdx.x; q < HPC * W * 16; q += blockDim.x) {
+    const int slot = q / (W * 16), rem = q % (W * 16), row = rem >> 4, part = rem & 15;
+    const int wh = blockIdx.x * HPC + slot;
+    if (wh >= nwh) continue;
+    const int win = wh / h, head = wh % h;
+    const size_t t = (size_t)win * W + row;
+    const int which = part >> 2, c8 = (part & 3) * 8;
+    uint4 v;
+    if (which < 3) {
+      v = *reinterpret_cast<const uint4*>(qkv + t * ld + which * d + head * 32 + c8);
+      if (which == 0) {
+        __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(hh[e]);
+          hh[e] = __floats2bfloat162_rn(f.x * scale, f.y * scale);
+        }
+      }
+    } else {
+      const float4 a = *reinterpret_cast<const float4*>(dout + t * d + head * 32 + c8);
+      const float4 b = *reinterpret_cast<const float4*>(dout + t * d + head * 32 + c8 + 4);
+      v.x = pack_bf16(a.x, a.y); v.y = pack_bf16(a.z, a.w); v.z = pack_bf16(b.x, b.y); v.w = pack_bf16(b.z, b.w);
     }
-    lses[tl] = lse[(size_t)t * h + head];
+    bf16* dst = which == 0 ? &qs[slot][row][c8] : which == 1 ? &ks[slot][row][c8] : which == 2 ? &vs[slot][row][c8]
+                                                                                           : &os[slot][row][c8];
+    *reinterpret_cast<uint4*>(dst) = v;
+  }
+  for (int q = threadIdx.x; q < HPC * W; q += blockDim.x) {
+    const int slot = q / W, row = q % W;
+    const int wh = blockIdx.x * HPC + slot;
+    if (wh >= nwh) continue;
+    lses[slot][row] = lse[((size_t)(wh / h) * W + row) * h + wh % h];
   }
   __syncthreads();
-  if (t < T) {
-    const int win = t / W, a = t % W, ws = win * W - t0;
-    const float* bp = bias + (((size_t)win * h + head) * W + a) * W;
-    float p[W], dp[W];
-    float D = 0.f;
+  const int slot = warp / WPH, rb = warp % WPH;
+  const int wh = blockIdx.x * HPC + slot;
+  const bool live = wh < nwh;
+  const int win = live ? wh / h : 0, head = live ? wh % h : 0;
+  const int g = lane >> 2, cq = 2 * (lane & 3);
+  const int r0 = rb * 16 + g, r1 = r0 + 8;     // this thread's two rows (queries in pass 1, keys in pass 2)
+  const float* bwh = bias + ((size_t)win * h + head) * W * W;
+  // A fragments (16 rows x 32) of a staged BF16 matrix
+  auto afrag = [&](bf16 (*m)[RS], uint32_t (&a)[2][4]) {
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      float s = bp[j], g = 0.f;
-#pragma unroll
-      for (int c = 0; c < 32; ++c) { s = fmaf(qs[tl][c], ks[ws + j][c], s); g = fmaf(dos[tl][c], vs[ws + j][c], g); }
-      p[j] = __expf(s - lses[tl]);
-      dp[j] = g;
-      D = fmaf(p[j], g, D);
+    for (int kk = 0; kk < 2; ++kk) {
+      a[kk][0] = *reinterpret_cast<const uint32_t*>(&m[r0][16 * kk + cq]);
+      a[kk][1] = *reinterpret_cast<const uint32_t*>(&m[r1][16 * kk + cq]);
+      a[kk][2] = *reinterpret_cast<const uint32_t*>(&m[r0][16 * kk + cq + 8]);
+      a[kk][3] = *reinterpret_cast<const uint32_t*>(&m[r1][16 * kk + cq + 8]);
     }
-    dd[tl] = D;
-    float dq[32];
+  };
+  // C[16 x W] = A[16 x 32] B^T with B the staged W x 32 matrix (B rows = output columns)
+  auto mm_nt = [&](const uint32_t (&a)[2][4], bf16 (*m)[RS], float (&c)[W / 8][4]) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c) dq[c] = 0.f;
-    float* dbp = dbias + (((size_t)win * h + head) * W + a) * W;
+    for (int j = 0; j < W / 8; ++j) {
+      c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const float ds = p[j] * (dp[j] - D);
-      dbp[j] = ds;
-#pragma unroll
-      for (int c = 0; c < 32; ++c) dq[c] = fmaf(ds, ks[ws + j][c], dq[c]);
+      for (int kk = 0; kk < 2; ++kk) {
+        uint32_t b0, b1;
+        ldsm_x2(b0, b1, &m[8 * j + (lane & 7)][16 * kk + ((lane >> 3) & 1) * 8]);
+        mma_bf16(c[j], a[kk], b0, b1);
+      }
     }
-    for (int c = 0; c < 32; ++c) dqkv[(size_t)t * ld + head * 32 + c] = dq[c] * scale;
+  };
+  // C[16 x 32] = X[16 x W] B with X in accumulator layout (rounded to BF16), B the staged W x 32
+  auto mm_nn = [&](const float (&x)[W / 8][4], bf16 (*m)[RS], float (&c)[4][4]) {
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < W / 16; ++kk) {
+      const uint32_t pa[4] = {pack_bf16(x[2 * kk][0], x[2 * kk][1]), pack_bf16(x[2 * kk][2], x[2 * kk][3]),
+                              pack_bf16(x[2 * kk + 1][0], x[2 * kk + 1][1]), pack_bf16(x[2 * kk + 1][2], x[2 * kk + 1][3])};
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        uint32_t b0, b1;
+        ldsm_x2_t(b0, b1, &m[16 * kk + (lane & 15)][8 * nt]);
+        mma_bf16(c[nt], pa, b0, b1);
+      }
+    }
+  };
+  auto store32 = [&](const float (&c)[4][4], int col0, float mul) {
+    const size_t t0 = (size_t)win * W + r0, t1 = t0 + 8;
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      *reinterpret_cast<float2*>(dqkv + t0 * ld + col0 + 8 * nt + cq) = make_float2(c[nt][0] * mul, c[nt][1] * mul);
+      *reinterpret_cast<float2*>(dqkv + t1 * ld + col0 + 8 * nt + cq) = make_float2(c[nt][2] * mul, c[nt][3] * mul);
+    }
+  };
+  float s[W / 8][4], dp[W / 8][4];
+  // ---- pass 1: rows are queries
+  if (live) {
+    uint32_t a[2][4];
+    afrag(qs[slot], a);
+    mm_nt(a, ks[slot], s);
+    afrag(os[slot], a);
+    mm_nt(a, vs[slot], dp);
+    const float l0 = lses[slot][r0], l1 = lses[slot][r1];
+    float D0 = 0.f, D1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < W / 8; ++j) {
+      const float2 b0 = *reinterpret_cast<const float2*>(bwh + (size_t)r0 * W + 8 * j + cq);
+      const float2 b1 = *reinterpret_cast<const float2*>(bwh + (size_t)r1 * W + 8 * j + cq);
+      s[j][0] = __expf(s[j][0] + b0.x - l0); s[j][1] = __expf(s[j][1] + b0.y - l0);
+      s[j][2] = __expf(s[j][2] + b1.x - l1); s[j][3] = __expf(s[j][3] + b1.y - l1);
+      D0 = fmaf(s[j][0], dp[j][0], fmaf(s[j][1], dp[j][1], D0));
+      D1 = fmaf(s[j][2], dp[j][2], fmaf(s[j][3], dp[j][3], D1));
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+      D0 += __shfl_xor_sync(0xffffffffu, D0, o);
+      D1 += __shfl_xor_sync(0xffffffffu, D1, o);
+    }
+    if ((lane & 3) == 0) { dds[slot][r0] = D0; dds[slot][r1] = D1; }
+    float* db = dbias + ((size_t)win * h + head) * W * W;
+#pragma unroll
+    for (int j = 0; j < W / 8; ++j) {
+      s[j][0] *= dp[j][0] - D0; s[j][1] *= dp[j][1] - D0;   // s now holds dS
+      s[j][2] *= dp[j][2] - D1; s[j][3] *= dp[j][3] - D1;
+      *reinterpret_cast<float2*>(db + (size_t)r0 * W + 8 * j + cq) = make_float2(s[j][0], s[j][1]);
+      *reinterpret_cast<float2*>(db + (size_t)r1 * W + 8 * j + cq) = make_float2(s[j][2], s[j][3]);
+    }
+    float c[4][4];
+    mm_nn(s, ks[slot], c);
+    store32(c, head * 32, scale);
   }
   __syncthreads();
-  if (t < T) {
-    const int win = t / W, jj = t % W, ws = win * W - t0;
-    float dk[32], dv[32];
+  // ---- pass 2: rows are keys
+  if (live) {
+    uint32_t a[2][4];
+    afrag(ks[slot], a);
+    mm_nt(a, qs[slot], s);          // S^T
+    afrag(vs[slot], a);
+    mm_nt(a, os[slot], dp);         // dP^T
 #pragma unroll
-    for (int c = 0; c < 32; ++c) { dk[c] = 0.f; dv[c] = 0.f; }
-#pragma unroll 4
-    for (int a = 0; a < W; ++a) {
-      const int q = ws + a;
-      float s = bias[(((size_t)win * h + head) * W + a) * W + jj], g = 0.f;
-#pragma unroll
-      for (int c = 0; c < 32; ++c) { s = fmaf(qs[q][c], ks[tl][c], s); g = fmaf(dos[q][c], vs[tl][c], g); }
-      const float p = __expf(s - lses[q]);
-      const float ds = p * (g - dd[q]);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) { dv[c] = fmaf(p, dos[q][c], dv[c]); dk[c] = fmaf(ds, qs[q][c], dk[c]); }
+    for (int j = 0; j < W / 8; ++j) {
+      const int i0 = 8 * j + cq, i1 = i0 + 1;    // query columns
+      const float e00 = bwh[(size_t)i0 * W + r0], e01 = bwh[(size_t)i1 * W + r0];
+      const float e10 = bwh[(size_t)i0 * W + r1], e11 = bwh[(size_t)i1 * W + r1];
+      const float li0 = lses[slot][i0], li1 = lses[slot][i1];
+      const float Di0 = dds[slot][i0], Di1 = dds[slot][i1];
+      s[j][0] = __expf(s[j][0] + e00 - li0); s[j][1] = __expf(s[j][1] + e01 - li1);
+      s[j][2] = __expf(s[j][2] + e10 - li0); s[j][3] = __expf(s[j][3] + e11 - li1);
+      dp[j][0] = s[j][0] * (dp[j][0] - Di0); dp[j][1] = s[j][1] * (dp[j][1] - Di1);   // dp now holds dS^T
+      dp[j][2] = s[j][2] * (dp[j][2] - Di0); dp[j][3] = s[j][3] * (dp[j][3] - Di1);
     }
-    for (int c = 0; c < 32; ++c) {
-      dqkv[(size_t)t * ld + d + head * 32 + c] = dk[c];
-      dqkv[(size_t)t * ld + 2 * d + head * 32 + c] = dv[c];
-    }
+    float c[4][4];
+    mm_nn(s, os[slot], c);          // dV = P^T dO
+    store32(c, 2 * d + head * 32, 1.f);
+    mm_nn(dp, qs[slot], c);         // dK = dS^T (Q / sqrt(32))
+    store32(c, d + head * 32, 1.f);
   }
 }
 

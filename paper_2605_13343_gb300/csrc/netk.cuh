@@ -1,6 +1,7 @@
 // Forward kernels of the hierarchical transformer (included by net.cu only).
 #pragma once
 #include "net.cuh"
+#include "mma_sync.cuh"
 
 namespace hm {
 namespace {
@@ -475,35 +476,12 @@ __global__ void layernorm_kernel(const float* __restrict__ x, const float* __res
   if (lane == 0) { mu[t] = mean; rs[t] = rstd; }
 }
 
-// Window attention on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulators):
-// per (window, head), S = Q K^T / sqrt(32) + bias, softmax by rows, O = P V (P rounded to BF16
-// for the second product).  A warp owns 16 query rows; K and V of the window-head are staged in
-// shared memory (rows padded to 80 bytes: conflict-free 8x8 matrix loads).  lse = max + log(sum)
-// per row for the backward pass.
-HM_INLINE uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-HM_INLINE void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-               "{%0,%1,%2,%3};"
-               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-HM_INLINE void ldsm_x2(uint32_t& r0, uint32_t& r1, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-               : "=r"(r0), "=r"(r1) : "r"((uint32_t)__cvta_generic_to_shared(p)));
-}
-HM_INLINE void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
-               : "=r"(r0), "=r"(r1) : "r"((uint32_t)__cvta_generic_to_shared(p)));
-}
-
 // Windowed attention of one stack (Sec. 4.2): softmax(Q K^T / sqrt(HD) + bias) V per window of W
-// tokens and head of HD channels, on mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  A
-// warp owns 16 query rows of one window-head; a CTA of NW = max(4, W / 16) warps takes NW / (W / 16)
-// window-heads, their K and V rows staged in shared memory.  lse = log-sum-exp per (token, head)
-// for the backward.
+// tokens and head of HD channels, on mma.sync m16n8k16 (BF16 operands, FP32 accumulation; P
+// rounded to BF16 for the second product).  A warp owns 16 query rows of one window-head; a CTA
+// of NW = max(4, W / 16) warps takes NW / (W / 16) window-heads, their K and V rows staged in
+// shared memory (rows padded by 16 bytes: conflict-free 8x8 matrix loads).  lse = max + log(sum)
+// per (token, head) for the backward.
 template <int W, int HD>
 __global__ void __launch_bounds__(32 * (W / 16 > 4 ? W / 16 : 4)) attention_kernel(
     const bf16* __restrict__ qkv, const float* __restrict__ bias, int T, int d, int h, bf16* __restrict__ out,

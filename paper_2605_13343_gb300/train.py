@@ -208,6 +208,7 @@ def main():
     window = []
     cycle = []
     nfam = len(fam_pools) if fam_pools is not None else 1
+    nsample = min(args.log_every, nfam * max(1, 10 // nfam))
     it_l, it_j, ok = evaluate(ctx, held, rtol)
     rec = dict(step=0, iters_learned=it_l, iters_jacobi=it_j, ok=ok, lr=lr, t=0.0)
     print(json.dumps(rec), flush=True)
@@ -222,11 +223,11 @@ def main():
         else:
             pick = rng.choice(len(small), size=args.batch, replace=False)
             batch = [small[i][0] for i in pick]
-        # the logged loss: the mean over the last nfam steps of each log cycle, one batch of every
-        # scale when training cycles through several (one scale's batch alone would make the
-        # plateau rule react to the scale, not to progress)
+        # the logged loss: the mean over the last `nsample` steps of each log cycle (a multiple of
+        # the number of scales, so that every scale is sampled equally): one batch alone is too
+        # noisy for the plateau rule, and one scale alone would make it react to the scale
         into_cycle = (-step) % args.log_every
-        want = into_cycle < nfam
+        want = into_cycle < nsample
         loss = h.train_step(ctx, batch, args.probes, lr, int(rng.integers(1 << 62)), want_loss=want)
         stop = False
         if want:
