@@ -859,6 +859,20 @@ def bandwidth_rows(h, torch, np, hbm_peak, steps, warmup):
         rows.append({"kernel": "apply_bf16_learned", "n": n, "us": ms * 1e3, "bytes": byts,
                      "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak})
         del pk, r, z
+    # FP8-E4M3 learned factors (one FP32 scale per block) at the largest size
+    n = 1 << 22
+    K = n // 64
+    w = h.packed_width(n, 64, 16, h.PRE_LEARNED)
+    pk8 = (torch.randn(w, device="cuda") * 64.0).clamp(-448, 448).to(torch.float8_e4m3fn)
+    sc8 = torch.full((4 * K + K - 1,), 1e-3, dtype=torch.float32, device="cuda")
+    fac8 = h.factors(h.PRE_LEARNED, pk8, n, 64, 16, sc8)
+    r = torch.randn(n, device="cuda")
+    z = torch.empty_like(r)
+    ms = timeit(lambda: h.apply(ctx, fac8, r, z))
+    byts = w + 4 * sc8.numel() + 12 * n
+    rows.append({"kernel": "apply_fp8_learned", "n": n, "us": ms * 1e3, "bytes": byts,
+                 "GBps": byts / ms / 1e6, "frac": byts / ms / 1e6 / hbm_peak})
+    del pk8, sc8, r, z
     del ctx
     torch.cuda.synchronize()
     return rows
