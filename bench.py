@@ -421,7 +421,8 @@ def main():
             secondary["batch64"] = {"error": str(exc)[:200]}
         try:
             br = bench_barriers(small, h, torch, np, inputs, emit=False)
-            secondary["barriers_rtol1e-8"] = {"weights": br["config"]["weights"], "sizes": br["sizes"]}
+            secondary["barriers_rtol1e-8"] = {"weights": br["config"]["weights"], "sizes": br["sizes"],
+                                              "paper_size_model": br["paper_size_model"]}
         except Exception as exc:
             secondary["barriers_rtol1e-8"] = {"error": str(exc)[:200]}
         torch.cuda.synchronize()
@@ -677,6 +678,38 @@ def bench_barriers(args, h, torch, np, inputs, emit=True, frames_per_size=20):
         rows[str(n)] = out
         del graphs
         torch.cuda.synchronize()
+    # the paper's model size (d 128, 3 layers, 8 heads of 16, leaf 128, rank 32; seeded weights)
+    # on the N = 8192 frames: inference time through the layered kernels (Table S5 reports the
+    # H200's inference at this size and N)
+    paper = None
+    try:
+        pc = dict(d=128, n_layers=3, n_heads=8, d_mlp=512, leaf=128, rank=32)
+        pw = inputs.network_blob(0, **pc)
+        pctx = h.Context(max_n=8192, leaf=128, rank=32, d_model=128, n_layers=3, n_heads=8, d_mlp=512,
+                         max_batch=1, weights=pw)
+        frs = [inputs.frame("barriers2d_8192", s_) for s_ in test_seeds[:5]]
+        psys = []
+        for fr in frs:
+            sg = h.System(fr["dims"])
+            h.assemble(torch.from_numpy(fr["rho"]).cuda(), sg, bc=h.BC_NEUMANN, face=h.FACE_RHO)
+            psys.append(sg)
+        ppk = torch.empty(h.packed_width(8192, 128, 32, h.PRE_LEARNED), dtype=torch.bfloat16, device="cuda")
+        for sg in psys[:2]:
+            h.infer_factors(pctx, [sg], ppk)
+        ts = []
+        for k, sg in enumerate(psys):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.infer_factors(pctx, [sg], ppk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        paper = {"infer_ms_n8192": statistics.mean(ts), "frames": len(ts), "path": "layered kernels",
+                 "config": "d128, 3 layers, 8 heads of 16, leaf 128, rank 32, seeded weights"}
+        pctx.close()
+    except Exception as exc:  # reported, not fatal
+        paper = {"error": str(exc)[:200]}
     line = {"metric": "ms/frame to rtol 1e-8 on the paper's barrier distribution (learned-H vs Jacobi PCG)",
             "value": rows["8192"]["learned"]["ms_per_frame"], "unit": "ms/frame", "n_gpus": 1,
             "steps": frames_per_size, "warmup": 2, "ms_per_step": rows["8192"]["learned"]["ms_per_frame"],
@@ -685,7 +718,7 @@ def bench_barriers(args, h, torch, np, inputs, emit=True, frames_per_size=20):
                                    "5% jitter, zero-flux), N=1024..16384, 20 test frames each (split seed 1), "
                                    "leaf 64 rank 16 d128 4 layers, BF16 factors, rtol 1e-8",
                        "weights": wsrc, "l2": "flushed (256 MiB write) before every frame, outside the timing"},
-            "sizes": rows}
+            "sizes": rows, "paper_size_model": paper}
     ctx.close()
     if emit:
         print(json.dumps(line), flush=True)

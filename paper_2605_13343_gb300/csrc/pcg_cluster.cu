@@ -69,7 +69,7 @@ struct CParams {
 
 // Shared-memory carve-up (byte offsets), identical in every CTA.
 struct CLayout {
-  size_t x, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tv, part, partff, rs, ws, leaf, bridge, gate, core, total;
+  size_t x, b, r, z, q, p0, p1, yd, coef, nbr, wm, uh, tv, part, partff, rs, ws, leaf, bridge, gate, core, total;
 };
 
 // Couplings a CTA's own leaves need: one per (level, cluster of the level) among its lpc leaves,
@@ -83,6 +83,7 @@ __host__ __device__ CLayout c_layout(int npc, int lpc, int tpc, int L, int R, in
   size_t p = 0;
   auto take = [&](size_t bytes) { size_t q = p; p = (p + bytes + 15) / 16 * 16; return q; };
   o.x = take(8 * (size_t)npc);
+  o.b = take(hmat && fsm == 2 ? 0 : 8 * (size_t)npc);   // the leaf-only mode reads b from global memory
   o.r = take(4 * (size_t)npc);
   o.z = take(4 * (size_t)npc);
   o.q = take(4 * (size_t)npc);
@@ -124,6 +125,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   const bool fleaf = P.fsm != 0;        // leaves in shared memory (padded rows, or swizzled with fsm 2)
   const CLayout lay = c_layout<T>(npc, P.lpc, P.tpc, L, R, F.nslot, F.learned != 0, hmat, P.fsm, F.levels);
   double* xs = reinterpret_cast<double*>(sm + lay.x);
+  double* bsm = reinterpret_cast<double*>(sm + lay.b);
   float* rv = reinterpret_cast<float*>(sm + lay.r);
   float* zv = reinterpret_cast<float*>(sm + lay.z);
   float* qv = reinterpret_cast<float*>(sm + lay.q);
@@ -143,6 +145,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   T* sgate = reinterpret_cast<T*>(sm + lay.gate);
   const int tid = threadIdx.x;
   const int n0 = me * npc;
+  const double* bsv = (hmat && P.fsm == 2) ? P.b + n0 : bsm;   // owned b (global memory in the leaf-only mode)
   const int LP = P.fsm == 2 ? L : L + kLeafPad;
   // factor share: shared-memory copies (fsm) or the packed tensor itself (L2-resident)
   const int LPs = fleaf ? LP : L;
@@ -175,6 +178,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   // ---------------- load: owned b, coefficients, factor share
   for (int i = tid; i < npc; i += blockDim.x) {
     const int g = n0 + i;
+    if (!(hmat && P.fsm == 2)) bsm[i] = P.b[g];
     coef[4 * i] = S.diag32[g];
     for (int a = 0; a < 3; ++a) {
       coef[4 * i + 1 + a] = a < S.mo.ndim ? S.w32[a][g] : 0.f;
@@ -646,7 +650,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   // ---------------- init: x = 0, r = b, p = 0, z = M r
   double acc = 0.0;
   for (int i = tid; i < npc; i += blockDim.x) {
-    const double bi = P.b[n0 + i];
+    const double bi = bsv[i];
     xs[i] = 0.0;
     rv[i] = (float)bi;
     pbuf[0][i] = 0.f;
@@ -737,7 +741,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
       float ri;
       if (replace) {
         const double ax = row64(g, xn, [&](int o, int l) { return fma(alpha, (double)gf(pn, o, l), gd(xs, o, l)); });
-        const double rd = P.b[g] - ax;
+        const double rd = bsv[i] - ax;
         ri = (float)rd;
         const double sq = rd * rd;   // the FP64 square, carried as a float-float pair
         const float sh = (float)sq;
@@ -813,7 +817,7 @@ __device__ __forceinline__ void pcg_cluster_body(const CParams<T>& P) {
   for (int i = tid; i < npc; i += blockDim.x) {
     const int g = n0 + i;
     const double ax = row64(g, xs[i], [&](int o, int l) { return gd(xs, o, l); });
-    const double rd = P.b[g] - ax;
+    const double rd = bsv[i] - ax;
     acc = fma(rd, rd, acc);
     P.x[g] = xs[i];
   }
