@@ -89,6 +89,11 @@ constexpr int kWarps = 8;
 HM_INLINE float2 bf2(uint32_t u) {
   return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
 }
+// Two FP8-E4M3 values (low byte first) to float2.
+HM_INLINE float2 f8x2(uint32_t u16) {
+  const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u16 & 0xFFFFu), __NV_E4M3);
+  return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
 
 // Vectorised restriction of one bridge slot (W: 64 x R row-major BF16 = 8R chunks of 16 B).
 // Lane holds chunks c = q*32 + lane (q < R/4): row c / (R/8), columns (lane % (R/8))*8 .. +7.
@@ -587,6 +592,169 @@ __global__ void __launch_bounds__(256) leaf_coupling_kernel(FactorView<__nv_bflo
   }
 }
 
+// ---------------------------------------------------------------- FP8-E4M3 learned factors
+// The learned layout with one FP32 scale per block (leaf block, core, one leaf's rows of a
+// bridge, one leaf's gates), leaf 64, rank 16.  A warp per leaf: the 4 KB leaf block comes in by
+// coalesced 16-byte loads (L2 evict-first) and is stored to shared memory with its 16-byte
+// chunks XOR-swizzled by row pair, chunk c of row i at c ^ ((i >> 1) & 3): a column-pair read
+// touches one 64-byte row, a row read by 8 consecutive lanes touches 8 distinct bank groups.
+constexpr int kR8Warps = 8;
+
+// Sums rows lane and lane + 32 of one bridge block (16 E4M3 values each) times r0, r1 over the
+// warp and stores the 16 results (reduce-scatter over lane bits 16, 8, 4, 2, then bit 1).
+HM_INLINE void restrict8_finish(const uint4 ua, const uint4 ub, float r0, float r1, int lane, float scale,
+                                float* __restrict__ out) {
+  float v[16];
+  const uint32_t wa[4] = {ua.x, ua.y, ua.z, ua.w}, wb[4] = {ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const float2 fa = f8x2(wa[q] >> (16 * hh)), fb = f8x2(wb[q] >> (16 * hh));
+      v[4 * q + 2 * hh] = fmaf(fa.x, r0, fb.x * r1);
+      v[4 * q + 2 * hh + 1] = fmaf(fa.y, r0, fb.y * r1);
+    }
+  }
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+  float a8[8], a4[4], a2[2];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) a8[t] = (h16 ? v[8 + t] : v[t]) + __shfl_xor_sync(0xffffffffu, h16 ? v[t] : v[8 + t], 16);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) a4[t] = (h8 ? a8[4 + t] : a8[t]) + __shfl_xor_sync(0xffffffffu, h8 ? a8[t] : a8[4 + t], 8);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) a2[t] = (h4 ? a4[2 + t] : a4[t]) + __shfl_xor_sync(0xffffffffu, h4 ? a4[t] : a4[2 + t], 4);
+  float a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 2);
+  a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+  if ((lane & 1) == 0) out[(h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0)] = a1 * scale;
+}
+
+__global__ void __launch_bounds__(32 * kR8Warps) apply_fp8_restrict_kernel(FactorView<__nv_fp8_e4m3> f,
+                                                                          const float* __restrict__ r,
+                                                                          float* __restrict__ ydiag,
+                                                                          float* __restrict__ uhat) {
+  pdl_entry();
+  __shared__ __align__(16) uint4 tiles[kR8Warps][256];
+  __shared__ __align__(16) float rstage[kR8Warps][64], wstage[kR8Warps][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4* tile = tiles[warp];
+  const uint8_t* tb = reinterpret_cast<const uint8_t*>(tile);
+  const float4* rs4 = reinterpret_cast<const float4*>(rstage[warp]);
+  const float4* ws4 = reinterpret_cast<const float4*>(wstage[warp]);
+  const uint64_t pol_f = pol_evict_first(), pol_b = pol_evict_last();
+  const int ch_col = lane >> 3, off_col = (2 * lane) & 15;       // the lane's column pair 2 lane, 2 lane + 1
+  for (int k = blockIdx.x * kR8Warps + warp; k < f.K; k += gridDim.x * kR8Warps) {
+    const uint4* src = reinterpret_cast<const uint4*>(f.leaf) + (size_t)k * 256;
+    uint4 lv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) lv[j] = ld_hint(src + 32 * j + lane, pol_f);
+    const uint4* br0 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)k * 64;
+    const uint4* br1 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)f.n + (size_t)k * 64;
+    const uint4 u0a = ld_hint(br0 + lane, pol_b), u0b = ld_hint(br0 + 32 + lane, pol_b);
+    const uint4 u1a = ld_hint(br1 + lane, pol_b), u1b = ld_hint(br1 + 32 + lane, pol_b);
+    const float r0 = r[(size_t)k * 64 + lane], r1 = r[(size_t)k * 64 + 32 + lane];
+    const uint8_t* gt = reinterpret_cast<const uint8_t*>(f.gate) + (size_t)k * 64;
+    const float sg = f.sc_gate[k], sl = f.sc_leaf[k];
+    const float ga = f8x2(gt[lane]).x * sg, gb = f8x2(gt[32 + lane]).x * sg;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = 32 * j + lane, row = c >> 2;
+      tile[row * 4 + ((c & 3) ^ ((row >> 1) & 3))] = lv[j];
+    }
+    rstage[warp][lane] = r0;
+    rstage[warp][32 + lane] = r1;
+    __syncwarp();
+    float2 w = make_float2(0.f, 0.f);                 // (F^T r) for columns 2 lane, 2 lane + 1
+#pragma unroll
+    for (int i4 = 0; i4 < 16; ++i4) {
+      const float4 rv = rs4[i4];
+      const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = 4 * i4 + u;
+        const uint32_t pr = *reinterpret_cast<const uint16_t*>(tb + i * 64 + ((ch_col ^ ((i >> 1) & 3)) << 4) + off_col);
+        w = __ffma2_rn(f8x2(pr), make_float2(rr[u], rr[u]), w);
+      }
+    }
+    reinterpret_cast<float2*>(wstage[warp])[lane] = make_float2(w.x * sl, w.y * sl);
+    __syncwarp();
+    float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);   // rows lane, lane + 32
+    const int swz = (lane >> 1) & 3;                                  // the same for row lane + 32
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 a = tile[lane * 4 + (c ^ swz)];
+      const uint4 b = tile[(lane + 32) * 4 + (c ^ swz)];
+      const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 x = ws4[4 * c + q];                // columns 16 c + 4 q .. + 3
+        ya = __ffma2_rn(f8x2(aw[q]), make_float2(x.x, x.y), ya);
+        ya = __ffma2_rn(f8x2(aw[q] >> 16), make_float2(x.z, x.w), ya);
+        yb = __ffma2_rn(f8x2(bw[q]), make_float2(x.x, x.y), yb);
+        yb = __ffma2_rn(f8x2(bw[q] >> 16), make_float2(x.z, x.w), yb);
+      }
+    }
+    ydiag[(size_t)k * 64 + lane] = fmaf(ga, r0, (ya.x + ya.y) * sl);
+    ydiag[(size_t)k * 64 + 32 + lane] = fmaf(gb, r1, (yb.x + yb.y) * sl);
+    restrict8_finish(u0a, u0b, r0, r1, lane, f.sc_bridge[k], uhat + (size_t)k * 16);
+    restrict8_finish(u1a, u1b, r0, r1, lane, f.sc_bridge[f.K + k], uhat + ((size_t)f.K + k) * 16);
+    __syncwarp();   // the tile and the stages are rewritten for the next leaf
+  }
+}
+
+// Prolongation for FP8 learned factors: z_k = ydiag_k + s_U U~_k a_0 + s_V V~_k a_1, the coupling
+// inputs a_s gathered per level from the tile outputs; leaves in descending order.
+__global__ void __launch_bounds__(32 * kWarps) apply_fp8_prolong_kernel(FactorView<__nv_fp8_e4m3> f,
+                                                                       const float* __restrict__ tcoup,
+                                                                       const float* __restrict__ ydiag,
+                                                                       float* __restrict__ z) {
+  pdl_entry();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t pol = pol_evict_first();
+  for (int kk = blockIdx.x * kWarps + warp; kk < f.K; kk += gridDim.x * kWarps) {
+    const int k = f.K - 1 - kk;
+    const uint4* br0 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)k * 64;
+    const uint4* br1 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)f.n + (size_t)k * 64;
+    const uint4 u0a = ld_hint(br0 + lane, pol), u0b = ld_hint(br0 + 32 + lane, pol);
+    const uint4 u1a = ld_hint(br1 + lane, pol), u1b = ld_hint(br1 + 32 + lane, pol);
+    float y0 = ydiag[(size_t)k * 64 + lane], y1 = ydiag[(size_t)k * 64 + 32 + lane];
+    float tv[24];
+#pragma unroll
+    for (int lev = 1; lev <= 24; ++lev) {
+      tv[lev - 1] = 0.f;
+      if (lev <= f.levels && lane < 16) {
+        const int cl = k >> (f.levels - lev);
+        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+        tv[lev - 1] = __ldg(tcoup + ((size_t)m * 2 + (cl & 1)) * 16 + lane);
+      }
+    }
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int lev = 1; lev <= 24; ++lev)
+      if (lev <= f.levels) {
+        if ((k >> (f.levels - lev)) & 1) a1 += tv[lev - 1]; else a0 += tv[lev - 1];
+      }
+    a0 *= f.sc_bridge[k];
+    a1 *= f.sc_bridge[f.K + k];
+    const uint32_t w0a[4] = {u0a.x, u0a.y, u0a.z, u0a.w}, w0b[4] = {u0b.x, u0b.y, u0b.z, u0b.w};
+    const uint32_t w1a[4] = {u1a.x, u1a.y, u1a.z, u1a.w}, w1b[4] = {u1b.x, u1b.y, u1b.z, u1b.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int e = 4 * q + 2 * hh;
+        const float c0 = __shfl_sync(0xffffffffu, a0, e), c0n = __shfl_sync(0xffffffffu, a0, e + 1);
+        const float c1 = __shfl_sync(0xffffffffu, a1, e), c1n = __shfl_sync(0xffffffffu, a1, e + 1);
+        const float2 p0 = f8x2(w0a[q] >> (16 * hh)), q0 = f8x2(w0b[q] >> (16 * hh));
+        const float2 p1 = f8x2(w1a[q] >> (16 * hh)), q1 = f8x2(w1b[q] >> (16 * hh));
+        y0 = fmaf(p0.x, c0, fmaf(p0.y, c0n, fmaf(p1.x, c1, fmaf(p1.y, c1n, y0))));
+        y1 = fmaf(q0.x, c0, fmaf(q0.y, c0n, fmaf(q1.x, c1, fmaf(q1.y, c1n, y1))));
+      }
+    }
+    z[(size_t)k * 64 + lane] = y0;
+    z[(size_t)k * 64 + 32 + lane] = y1;
+  }
+}
+
 // ---------------------------------------------------------------- blocked strip sums (learned)
 // The coupling stage for learned factors (bridge slot = side) in two passes over blocks of
 // up to 256 consecutive items (leaves, or block totals one level up):
@@ -632,8 +800,8 @@ HM_INLINE float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + 
 // Tile (j, tl) of the block (clusters of 2^j items) is global tile m = 2^(lev-1) - 1 + t with
 // lev = levels - jbase - j and t = (block * 2^jl >> (j + 1)) + tl.  A half-warp computes one
 // tile: lane e < R of it gives t^r[e] (core row e) and t^c[e] (core column e).
-template <int R>
-__global__ void __launch_bounds__(1024) block_up_kernel(FactorView<__nv_bfloat16> f, const float* __restrict__ src,
+template <int R, class T = __nv_bfloat16>
+__global__ void __launch_bounds__(1024) block_up_kernel(FactorView<T> f, const float* __restrict__ src,
                                                         int n_items, int jl, int jbase, float* __restrict__ bsum,
                                                         float* __restrict__ tcoup) {
   static_assert(R <= 16, "one output pair per lane of a half-warp");
@@ -676,32 +844,50 @@ __global__ void __launch_bounds__(1024) block_up_kernel(FactorView<__nv_bfloat16
     const int m = (1 << (f.levels - jbase - j - 1)) - 1 + (i0 >> (j + 1)) + tl;
     const float* sr = sums + (0 * nodes + node_off(nb, j) + 2 * tl) * R;       // row cluster, slot 0
     const float* sc = sums + (1 * nodes + node_off(nb, j) + 2 * tl + 1) * R;   // column cluster, slot 1
-    // the core straight from global memory (row e by 16-byte loads, column e through L1): without
-    // a staged copy the CTA needs only the sums and three CTAs fit an SM
-    const __nv_bfloat16* Bs = f.core + (size_t)m * R * R;
-    const uint4* row = reinterpret_cast<const uint4*>(Bs + e * R);
-    const float4* sc4 = reinterpret_cast<const float4*>(sc);
-    const float4* sr4 = reinterpret_cast<const float4*>(sr);
-    float2 a2 = make_float2(0.f, 0.f);
+    float a2x, tc;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+      // the core straight from global memory (row e by 16-byte loads, column e through L1): without
+      // a staged copy the CTA needs only the sums and two CTAs fit an SM
+      const __nv_bfloat16* Bs = f.core + (size_t)m * R * R;
+      const uint4* row = reinterpret_cast<const uint4*>(Bs + e * R);
+      const float4* sc4 = reinterpret_cast<const float4*>(sc);
+      const float4* sr4 = reinterpret_cast<const float4*>(sr);
+      float2 a2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int c = 0; c < R / 8; ++c) {
-      const uint4 u = __ldg(row + c);
-      const float4 s0 = sc4[2 * c], s1 = sc4[2 * c + 1];
-      a2 = __ffma2_rn(bf2(u.x), make_float2(s0.x, s0.y), a2);
-      a2 = __ffma2_rn(bf2(u.y), make_float2(s0.z, s0.w), a2);
-      a2 = __ffma2_rn(bf2(u.z), make_float2(s1.x, s1.y), a2);
-      a2 = __ffma2_rn(bf2(u.w), make_float2(s1.z, s1.w), a2);
-    }
-    float tc = 0.f;
+      for (int c = 0; c < R / 8; ++c) {
+        const uint4 u = __ldg(row + c);
+        const float4 s0 = sc4[2 * c], s1 = sc4[2 * c + 1];
+        a2 = __ffma2_rn(bf2(u.x), make_float2(s0.x, s0.y), a2);
+        a2 = __ffma2_rn(bf2(u.y), make_float2(s0.z, s0.w), a2);
+        a2 = __ffma2_rn(bf2(u.z), make_float2(s1.x, s1.y), a2);
+        a2 = __ffma2_rn(bf2(u.w), make_float2(s1.z, s1.w), a2);
+      }
+      tc = 0.f;
 #pragma unroll
-    for (int q4 = 0; q4 < Q; ++q4) {
-      const float4 v = sr4[q4];
-      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 0) * R + e)), v.x, tc);
-      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 1) * R + e)), v.y, tc);
-      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 2) * R + e)), v.z, tc);
-      tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 3) * R + e)), v.w, tc);
+      for (int q4 = 0; q4 < Q; ++q4) {
+        const float4 v = sr4[q4];
+        tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 0) * R + e)), v.x, tc);
+        tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 1) * R + e)), v.y, tc);
+        tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 2) * R + e)), v.z, tc);
+        tc = fmaf(__bfloat162float(__ldg(Bs + (4 * q4 + 3) * R + e)), v.w, tc);
+      }
+      a2x = a2.x + a2.y;
+    } else {
+      // FP8-E4M3 core with its block scale: row e and column e as bytes
+      const uint8_t* Bs = reinterpret_cast<const uint8_t*>(f.core) + (size_t)m * R * R;
+      float ar = 0.f, ac = 0.f;
+#pragma unroll
+      for (int c = 0; c < R; c += 2) {
+        const float2 rv = f8x2(*reinterpret_cast<const uint16_t*>(Bs + e * R + c));
+        ar = fmaf(rv.x, sc[c], fmaf(rv.y, sc[c + 1], ar));
+        const float2 cv = make_float2(f8x2(__ldg(Bs + c * R + e)).x, f8x2(__ldg(Bs + (c + 1) * R + e)).x);
+        ac = fmaf(cv.x, sr[c], fmaf(cv.y, sr[c + 1], ac));
+      }
+      const float scb = f.sc_core[m];
+      a2x = ar * scb;
+      tc = ac * scb;
     }
-    tcoup[(size_t)m * 2 * R + e] = a2.x + a2.y;
+    tcoup[(size_t)m * 2 * R + e] = a2x;
     tcoup[(size_t)m * 2 * R + R + e] = tc;
   }
 }
@@ -847,6 +1033,41 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
     case 16: launch_pdl_bw(apply_warp_prolong_kernel<16>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
     default: launch_pdl_bw(apply_warp_prolong_kernel<32>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
   }
+  return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+}
+
+// FP8-E4M3 learned factors, leaf 64, rank 16, enough leaves for the blocked coupling stage:
+// restriction (a warp per leaf), the two block_up passes, prolongation; 1 when not applicable.
+int apply_fp8_launch(Ctx* c, const FactorView<__nv_fp8_e4m3>& f, const float* r, float* z, float* ydiag, float* uhat,
+                     float* tcoup, cudaStream_t st) {
+  if (f.L != 64 || f.r != 16 || !f.learned || f.nslot != 2 || !f.sc_leaf || f.levels > 24) return 1;
+  if (f.K < 2 * kBlk || f.K > kBlk * kBlk || !c->tree || 4LL * f.K * f.r > c->tree_cap) return 1;
+  if ((reinterpret_cast<uintptr_t>(f.leaf) | reinterpret_cast<uintptr_t>(f.bridge)) & 15) return 1;
+  const int nb = f.K / kBlk;
+  float* bsum = c->tree + 2LL * f.K * f.r;
+  int jnb = 0;
+  while ((1 << jnb) < nb) ++jnb;
+  const int parts = std::max(1, std::min(16, nb / 16));
+  auto smem_up = [&](int items) { return (size_t)2 * (2 * items - 1) * f.r * 4; };
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(block_up_kernel<16, __nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return true;
+  });
+  const int gr = std::max(1, std::min((f.K + kR8Warps - 1) / kR8Warps, c->num_sms * 4));
+  const float* r_in = r;
+  launch_pdl_bw(apply_fp8_restrict_kernel, dim3(gr), dim3(32 * kR8Warps), 0, st, f, r_in, ydiag, uhat);
+  float* nobsum = nullptr;
+  const float* up_in = uhat;
+  const float* top_in = bsum;
+  launch_pdl_bw(block_up_kernel<16, __nv_fp8_e4m3>, dim3(nb), dim3(1024), smem_up(kBlk), st, f, up_in, (int)f.K, kBlkLog, 0,
+                bsum, tcoup);
+  launch_pdl_bw(block_up_kernel<16, __nv_fp8_e4m3>, dim3(1, parts), dim3(1024), smem_up(nb), st, f, top_in, nb, jnb,
+                kBlkLog, nobsum, tcoup);
+  const int gp = std::max(1, std::min((f.K + kWarps - 1) / kWarps, c->num_sms * 8));
+  const float* tc_in = tcoup;
+  const float* yd_in = ydiag;
+  launch_pdl_bw(apply_fp8_prolong_kernel, dim3(gp), dim3(32 * kWarps), 0, st, f, tc_in, yd_in, z);
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 

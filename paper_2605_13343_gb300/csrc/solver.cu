@@ -604,6 +604,8 @@ size_t apply_smem_bytes(int L, int R, int nslot) {
   return std::max(a, std::max(b, c)) * sizeof(float);
 }
 
+int apply_fp8_launch(Ctx* c, const FactorView<__nv_fp8_e4m3>& f, const float* r, float* z, float* ydiag, float* uhat,
+                     float* tcoup, cudaStream_t st);
 int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r, float* z, float* ydiag,
                       float* uhat, float* tcoup, cudaStream_t st,
                       void (*tile_launch)(const FactorView<__nv_bfloat16>&, const float*, float*, int, cudaStream_t));
@@ -619,6 +621,10 @@ int launch_apply(Ctx* c, const FactorView<T>& f, const float* r, float* z, cudaS
   if constexpr (std::is_same<T, __nv_bfloat16>::value) {
     // warp-per-leaf kernels for the common BF16, leaf-64 shapes
     const int rc = apply_warp_launch(c, f, r, z, c->s.ydiag, c->s.uhat, c->s.tcoup, st, tile_launch_bf16);
+    if (rc <= 0) return rc;
+  }
+  if constexpr (std::is_same<T, __nv_fp8_e4m3>::value) {
+    const int rc = apply_fp8_launch(c, f, r, z, c->s.ydiag, c->s.uhat, c->s.tcoup, st);
     if (rc <= 0) return rc;
   }
   const size_t smem = apply_smem_bytes(f.L, f.r, f.nslot);
