@@ -701,53 +701,126 @@ __global__ void __launch_bounds__(32 * kR8Warps) apply_fp8_restrict_kernel(Facto
   }
 }
 
-// Prolongation for FP8 learned factors: z_k = ydiag_k + s_U U~_k a_0 + s_V V~_k a_1, the coupling
-// inputs a_s gathered per level from the tile outputs; leaves in descending order.
-__global__ void __launch_bounds__(32 * kWarps) apply_fp8_prolong_kernel(FactorView<__nv_fp8_e4m3> f,
-                                                                       const float* __restrict__ tcoup,
-                                                                       const float* __restrict__ ydiag,
-                                                                       float* __restrict__ z) {
+// Prolongation of the learned layout (rank 16) after the blocked coupling stage, BF16 or FP8:
+// z_k = ydiag_k + U~_k a_0 + V~_k a_1.  A CTA takes 64 consecutive leaves (descending, as the
+// restriction ascends, so recently read bridges hit in L2): the tiles of the levels whose
+// clusters hold all 64 leaves are read once per CTA into shared memory (every leaf would
+// otherwise fetch the same few tile outputs, a hot spot in L2); each warp then gathers the
+// remaining six levels for its leaves.
+template <class T>
+__global__ void __launch_bounds__(256) apply_learned_prolong_kernel(FactorView<T> f, const float* __restrict__ tcoup,
+                                                                    const float* __restrict__ ydiag,
+                                                                    float* __restrict__ z) {
+  constexpr int LPC = 64, kLgLPC = 6;
   pdl_entry();
+  __shared__ float atop[2][16];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t pol = pol_evict_first();
-  for (int kk = blockIdx.x * kWarps + warp; kk < f.K; kk += gridDim.x * kWarps) {
-    const int k = f.K - 1 - kk;
-    const uint4* br0 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)k * 64;
-    const uint4* br1 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)f.n + (size_t)k * 64;
-    const uint4 u0a = ld_hint(br0 + lane, pol), u0b = ld_hint(br0 + 32 + lane, pol);
-    const uint4 u1a = ld_hint(br1 + lane, pol), u1b = ld_hint(br1 + 32 + lane, pol);
-    float y0 = ydiag[(size_t)k * 64 + lane], y1 = ydiag[(size_t)k * 64 + 32 + lane];
+  const int kbase = (gridDim.x - 1 - blockIdx.x) * LPC;
+  const int ntop = f.levels > kLgLPC ? f.levels - kLgLPC : 0;   // levels shared by the whole chunk
+  if (warp == 0 && lane < 16) {
     float tv[24];
 #pragma unroll
     for (int lev = 1; lev <= 24; ++lev) {
       tv[lev - 1] = 0.f;
-      if (lev <= f.levels && lane < 16) {
-        const int cl = k >> (f.levels - lev);
-        const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-        tv[lev - 1] = __ldg(tcoup + ((size_t)m * 2 + (cl & 1)) * 16 + lane);
+      if (lev <= ntop) {
+        const int cl = kbase >> (f.levels - lev);
+        tv[lev - 1] = __ldg(tcoup + (((size_t)(1 << (lev - 1)) - 1 + (cl >> 1)) * 2 + (cl & 1)) * 16 + lane);
       }
     }
-    float a0 = 0.f, a1 = 0.f;
+    float t0 = 0.f, t1 = 0.f;
 #pragma unroll
     for (int lev = 1; lev <= 24; ++lev)
-      if (lev <= f.levels) {
-        if ((k >> (f.levels - lev)) & 1) a1 += tv[lev - 1]; else a0 += tv[lev - 1];
+      if (lev <= ntop) {
+        if ((kbase >> (f.levels - lev)) & 1) t1 += tv[lev - 1]; else t0 += tv[lev - 1];
       }
-    a0 *= f.sc_bridge[k];
-    a1 *= f.sc_bridge[f.K + k];
-    const uint32_t w0a[4] = {u0a.x, u0a.y, u0a.z, u0a.w}, w0b[4] = {u0b.x, u0b.y, u0b.z, u0b.w};
-    const uint32_t w1a[4] = {u1a.x, u1a.y, u1a.z, u1a.w}, w1b[4] = {u1b.x, u1b.y, u1b.z, u1b.w};
+    atop[0][lane] = t0;
+    atop[1][lane] = t1;
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int j = 0; j < LPC / 8; ++j) {
+    const int k = kbase + LPC - 1 - (8 * j + warp);
+    float y0 = ydiag[(size_t)k * 64 + lane], y1 = ydiag[(size_t)k * 64 + 32 + lane];
+    float a0 = 0.f, a1 = 0.f;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+      const uint4* w0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane) * 16);
+      const uint4* w1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)k * 64 + lane + 32) * 16);
+      const uint4* v0 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane) * 16);
+      const uint4* v1 = reinterpret_cast<const uint4*>(f.bridge + ((size_t)f.n + (size_t)k * 64 + lane + 32) * 16);
+      uint4 p0[2], q0[2], p1[2], q1[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+      for (int c = 0; c < 2; ++c) {
+        p0[c] = ld_hint(w0 + c, pol);
+        q0[c] = ld_hint(w1 + c, pol);
+        p1[c] = ld_hint(v0 + c, pol);
+        q1[c] = ld_hint(v1 + c, pol);
+      }
+      if (lane < 16) {
+        float tv[kLgLPC];
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int e = 4 * q + 2 * hh;
-        const float c0 = __shfl_sync(0xffffffffu, a0, e), c0n = __shfl_sync(0xffffffffu, a0, e + 1);
-        const float c1 = __shfl_sync(0xffffffffu, a1, e), c1n = __shfl_sync(0xffffffffu, a1, e + 1);
-        const float2 p0 = f8x2(w0a[q] >> (16 * hh)), q0 = f8x2(w0b[q] >> (16 * hh));
-        const float2 p1 = f8x2(w1a[q] >> (16 * hh)), q1 = f8x2(w1b[q] >> (16 * hh));
-        y0 = fmaf(p0.x, c0, fmaf(p0.y, c0n, fmaf(p1.x, c1, fmaf(p1.y, c1n, y0))));
-        y1 = fmaf(q0.x, c0, fmaf(q0.y, c0n, fmaf(q1.x, c1, fmaf(q1.y, c1n, y1))));
+        for (int q = 0; q < kLgLPC; ++q) {
+          const int lev = ntop + 1 + q;
+          tv[q] = 0.f;
+          if (lev <= f.levels) {
+            const int cl = k >> (f.levels - lev);
+            tv[q] = __ldg(tcoup + (((size_t)(1 << (lev - 1)) - 1 + (cl >> 1)) * 2 + (cl & 1)) * 16 + lane);
+          }
+        }
+        a0 = atop[0][lane];
+        a1 = atop[1][lane];
+#pragma unroll
+        for (int q = 0; q < kLgLPC; ++q) {
+          const int lev = ntop + 1 + q;
+          if (lev <= f.levels) {
+            if ((k >> (f.levels - lev)) & 1) a1 += tv[q]; else a0 += tv[q];
+          }
+        }
+      }
+      prolong_rows<16>(p0, q0, a0, y0, y1);
+      prolong_rows<16>(p1, q1, a1, y0, y1);
+    } else {
+      const uint4* br0 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)k * 64;
+      const uint4* br1 = reinterpret_cast<const uint4*>(f.bridge) + (size_t)f.n + (size_t)k * 64;
+      const uint4 u0a = ld_hint(br0 + lane, pol), u0b = ld_hint(br0 + 32 + lane, pol);
+      const uint4 u1a = ld_hint(br1 + lane, pol), u1b = ld_hint(br1 + 32 + lane, pol);
+      if (lane < 16) {
+        float tv[kLgLPC];
+#pragma unroll
+        for (int q = 0; q < kLgLPC; ++q) {
+          const int lev = ntop + 1 + q;
+          tv[q] = 0.f;
+          if (lev <= f.levels) {
+            const int cl = k >> (f.levels - lev);
+            tv[q] = __ldg(tcoup + (((size_t)(1 << (lev - 1)) - 1 + (cl >> 1)) * 2 + (cl & 1)) * 16 + lane);
+          }
+        }
+        a0 = atop[0][lane];
+        a1 = atop[1][lane];
+#pragma unroll
+        for (int q = 0; q < kLgLPC; ++q) {
+          const int lev = ntop + 1 + q;
+          if (lev <= f.levels) {
+            if ((k >> (f.levels - lev)) & 1) a1 += tv[q]; else a0 += tv[q];
+          }
+        }
+        a0 *= f.sc_bridge[k];
+        a1 *= f.sc_bridge[f.K + k];
+      }
+      const uint32_t w0a[4] = {u0a.x, u0a.y, u0a.z, u0a.w}, w0b[4] = {u0b.x, u0b.y, u0b.z, u0b.w};
+      const uint32_t w1a[4] = {u1a.x, u1a.y, u1a.z, u1a.w}, w1b[4] = {u1b.x, u1b.y, u1b.z, u1b.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int e = 4 * q + 2 * hh;
+          const float c0 = __shfl_sync(0xffffffffu, a0, e), c0n = __shfl_sync(0xffffffffu, a0, e + 1);
+          const float c1 = __shfl_sync(0xffffffffu, a1, e), c1n = __shfl_sync(0xffffffffu, a1, e + 1);
+          const float2 pa = f8x2(w0a[q] >> (16 * hh)), qa = f8x2(w0b[q] >> (16 * hh));
+          const float2 pb = f8x2(w1a[q] >> (16 * hh)), qb = f8x2(w1b[q] >> (16 * hh));
+          y0 = fmaf(pa.x, c0, fmaf(pa.y, c0n, fmaf(pb.x, c1, fmaf(pb.y, c1n, y0))));
+          y1 = fmaf(qa.x, c0, fmaf(qa.y, c0n, fmaf(qb.x, c1, fmaf(qb.y, c1n, y1))));
+        }
       }
     }
     z[(size_t)k * 64 + lane] = y0;
@@ -1028,6 +1101,10 @@ int apply_warp_launch(Ctx* c, const FactorView<__nv_bfloat16>& f, const float* r
   }
   const float* tc_in = tcoup;
   const float* yd_in = ydiag;
+  if (blocked && f.r == 16) {
+    launch_pdl_bw(apply_learned_prolong_kernel<__nv_bfloat16>, dim3(f.K / 64), dim3(256), 0, st, f, tc_in, yd_in, z);
+    return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
+  }
   switch (f.r) {
     case 8: launch_pdl_bw(apply_warp_prolong_kernel<8>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
     case 16: launch_pdl_bw(apply_warp_prolong_kernel<16>, dim3(gridp), dim3(32 * kWarps), 0, st, f, tc_in, acoup, yd_in, z); break;
@@ -1054,7 +1131,7 @@ int apply_fp8_launch(Ctx* c, const FactorView<__nv_fp8_e4m3>& f, const float* r,
     cudaFuncSetAttribute(block_up_kernel<16, __nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     return true;
   });
-  const int gr = std::max(1, std::min((f.K + kR8Warps - 1) / kR8Warps, c->num_sms * 4));
+  const int gr = std::max(1, std::min((f.K + kR8Warps - 1) / kR8Warps, c->num_sms * 6));   // 6 CTAs (48 warps) per SM
   const float* r_in = r;
   launch_pdl_bw(apply_fp8_restrict_kernel, dim3(gr), dim3(32 * kR8Warps), 0, st, f, r_in, ydiag, uhat);
   float* nobsum = nullptr;
@@ -1064,10 +1141,9 @@ int apply_fp8_launch(Ctx* c, const FactorView<__nv_fp8_e4m3>& f, const float* r,
                 bsum, tcoup);
   launch_pdl_bw(block_up_kernel<16, __nv_fp8_e4m3>, dim3(1, parts), dim3(1024), smem_up(nb), st, f, top_in, nb, jnb,
                 kBlkLog, nobsum, tcoup);
-  const int gp = std::max(1, std::min((f.K + kWarps - 1) / kWarps, c->num_sms * 8));
   const float* tc_in = tcoup;
   const float* yd_in = ydiag;
-  launch_pdl_bw(apply_fp8_prolong_kernel, dim3(gp), dim3(32 * kWarps), 0, st, f, tc_in, yd_in, z);
+  launch_pdl_bw(apply_learned_prolong_kernel<__nv_fp8_e4m3>, dim3(f.K / 64), dim3(256), 0, st, f, tc_in, yd_in, z);
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
