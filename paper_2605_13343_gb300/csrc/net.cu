@@ -83,32 +83,46 @@ static bool net_shape_ok(const hmpcg_config& c) {
 bool net_train_shape_ok(const hmpcg_config& c) { return c.d_model / c.n_heads == 32 && c.leaf <= 64; }
 
 
-// One CTA per weight tensor: FP32 master (dense) -> BF16 copy (padded layout).
+// FP32 master (dense) -> BF16 copy (padded layout); CTA (s, y) takes a share of tensor s.
 __global__ void cast_bf16_kernel(const float* __restrict__ a, bf16* __restrict__ b, const int64_t* __restrict__ segs,
                                  int nseg) {
   const int s = blockIdx.x;
   if (s >= nseg) return;
   const int64_t o32 = segs[3 * s], o16 = segs[3 * s + 1], n = segs[3 * s + 2];
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[o16 + i] = __float2bfloat16_rn(a[o32 + i]);
+  for (int64_t i = blockIdx.y * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.y * blockDim.x)
+    b[o16 + i] = __float2bfloat16_rn(a[o32 + i]);
 }
 
-// One CTA per weight matrix: BF16 transposed copy (rows x cols -> cols x rows).
+// FP32 master weights -> transposed BF16 copies (segment s: rows x cols -> cols x rows), by
+// 32 x 32 tiles through shared memory so that reads and writes are both coalesced; CTA (s, y)
+// takes tiles y, y + gridDim.y, ... of segment s.
 __global__ void transpose_w_kernel(const float* __restrict__ a, bf16* __restrict__ b, const int64_t* __restrict__ segs,
                                    int nseg) {
+  __shared__ float tile[32][33];
   const int s = blockIdx.x;
   if (s >= nseg) return;
-  const int64_t o32 = segs[5 * s], o16 = segs[5 * s + 1], n = segs[5 * s + 2], rows = segs[5 * s + 3],
-                cols = segs[5 * s + 4];
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const int64_t rr = i / cols, cc = i % cols;
-    b[o16 + cc * rows + rr] = __float2bfloat16_rn(a[o32 + i]);
+  const int64_t o32 = segs[5 * s], o16 = segs[5 * s + 1], rows = segs[5 * s + 3], cols = segs[5 * s + 4];
+  const int64_t tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int64_t t = blockIdx.y; t < tr * tc; t += gridDim.y) {
+    const int64_t r0 = (t / tc) * 32, c0 = (t % tc) * 32;
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t r = r0 + q, c = c0 + tx;
+      tile[q][tx] = (r < rows && c < cols) ? a[o32 + r * cols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+      const int64_t c = c0 + q, r = r0 + tx;   // output row c, column r
+      if (c < cols && r < rows) b[o16 + c * rows + r] = __float2bfloat16_rn(tile[tx][q]);
+    }
   }
 }
 
 void net_refresh_bf16(Net* N, cudaStream_t st) {
   const int nseg = (int)N->off.seg32.size();
-  cast_bf16_kernel<<<nseg, 256, 0, st>>>(N->w32, N->w16, N->segs, nseg);
-  if (N->w16t) transpose_w_kernel<<<nseg, 256, 0, st>>>(N->w32, N->w16t, N->segs5, nseg);
+  cast_bf16_kernel<<<dim3(nseg, 16), 256, 0, st>>>(N->w32, N->w16, N->segs, nseg);
+  if (N->w16t) transpose_w_kernel<<<dim3(nseg, 16), 256, 0, st>>>(N->w32, N->w16t, N->segs5, nseg);
 }
 
 void net_destroy(Ctx* c);

@@ -991,31 +991,52 @@ __global__ void hwb_rc_kernel(const SysBatch sb, const float* __restrict__ dud, 
   if (t >= sb.B * sb.n) return;
   const int b = t / sb.n, i = t % sb.n;
   const int k = i / sb.L;
-  int toks[32], chs[32];
+  // per level: the tile token whose row (column) chunk holds node i, and 1 / chunk size (a power
+  // of two, so the product equals the division)
+  int toks[24];
+  float ich[24];
   int sides = 0, nl = 0;
-  for (int lev = 1; lev <= sb.levels; ++lev) {
-    const int S = sb.K >> lev;
-    const int cl = k / S;
-    const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-    const int ch = S * sb.L / sb.r;
-    const int a = (i - cl * S * sb.L) / ch;
-    toks[nl] = (b * sb.MH + m) * sb.r + a;
-    chs[nl] = ch;
-    if (cl & 1) sides |= 1 << nl;
-    ++nl;
+#pragma unroll
+  for (int lev = 1; lev <= 24; ++lev) {
+    toks[lev - 1] = 0;
+    ich[lev - 1] = 0.f;
+    if (lev <= sb.levels) {
+      const int S = sb.K >> lev;
+      const int cl = k / S;
+      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+      const int ch = S * sb.L / sb.r;
+      const int a = (i - cl * S * sb.L) / ch;
+      toks[lev - 1] = (b * sb.MH + m) * sb.r + a;
+      ich[lev - 1] = 1.f / (float)ch;
+      if (cl & 1) sides |= 1 << (lev - 1);
+      ++nl;
+    }
   }
   const float nr = (float)(1 + (nl - __popc(sides))), nc = (float)(1 + __popc(sides));
-  for (int c = lane; c < d; c += 32) {
-    float rr = dud[(size_t)t * 4 * d + d + c], cc = dud[(size_t)t * 4 * d + 2 * d + c];
-    for (int q = 0; q < nl; ++q) {
-      if ((sides >> q) & 1) cc += duo[(size_t)toks[q] * 4 * d + 2 * d + c] / chs[q];
-      else rr += duo[(size_t)toks[q] * 4 * d + d + c] / chs[q];
+  // 4 channels per lane per pass; every level's row issued before the sums
+  for (int c = 4 * lane; c < d; c += 128) {
+    const float4* du4 = reinterpret_cast<const float4*>(dud + (size_t)t * 4 * d);
+    float4 rr = du4[(d + c) >> 2], cc = du4[(2 * d + c) >> 2];
+    const float4 own = du4[c >> 2];
+    float4 v[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+      const int off = ((sides >> q) & 1) ? 2 * d : d;
+      v[q] = q < nl ? *reinterpret_cast<const float4*>(duo + (size_t)toks[q] * 4 * d + off + c) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    rr /= nr;
-    cc /= nc;
-    er[(size_t)t * d + c] = rr;
-    ec[(size_t)t * d + c] = cc;
-    dy2d[(size_t)t * d + c] = dud[(size_t)t * 4 * d + c] + rr + cc + dg[(size_t)b * d + c];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+      const float s = ich[q];
+      if ((sides >> q) & 1) { cc.x += v[q].x * s; cc.y += v[q].y * s; cc.z += v[q].z * s; cc.w += v[q].w * s; }
+      else { rr.x += v[q].x * s; rr.y += v[q].y * s; rr.z += v[q].z * s; rr.w += v[q].w * s; }
+    }
+    rr.x /= nr; rr.y /= nr; rr.z /= nr; rr.w /= nr;
+    cc.x /= nc; cc.y /= nc; cc.z /= nc; cc.w /= nc;
+    *reinterpret_cast<float4*>(er + (size_t)t * d + c) = rr;
+    *reinterpret_cast<float4*>(ec + (size_t)t * d + c) = cc;
+    const float4 g = *reinterpret_cast<const float4*>(dg + (size_t)b * d + c);
+    *reinterpret_cast<float4*>(dy2d + (size_t)t * d + c) =
+        make_float4(own.x + rr.x + cc.x + g.x, own.y + rr.y + cc.y + g.y, own.z + rr.z + cc.z + g.z, own.w + rr.w + cc.w + g.w);
   }
 }
 // Highway ablation: the LN2 output's gradient is the first d columns of the FFN-input gradient.
