@@ -80,7 +80,7 @@ static bool net_shape_ok(const hmpcg_config& c) {
          c.leaf >= 16 && c.leaf <= 128 && (c.leaf & (c.leaf - 1)) == 0 && c.rank % 16 == 0 && c.leaf % c.rank == 0 &&
          c.rank <= 32 && c.max_batch >= 1 && c.max_batch <= kMaxSys;
 }
-bool net_train_shape_ok(const hmpcg_config& c) { return c.d_model / c.n_heads == 32 && c.leaf <= 64; }
+bool net_train_shape_ok(const hmpcg_config& c) { return net_shape_ok(c); }
 
 
 // FP32 master (dense) -> BF16 copy (padded layout); CTA (s, y) takes a share of tensor s.

@@ -98,7 +98,8 @@ static int train_alloc(Net* N, int nz) {
   T->dwpart = (float*)alloc(4 * 256 * wide * wide);
   T->part2_cap = 1024 * std::max<int64_t>(wide * 2, d * kFeat + 64);
   T->part2 = (float*)alloc(4 * T->part2_cap);
-  T->edgepart = (float*)alloc(4 * ((std::max(Td * L, To * r) + 127) / 128) * 300);
+  // per-CTA partial gradients of the edge MLP: kEdgeHidden * (4 + 1 + h) + h values each (h <= 8)
+  T->edgepart = (float*)alloc(4 * ((std::max(Td * L, To * r) + 127) / 128) * (kEdgeHidden * 13 + 8));
   T->lnpart = (float*)alloc(4 * ((Tmax + 7) / 8) * 2 * d);
   T->featdw = (float*)alloc(4 * ((Td + 63) / 64) * d * kFeat);
   T->gpart = (double*)alloc(8 * B * ((n + 63) / 64 + (MH * r + 63) / 64) * d);
@@ -175,6 +176,24 @@ static void ln_bwd(Net* N, const float* dy, int ldy, const float* x, const float
 
 #define TR_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
 
+// Attention backward launch: W tokens per window, head dim hd; a CTA of max(4, W / 16) warps.
+static int launch_attention_bwd(int W, int hd, int T, int d, int h, const bf16* qkv, const float* bias, const float* lse,
+                                const float* gO, float* gqkv, float* dbias, cudaStream_t st) {
+  const int nwh = (T / W) * h;
+#define HM_ABWD(WW, HH)                                                                                    \
+  if (W == WW && hd == HH) {                                                                              \
+    constexpr int nw = WW / 16 > 4 ? WW / 16 : 4;                                                          \
+    constexpr int hpc = nw / (WW / 16);                                                                    \
+    attention_bwd_mma_kernel<WW, HH><<<(nwh + hpc - 1) / hpc, 32 * nw, 0, st>>>(qkv, bias, lse, gO, T, d, h, gqkv, \
+                                                                              dbias);                      \
+    return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;                                    \
+  }
+  HM_ABWD(128, 32) HM_ABWD(64, 32) HM_ABWD(32, 32) HM_ABWD(16, 32)
+  HM_ABWD(128, 16) HM_ABWD(64, 16) HM_ABWD(32, 16) HM_ABWD(16, 16)
+#undef HM_ABWD
+  return HMPCG_E_SHAPE;
+}
+
 int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float lr, uint64_t seed, float* loss_out,
                    cudaStream_t st) {
   Net* N = c->net;
@@ -205,7 +224,13 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   // ---- forward, factors, Y = M W, loss
   TR_TRY(net_forward(N, sb, st));
   TR_TRY(net_pack_f32(N, sb, T->pk, st));
-  tapply_restrict_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->w, T->y, T->uh, T->vh);
+  static std::atomic<unsigned long long> attr_rs{0};
+  if (!once_per_device(attr_rs, [] {
+        return cudaFuncSetAttribute(tbwd_restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 33 * 4) ==
+               cudaSuccess;
+      }))
+    return HMPCG_E_CUDA;
+  tapply_restrict_kernel<<<B * sb.K, 256, (size_t)2 * L * 33 * 4, st>>>(sb, nz, T->pk, T->w, T->y, T->uh, T->vh);
   tapply_tile_kernel<<<B * MH, 256, 0, st>>>(sb, nz, T->pk, T->uh, T->vh, T->sr, T->sc, T->tr, T->tc);
   tapply_prolong_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->tr, T->tc, T->y, T->au, T->av);
   if (N->loss_kind == HMPCG_LOSS_SAI) {
@@ -216,7 +241,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
     loss_grad_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->y, T->sums, T->dy);
   }
   // ---- apply backward -> gradient of the packed factors
-  tbwd_restrict_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->w, T->dy, T->dpk, T->qu, T->qv);
+  tbwd_restrict_kernel<<<B * sb.K, 256, (size_t)4 * L * 33 * 4, st>>>(sb, nz, T->pk, T->w, T->dy, T->dpk, T->qu, T->qv);
   tbwd_tile_kernel<<<B * MH, 256, 0, st>>>(sb, nz, T->pk, T->qu, T->qv, T->sr, T->sc, T->dpk, T->ur, T->uc);
   tbwd_prolong_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->w, T->dy, T->au, T->av, T->ur, T->uc, T->dpk);
   // ---- decoder backward
@@ -277,17 +302,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
       const int Wn = s == 0 ? L : r;
       ln_bwd(N, T->gY[s], d, a.x_mid, a.mu2, a.rs2, bo.ln2g, bo.ln2b, Tt, T->gx[s], 1, st);
       TR_TRY(linear_bwd(N, T->gx[s], d, a.o, d, Tt, d, d, bo.outw, bo.outb, T->gO[s], 0, st));
-      {
-        const int nwh = (Tt / Wn) * h;   // window-heads; a CTA of 4 warps takes 64 / Wn of them
-        const int hpc = 64 / Wn;
-        const dim3 ag((nwh + hpc - 1) / hpc);
-        if (Wn == 64)
-          attention_bwd_mma_kernel<64><<<ag, 128, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
-        else if (Wn == 32)
-          attention_bwd_mma_kernel<32><<<ag, 128, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
-        else
-          attention_bwd_mma_kernel<16><<<ag, 128, 0, st>>>(a.qkv, a.bias, a.lse, T->gO[s], Tt, d, h, T->gH[s], T->dbias);
-      }
+      TR_TRY(launch_attention_bwd(Wn, d / h, Tt, d, h, a.qkv, a.bias, a.lse, T->gO[s], T->gH[s], T->dbias, st));
       {
         const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;
         if (s == 0) {

@@ -109,12 +109,14 @@ HM_INLINE PackOff pack_off(const SysBatch& sb) {
 }
 
 // Stage (i) and restriction for leaf (b, k) with nz right-hand sides:
-// y = F (F^T W) + g W;  uh = U~^T W;  vh = V~^T W.   (L <= 64, r <= 32, nz <= 32)
+// y = F (F^T W) + g W;  uh = U~^T W;  vh = V~^T W.   (L <= 128, r <= 32, nz <= 32; dynamic shared
+// memory: 2 L x 33 floats)
 __global__ void tapply_restrict_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
                                        const float* __restrict__ w, float* __restrict__ y,
                                        float* __restrict__ uh, float* __restrict__ vh) {
-  __shared__ float ws[64][33];
-  __shared__ float p1[64][33];
+  extern __shared__ float tsm[];
+  float (*ws)[33] = reinterpret_cast<float (*)[33]>(tsm);
+  float (*p1)[33] = reinterpret_cast<float (*)[33]>(tsm + sb.L * 33);
   const int L = sb.L, r = sb.r;
   const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
   const PackOff o = pack_off(sb);
@@ -323,7 +325,11 @@ __global__ void sai_grad_kernel(const SysBatch sb, int nz, const float* __restri
 __global__ void tbwd_restrict_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
                                      const float* __restrict__ w, const float* __restrict__ gy,
                                      float* __restrict__ dpk, float* __restrict__ qu, float* __restrict__ qv) {
-  __shared__ float ws[64][33], gs[64][33], p1[64][33], p2[64][33];
+  extern __shared__ float tsm[];   // 4 L x 33 floats (L <= 128)
+  float (*ws)[33] = reinterpret_cast<float (*)[33]>(tsm);
+  float (*gs)[33] = reinterpret_cast<float (*)[33]>(tsm + sb.L * 33);
+  float (*p1)[33] = reinterpret_cast<float (*)[33]>(tsm + 2 * sb.L * 33);
+  float (*p2)[33] = reinterpret_cast<float (*)[33]>(tsm + 3 * sb.L * 33);
   const int L = sb.L, r = sb.r;
   const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
   const PackOff o = pack_off(sb);
@@ -623,38 +629,42 @@ __global__ void layernorm_bwd_kernel(const float* __restrict__ dy, int ldy, cons
 
 // ------------------------------------------------------------------ attention backward
 // Backward of the windowed attention on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
-// accumulators), head dim 32.  Per window-head, with Q scaled by 1/sqrt(32):
+// accumulators), windows of W (16 ... 128) tokens, head dim HD (16 or 32).  Per window-head, with
+// Q scaled by 1/sqrt(HD):
 //   pass 1, a warp per 16 query rows:  S = Q K^T + bias, P = exp(S - lse), dP = dO V^T,
-//     D = rowsum(P o dP), dS = P o (dP - D) -> dbias; dQ = dS K / sqrt(32);
+//     D = rowsum(P o dP), dS = P o (dP - D) -> dbias; dQ = dS K / sqrt(HD);
 //   pass 2, a warp per 16 key rows (transposed products, P^T recomputed):  dV = P^T dO,
 //     dK = dS^T Q.
 // P, dS and dO are rounded to BF16 as operands of the second products.
-template <int W>
-__global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __restrict__ qkv,
+template <int W, int HD>
+__global__ void __launch_bounds__(32 * (W / 16 > 4 ? W / 16 : 4)) attention_bwd_mma_kernel(const bf16* __restrict__ qkv,
                                                                 const float* __restrict__ bias,
                                                                 const float* __restrict__ lse,
                                                                 const float* __restrict__ dout, int T, int d, int h,
                                                                 float* __restrict__ dqkv, float* __restrict__ dbias) {
+  static_assert(HD == 16 || HD == 32, "head dims of the tensor-core fragments");
   constexpr int WPH = W / 16;                // warps per window-head
-  constexpr int HPC = 4 / WPH;               // window-heads per CTA (4 warps)
-  constexpr int RS = 40;                     // shared row stride in BF16 elements (80 bytes)
+  constexpr int NW = WPH > 4 ? WPH : 4;      // warps per CTA
+  constexpr int HPC = NW / WPH;              // window-heads per CTA
+  constexpr int RS = HD + 8;                 // shared row stride in BF16 elements (16-byte pad)
+  constexpr int KS = HD / 16, NT = HD / 8, PPR = HD / 8;   // k-steps, n-tiles, 16-byte parts per row
   __shared__ __align__(16) bf16 qs[HPC][W][RS], ks[HPC][W][RS], vs[HPC][W][RS], os[HPC][W][RS];
   __shared__ float lses[HPC][W], dds[HPC][W];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwh = (T / W) * h;
   const size_t ld = 3 * (size_t)d;
-  const float scale = 0.17677669529663688f;   // 1 / sqrt(32)
-  // stage Q (scaled), K, V and dO of the CTA's window-heads: 16 parts of 8 values per row
-  for (int q = threadIdx.x; q < HPC * W * 16; q += blockDim.x) {
-    const int slot = q / (W * 16), rem = q % (W * 16), row = rem >> 4, part = rem & 15;
+  const float scale = HD == 32 ? 0.17677669529663688f : 0.25f;   // 1 / sqrt(HD)
+  // stage Q (scaled), K, V and dO of the CTA's window-heads: 4 PPR parts of 8 values per row
+  for (int q = threadIdx.x; q < HPC * W * 4 * PPR; q += blockDim.x) {
+    const int slot = q / (W * 4 * PPR), rem = q % (W * 4 * PPR), row = rem / (4 * PPR), part = rem % (4 * PPR);
     const int wh = blockIdx.x * HPC + slot;
     if (wh >= nwh) continue;
     const int win = wh / h, head = wh % h;
     const size_t t = (size_t)win * W + row;
-    const int which = part >> 2, c8 = (part & 3) * 8;
+    const int which = part / PPR, c8 = (part % PPR) * 8;
     uint4 v;
     if (which < 3) {
-      v = *reinterpret_cast<const uint4*>(qkv + t * ld + which * d + head * 32 + c8);
+      v = *reinterpret_cast<const uint4*>(qkv + t * ld + which * d + head * HD + c8);
       if (which == 0) {
         __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&v);
 #pragma unroll
@@ -664,8 +674,8 @@ __global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __re
         }
       }
     } else {
-      const float4 a = *reinterpret_cast<const float4*>(dout + t * d + head * 32 + c8);
-      const float4 b = *reinterpret_cast<const float4*>(dout + t * d + head * 32 + c8 + 4);
+      const float4 a = *reinterpret_cast<const float4*>(dout + t * d + head * HD + c8);
+      const float4 b = *reinterpret_cast<const float4*>(dout + t * d + head * HD + c8 + 4);
       v.x = pack_bf16(a.x, a.y); v.y = pack_bf16(a.z, a.w); v.z = pack_bf16(b.x, b.y); v.w = pack_bf16(b.z, b.w);
     }
     bf16* dst = which == 0 ? &qs[slot][row][c8] : which == 1 ? &ks[slot][row][c8] : which == 2 ? &vs[slot][row][c8]
@@ -686,49 +696,49 @@ __global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __re
   const int g = lane >> 2, cq = 2 * (lane & 3);
   const int r0 = rb * 16 + g, r1 = r0 + 8;     // this thread's two rows (queries in pass 1, keys in pass 2)
   const float* bwh = bias + ((size_t)win * h + head) * W * W;
-  // A fragments (16 rows x 32) of a staged BF16 matrix
-  auto afrag = [&](bf16 (*m)[RS], uint32_t (&a)[2][4]) {
+  // A fragments (16 rows x HD) of a staged BF16 matrix
+  auto afrag = [&](bf16 (*m)[RS], uint32_t (&a)[KS][4]) {
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
+    for (int kk = 0; kk < KS; ++kk) {
       a[kk][0] = *reinterpret_cast<const uint32_t*>(&m[r0][16 * kk + cq]);
       a[kk][1] = *reinterpret_cast<const uint32_t*>(&m[r1][16 * kk + cq]);
       a[kk][2] = *reinterpret_cast<const uint32_t*>(&m[r0][16 * kk + cq + 8]);
       a[kk][3] = *reinterpret_cast<const uint32_t*>(&m[r1][16 * kk + cq + 8]);
     }
   };
-  // C[16 x W] = A[16 x 32] B^T with B the staged W x 32 matrix (B rows = output columns)
-  auto mm_nt = [&](const uint32_t (&a)[2][4], bf16 (*m)[RS], float (&c)[W / 8][4]) {
+  // C[16 x W] = A[16 x HD] B^T with B the staged W x HD matrix (B rows = output columns)
+  auto mm_nt = [&](const uint32_t (&a)[KS][4], bf16 (*m)[RS], float (&c)[W / 8][4]) {
 #pragma unroll
     for (int j = 0; j < W / 8; ++j) {
       c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
 #pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
+      for (int kk = 0; kk < KS; ++kk) {
         uint32_t b0, b1;
         ldsm_x2(b0, b1, &m[8 * j + (lane & 7)][16 * kk + ((lane >> 3) & 1) * 8]);
         mma_bf16(c[j], a[kk], b0, b1);
       }
     }
   };
-  // C[16 x 32] = X[16 x W] B with X in accumulator layout (rounded to BF16), B the staged W x 32
-  auto mm_nn = [&](const float (&x)[W / 8][4], bf16 (*m)[RS], float (&c)[4][4]) {
+  // C[16 x HD] = X[16 x W] B with X in accumulator layout (rounded to BF16), B the staged W x HD
+  auto mm_nn = [&](const float (&x)[W / 8][4], bf16 (*m)[RS], float (&c)[NT][4]) {
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+    for (int nt = 0; nt < NT; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < W / 16; ++kk) {
       const uint32_t pa[4] = {pack_bf16(x[2 * kk][0], x[2 * kk][1]), pack_bf16(x[2 * kk][2], x[2 * kk][3]),
                               pack_bf16(x[2 * kk + 1][0], x[2 * kk + 1][1]), pack_bf16(x[2 * kk + 1][2], x[2 * kk + 1][3])};
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
+      for (int nt = 0; nt < NT; ++nt) {
         uint32_t b0, b1;
         ldsm_x2_t(b0, b1, &m[16 * kk + (lane & 15)][8 * nt]);
         mma_bf16(c[nt], pa, b0, b1);
       }
     }
   };
-  auto store32 = [&](const float (&c)[4][4], int col0, float mul) {
+  auto store32 = [&](const float (&c)[NT][4], int col0, float mul) {
     const size_t t0 = (size_t)win * W + r0, t1 = t0 + 8;
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
+    for (int nt = 0; nt < NT; ++nt) {
       *reinterpret_cast<float2*>(dqkv + t0 * ld + col0 + 8 * nt + cq) = make_float2(c[nt][0] * mul, c[nt][1] * mul);
       *reinterpret_cast<float2*>(dqkv + t1 * ld + col0 + 8 * nt + cq) = make_float2(c[nt][2] * mul, c[nt][3] * mul);
     }
@@ -736,7 +746,7 @@ __global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __re
   float s[W / 8][4], dp[W / 8][4];
   // ---- pass 1: rows are queries
   if (live) {
-    uint32_t a[2][4];
+    uint32_t a[KS][4];
     afrag(qs[slot], a);
     mm_nt(a, ks[slot], s);
     afrag(os[slot], a);
@@ -766,14 +776,14 @@ __global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __re
       *reinterpret_cast<float2*>(db + (size_t)r0 * W + 8 * j + cq) = make_float2(s[j][0], s[j][1]);
       *reinterpret_cast<float2*>(db + (size_t)r1 * W + 8 * j + cq) = make_float2(s[j][2], s[j][3]);
     }
-    float c[4][4];
+    float c[NT][4];
     mm_nn(s, ks[slot], c);
-    store32(c, head * 32, scale);
+    store32(c, head * HD, scale);
   }
   __syncthreads();
   // ---- pass 2: rows are keys
   if (live) {
-    uint32_t a[2][4];
+    uint32_t a[KS][4];
     afrag(ks[slot], a);
     mm_nt(a, qs[slot], s);          // S^T
     afrag(vs[slot], a);
@@ -790,11 +800,11 @@ __global__ void __launch_bounds__(128) attention_bwd_mma_kernel(const bf16* __re
       dp[j][0] = s[j][0] * (dp[j][0] - Di0); dp[j][1] = s[j][1] * (dp[j][1] - Di1);   // dp now holds dS^T
       dp[j][2] = s[j][2] * (dp[j][2] - Di0); dp[j][3] = s[j][3] * (dp[j][3] - Di1);
     }
-    float c[4][4];
+    float c[NT][4];
     mm_nn(s, os[slot], c);          // dV = P^T dO
-    store32(c, 2 * d + head * 32, 1.f);
+    store32(c, 2 * d + head * HD, 1.f);
     mm_nn(dp, qs[slot], c);         // dK = dS^T (Q / sqrt(32))
-    store32(c, d + head * 32, 1.f);
+    store32(c, d + head * HD, 1.f);
   }
 }
 
