@@ -224,12 +224,16 @@ enum { HMPCG_INFER_LAYERED = 0, HMPCG_INFER_FUSED = 1 };
 int hmpcg_set_infer_mode(void* ctx, int32_t mode);
 
 /* One optimiser step of the cosine-Hutchinson objective (Sec. 6.1 Eq. 7;
- * Supp. C): n_probes Rademacher probes per system drawn from SplitMix64 keyed
- * by (step_seed, system); W = A Z; Y = M W; loss = mean over systems of
- * 1 - <Z, Y>_F / (||Z||_F ||Y||_F); backward through the apply and the
- * network; global-norm clip to 1; AdamW (beta 0.9/0.999, eps 1e-8, wd 1e-4).
- * If loss_out (host) is non-NULL the stream is synchronised and the mean loss
- * written. */
+ * Supp. C): n_probes probes per system (Rademacher by default, see
+ * hmpcg_set_train_probes) drawn from SplitMix64 keyed by (step_seed, system);
+ * W = A Z; Y = M W; loss = mean over systems of 1 - <Z, Y>_F / (||Z||_F ||Y||_F)
+ * (or the SAI loss, see hmpcg_set_train_loss); backward through the apply and
+ * the network; global-norm clip to 1; AdamW (beta 0.9/0.999, eps 1e-8, wd 1e-4).
+ * n_probes is 1 ... 128 (the paper's K_z = max(64, ceil(sqrt N))), with
+ * 4 max(leaf, rank) (n_probes + 1) floats <= 227 KB of shared memory; the first
+ * call sizes the probe buffers to max(32, n_probes), and a later call with more
+ * probes returns HMPCG_E_SHAPE.  If loss_out (host) is non-NULL the stream is
+ * synchronised and the mean loss written. */
 int hmpcg_train_step(void* ctx, const hmpcg_system* systems, int32_t nsys,
                      int32_t n_probes, float lr, uint64_t step_seed,
                      float* loss_out, void* stream);

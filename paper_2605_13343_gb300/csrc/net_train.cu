@@ -10,6 +10,8 @@
 #include "netb.cuh"
 
 namespace hm {
+constexpr int kMaxProbes = 128;                       // probes per system in one training step
+constexpr size_t kTrainSmemMax = 227 * 1024;          // dynamic shared memory of the multi-RHS apply
 
 struct Train {
   int nz_max;
@@ -59,7 +61,7 @@ static int train_alloc(Net* N, int nz) {
   const int64_t K = n / L, MH = K - 1;
   const int64_t Td = B * n, To = B * MH * r;
   const int64_t P = K * L * L + MH * r * r + 2 * n * r + n;
-  T->nz_max = 32;
+  T->nz_max = std::max(32, nz);   // the first step fixes the probe capacity
   const int64_t nzm = T->nz_max;
   T->z = (float*)alloc(4 * Td * nzm); T->w = (float*)alloc(4 * Td * nzm);
   T->y = (float*)alloc(4 * Td * nzm); T->dy = (float*)alloc(4 * Td * nzm);
@@ -199,9 +201,12 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   Net* N = c->net;
   SysBatch sb;
   TR_TRY(make_batch(N->cfg, systems, nsys, sb));
-  if (nz < 1 || nz > 32 || !net_train_shape_ok(N->cfg)) return HMPCG_E_SHAPE;
+  if (nz < 1 || nz > kMaxProbes || !net_train_shape_ok(N->cfg)) return HMPCG_E_SHAPE;
+  // the multi-RHS apply keeps up to four (L or r) x (nz + 1) FP32 tiles in shared memory
+  if ((size_t)4 * std::max(N->cfg.leaf, N->cfg.rank) * (nz + 1) * 4 > kTrainSmemMax) return HMPCG_E_SHAPE;
   N->num_sms = c->num_sms;
   TR_TRY(train_alloc(N, nz));
+  if (nz > N->tr->nz_max) return HMPCG_E_SHAPE;
   Train* T = N->tr;
   const hmpcg_config& cf = N->cfg;
   const WeightOff& o = N->off;
@@ -226,13 +231,18 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   TR_TRY(net_pack_f32(N, sb, T->pk, st));
   static std::atomic<unsigned long long> attr_rs{0};
   if (!once_per_device(attr_rs, [] {
-        return cudaFuncSetAttribute(tbwd_restrict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 128 * 33 * 4) ==
-               cudaSuccess;
+        bool ok = true;
+        for (const void* k : {(const void*)tapply_restrict_kernel, (const void*)tapply_tile_kernel,
+                              (const void*)tapply_prolong_kernel, (const void*)tbwd_restrict_kernel,
+                              (const void*)tbwd_tile_kernel, (const void*)tbwd_prolong_kernel})
+          ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrainSmemMax) == cudaSuccess;
+        return ok;
       }))
     return HMPCG_E_CUDA;
-  tapply_restrict_kernel<<<B * sb.K, 256, (size_t)2 * L * 33 * 4, st>>>(sb, nz, T->pk, T->w, T->y, T->uh, T->vh);
-  tapply_tile_kernel<<<B * MH, 256, 0, st>>>(sb, nz, T->pk, T->uh, T->vh, T->sr, T->sc, T->tr, T->tc);
-  tapply_prolong_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->pk, T->tr, T->tc, T->y, T->au, T->av);
+  const size_t zs = (size_t)(nz + 1) * 4;   // bytes of one shared-memory row of the multi-RHS tiles
+  tapply_restrict_kernel<<<B * sb.K, 256, 2 * L * zs, st>>>(sb, nz, T->pk, T->w, T->y, T->uh, T->vh);
+  tapply_tile_kernel<<<B * MH, 256, 2 * r * zs, st>>>(sb, nz, T->pk, T->uh, T->vh, T->sr, T->sc, T->tr, T->tc);
+  tapply_prolong_kernel<<<B * sb.K, 256, 2 * r * zs, st>>>(sb, nz, T->pk, T->tr, T->tc, T->y, T->au, T->av);
   if (N->loss_kind == HMPCG_LOSS_SAI) {
     sai_sums_kernel<<<B, 256, 0, st>>>(sb, nz, T->z, T->y, T->sums);
     sai_grad_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->y, T->sums, T->dy);
@@ -241,9 +251,9 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
     loss_grad_kernel<<<(unsigned)((nzt + 255) / 256), 256, 0, st>>>(sb, nz, T->z, T->y, T->sums, T->dy);
   }
   // ---- apply backward -> gradient of the packed factors
-  tbwd_restrict_kernel<<<B * sb.K, 256, (size_t)4 * L * 33 * 4, st>>>(sb, nz, T->pk, T->w, T->dy, T->dpk, T->qu, T->qv);
-  tbwd_tile_kernel<<<B * MH, 256, 0, st>>>(sb, nz, T->pk, T->qu, T->qv, T->sr, T->sc, T->dpk, T->ur, T->uc);
-  tbwd_prolong_kernel<<<B * sb.K, 256, 0, st>>>(sb, nz, T->w, T->dy, T->au, T->av, T->ur, T->uc, T->dpk);
+  tbwd_restrict_kernel<<<B * sb.K, 256, 4 * L * zs, st>>>(sb, nz, T->pk, T->w, T->dy, T->dpk, T->qu, T->qv);
+  tbwd_tile_kernel<<<B * MH, 256, 4 * r * zs, st>>>(sb, nz, T->pk, T->qu, T->qv, T->sr, T->sc, T->dpk, T->ur, T->uc);
+  tbwd_prolong_kernel<<<B * sb.K, 256, 4 * r * zs, st>>>(sb, nz, T->w, T->dy, T->au, T->av, T->ur, T->uc, T->dpk);
   // ---- decoder backward
   pack_bwd_nodes_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, T->dpk, N->gate_logit, T->dfrow, T->dnode,
                                                       T->dnode + (size_t)Td * 2 * r);

@@ -109,40 +109,41 @@ HM_INLINE PackOff pack_off(const SysBatch& sb) {
 }
 
 // Stage (i) and restriction for leaf (b, k) with nz right-hand sides:
-// y = F (F^T W) + g W;  uh = U~^T W;  vh = V~^T W.   (L <= 128, r <= 32, nz <= 32; dynamic shared
-// memory: 2 L x 33 floats)
+// y = F (F^T W) + g W;  uh = U~^T W;  vh = V~^T W.   (Dynamic shared memory: 2 L x (nz + 1)
+// floats.)
 __global__ void tapply_restrict_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
                                        const float* __restrict__ w, float* __restrict__ y,
                                        float* __restrict__ uh, float* __restrict__ vh) {
-  extern __shared__ float tsm[];
-  float (*ws)[33] = reinterpret_cast<float (*)[33]>(tsm);
-  float (*p1)[33] = reinterpret_cast<float (*)[33]>(tsm + sb.L * 33);
+  extern __shared__ float tsm[];   // 2 arrays of L rows x (nz + 1) floats
+  const int ZS = nz + 1;
+  float* ws = tsm + 0 * sb.L * ZS;
+  float* p1 = tsm + 1 * sb.L * ZS;
   const int L = sb.L, r = sb.r;
   const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
   const PackOff o = pack_off(sb);
   const float* P = pk + (size_t)b * o.P;
   const float* F = P + (int64_t)k * L * L;
   const size_t nb = (size_t)b * sb.n + (size_t)k * L;
-  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) ws[q / nz][q % nz] = w[(nb + q / nz) * nz + q % nz];
+  for (int q = threadIdx.x; q < L * nz; q += blockDim.x) ws[(q / nz) * ZS + (q % nz)] = w[(nb + q / nz) * nz + q % nz];
   __syncthreads();
   for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
     const int i = q / nz, c = q % nz;     // p1[i][c] = sum_a F[a][i] W[a][c]
     float s = 0.f;
-    for (int a = 0; a < L; ++a) s = fmaf(F[a * L + i], ws[a][c], s);
-    p1[i][c] = s;
+    for (int a = 0; a < L; ++a) s = fmaf(F[a * L + i], ws[(a) * ZS + (c)], s);
+    p1[(i) * ZS + (c)] = s;
   }
   for (int q = threadIdx.x; q < 2 * r * nz; q += blockDim.x) {
     const int side = q / (r * nz), e = (q / nz) % r, c = q % nz;
     const float* Ub = P + (side ? o.V : o.U) + ((size_t)k * L) * r;
     float s = 0.f;
-    for (int a = 0; a < L; ++a) s = fmaf(Ub[a * r + e], ws[a][c], s);
+    for (int a = 0; a < L; ++a) s = fmaf(Ub[a * r + e], ws[(a) * ZS + (c)], s);
     (side ? vh : uh)[(((size_t)b * sb.K + k) * r + e) * nz + c] = s;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
     const int i = q / nz, c = q % nz;
-    float s = P[o.G + (int64_t)k * L + i] * ws[i][c];
-    for (int a = 0; a < L; ++a) s = fmaf(F[i * L + a], p1[a][c], s);
+    float s = P[o.G + (int64_t)k * L + i] * ws[(i) * ZS + (c)];
+    for (int a = 0; a < L; ++a) s = fmaf(F[i * L + a], p1[(a) * ZS + (c)], s);
     y[(nb + i) * nz + c] = s;
   }
 }
@@ -153,7 +154,10 @@ __global__ void tapply_tile_kernel(const SysBatch sb, int nz, const float* __res
                                    const float* __restrict__ uh, const float* __restrict__ vh,
                                    float* __restrict__ sr_out, float* __restrict__ sc_out,
                                    float* __restrict__ tr, float* __restrict__ tc) {
-  __shared__ float sr[32][33], sc[32][33];
+  extern __shared__ float tsm[];   // 2 arrays of r rows x (nz + 1) floats
+  const int ZS = nz + 1;
+  float* sr = tsm + 0 * sb.r * ZS;
+  float* sc = tsm + 1 * sb.r * ZS;
   const int r = sb.r;
   const int b = blockIdx.x / sb.MH, m = blockIdx.x % sb.MH;
   const TGeo g = tgeo(sb, m);
@@ -167,8 +171,8 @@ __global__ void tapply_tile_kernel(const SysBatch sb, int nz, const float* __res
       a0 += uh[(((size_t)b * sb.K + kr0 + kk) * r + e) * nz + c];
       a1 += vh[(((size_t)b * sb.K + kc0 + kk) * r + e) * nz + c];
     }
-    sr[e][c] = a0;
-    sc[e][c] = a1;
+    sr[(e) * ZS + (c)] = a0;
+    sc[(e) * ZS + (c)] = a1;
     if (sr_out) {
       sr_out[(((size_t)b * sb.MH + m) * r + e) * nz + c] = a0;
       sc_out[(((size_t)b * sb.MH + m) * r + e) * nz + c] = a1;
@@ -179,8 +183,8 @@ __global__ void tapply_tile_kernel(const SysBatch sb, int nz, const float* __res
     const int e = q / nz, c = q % nz;
     float s0 = 0.f, s1 = 0.f;
     for (int f = 0; f < r; ++f) {
-      s0 = fmaf(Bm[e * r + f], sc[f][c], s0);   // (B sc)[e]
-      s1 = fmaf(Bm[f * r + e], sr[f][c], s1);   // (B^T sr)[e]
+      s0 = fmaf(Bm[e * r + f], sc[(f) * ZS + (c)], s0);   // (B sc)[e]
+      s1 = fmaf(Bm[f * r + e], sr[(f) * ZS + (c)], s1);   // (B^T sr)[e]
     }
     tr[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s0;
     tc[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s1;
@@ -206,7 +210,10 @@ HM_INLINE void gather_levels(const SysBatch& sb, int b, int k, int e, int c, int
 __global__ void tapply_prolong_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
                                       const float* __restrict__ tr, const float* __restrict__ tc,
                                       float* __restrict__ y, float* __restrict__ au_out, float* __restrict__ av_out) {
-  __shared__ float au[32][33], av[32][33];
+  extern __shared__ float tsm[];   // 2 arrays of r rows x (nz + 1) floats
+  const int ZS = nz + 1;
+  float* au = tsm + 0 * sb.r * ZS;
+  float* av = tsm + 1 * sb.r * ZS;
   const int L = sb.L, r = sb.r;
   const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
   const PackOff o = pack_off(sb);
@@ -215,8 +222,8 @@ __global__ void tapply_prolong_kernel(const SysBatch sb, int nz, const float* __
     const int e = q / nz, c = q % nz;
     float a0, a1;
     gather_levels(sb, b, k, e, c, nz, tr, tc, a0, a1);
-    au[e][c] = a0;
-    av[e][c] = a1;
+    au[(e) * ZS + (c)] = a0;
+    av[(e) * ZS + (c)] = a1;
     au_out[(((size_t)b * sb.K + k) * r + e) * nz + c] = a0;
     av_out[(((size_t)b * sb.K + k) * r + e) * nz + c] = a1;
   }
@@ -227,7 +234,7 @@ __global__ void tapply_prolong_kernel(const SysBatch sb, int nz, const float* __
     const float* Ur = P + o.U + (nb - (size_t)b * sb.n + i) * r;
     const float* Vr = P + o.V + (nb - (size_t)b * sb.n + i) * r;
     float s = y[(nb + i) * nz + c];
-    for (int e = 0; e < r; ++e) s = fmaf(Ur[e], au[e][c], fmaf(Vr[e], av[e][c], s));
+    for (int e = 0; e < r; ++e) s = fmaf(Ur[e], au[(e) * ZS + (c)], fmaf(Vr[e], av[(e) * ZS + (c)], s));
     y[(nb + i) * nz + c] = s;
   }
 }
@@ -325,11 +332,12 @@ __global__ void sai_grad_kernel(const SysBatch sb, int nz, const float* __restri
 __global__ void tbwd_restrict_kernel(const SysBatch sb, int nz, const float* __restrict__ pk,
                                      const float* __restrict__ w, const float* __restrict__ gy,
                                      float* __restrict__ dpk, float* __restrict__ qu, float* __restrict__ qv) {
-  extern __shared__ float tsm[];   // 4 L x 33 floats (L <= 128)
-  float (*ws)[33] = reinterpret_cast<float (*)[33]>(tsm);
-  float (*gs)[33] = reinterpret_cast<float (*)[33]>(tsm + sb.L * 33);
-  float (*p1)[33] = reinterpret_cast<float (*)[33]>(tsm + 2 * sb.L * 33);
-  float (*p2)[33] = reinterpret_cast<float (*)[33]>(tsm + 3 * sb.L * 33);
+  extern __shared__ float tsm[];   // 4 arrays of L rows x (nz + 1) floats
+  const int ZS = nz + 1;
+  float* ws = tsm + 0 * sb.L * ZS;
+  float* gs = tsm + 1 * sb.L * ZS;
+  float* p1 = tsm + 2 * sb.L * ZS;
+  float* p2 = tsm + 3 * sb.L * ZS;
   const int L = sb.L, r = sb.r;
   const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
   const PackOff o = pack_off(sb);
@@ -338,34 +346,34 @@ __global__ void tbwd_restrict_kernel(const SysBatch sb, int nz, const float* __r
   const float* F = P + (int64_t)k * L * L;
   const size_t nb = (size_t)b * sb.n + (size_t)k * L;
   for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
-    ws[q / nz][q % nz] = w[(nb + q / nz) * nz + q % nz];
-    gs[q / nz][q % nz] = gy[(nb + q / nz) * nz + q % nz];
+    ws[(q / nz) * ZS + (q % nz)] = w[(nb + q / nz) * nz + q % nz];
+    gs[(q / nz) * ZS + (q % nz)] = gy[(nb + q / nz) * nz + q % nz];
   }
   __syncthreads();
   for (int q = threadIdx.x; q < L * nz; q += blockDim.x) {
     const int i = q / nz, c = q % nz;
     float s1 = 0.f, s2 = 0.f;
-    for (int a = 0; a < L; ++a) { s1 = fmaf(F[a * L + i], ws[a][c], s1); s2 = fmaf(F[a * L + i], gs[a][c], s2); }
-    p1[i][c] = s1;
-    p2[i][c] = s2;
+    for (int a = 0; a < L; ++a) { s1 = fmaf(F[a * L + i], ws[(a) * ZS + (c)], s1); s2 = fmaf(F[a * L + i], gs[(a) * ZS + (c)], s2); }
+    p1[(i) * ZS + (c)] = s1;
+    p2[(i) * ZS + (c)] = s2;
   }
   for (int q = threadIdx.x; q < 2 * r * nz; q += blockDim.x) {
     const int side = q / (r * nz), e = (q / nz) % r, c = q % nz;
     const float* Ub = P + (side ? o.V : o.U) + ((size_t)k * L) * r;
     float s = 0.f;
-    for (int a = 0; a < L; ++a) s = fmaf(Ub[a * r + e], gs[a][c], s);
+    for (int a = 0; a < L; ++a) s = fmaf(Ub[a * r + e], gs[(a) * ZS + (c)], s);
     (side ? qv : qu)[(((size_t)b * sb.K + k) * r + e) * nz + c] = s;
   }
   for (int i = threadIdx.x; i < L; i += blockDim.x) {
     float s = 0.f;
-    for (int c = 0; c < nz; ++c) s = fmaf(gs[i][c], ws[i][c], s);
+    for (int c = 0; c < nz; ++c) s = fmaf(gs[(i) * ZS + (c)], ws[(i) * ZS + (c)], s);
     D[o.G + (int64_t)k * L + i] = s;
   }
   __syncthreads();
   for (int q = threadIdx.x; q < L * L; q += blockDim.x) {
     const int i = q / L, j = q % L;
     float s = 0.f;
-    for (int c = 0; c < nz; ++c) s = fmaf(gs[i][c], p1[j][c], fmaf(ws[i][c], p2[j][c], s));
+    for (int c = 0; c < nz; ++c) s = fmaf(gs[(i) * ZS + (c)], p1[(j) * ZS + (c)], fmaf(ws[(i) * ZS + (c)], p2[(j) * ZS + (c)], s));
     D[(int64_t)k * L * L + q] = s;
   }
 }
@@ -375,7 +383,12 @@ __global__ void tbwd_tile_kernel(const SysBatch sb, int nz, const float* __restr
                                  const float* __restrict__ qu, const float* __restrict__ qv,
                                  const float* __restrict__ srs, const float* __restrict__ scs,
                                  float* __restrict__ dpk, float* __restrict__ ur, float* __restrict__ uc) {
-  __shared__ float qr[32][33], qc[32][33], sr[32][33], sc[32][33];
+  extern __shared__ float tsm[];   // 4 arrays of r rows x (nz + 1) floats
+  const int ZS = nz + 1;
+  float* qr = tsm + 0 * sb.r * ZS;
+  float* qc = tsm + 1 * sb.r * ZS;
+  float* sr = tsm + 2 * sb.r * ZS;
+  float* sc = tsm + 3 * sb.r * ZS;
   const int r = sb.r;
   const int b = blockIdx.x / sb.MH, m = blockIdx.x % sb.MH;
   const TGeo g = tgeo(sb, m);
@@ -389,24 +402,24 @@ __global__ void tbwd_tile_kernel(const SysBatch sb, int nz, const float* __restr
       a0 += qu[(((size_t)b * sb.K + kr0 + kk) * r + e) * nz + c];
       a1 += qv[(((size_t)b * sb.K + kc0 + kk) * r + e) * nz + c];
     }
-    qr[e][c] = a0;
-    qc[e][c] = a1;
-    sr[e][c] = srs[(((size_t)b * sb.MH + m) * r + e) * nz + c];
-    sc[e][c] = scs[(((size_t)b * sb.MH + m) * r + e) * nz + c];
+    qr[(e) * ZS + (c)] = a0;
+    qc[(e) * ZS + (c)] = a1;
+    sr[(e) * ZS + (c)] = srs[(((size_t)b * sb.MH + m) * r + e) * nz + c];
+    sc[(e) * ZS + (c)] = scs[(((size_t)b * sb.MH + m) * r + e) * nz + c];
   }
   __syncthreads();
   for (int q = threadIdx.x; q < r * r; q += blockDim.x) {
     const int e = q / r, f = q % r;
     float s = 0.f;
-    for (int c = 0; c < nz; ++c) s = fmaf(qr[e][c], sc[f][c], fmaf(sr[e][c], qc[f][c], s));
+    for (int c = 0; c < nz; ++c) s = fmaf(qr[(e) * ZS + (c)], sc[(f) * ZS + (c)], fmaf(sr[(e) * ZS + (c)], qc[(f) * ZS + (c)], s));
     dpk[(size_t)b * o.P + o.B + (int64_t)m * r * r + q] = s;
   }
   for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
     const int e = q / nz, c = q % nz;
     float s0 = 0.f, s1 = 0.f;
     for (int f = 0; f < r; ++f) {
-      s0 = fmaf(Bm[e * r + f], qc[f][c], s0);
-      s1 = fmaf(Bm[f * r + e], qr[f][c], s1);
+      s0 = fmaf(Bm[e * r + f], qc[(f) * ZS + (c)], s0);
+      s1 = fmaf(Bm[f * r + e], qr[(f) * ZS + (c)], s1);
     }
     ur[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s0;
     uc[(((size_t)b * sb.MH + m) * r + e) * nz + c] = s1;
@@ -419,18 +432,23 @@ __global__ void tbwd_prolong_kernel(const SysBatch sb, int nz, const float* __re
                                     const float* __restrict__ gy, const float* __restrict__ au_s,
                                     const float* __restrict__ av_s, const float* __restrict__ ur,
                                     const float* __restrict__ uc, float* __restrict__ dpk) {
-  __shared__ float au[32][33], av[32][33], bu[32][33], bv[32][33];
+  extern __shared__ float tsm[];   // 4 arrays of r rows x (nz + 1) floats
+  const int ZS = nz + 1;
+  float* au = tsm + 0 * sb.r * ZS;
+  float* av = tsm + 1 * sb.r * ZS;
+  float* bu = tsm + 2 * sb.r * ZS;
+  float* bv = tsm + 3 * sb.r * ZS;
   const int L = sb.L, r = sb.r;
   const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
   const PackOff o = pack_off(sb);
   for (int q = threadIdx.x; q < r * nz; q += blockDim.x) {
     const int e = q / nz, c = q % nz;
-    au[e][c] = au_s[(((size_t)b * sb.K + k) * r + e) * nz + c];
-    av[e][c] = av_s[(((size_t)b * sb.K + k) * r + e) * nz + c];
+    au[(e) * ZS + (c)] = au_s[(((size_t)b * sb.K + k) * r + e) * nz + c];
+    av[(e) * ZS + (c)] = av_s[(((size_t)b * sb.K + k) * r + e) * nz + c];
     float b0, b1;
     gather_levels(sb, b, k, e, c, nz, ur, uc, b0, b1);
-    bu[e][c] = b0;
-    bv[e][c] = b1;
+    bu[(e) * ZS + (c)] = b0;
+    bv[(e) * ZS + (c)] = b1;
   }
   __syncthreads();
   const size_t nb = (size_t)b * sb.n + (size_t)k * L;
@@ -440,8 +458,8 @@ __global__ void tbwd_prolong_kernel(const SysBatch sb, int nz, const float* __re
     float su = 0.f, sv = 0.f;
     for (int c = 0; c < nz; ++c) {
       const float gg = gy[(nb + i) * nz + c], ww = w[(nb + i) * nz + c];
-      su = fmaf(gg, au[e][c], fmaf(ww, bu[e][c], su));
-      sv = fmaf(gg, av[e][c], fmaf(ww, bv[e][c], sv));
+      su = fmaf(gg, au[(e) * ZS + (c)], fmaf(ww, bu[(e) * ZS + (c)], su));
+      sv = fmaf(gg, av[(e) * ZS + (c)], fmaf(ww, bv[(e) * ZS + (c)], sv));
     }
     D[o.U + ((int64_t)k * L + i) * r + e] = su;
     D[o.V + ((int64_t)k * L + i) * r + e] = sv;

@@ -87,7 +87,9 @@ LOSS_TOL = 1e-2
     (CFG3, (16, 16, 16), [5, 6], 16, "gaussian", "cosine", True),
     (CFG3, (16, 16, 16), [3, 4], 16, "rademacher", "sai", True),
     (CFG3, (16, 16, 16), [3, 4], 16, "rademacher", "cosine", False),
-    (PAPER, (64, 64), [3], 16, "rademacher", "cosine", True)])
+    (PAPER, (64, 64), [3], 16, "rademacher", "cosine", True),
+    # the paper's probe objective as printed: K_z = max(64, sqrt(4096)) = 64 smoothed Gaussian probes
+    (CFG3, (16, 16, 16), [3, 4], 64, "gaussian", "cosine", True)])
 def test_train_step_gradient_parity(cfg, dims, seeds, nz, probes, loss_kind, highway):
     # The paper-size network (rank 32) forms tile cores B_m = U_m V_m^T whose entries cancel: on
     # 2D frames the ratio ||(|U_m||V_m|^T)|| / ||U_m V_m^T|| is 4.3, 14.9 and 20.0 on systems 3, 4
