@@ -363,6 +363,22 @@ static int gemm(const bf16* A, int lda, const bf16* Bw, int M, int Nn, int Kk, c
 
 #define NET_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
 
+// Row and column highways of the diagonal tokens: one CTA per leaf with the leaf's gathered
+// tile tokens staged in shared memory.
+static int launch_highway_rc(const SysBatch& sb, const float* yd, const float* yo, int d, float* rhw, float* chw,
+                             bf16* ud, cudaStream_t st) {
+  const size_t sm = (size_t)leaf_level_rows(sb.L, sb.r, sb.levels) * d * sizeof(float);
+  if (sb.levels > 24 || d % 4 || sm > (size_t)kLeafGatherSmemMax) return HMPCG_E_SHAPE;
+  static std::atomic<unsigned long long> attr{0};
+  if (!once_per_device(attr, [] {
+        return cudaFuncSetAttribute(highway_rc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kLeafGatherSmemMax) == cudaSuccess;
+      }))
+    return HMPCG_E_CUDA;
+  pdl_launch(highway_rc_kernel, dim3(sb.B * sb.K), dim3(256), sm, st, sb, yd, yo, d, rhw, chw, ud);
+  return HMPCG_OK;
+}
+
 int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
   const hmpcg_config& cf = N->cfg;
   const WeightOff& o = N->off;
@@ -476,7 +492,7 @@ int net_forward(Net* N, const SysBatch& sb, cudaStream_t st) {
       pdl_launch(concat_g_kernel, dim3((Td + 7) / 8), dim3(256), 0, sO, N->gmean, n, Td, d, ad.u);
     }
     if (N->use_highways) {
-      pdl_launch(highway_rc_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u);
+      NET_TRY(launch_highway_rc(sb, ad.y2f, ao.y2f, d, N->rhw, N->chw, ad.u, st));
     } else {
       // ablation: the FFN reads [y, 0, 0, 0]
       pdl_launch(hw_zero_kernel, dim3((Td + 7) / 8), dim3(256), 0, st, Td, d, ad.u);

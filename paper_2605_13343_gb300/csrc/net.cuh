@@ -165,6 +165,56 @@ struct SysBatch {
 int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, SysBatch& sb);
 bool net_train_shape_ok(const hmpcg_config& c);
 
+// ---- the tile tokens one leaf's diagonal tokens gather (Sec. 4.2 pooling, Sec. 4.3 highways)
+// At level lev the leaf k lies in cluster cl = k >> (levels - lev) of S = K >> lev leaves; the
+// tile of that level is m = 2^(lev-1) - 1 + (cl >> 1), and the leaf's cluster is its row cluster
+// (cl even) or its column cluster (cl odd).  Node i of the cluster falls in chunk
+// a = (i - cl S L) / ch of the tile's tokens, ch = S L / r.  The leaf's L nodes cover the chunks
+// a0 .. a0 + na - 1 (na = max(1, L / ch)), so a CTA that owns a leaf stages those na token rows of
+// every level once and its L tokens read them from shared memory.
+struct LeafLevels {
+  int row0[25];    // first staged row of each level; row0[levels] = rows in all
+  int src[24];     // token index of the level's chunk a0 within the off-diagonal stack
+  int off[24];     // the leaf's first node relative to its cluster's first node
+  int lgch[24];    // log2 of the chunk size ch
+  unsigned side;   // bit lev - 1: the leaf's cluster is the column cluster of the level's tile
+};
+// staged rows per leaf (the same for every leaf of a batch)
+constexpr int kLeafGatherSmemMax = 112 * 1024;   // dynamic shared memory of the leaf-gather kernels
+inline int leaf_level_rows(int L, int r, int levels) {
+  int rows = 0;
+  for (int lev = 1; lev <= levels; ++lev) {
+    const long ch = ((long)L << (levels - lev)) / r;
+    rows += ch >= L ? 1 : (int)(L / ch);
+  }
+  return rows;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void leaf_levels(const SysBatch& sb, int b, int k, LeafLevels& g) {
+  const int lgL = 31 - __clz(sb.L), lgr = 31 - __clz(sb.r);
+  int rows = 0;
+  g.side = 0u;
+  for (int lev = 1; lev <= sb.levels; ++lev) {
+    const int lgS = sb.levels - lev;
+    const int cl = k >> lgS;
+    const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
+    const int lgch = lgS + lgL - lgr;
+    const int off = (k - (cl << lgS)) << lgL;
+    g.row0[lev - 1] = rows;
+    g.src[lev - 1] = (b * sb.MH + m) * sb.r + (off >> lgch);
+    g.off[lev - 1] = off;
+    g.lgch[lev - 1] = lgch;
+    if (cl & 1) g.side |= 1u << (lev - 1);
+    rows += lgch >= lgL ? 1 : (sb.L >> lgch);
+  }
+  g.row0[sb.levels] = rows;
+}
+// staged row of level index q (0-based) for the leaf's node kk
+__device__ __forceinline__ int leaf_level_row(const LeafLevels& g, int q, int kk) {
+  return g.row0[q] + ((g.off[q] + kk) >> g.lgch[q]) - (g.off[q] >> g.lgch[q]);
+}
+#endif
+
 // ---- fused inference layers (net_fused.cu): one stack's buffers and parameters of one layer
 struct FusedStack {
   const float* x_in;      // residual stream entering the layer [T][d]

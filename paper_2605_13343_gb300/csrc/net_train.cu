@@ -133,12 +133,16 @@ static void reduce_parts(Train* T, const float* part, int nparts, int64_t n, flo
 // grad[woff] = dY^T x (split-K tensor-core GEMM over tokens), grad[boff] = colsum(dY),
 // dX (FP32 [T][Kin], may accumulate) = dY W (tensor-core GEMM with the transposed weight).
 static int linear_bwd(Net* N, const float* dY, int ldy, const bf16* X, int ldx, int Tn, int Nout, int Kin,
-                      int64_t woff, int64_t boff, float* dX, int accumulate, cudaStream_t st) {
+                      int64_t woff, int64_t boff, float* dX, int accumulate, cudaStream_t st,
+                      const bf16* gelu_pre = nullptr) {
   Train* T = N->tr;
   const int tb = (Tn + 63) / 64;
-  prep_dy_kernel<<<dim3(tb, (Nout + 63) / 64), 256, 0, st>>>(dY, ldy, Tn, Nout, T->d16, T->d16t, T->colpart);
+  const int vdy = ((uintptr_t)dY % 16 == 0 && ldy % 4 == 0 && Nout % 4 == 0 && (uintptr_t)gelu_pre % 8 == 0) ? 1 : 0;
+  prep_dy_kernel<<<dim3(tb, (Nout + 63) / 64), 256, 0, st>>>(dY, ldy, Tn, Nout, gelu_pre, T->d16, T->d16t,
+                                                             T->colpart, vdy);
   if (boff >= 0) reduce_parts(T, T->colpart, tb, Nout, N->grad + boff, 0, st);
-  transpose_bf16_kernel<<<dim3(tb, (Kin + 63) / 64), 256, 0, st>>>(X, ldx, Tn, Kin, T->xt);
+  const int vx = ((uintptr_t)X % 16 == 0 && ldx % 8 == 0 && Kin % 8 == 0) ? 1 : 0;
+  transpose_bf16_kernel<<<dim3(tb, (Kin + 63) / 64), 256, 0, st>>>(X, ldx, Tn, Kin, T->xt, vx);
   {
     GemmArgs g;
     g.A = T->d16t; g.lda = Tn; g.B = T->xt; g.ldb = Tn;
@@ -239,6 +243,17 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
         return ok;
       }))
     return HMPCG_E_CUDA;
+  // leaf-gather kernels of the highway and pooling backward: the leaf's tile-token slices
+  const size_t lg_smem = (size_t)leaf_level_rows(L, r, sb.levels) * N->cfg.d_model * sizeof(float);
+  if (sb.levels > 24 || lg_smem > (size_t)kLeafGatherSmemMax) return HMPCG_E_SHAPE;
+  static std::atomic<unsigned long long> attr_lg{0};
+  if (!once_per_device(attr_lg, [] {
+        bool ok = true;
+        for (const void* k : {(const void*)hwb_rc_kernel, (const void*)pool_bwd_kernel})
+          ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeafGatherSmemMax) == cudaSuccess;
+        return ok;
+      }))
+    return HMPCG_E_CUDA;
   const size_t zs = (size_t)(nz + 1) * 4;   // bytes of one shared-memory row of the multi-RHS tiles
   tapply_restrict_kernel<<<B * sb.K, 256, 2 * L * zs, st>>>(sb, nz, T->pk, T->w, T->y, T->uh, T->vh);
   tapply_tile_kernel<<<B * MH, 256, 2 * r * zs, st>>>(sb, nz, T->pk, T->uh, T->vh, T->sr, T->sc, T->tr, T->tc);
@@ -262,8 +277,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   float* dyf0 = T->gY[0];
   float* dyf1 = T->gY[1];
   TR_TRY(linear_bwd(N, T->dfrow, L, N->leafh, d, Td, L, d, o.leaf2w, o.leaf2b, T->gT, 0, st));
-  gelu_bwd_kernel<<<(unsigned)(((int64_t)Td * d + 255) / 256), 256, 0, st>>>(T->gT, N->leafhpre, (int64_t)Td * d);
-  TR_TRY(linear_bwd(N, T->gT, d, N->yf[0], d, Td, d, d, o.leaf1w, o.leaf1b, dyf0, 0, st));
+  TR_TRY(linear_bwd(N, T->gT, d, N->yf[0], d, Td, d, d, o.leaf1w, o.leaf1b, dyf0, 0, st, N->leafhpre));
   // node head: rows 0..2r-1 (U~, V~) by GEMMs, row 2r (gate) by small kernels
   TR_TRY(linear_bwd(N, T->dnode, 2 * r, N->yf[0], d, Td, 2 * r, d, o.nodew, o.nodeb, nullptr, 0, st));
   small_dx_kernel<<<(unsigned)(((int64_t)Td * d + 255) / 256), 256, 0, st>>>(T->dnode, 2 * r, N->w32 + o.nodew, Td,
@@ -291,8 +305,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
       const BlockOff& bo = o.blk[s][l];
       const int Tt = s == 0 ? Td : To;
       TR_TRY(linear_bwd(N, T->gx[s], d, a.hact, dm, Tt, d, dm, bo.f2w, bo.f2b, T->gH[s], 0, st));
-      gelu_bwd_kernel<<<(unsigned)(((int64_t)Tt * dm + 255) / 256), 256, 0, st>>>(T->gH[s], a.hpre, (int64_t)Tt * dm);
-      TR_TRY(linear_bwd(N, T->gH[s], dm, a.u, 4 * d, Tt, dm, 4 * d, bo.f1w, bo.f1b, T->gU[s], 0, st));
+      TR_TRY(linear_bwd(N, T->gH[s], dm, a.u, 4 * d, Tt, dm, 4 * d, bo.f1w, bo.f1b, T->gU[s], 0, st, a.hpre));
     }
     if (!N->use_highways) {
       // highway ablation: the highway slices of the FFN input are constants, only y gets a gradient
@@ -302,7 +315,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
       const int nch_d = (n + 63) / 64, nch_o = (MH * r + 63) / 64;
       hwb_g_partial_kernel<<<dim3(nch_d + nch_o, B), 128, 0, st>>>(sb, T->gU[0], T->gU[1], d, nch_d, nch_o, T->gpart);
       hwb_g_final_kernel<<<B, 128, 0, st>>>(sb, T->gpart, d, nch_d + nch_o, T->dgh);
-      hwb_rc_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, T->gU[0], T->gU[1], T->dgh, d, T->er, T->ec, T->gY[0]);
+      hwb_rc_kernel<<<B * sb.K, 256, lg_smem, st>>>(sb, T->gU[0], T->gU[1], T->dgh, d, T->er, T->ec, T->gY[0]);
       hwb_off_kernel<<<To, 128, 0, st>>>(sb, T->gU[1], T->er, T->ec, T->dgh, d, T->gY[1]);
     }
     for (int s = 0; s < 2; ++s) {
@@ -341,11 +354,11 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   }
   // ---- pool, GCN, encoder
   TR_TRY(linear_bwd(N, T->gx[1], d, N->pooled, 2 * d, To, d, 2 * d, o.poolw, o.poolb, T->gP, 0, st));
-  pool_bwd_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, T->gP, d, T->gx[0]);
+  pool_bwd_kernel<<<B * sb.K, 256, lg_smem, st>>>(sb, T->gP, d, T->gx[0]);
   for (int g = 1; g >= 0; --g) {
-    cudaMemcpyAsync(T->gT, T->gx[0], sizeof(float) * (size_t)Td * d, cudaMemcpyDeviceToDevice, st);
-    gelu_bwd_kernel<<<(unsigned)(((int64_t)Td * d + 255) / 256), 256, 0, st>>>(T->gT, N->gpre[g], (int64_t)Td * d);
-    TR_TRY(linear_bwd(N, T->gT, d, N->pm[g], d, Td, d, d, o.gcnw[g], o.gcnb[g], T->gM, 0, st));
+    // the GELU branch's gradient gx0 * GELU'(pre) is formed inside the linear backward; gx0 itself
+    // carries on along the residual path and receives P^T (W^T ...) below
+    TR_TRY(linear_bwd(N, T->gx[0], d, N->pm[g], d, Td, d, d, o.gcnw[g], o.gcnb[g], T->gM, 0, st, N->gpre[g]));
     prop_t_kernel<<<(Td + 7) / 8, 256, 0, st>>>(sb, T->gM, d, T->gx[0]);
   }
   TR_TRY(linear_bwd(N, T->gx[0], d, N->h1, d, Td, d, d, o.enc2w, o.enc2b, T->gT, 0, st));

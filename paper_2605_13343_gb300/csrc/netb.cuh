@@ -11,6 +11,12 @@ HM_INLINE float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.7071067811
 HM_INLINE float gelu_grad(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
 }
+// GELU and its derivative from one erf evaluation
+HM_INLINE void gelu_both(float x, float& y, float& dy) {
+  const float e = 1.f + erff(x * 0.70710678118654752f);
+  y = 0.5f * x * e;
+  dy = 0.5f * e + x * 0.3989422804014327f * expf(-0.5f * x * x);
+}
 HM_INLINE unsigned compactb(unsigned v, unsigned mask) {
   unsigned out = 0, bit = 0;
   while (mask) {
@@ -516,38 +522,119 @@ __global__ void pack_bwd_tiles_kernel(const SysBatch sb, const float* __restrict
 
 // ------------------------------------------------------------------ generic helpers
 // dY (FP32, T x N, row stride ldy) -> BF16 copy (T x N), BF16 transpose (N x T), and
-// per-64-token column sums (bias gradient partials).
-__global__ void prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int N, bf16* __restrict__ d16,
-                               bf16* __restrict__ d16t, float* __restrict__ colpart) {
-  __shared__ float tile[64][65];
+// per-64-token column sums (bias gradient partials, four 16-row sums added pairwise).  With pre
+// (BF16 T x N, the pre-activation of a GELU whose output the layer read) dY is first multiplied
+// by GELU'(pre) in FP32: the activation's backward folded into this pass.  A 64 x 64 tile per
+// CTA.  vec (dy 16-byte aligned, ldy and N multiples of 4): float4 loads and 8-byte BF16
+// stores; T a multiple of 8 as well: the transpose is stored 8 tokens (16 bytes) at a time.
+__global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int N,
+                                                      const bf16* __restrict__ pre, bf16* __restrict__ d16,
+                                                      bf16* __restrict__ d16t, float* __restrict__ colpart, int vec) {
+  __shared__ __align__(16) float tile[64][68];
+  __shared__ float red[4][64];
   const int t0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
-  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
-    const int tt = q / 64, nn = q % 64;
-    const int t = t0 + tt, n = n0 + nn;
-    float v = (t < T && n < N) ? dy[(size_t)t * ldy + n] : 0.f;
-    tile[tt][nn] = v;
-    if (t < T && n < N && d16) d16[(size_t)t * N + n] = __float2bfloat16_rn(v);
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
-    const int nn = q / 64, tt = q % 64;
-    const int t = t0 + tt, n = n0 + nn;
-    if (t < T && n < N && d16t) d16t[(size_t)n * T + t] = __float2bfloat16_rn(tile[tt][nn]);
-  }
-  if (colpart) {
-    for (int nn = threadIdx.x; nn < 64; nn += blockDim.x) {
-      if (n0 + nn >= N) continue;
-      float s = 0.f;
-      for (int tt = 0; tt < 64; ++tt) s += tile[tt][nn];
-      colpart[(size_t)blockIdx.x * N + n0 + nn] = s;
+  if (vec) {
+    for (int q = threadIdx.x; q < 64 * 16; q += blockDim.x) {
+      const int tt = q >> 4, nn = 4 * (q & 15);
+      const int t = t0 + tt, n = n0 + nn;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (t < T && n < N) {
+        v = *reinterpret_cast<const float4*>(dy + (size_t)t * ldy + n);
+        if (pre) {
+          const uint2 pr = *reinterpret_cast<const uint2*>(pre + (size_t)t * N + n);
+          const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&pr.x);
+          const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&pr.y);
+          v.x *= gelu_grad(__low2float(p01)); v.y *= gelu_grad(__high2float(p01));
+          v.z *= gelu_grad(__low2float(p23)); v.w *= gelu_grad(__high2float(p23));
+        }
+        if (d16) {
+          const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+          *reinterpret_cast<uint2*>(d16 + (size_t)t * N + n) =
+              make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+        }
+      }
+      *reinterpret_cast<float4*>(&tile[tt][nn]) = v;
+    }
+  } else {
+    for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+      const int tt = q / 64, nn = q % 64;
+      const int t = t0 + tt, n = n0 + nn;
+      float v = (t < T && n < N) ? dy[(size_t)t * ldy + n] : 0.f;
+      if (pre && t < T && n < N) v *= gelu_grad(__bfloat162float(pre[(size_t)t * N + n]));
+      tile[tt][nn] = v;
+      if (t < T && n < N && d16) d16[(size_t)t * N + n] = __float2bfloat16_rn(v);
     }
   }
+  __syncthreads();
+  if (d16t) {
+    const bool v8 = vec && (T % 8) == 0;
+    for (int q = threadIdx.x; q < 64 * 8; q += blockDim.x) {
+      const int nn = q & 63, c = q >> 6;
+      const int n = n0 + nn, t = t0 + 8 * c;
+      if (n >= N || t >= T) continue;
+      if (v8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const __nv_bfloat162 p = __floats2bfloat162_rn(tile[8 * c + 2 * j][nn], tile[8 * c + 2 * j + 1][nn]);
+          w[j] = *reinterpret_cast<const uint32_t*>(&p);
+        }
+        *reinterpret_cast<uint4*>(d16t + (size_t)n * T + t) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        for (int j = 0; j < 8 && t + j < T; ++j) d16t[(size_t)n * T + t + j] = __float2bfloat16_rn(tile[8 * c + j][nn]);
+      }
+    }
+  }
+  if (colpart) {
+    {
+      const int nn = threadIdx.x & 63, gq = threadIdx.x >> 6;   // 256 threads: 64 columns x 4 row groups
+      float s = 0.f;
+      for (int tt = 16 * gq; tt < 16 * gq + 16; ++tt) s += tile[tt][nn];
+      red[gq][nn] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && n0 + (int)threadIdx.x < N)
+      colpart[(size_t)blockIdx.x * N + n0 + threadIdx.x] =
+          (red[0][threadIdx.x] + red[1][threadIdx.x]) + (red[2][threadIdx.x] + red[3][threadIdx.x]);
+  }
 }
-// BF16 (T x K, row stride ld) -> BF16 transpose (K x T).
-// xt[k][t] = x[t][k] for a 64 x 64 tile per CTA, moved as BF16 pairs (T, K and ld even).
-__global__ void transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K, bf16* __restrict__ xt) {
-  __shared__ bf16 tile[64][66];
+// BF16 (T x K, row stride ld) -> BF16 transpose (K x T), a 64 x 64 tile per CTA.  vec (x 16-byte
+// aligned, ld and K multiples of 8): 16-byte loads; T a multiple of 8 as well: 16-byte stores of
+// 8 consecutive tokens.  Otherwise BF16 pairs (T, K and ld even).
+__global__ void __launch_bounds__(256) transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K,
+                                                             bf16* __restrict__ xt, int vec) {
+  __shared__ __align__(16) bf16 tile[64][72];
   const int t0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
+  if (vec) {
+    for (int q = threadIdx.x; q < 64 * 8; q += blockDim.x) {
+      const int tt = q >> 3, kk = 8 * (q & 7);
+      const int t = t0 + tt, k = k0 + kk;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (t < T && k < K) v = *reinterpret_cast<const uint4*>(x + (size_t)t * ld + k);
+      *reinterpret_cast<uint4*>(&tile[tt][kk]) = v;
+    }
+    __syncthreads();
+    const bool v8 = (T % 8) == 0;
+    for (int q = threadIdx.x; q < 64 * 8; q += blockDim.x) {
+      const int kk = q & 63, c = q >> 6;
+      const int k = k0 + kk, t = t0 + 8 * c;
+      if (k >= K || t >= T) continue;
+      if (v8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          __nv_bfloat162 p;
+          p.x = tile[8 * c + 2 * j][kk];
+          p.y = tile[8 * c + 2 * j + 1][kk];
+          w[j] = *reinterpret_cast<const uint32_t*>(&p);
+        }
+        *reinterpret_cast<uint4*>(xt + (size_t)k * T + t) = make_uint4(w[0], w[1], w[2], w[3]);
+      } else {
+        for (int j = 0; j < 8 && t + j < T; ++j) xt[(size_t)k * T + t + j] = tile[8 * c + j][kk];
+      }
+    }
+    return;
+  }
   for (int q = threadIdx.x; q < 64 * 32; q += blockDim.x) {
     const int tt = q / 32, kk = 2 * (q % 32);
     const int t = t0 + tt, k = k0 + kk;
@@ -850,8 +937,7 @@ __global__ void edge_bwd_kernel(const SysBatch sb, int diag, const float* __rest
                                 const float* b1, const float* w2, const float* b2, int h, int W,
                                 const float* __restrict__ dbias, int npairs, float* __restrict__ part) {
   __shared__ EdgeW s;
-  __shared__ float es[128][5], zs[128][kEdgeHidden + 1], hs[128][kEdgeHidden + 1], dzs[128][kEdgeHidden + 1],
-      dos[128][9];
+  __shared__ float es[128][5], hs[128][kEdgeHidden + 1], dzs[128][kEdgeHidden + 1], dos[128][9];
   for (int q = threadIdx.x; q < kEdgeHidden * 4; q += blockDim.x) s.w1[q] = w1[q];
   for (int q = threadIdx.x; q < kEdgeHidden; q += blockDim.x) s.b1[q] = b1[q];
   for (int q = threadIdx.x; q < h * kEdgeHidden; q += blockDim.x) s.w2[q] = w2[q];
@@ -876,9 +962,10 @@ __global__ void edge_bwd_kernel(const SysBatch sb, int diag, const float* __rest
     for (int q = 0; q < 4; ++q) z = fmaf(s.w1[kk * 4 + q], e[q], z);
     float dh = 0.f;
     for (int hh = 0; hh < h; ++hh) dh = fmaf(s.w2[hh * kEdgeHidden + kk], dout[hh], dh);
-    zs[pl][kk] = z;
-    hs[pl][kk] = gelu_f(z);
-    dzs[pl][kk] = (pidx < npairs) ? dh * gelu_grad(z) : 0.f;
+    float gz, gd;
+    gelu_both(z, gz, gd);
+    hs[pl][kk] = gz;
+    dzs[pl][kk] = (pidx < npairs) ? dh * gd : 0.f;
   }
   __syncthreads();
   const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;
@@ -912,8 +999,7 @@ __global__ void edge_bwd_leaf_kernel(const SysBatch sb, int mode, const float* w
                                      const float* b2, int h, const float* __restrict__ dsum,
                                      const float* __restrict__ dbias, int nunits, float* __restrict__ part) {
   __shared__ EdgeW s;
-  __shared__ float es[128][5], zs[128][kEdgeHidden + 1], hs[128][kEdgeHidden + 1], dzs[128][kEdgeHidden + 1],
-      dos[128][9];
+  __shared__ float es[128][5], hs[128][kEdgeHidden + 1], dzs[128][kEdgeHidden + 1], dos[128][9];
   for (int q = threadIdx.x; q < kEdgeHidden * 4; q += blockDim.x) s.w1[q] = w1[q];
   for (int q = threadIdx.x; q < kEdgeHidden; q += blockDim.x) s.b1[q] = b1[q];
   for (int q = threadIdx.x; q < h * kEdgeHidden; q += blockDim.x) s.w2[q] = w2[q];
@@ -960,9 +1046,10 @@ __global__ void edge_bwd_leaf_kernel(const SysBatch sb, int mode, const float* w
     for (int q = 0; q < 4; ++q) z = fmaf(s.w1[kk * 4 + q], e[q], z);
     float dh = 0.f;
     for (int hh = 0; hh < h; ++hh) dh = fmaf(s.w2[hh * kEdgeHidden + kk], dout[hh], dh);
-    zs[pl][kk] = z;
-    hs[pl][kk] = valid ? gelu_f(z) : 0.f;
-    dzs[pl][kk] = valid ? dh * gelu_grad(z) : 0.f;
+    float gz, gd;
+    gelu_both(z, gz, gd);
+    hs[pl][kk] = valid ? gz : 0.f;
+    dzs[pl][kk] = valid ? dh * gd : 0.f;
   }
   __syncthreads();
   const int np = kEdgeHidden * 4 + kEdgeHidden + h * kEdgeHidden + h;
@@ -1011,60 +1098,55 @@ __global__ void hwb_g_final_kernel(const SysBatch sb, const double* __restrict__
   }
 }
 // Diagonal tokens: er = d r_hw / cnt_r, ec = d c_hw / cnt_c; dy2d = du_own + er + ec + dg.
-__global__ void hwb_rc_kernel(const SysBatch sb, const float* __restrict__ dud, const float* __restrict__ duo,
-                              const float* __restrict__ dg, int d, float* __restrict__ er, float* __restrict__ ec,
-                              float* __restrict__ dy2d) {
+// d r_hw of node i is its own row-highway gradient plus, for every level whose tile has i's
+// cluster as its row cluster, that tile token's row-chunk-mean gradient / chunk size (column
+// highways alike).  One CTA per leaf stages the leaf's gathered token slices (LeafLevels) in
+// shared memory, already divided by the chunk size (a power of two: exact).
+__global__ void __launch_bounds__(256) hwb_rc_kernel(const SysBatch sb, const float* __restrict__ dud,
+                                                     const float* __restrict__ duo, const float* __restrict__ dg,
+                                                     int d, float* __restrict__ er, float* __restrict__ ec,
+                                                     float* __restrict__ dy2d) {
+  extern __shared__ float4 lgst[];
+  __shared__ LeafLevels g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  if (t >= sb.B * sb.n) return;
-  const int b = t / sb.n, i = t % sb.n;
-  const int k = i / sb.L;
-  // per level: the tile token whose row (column) chunk holds node i, and 1 / chunk size (a power
-  // of two, so the product equals the division)
-  int toks[24];
-  float ich[24];
-  int sides = 0, nl = 0;
-#pragma unroll
-  for (int lev = 1; lev <= 24; ++lev) {
-    toks[lev - 1] = 0;
-    ich[lev - 1] = 0.f;
-    if (lev <= sb.levels) {
-      const int S = sb.K >> lev;
-      const int cl = k / S;
-      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-      const int ch = S * sb.L / sb.r;
-      const int a = (i - cl * S * sb.L) / ch;
-      toks[lev - 1] = (b * sb.MH + m) * sb.r + a;
-      ich[lev - 1] = 1.f / (float)ch;
-      if (cl & 1) sides |= 1 << (lev - 1);
-      ++nl;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  if (threadIdx.x == 0) leaf_levels(sb, b, k, g);
+  __syncthreads();
+  const int nl = sb.levels, d4 = d >> 2;
+  const int rows = g.row0[nl];
+  for (int q = warp; q < rows; q += 8) {
+    int l = 0;
+    while (g.row0[l + 1] <= q) ++l;
+    const int off = ((g.side >> l) & 1) ? 2 * d : d;
+    const float4* src = reinterpret_cast<const float4*>(duo + (size_t)(g.src[l] + q - g.row0[l]) * 4 * d + off);
+    const float s = 1.f / (float)(1 << g.lgch[l]);   // exact
+    for (int c = lane; c < d4; c += 32) {
+      const float4 v = src[c];
+      lgst[q * d4 + c] = make_float4(v.x * s, v.y * s, v.z * s, v.w * s);
     }
   }
-  const float nr = (float)(1 + (nl - __popc(sides))), nc = (float)(1 + __popc(sides));
-  // 4 channels per lane per pass; every level's row issued before the sums
-  for (int c = 4 * lane; c < d; c += 128) {
-    const float4* du4 = reinterpret_cast<const float4*>(dud + (size_t)t * 4 * d);
-    float4 rr = du4[(d + c) >> 2], cc = du4[(2 * d + c) >> 2];
-    const float4 own = du4[c >> 2];
-    float4 v[24];
-#pragma unroll
-    for (int q = 0; q < 24; ++q) {
-      const int off = ((sides >> q) & 1) ? 2 * d : d;
-      v[q] = q < nl ? *reinterpret_cast<const float4*>(duo + (size_t)toks[q] * 4 * d + off + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  const float nr = (float)(1 + (nl - __popc(g.side))), nc = (float)(1 + __popc(g.side));
+  for (int kk = warp; kk < sb.L; kk += 8) {
+    const size_t t = (size_t)b * sb.n + (size_t)k * sb.L + kk;
+    const float4* du4 = reinterpret_cast<const float4*>(dud + t * 4 * d);
+    for (int c = lane; c < d4; c += 32) {
+      float4 rr = du4[d4 + c], cc = du4[2 * d4 + c];
+      const float4 own = du4[c];
+      for (int q = 0; q < nl; ++q) {
+        const float4 v = lgst[leaf_level_row(g, q, kk) * d4 + c];
+        if ((g.side >> q) & 1) { cc.x += v.x; cc.y += v.y; cc.z += v.z; cc.w += v.w; }
+        else { rr.x += v.x; rr.y += v.y; rr.z += v.z; rr.w += v.w; }
+      }
+      rr.x /= nr; rr.y /= nr; rr.z /= nr; rr.w /= nr;
+      cc.x /= nc; cc.y /= nc; cc.z /= nc; cc.w /= nc;
+      reinterpret_cast<float4*>(er + t * d)[c] = rr;
+      reinterpret_cast<float4*>(ec + t * d)[c] = cc;
+      const float4 gg = reinterpret_cast<const float4*>(dg + (size_t)b * d)[c];
+      reinterpret_cast<float4*>(dy2d + t * d)[c] =
+          make_float4(own.x + rr.x + cc.x + gg.x, own.y + rr.y + cc.y + gg.y, own.z + rr.z + cc.z + gg.z,
+                      own.w + rr.w + cc.w + gg.w);
     }
-#pragma unroll
-    for (int q = 0; q < 24; ++q) {
-      const float s = ich[q];
-      if ((sides >> q) & 1) { cc.x += v[q].x * s; cc.y += v[q].y * s; cc.z += v[q].z * s; cc.w += v[q].w * s; }
-      else { rr.x += v[q].x * s; rr.y += v[q].y * s; rr.z += v[q].z * s; rr.w += v[q].w * s; }
-    }
-    rr.x /= nr; rr.y /= nr; rr.z /= nr; rr.w /= nr;
-    cc.x /= nc; cc.y /= nc; cc.z /= nc; cc.w /= nc;
-    *reinterpret_cast<float4*>(er + (size_t)t * d + c) = rr;
-    *reinterpret_cast<float4*>(ec + (size_t)t * d + c) = cc;
-    const float4 g = *reinterpret_cast<const float4*>(dg + (size_t)b * d + c);
-    *reinterpret_cast<float4*>(dy2d + (size_t)t * d + c) =
-        make_float4(own.x + rr.x + cc.x + g.x, own.y + rr.y + cc.y + g.y, own.z + rr.z + cc.z + g.z, own.w + rr.w + cc.w + g.w);
   }
 }
 // Highway ablation: the LN2 output's gradient is the first d columns of the FFN-input gradient.
@@ -1094,48 +1176,83 @@ __global__ void hwb_off_kernel(const SysBatch sb, const float* __restrict__ duo,
 
 // ------------------------------------------------------------------ pool, GCN, encoder backward
 // dx[j] += dpooled row part / ch for the token whose row chunk holds j, column part for
-// the token whose column chunk holds j (one per level).
-__global__ void pool_bwd_kernel(const SysBatch sb, const float* __restrict__ dpooled, int d, float* __restrict__ dx) {
+// the token whose column chunk holds j (one per level).  One CTA per leaf: the leaf's gathered
+// slices (LeafLevels) are staged in shared memory, divided by the chunk size (exact).
+__global__ void __launch_bounds__(256) pool_bwd_kernel(const SysBatch sb, const float* __restrict__ dpooled, int d,
+                                                       float* __restrict__ dx) {
+  extern __shared__ float4 lgst[];
+  __shared__ LeafLevels g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  if (t >= sb.B * sb.n) return;
-  const int b = t / sb.n, i = t % sb.n;
-  const int k = i / sb.L;
-  for (int c = lane; c < d; c += 32) {
-    float acc = dx[(size_t)t * d + c];
-    for (int lev = 1; lev <= sb.levels; ++lev) {
-      const int S = sb.K >> lev;
-      const int cl = k / S;
-      const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-      const int ch = S * sb.L / sb.r;
-      const int a = (i - cl * S * sb.L) / ch;
-      const size_t tok = ((size_t)b * sb.MH + m) * sb.r + a;
-      acc += dpooled[tok * 2 * d + ((cl & 1) ? d : 0) + c] / ch;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  if (threadIdx.x == 0) leaf_levels(sb, b, k, g);
+  __syncthreads();
+  const int nl = sb.levels, d4 = d >> 2;
+  const int rows = g.row0[nl];
+  for (int q = warp; q < rows; q += 8) {
+    int l = 0;
+    while (g.row0[l + 1] <= q) ++l;
+    const int off = ((g.side >> l) & 1) ? d : 0;
+    const float4* src = reinterpret_cast<const float4*>(dpooled + (size_t)(g.src[l] + q - g.row0[l]) * 2 * d + off);
+    const float s = 1.f / (float)(1 << g.lgch[l]);   // exact
+    for (int c = lane; c < d4; c += 32) {
+      const float4 v = src[c];
+      lgst[q * d4 + c] = make_float4(v.x * s, v.y * s, v.z * s, v.w * s);
     }
-    dx[(size_t)t * d + c] = acc;
+  }
+  __syncthreads();
+  for (int kk = warp; kk < sb.L; kk += 8) {
+    float4* x4 = reinterpret_cast<float4*>(dx + ((size_t)b * sb.n + (size_t)k * sb.L + kk) * d);
+    for (int c = lane; c < d4; c += 32) {
+      float4 acc = x4[c];
+      for (int q = 0; q < nl; ++q) {
+        const float4 v = lgst[leaf_level_row(g, q, kk) * d4 + c];
+        acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+      }
+      x4[c] = acc;
+    }
   }
 }
-// dx_g += P^T v with P = D^-1 A: (P^T v)_j = v_j - sum_{i nbr j} (w_ij / d_i) v_i.
+// dx_g += P^T v with P = D^-1 A: (P^T v)_j = v_j - sum_{i nbr j} (w_ij / d_i) v_i, the
+// coefficients formed in FP32 as the forward forms them.  Warp per node: lane q < 2 ndim finds
+// neighbour q (axis q / 2, + side for even q) and its coefficient; 4 channels per lane.
 __global__ void prop_t_kernel(const SysBatch sb, const float* __restrict__ v, int d, float* __restrict__ dx) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
   if (t >= sb.B * sb.n) return;
   const int b = t / sb.n, j = t % sb.n;
   const size_t base = (size_t)b * sb.n;
-  const double* dg = sb.diag[b];
-  int is[6];
-  float cs[6];
-  int ni = 0;
-  for (int a = 0; a < sb.ndim; ++a) {
-    const int ip = sb.mo.plus(j, a);
-    if (ip >= 0) { is[ni] = ip; cs[ni++] = (float)(sb.w[b][a][j] / dg[ip]); }
-    const int im = sb.mo.minus(j, a);
-    if (im >= 0) { is[ni] = im; cs[ni++] = (float)(sb.w[b][a][im] / dg[im]); }
+  int nb = -1;
+  float cf = 0.f;
+  if (lane < 2 * sb.ndim) {
+    const int a = lane >> 1;
+    const int i = (lane & 1) ? sb.mo.minus(j, a) : sb.mo.plus(j, a);
+    if (i >= 0) {
+      nb = i;
+      cf = (float)sb.w[b][a][(lane & 1) ? i : j] / (float)sb.diag[b][i];
+    }
   }
-  for (int c = lane; c < d; c += 32) {
-    float s = v[(size_t)t * d + c];
-    for (int q = 0; q < ni; ++q) s = fmaf(-cs[q], v[(base + is[q]) * d + c], s);
-    dx[(size_t)t * d + c] += s;
+  int nbs[6];
+  float cfs[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    nbs[q] = __shfl_sync(0xffffffffu, nb, q);
+    cfs[q] = __shfl_sync(0xffffffffu, cf, q);
+  }
+  const int d4 = d >> 2;
+  for (int c = lane; c < d4; c += 32) {
+    float4 s = reinterpret_cast<const float4*>(v + (size_t)t * d)[c];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if (q < 2 * sb.ndim && nbs[q] >= 0) {
+        const float4 u = reinterpret_cast<const float4*>(v + (base + nbs[q]) * d)[c];
+        s.x = fmaf(-cfs[q], u.x, s.x); s.y = fmaf(-cfs[q], u.y, s.y);
+        s.z = fmaf(-cfs[q], u.z, s.z); s.w = fmaf(-cfs[q], u.w, s.w);
+      }
+    }
+    float4* o = reinterpret_cast<float4*>(dx + (size_t)t * d) + c;
+    float4 x = *o;
+    x.x += s.x; x.y += s.y; x.z += s.z; x.w += s.w;
+    *o = x;
   }
 }
 // Partial sums over 64-token chunks of outer products A^T B (A: T x p FP32, B: T x q FP32),

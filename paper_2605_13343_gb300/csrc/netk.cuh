@@ -602,54 +602,51 @@ __global__ void __launch_bounds__(32 * (W / 16 > 4 ? W / 16 : 4)) attention_kern
 }
 
 // Axial highway buffers for the diagonal tokens (mean over the tokens covering each
-// row / column) and their BF16 copies into the FFN input (columns d..3d).
-__global__ void highway_rc_kernel(const SysBatch sb, const float* __restrict__ yd, const float* __restrict__ yo, int d,
-                                  float* __restrict__ rhw, float* __restrict__ chw, bf16* __restrict__ ud) {
+// row / column) and their BF16 copies into the FFN input (columns d..3d).  One CTA per leaf:
+// the tile tokens its nodes gather (LeafLevels) are staged in shared memory once, then each
+// warp takes every eighth node of the leaf, 4 channels per lane.
+__global__ void __launch_bounds__(256) highway_rc_kernel(const SysBatch sb, const float* __restrict__ yd,
+                                                         const float* __restrict__ yo, int d, float* __restrict__ rhw,
+                                                         float* __restrict__ chw, bf16* __restrict__ ud) {
   pdl_entry();
+  extern __shared__ float4 hwst[];
+  __shared__ LeafLevels g;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  if (t >= sb.B * sb.n) return;
-  const int b = t / sb.n, i = t % sb.n;
-  const int k = i / sb.L;
-  int toks[24];
-  int sides = 0, nl = 0;
-  // K, L, r and every chunk are powers of two: shifts instead of divisions
-  const int lgL = ilog2i(sb.L), lgr = ilog2i(sb.r);
-  for (int lev = 1; lev <= sb.levels && lev <= 24; ++lev) {
-    const int lgS = sb.levels - lev;                     // S = K >> lev leaves per side
-    const int cl = k >> lgS;
-    const int m = (1 << (lev - 1)) - 1 + (cl >> 1);
-    const int a = (i - (cl << (lgS + lgL))) >> (lgS + lgL - lgr);
-    toks[nl] = (b * sb.MH + m) * sb.r + a;
-    if (cl & 1) sides |= 1 << nl;
-    ++nl;
+  const int b = blockIdx.x / sb.K, k = blockIdx.x % sb.K;
+  if (threadIdx.x == 0) leaf_levels(sb, b, k, g);
+  __syncthreads();
+  const int nl = sb.levels, d4 = d >> 2;
+  const int rows = g.row0[nl];
+  for (int q = warp; q < rows; q += 8) {
+    int l = 0;
+    while (g.row0[l + 1] <= q) ++l;
+    const float4* src = reinterpret_cast<const float4*>(yo + (size_t)(g.src[l] + q - g.row0[l]) * d);
+    for (int c = lane; c < d4; c += 32) hwst[q * d4 + c] = src[c];
   }
-  const float inr = 1.f / (float)(1 + (nl - __popc(sides))), inc = 1.f / (float)(1 + __popc(sides));
-  // 4 channels per lane per pass; every level's load issued before the sums
-  for (int c = 4 * lane; c < d; c += 128) {
-    const float4 y = *reinterpret_cast<const float4*>(yd + (size_t)t * d + c);
-    float4 v[24];
-#pragma unroll
-    for (int q = 0; q < 24; ++q)
-      v[q] = q < nl ? *reinterpret_cast<const float4*>(yo + (size_t)toks[q] * d + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 rs = y, cs = y;
-#pragma unroll
-    for (int q = 0; q < 24; ++q) {
-      const bool col = (sides >> q) & 1;      // levels past nl hold zeros
-      rs.x += col ? 0.f : v[q].x; rs.y += col ? 0.f : v[q].y; rs.z += col ? 0.f : v[q].z; rs.w += col ? 0.f : v[q].w;
-      cs.x += col ? v[q].x : 0.f; cs.y += col ? v[q].y : 0.f; cs.z += col ? v[q].z : 0.f; cs.w += col ? v[q].w : 0.f;
+  __syncthreads();
+  const float inr = 1.f / (float)(1 + (nl - __popc(g.side))), inc = 1.f / (float)(1 + __popc(g.side));
+  for (int kk = warp; kk < sb.L; kk += 8) {
+    const size_t t = (size_t)b * sb.n + (size_t)k * sb.L + kk;
+    for (int c = lane; c < d4; c += 32) {
+      const float4 y = reinterpret_cast<const float4*>(yd + t * d)[c];
+      float4 rs = y, cs = y;
+      for (int q = 0; q < nl; ++q) {
+        const float4 v = hwst[leaf_level_row(g, q, kk) * d4 + c];
+        if ((g.side >> q) & 1) { cs.x += v.x; cs.y += v.y; cs.z += v.z; cs.w += v.w; }
+        else { rs.x += v.x; rs.y += v.y; rs.z += v.z; rs.w += v.w; }
+      }
+      rs.x *= inr; rs.y *= inr; rs.z *= inr; rs.w *= inr;
+      cs.x *= inc; cs.y *= inc; cs.z *= inc; cs.w *= inc;
+      reinterpret_cast<float4*>(rhw + t * d)[c] = rs;
+      reinterpret_cast<float4*>(chw + t * d)[c] = cs;
+      bf16* u = ud + t * 4 * d;
+      const __nv_bfloat162 r01 = __floats2bfloat162_rn(rs.x, rs.y), r23 = __floats2bfloat162_rn(rs.z, rs.w);
+      const __nv_bfloat162 c01 = __floats2bfloat162_rn(cs.x, cs.y), c23 = __floats2bfloat162_rn(cs.z, cs.w);
+      *reinterpret_cast<uint2*>(u + d + 4 * c) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&r01), *reinterpret_cast<const uint32_t*>(&r23));
+      *reinterpret_cast<uint2*>(u + 2 * d + 4 * c) =
+          make_uint2(*reinterpret_cast<const uint32_t*>(&c01), *reinterpret_cast<const uint32_t*>(&c23));
     }
-    rs.x *= inr; rs.y *= inr; rs.z *= inr; rs.w *= inr;
-    cs.x *= inc; cs.y *= inc; cs.z *= inc; cs.w *= inc;
-    *reinterpret_cast<float4*>(rhw + (size_t)t * d + c) = rs;
-    *reinterpret_cast<float4*>(chw + (size_t)t * d + c) = cs;
-    bf16* u = ud + (size_t)t * 4 * d;
-    const __nv_bfloat162 r01 = __floats2bfloat162_rn(rs.x, rs.y), r23 = __floats2bfloat162_rn(rs.z, rs.w);
-    const __nv_bfloat162 c01 = __floats2bfloat162_rn(cs.x, cs.y), c23 = __floats2bfloat162_rn(cs.z, cs.w);
-    *reinterpret_cast<uint2*>(u + d + c) =
-        make_uint2(*reinterpret_cast<const uint32_t*>(&r01), *reinterpret_cast<const uint32_t*>(&r23));
-    *reinterpret_cast<uint2*>(u + 2 * d + c) =
-        make_uint2(*reinterpret_cast<const uint32_t*>(&c01), *reinterpret_cast<const uint32_t*>(&c23));
   }
 }
 
