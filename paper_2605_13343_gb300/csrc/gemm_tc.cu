@@ -1,14 +1,20 @@
 // BF16 GEMM on the 5th-generation tensor cores: C[M x N] = A[M x K] . B[N x K]^T.
 //
-// One CTA computes a 128 x BN tile.  A TMA producer thread streams 128x64 and
-// BNx64 K-major tiles (128-byte swizzle) into a 3-stage shared-memory ring; one
-// thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM);
-// tcgen05.commit frees ring slots through mbarriers.  Four warps then read the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows),
-// transpose 32x32 blocks through the freed ring memory so that global accesses are
-// coalesced along rows, and run the fused epilogue: + bias, GELU, + residual, FP32 / BF16 / transposed BF16
-// stores.  Every mbarrier wait is bounded; a timeout sets an error flag, and the
-// CTA still waits for its MMAs and frees its TMEM before it returns.
+// Persistent: one CTA per SM walks the 128 x BN output tiles (column tiles fastest, so the CTAs
+// running at the same time share row blocks of A in L2).  Ten warps with fixed roles:
+//   warp 8   one thread streams 128x64 and BNx64 K-major tiles (TMA, 128-byte swizzle) into a
+//            6-stage shared-memory ring (4 for 256-wide tiles) that runs on across tiles;
+//   warp 9   one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate) into one of two
+//            TMEM accumulators, alternating per tile; tcgen05.commit frees ring slots and marks
+//            an accumulator full;
+//   warps 0-7 the epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows) of column half
+//            w / 4 with tcgen05.ld, transposes 32x32 blocks through
+//            their own shared staging block so that global accesses run along rows, and the fused
+//            epilogue (+ bias, GELU, + residual, FP32 / BF16 / transposed BF16 stores); then they
+//            hand the accumulator back.
+// So the epilogue of one tile overlaps the MMAs of the next.  Every mbarrier wait is bounded; a
+// timeout sets a shared flag that ends every role's loop and an error flag for the host, and the
+// CTA waits (bounded) for its MMAs and frees its TMEM before it returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cstdio>
@@ -22,29 +28,40 @@
 
 namespace hm {
 
+constexpr int kGemmEpiWarps = 8;   // two per TMEM lane quadrant, one column half each
+// ring depth: as many stages as fit beside the epilogue staging (6 for tiles up to 128 wide)
 template <int BN>
-__global__ void __launch_bounds__(128)
+__host__ __device__ constexpr int gemm_stages() { return BN >= 256 ? 4 : 6; }
+template <int BN>
+constexpr size_t gemm_smem_bytes() {
+  return (size_t)gemm_stages<BN>() * (128 * 64 * 2 + BN * 64 * 2) + kGemmEpiWarps * 32 * 33 * 4 + 1024;
+}
+
+HM_INLINE void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(32 * (kGemmEpiWarps + 2))
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        const GemmEpi ep, int M, int N, int K) {
+                        const GemmEpi ep, int M, int N, int K, int ksplit) {
   using namespace tc;
-  constexpr int BM = 128, BK = 64, STAGES = 3;
+  constexpr int BM = 128, BK = 64, STAGES = gemm_stages<BN>();
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-  constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators of BN columns
   extern __shared__ uint8_t smem_raw[];
   // align to 1024 B (128-byte swizzle atoms) by pointer arithmetic on the shared array, so
   // that the compiler keeps knowing these are shared-memory addresses
   uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_done;
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], acc_full[2], acc_empty[2], bar_done;
   __shared__ uint32_t tmem_base_s;
-  __shared__ int fail_s;
+  __shared__ volatile int fail_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  // split-K: CTA z reduces k-blocks [kb0, kb1) and writes its own FP32 partial tile
+  // tiles: column tile fastest, then row tile, then split-K slice z (k-blocks [z kps, (z+1) kps))
+  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   const int nk_all = (K + BK - 1) / BK;
-  const int kps = (nk_all + gridDim.z - 1) / gridDim.z;
-  const int kb0 = blockIdx.z * kps;
-  const int kb1 = min(nk_all, kb0 + kps);
-  const int nk = max(0, kb1 - kb0);
+  const int kps = (nk_all + ksplit - 1) / ksplit;
+  const int ntiles = mt * nt * ksplit;
   uint8_t* sa = smem;
   uint8_t* sb = smem + STAGES * A_BYTES;
 
@@ -52,6 +69,10 @@ __global__ void __launch_bounds__(128)
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&acc_full[b]), 1);
+      mbar_init(smem_u32(&acc_empty[b]), kGemmEpiWarps);   // one arrival per epilogue warp
     }
     mbar_init(smem_u32(&bar_done), 1);
     fail_s = 0;
@@ -70,122 +91,165 @@ __global__ void __launch_bounds__(128)
   const uint32_t tmem = tmem_base_s;
   pdl_entry();   // the set-up above overlaps the previous kernel; operands are read only after it
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), ((kb / STAGES) - 1) & 1)) {
-        fail_s = 1;
-        break;
+  if (warp == kGemmEpiWarps) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int g = 0;   // k-blocks loaded by this CTA so far (ring position)
+      for (int t = blockIdx.x; t < ntiles && !fail_s; t += gridDim.x) {
+        const int n0 = (t % nt) * BN, m0 = ((t / nt) % mt) * BM, z = t / (nt * mt);
+        const int kb0 = z * kps, nk = max(0, min(nk_all, kb0 + kps) - kb0);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !mbar_wait(smem_u32(&bar_empty[s]), ((g / STAGES) - 1) & 1)) {
+            fail_s = 1;
+            break;
+          }
+          const uint32_t fb = smem_u32(&bar_full[s]);
+          mbar_expect_tx(fb, A_BYTES + B_BYTES);
+          tma_load_2d(smem_u32(sa + s * A_BYTES), &tmA, (kb0 + kb) * BK, m0, fb);
+          tma_load_2d(smem_u32(sb + s * B_BYTES), &tmB, (kb0 + kb) * BK, n0, fb);
+        }
       }
-      const uint32_t fb = smem_u32(&bar_full[s]);
-      mbar_expect_tx(fb, A_BYTES + B_BYTES);
-      tma_load_2d(smem_u32(sa + s * A_BYTES), &tmA, (kb0 + kb) * BK, m0, fb);
-      tma_load_2d(smem_u32(sb + s * B_BYTES), &tmB, (kb0 + kb) * BK, n0, fb);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(smem_u32(&bar_full[s]), (kb / STAGES) & 1)) {
+  } else if (warp == kGemmEpiWarps + 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int g = 0, it = 0;
+      for (int t = blockIdx.x; t < ntiles && !fail_s; t += gridDim.x, ++it) {
+        const int buf = it & 1;
+        if (it >= 2 && !mbar_wait(smem_u32(&acc_empty[buf]), ((it >> 1) - 1) & 1, 1l << 24)) {
+          fail_s = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int z = t / (nt * mt);
+        const int kb0 = z * kps, nk = max(0, min(nk_all, kb0 + kps) - kb0);
+        const uint32_t acc = tmem + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait(smem_u32(&bar_full[s]), (g / STAGES) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ad = sw128_desc(smem_u32(sa + s * A_BYTES));
+          const uint64_t bd = sw128_desc(smem_u32(sb + s * B_BYTES));
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            mma_bf16(acc, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+          mma_commit(smem_u32(&bar_empty[s]));
+        }
+        if (!ok) {
+          fail_s = 1;
+          break;
+        }
+        mma_commit(smem_u32(&acc_full[buf]));
+      }
+      mma_commit(smem_u32(&bar_done));   // arrives once every MMA issued here has completed
+    }
+  } else {
+    // ---------------- epilogue (warps 0-7): TMEM -> registers -> shared (transpose) -> global
+    float* stage = reinterpret_cast<float*>(smem + STAGES * (A_BYTES + B_BYTES)) + warp * (32 * 33);
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles && !fail_s; t += gridDim.x, ++it) {
+      const int buf = it & 1;
+      if (!mbar_wait(smem_u32(&acc_full[buf]), (it >> 1) & 1, 1l << 24)) {
         fail_s = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t ad = sw128_desc(smem_u32(sa + s * A_BYTES));
-      const uint64_t bd = sw128_desc(smem_u32(sb + s * B_BYTES));
+      const int n0 = (t % nt) * BN, m0 = ((t / nt) % mt) * BM, z = t / (nt * mt);
+      const int kb0 = z * kps;
+      const bool empty_k = min(nk_all, kb0 + kps) - kb0 <= 0;
+      const int quad = warp & 3, half = warp >> 2;
+      const int rbase = m0 + quad * 32;
+      const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN);
+      constexpr int CW = BN / 2 < 32 ? 32 : BN / 2;   // columns per warp
+      for (int c = half * CW; c < (half + 1) * CW && c < BN; c += 32) {
+        float v[32];
+        tmem_ld16(acc + (uint32_t)c, v);
+        tmem_ld16(acc + (uint32_t)(c + 16), v + 16);
+        if (empty_k) {
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k)
-        mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-      mma_commit(smem_u32(&bar_empty[s]));
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
+        if (n0 + c >= N) continue;   // uniform across the warp
+        if (ep.out16T && rbase + lane < M) {
+          // transposed copy: lanes are consecutive rows, so each column store is contiguous
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (n0 + c + j < N) {
+              float y = v[j] + (ep.bias ? ep.bias[n0 + c + j] : 0.f);
+              if (ep.act == 1) y = gelu_f(y);
+              ep.out16T[(size_t)(n0 + c + j) * ep.ldT + rbase + lane] = __float2bfloat16_rn(y);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+        __syncwarp();
+        // lane -> 4 consecutive columns of rows rg, rg + 4, ..., rg + 28: every store instruction
+        // writes 16 B per lane and 4 full 128-byte row segments per warp
+        const int cg = lane & 7, rg = lane >> 3;
+        const int col = n0 + c + 4 * cg;
+        if (col < N) {   // N % 16 == 0, so the 4 columns are all valid
+          float4 bias4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (ep.bias) bias4 = make_float4(ep.bias[col], ep.bias[col + 1], ep.bias[col + 2], ep.bias[col + 3]);
+          float4 res[8];
+          if (ep.resid) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int row = rbase + rg + 4 * q;
+              res[q] = row < M ? *reinterpret_cast<const float4*>(ep.resid + (size_t)row * ep.ldr + col)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int rr = rg + 4 * q;
+            const int row = rbase + rr;
+            if (row >= M) continue;
+            float tv[4] = {stage[rr * 33 + 4 * cg] + bias4.x, stage[rr * 33 + 4 * cg + 1] + bias4.y,
+                           stage[rr * 33 + 4 * cg + 2] + bias4.z, stage[rr * 33 + 4 * cg + 3] + bias4.w};
+            if (ep.pre16) {
+              uint2 pk;
+              __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&pk);
+              hh[0] = __floats2bfloat162_rn(tv[0], tv[1]);
+              hh[1] = __floats2bfloat162_rn(tv[2], tv[3]);
+              *reinterpret_cast<uint2*>(ep.pre16 + (size_t)row * ep.ldpre + col) = pk;
+            }
+            if (ep.act == 1) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) tv[e] = gelu_f(tv[e]);
+            }
+            if (ep.resid) { tv[0] += res[q].x; tv[1] += res[q].y; tv[2] += res[q].z; tv[3] += res[q].w; }
+            if (ep.out32)
+              *reinterpret_cast<float4*>(ep.out32 + (size_t)z * ep.zstride + (size_t)row * ep.ld32 + col) =
+                  make_float4(tv[0], tv[1], tv[2], tv[3]);
+            if (ep.out16) {
+              uint2 pk;
+              __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&pk);
+              hh[0] = __floats2bfloat162_rn(tv[0], tv[1]);
+              hh[1] = __floats2bfloat162_rn(tv[2], tv[3]);
+              *reinterpret_cast<uint2*>(ep.out16 + (size_t)row * ep.ld16 + col) = pk;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      // this warp's TMEM lanes of the accumulator have been read: hand it back to the MMA thread
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
     }
-    mma_commit(smem_u32(&bar_done));
   }
-  __syncwarp();
-  const bool empty_k = (nk == 0);
-
-  // ---------------- epilogue: TMEM -> registers -> shared (transpose) -> coalesced global
-  const bool done = mbar_wait(smem_u32(&bar_done), 0, 1l << 24);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const bool ok = done && !fail_s;
-  // The ring buffers are free once every MMA has completed: each warp stages a
-  // 32 x 32 FP32 block there so that lanes walk columns when touching global memory.
-  float* stage = reinterpret_cast<float*>(smem) + warp * (32 * 33);
-  const int rbase = m0 + warp * 32;
-  for (int c = 0; c < BN; c += 32) {
-    float v[32];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c + 16), v + 16);
-    if (empty_k) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = 0.f;
-    }
-    if (!ok || n0 + c >= N) continue;   // uniform across the warp
-    if (ep.out16T && rbase + lane < M) {
-      // transposed copy: lanes are consecutive rows, so each column store is contiguous
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (n0 + c + j < N) {
-          float y = v[j] + (ep.bias ? ep.bias[n0 + c + j] : 0.f);
-          if (ep.act == 1) y = gelu_f(y);
-          ep.out16T[(size_t)(n0 + c + j) * ep.ldT + rbase + lane] = __float2bfloat16_rn(y);
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
-    __syncwarp();
-    // lane -> 4 consecutive columns of rows rg, rg + 4, ..., rg + 28: every store instruction
-    // writes 16 B per lane and 4 full 128-byte row segments per warp
-    const int cg = lane & 7, rg = lane >> 3;
-    const int col = n0 + c + 4 * cg;
-    if (col < N) {   // N % 16 == 0, so the 4 columns are all valid
-      float4 bias4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (ep.bias) bias4 = make_float4(ep.bias[col], ep.bias[col + 1], ep.bias[col + 2], ep.bias[col + 3]);
-      float4 res[8];
-      if (ep.resid) {
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int row = rbase + rg + 4 * it;
-          res[it] = row < M ? *reinterpret_cast<const float4*>(ep.resid + (size_t)row * ep.ldr + col)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-#pragma unroll
-      for (int it = 0; it < 8; ++it) {
-        const int rr = rg + 4 * it;
-        const int row = rbase + rr;
-        if (row >= M) continue;
-        float t[4] = {stage[rr * 33 + 4 * cg] + bias4.x, stage[rr * 33 + 4 * cg + 1] + bias4.y,
-                      stage[rr * 33 + 4 * cg + 2] + bias4.z, stage[rr * 33 + 4 * cg + 3] + bias4.w};
-        if (ep.pre16) {
-          uint2 pk;
-          __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&pk);
-          hh[0] = __floats2bfloat162_rn(t[0], t[1]);
-          hh[1] = __floats2bfloat162_rn(t[2], t[3]);
-          *reinterpret_cast<uint2*>(ep.pre16 + (size_t)row * ep.ldpre + col) = pk;
-        }
-        if (ep.act == 1) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) t[q] = gelu_f(t[q]);
-        }
-        if (ep.resid) { t[0] += res[it].x; t[1] += res[it].y; t[2] += res[it].z; t[3] += res[it].w; }
-        if (ep.out32)
-          *reinterpret_cast<float4*>(ep.out32 + (size_t)blockIdx.z * ep.zstride + (size_t)row * ep.ld32 + col) =
-              make_float4(t[0], t[1], t[2], t[3]);
-        if (ep.out16) {
-          uint2 pk;
-          __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&pk);
-          hh[0] = __floats2bfloat162_rn(t[0], t[1]);
-          hh[1] = __floats2bfloat162_rn(t[2], t[3]);
-          *reinterpret_cast<uint2*>(ep.out16 + (size_t)row * ep.ld16 + col) = pk;
-        }
-      }
-    }
-    __syncwarp();
-  }
-  if (!ok && threadIdx.x == 0 && ep.err) atomicExch(ep.err, (int)HMPCG_E_TIMEOUT);
+  __syncwarp();   // lanes 1-31 of the producer and MMA warps wait here for lane 0
+  __syncthreads();
+  // every MMA of this CTA has completed before TMEM is freed (immediate unless a wait failed)
+  const bool drained = mbar_wait(smem_u32(&bar_done), 0, 1l << 24);
+  if ((fail_s || !drained) && threadIdx.x == 0 && ep.err) atomicExch(ep.err, (int)HMPCG_E_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
@@ -222,10 +286,28 @@ bool tma_map_bf16(CUtensorMap* map, const void* base, int rows, int cols, int ld
   return r == CUDA_SUCCESS;
 }
 
+// SM count of the current device, queried once per device and cached only when the query
+// succeeds; devices past the table, or a failed query, fall back to 148 SMs.
+static int device_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> sm_count[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  int sms = (dev >= 0 && dev < kMaxDev) ? sm_count[dev].load(std::memory_order_relaxed) : 0;
+  if (sms <= 0) {
+    if (dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+      if (dev < kMaxDev) sm_count[dev].store(sms, std::memory_order_relaxed);
+    } else {
+      cudaGetLastError();
+      sms = 148;
+    }
+  }
+  return sms;
+}
+
 template <int BN>
 static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) {
-  constexpr int STAGES = 3;
-  const size_t smem = STAGES * (128 * 64 * 2 + BN * 64 * 2) + 1024;
+  const size_t smem = gemm_smem_bytes<BN>();
   static std::atomic<unsigned long long> attr_set{0};
   if (!once_per_device(attr_set, [&] {
         return cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
@@ -234,10 +316,14 @@ static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) 
     return HMPCG_E_CUDA;
   CUtensorMap mb;
   if (!tma_map_bf16(&mb, g.B, g.N, g.K, g.ldb, BN)) return HMPCG_E_INVALID;
-  dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, std::max(1, g.ksplit));
+  const int ks = std::max(1, g.ksplit);
+  const int64_t tiles = ((int64_t)(g.M + 127) / 128) * ((g.N + BN - 1) / BN) * ks;
+  if (tiles > INT32_MAX) return HMPCG_E_SHAPE;
+  // persistent: at most one CTA per SM (the shared-memory ring admits one)
+  const int grid = (int)std::min<int64_t>(tiles, device_sms());
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(128);
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * (kGemmEpiWarps + 2));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -245,7 +331,7 @@ static int launch_bn(const GemmArgs& g, const CUtensorMap& ma, cudaStream_t st) 
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, gemm_bf16_tc_kernel<BN>, ma, mb, g.ep, g.M, g.N, g.K) != cudaSuccess)
+  if (cudaLaunchKernelEx(&cfg, gemm_bf16_tc_kernel<BN>, ma, mb, g.ep, g.M, g.N, g.K, ks) != cudaSuccess)
     return HMPCG_E_CUDA;
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
@@ -268,22 +354,7 @@ int gemm_bf16(const GemmArgs& g, cudaStream_t st) {
     // candidate width (warm-up + 3 timed runs each, CUDA events) and keeps the fastest; calls
     // during capture, GEMMs that add into their own output, and split-K use the rule below
     bn = (g.N % 128 == 0 && g.N >= 128) ? 128 : 64;
-    // SM count per device, queried on the first call (before any capture) and cached only when
-    // the query succeeds; devices past the table, or a failed query, fall back to 148 SMs (the
-    // rule below then errs towards wide tiles)
-    constexpr int kMaxDev = 64;
-    static std::atomic<int> sm_count[kMaxDev];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
-    int sms = (dev >= 0 && dev < kMaxDev) ? sm_count[dev].load(std::memory_order_relaxed) : 0;
-    if (sms <= 0) {
-      if (dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
-        if (dev < kMaxDev) sm_count[dev].store(sms, std::memory_order_relaxed);
-      } else {
-        cudaGetLastError();
-        sms = 148;
-      }
-    }
+    const int sms = device_sms();
     const int64_t tiles128 = ((int64_t)(g.M + 127) / 128) * ((g.N + 127) / 128) * std::max(1, g.ksplit);
     if (bn == 128 && tiles128 < sms) bn = 64;   // rule: fewer 128-wide tiles than SMs -> narrower tiles
     static std::map<std::tuple<int, int, int, int, int>, int> tuned;

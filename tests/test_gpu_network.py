@@ -22,7 +22,8 @@ CFG = dict(d=128, n_layers=4, n_heads=4, d_mlp=512, leaf=64, rank=16)
 
 @pytest.mark.parametrize("m,n,k,bias,act", [(8192, 384, 128, True, 0), (2032, 128, 512, True, 1),
                                             (100, 64, 64, False, 0), (300, 32, 128, True, 1),
-                                            (4096, 256, 256, False, 1), (128, 512, 512, True, 0)])
+                                            (4096, 256, 256, False, 1), (128, 512, 512, True, 0),
+                                            (32768, 512, 256, True, 1), (20000, 128, 512, False, 0)])
 def test_gemm_tc_matches_torch(m, n, k, bias, act):
     torch.backends.cuda.matmul.allow_tf32 = False
     g = torch.Generator(device="cuda").manual_seed(m + n + k)
