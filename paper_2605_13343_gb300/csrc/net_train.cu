@@ -169,15 +169,18 @@ static int linear_bwd(Net* N, const float* dY, int ldy, const bf16* X, int ldx, 
   return cudaGetLastError() == cudaSuccess ? HMPCG_OK : HMPCG_E_CUDA;
 }
 
-static void ln_bwd(Net* N, const float* dy, int ldy, const float* x, const float* mu, const float* rs, int64_t goff,
-                   int64_t boff, int Tn, float* dx, int acc, cudaStream_t st) {
+static int ln_bwd(Net* N, const float* dy, int ldy, const float* x, const float* mu, const float* rs, int64_t goff,
+                  int64_t boff, int Tn, float* dx, int acc, cudaStream_t st) {
   Train* T = N->tr;
   const int d = N->cfg.d_model;
-  const int nb = (Tn + 7) / 8;
+  auto al16 = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+  if (d % 4 || d > 256 || ldy % 4 || !al16(dy) || !al16(x) || !al16(dx)) return HMPCG_E_SHAPE;
+  const int nb = (Tn + kLnTok - 1) / kLnTok;
   layernorm_bwd_kernel<<<nb, 256, 0, st>>>(dy, ldy, x, mu, rs, N->w32 + goff, Tn, d, dx, acc, T->lnpart);
   // lnpart rows are [dgamma (d) | dbeta (d)]; gamma and beta are adjacent in the blob
   (void)boff;
   reduce_parts(T, T->lnpart, nb, 2 * d, N->grad + goff, 0, st);
+  return HMPCG_OK;
 }
 
 #define TR_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
@@ -296,7 +299,8 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
   TR_TRY(linear_bwd(N, T->doffo, 2 * r, N->yf[1], d, To, 2 * r, d, o.offw, o.offb, dyf1, 0, st));
   for (int s = 0; s < 2; ++s) {
     const int Tt = s == 0 ? Td : To;
-    ln_bwd(N, s == 0 ? dyf0 : dyf1, d, N->x_final[s], N->muf[s], N->rsf[s], o.lnfg[s], o.lnfb[s], Tt, T->gx[s], 0, st);
+    TR_TRY(ln_bwd(N, s == 0 ? dyf0 : dyf1, d, N->x_final[s], N->muf[s], N->rsf[s], o.lnfg[s], o.lnfb[s], Tt, T->gx[s], 0,
+                  st));
   }
   // ---- transformer layers, last to first
   for (int l = cf.n_layers - 1; l >= 0; --l) {
@@ -323,7 +327,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
       const BlockOff& bo = o.blk[s][l];
       const int Tt = s == 0 ? Td : To;
       const int Wn = s == 0 ? L : r;
-      ln_bwd(N, T->gY[s], d, a.x_mid, a.mu2, a.rs2, bo.ln2g, bo.ln2b, Tt, T->gx[s], 1, st);
+      TR_TRY(ln_bwd(N, T->gY[s], d, a.x_mid, a.mu2, a.rs2, bo.ln2g, bo.ln2b, Tt, T->gx[s], 1, st));
       TR_TRY(linear_bwd(N, T->gx[s], d, a.o, d, Tt, d, d, bo.outw, bo.outb, T->gO[s], 0, st));
       TR_TRY(launch_attention_bwd(Wn, d / h, Tt, d, h, a.qkv, a.bias, a.lse, T->gO[s], T->gH[s], T->dbias, st));
       {
@@ -349,7 +353,7 @@ int net_train_step(Ctx* c, const hmpcg_system* systems, int nsys, int nz, float 
         }
       }
       TR_TRY(linear_bwd(N, T->gH[s], 3 * d, a.y1, d, Tt, 3 * d, d, bo.qkvw, bo.qkvb, T->gY[s], 0, st));
-      ln_bwd(N, T->gY[s], d, a.x_in, a.mu1, a.rs1, bo.ln1g, bo.ln1b, Tt, T->gx[s], 1, st);
+      TR_TRY(ln_bwd(N, T->gY[s], d, a.x_in, a.mu1, a.rs1, bo.ln1g, bo.ln1b, Tt, T->gx[s], 1, st));
     }
   }
   // ---- pool, GCN, encoder

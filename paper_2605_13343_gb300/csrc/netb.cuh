@@ -690,43 +690,78 @@ __global__ void gelu_bwd_kernel(float* __restrict__ g, const bf16* __restrict__ 
   if (i < n) g[i] *= gelu_grad(__bfloat162float(pre[i]));
 }
 
-// LayerNorm backward (warp per token): dx (+)= rs (dy g - mean(dy g) - xh mean(dy g xh));
-// per-CTA partials of dgamma = sum dy xh and dbeta = sum dy (8 tokens per CTA).
-__global__ void layernorm_bwd_kernel(const float* __restrict__ dy, int ldy, const float* __restrict__ x,
-                                     const float* __restrict__ mu, const float* __restrict__ rs,
-                                     const float* __restrict__ gam, int T, int d, float* __restrict__ dx,
-                                     int accumulate, float* __restrict__ gpart) {
-  __shared__ float pg[8][256], pb[8][256];
+// LayerNorm backward: dx (+)= rs (dy g - mean(dy g) - xh mean(dy g xh)); per-CTA partials of
+// dgamma = sum dy xh and dbeta = sum dy.  A CTA of 8 warps takes kLnTok tokens, a warp every
+// eighth of them, 4 channels per lane (d a multiple of 4, at most 256); each lane keeps its
+// channels' partial sums over its tokens in registers, and the warps' sums are added in a fixed
+// order at the end.
+constexpr int kLnTok = 64;
+__global__ void __launch_bounds__(256) layernorm_bwd_kernel(const float* __restrict__ dy, int ldy,
+                                                            const float* __restrict__ x, const float* __restrict__ mu,
+                                                            const float* __restrict__ rs, const float* __restrict__ gam,
+                                                            int T, int d, float* __restrict__ dx, int accumulate,
+                                                            float* __restrict__ gpart) {
+  __shared__ float4 pg[8][64], pb[8][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  const int per = d / 32;
-  float xh[8], g[8];
-  if (t < T) {
+  const int d4 = d >> 2;
+  float4 ag[2], ab[2], gm[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    ag[j] = ab[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int c4 = lane + 32 * j;
+    gm[j] = c4 < d4 ? make_float4(gam[4 * c4], gam[4 * c4 + 1], gam[4 * c4 + 2], gam[4 * c4 + 3])
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const float invd = 1.f / (float)d;
+  for (int tt = warp; tt < kLnTok; tt += 8) {
+    const int t = blockIdx.x * kLnTok + tt;
+    if (t >= T) break;
+    const float m = mu[t], r = rs[t];
+    float4 xh[2], g[2];
     float s1 = 0.f, s2 = 0.f;
-    for (int q = 0; q < per; ++q) {
-      const int c = lane + 32 * q;
-      xh[q] = (x[(size_t)t * d + c] - mu[t]) * rs[t];
-      g[q] = dy[(size_t)t * ldy + c];
-      const float gg = g[q] * gam[c];
-      s1 += gg;
-      s2 += gg * xh[q];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c4 = lane + 32 * j;
+      if (c4 < d4) {
+        const float4 xv = reinterpret_cast<const float4*>(x + (size_t)t * d)[c4];
+        g[j] = reinterpret_cast<const float4*>(dy + (size_t)t * ldy)[c4];
+        xh[j] = make_float4((xv.x - m) * r, (xv.y - m) * r, (xv.z - m) * r, (xv.w - m) * r);
+        const float4 gg = make_float4(g[j].x * gm[j].x, g[j].y * gm[j].y, g[j].z * gm[j].z, g[j].w * gm[j].w);
+        s1 += (gg.x + gg.y) + (gg.z + gg.w);
+        s2 += (gg.x * xh[j].x + gg.y * xh[j].y) + (gg.z * xh[j].z + gg.w * xh[j].w);
+      }
     }
-    s1 = warp_sum(s1) / d;
-    s2 = warp_sum(s2) / d;
-    for (int q = 0; q < per; ++q) {
-      const int c = lane + 32 * q;
-      const float v = rs[t] * (g[q] * gam[c] - s1 - xh[q] * s2);
-      dx[(size_t)t * d + c] = accumulate ? dx[(size_t)t * d + c] + v : v;
-      pg[warp][c] = g[q] * xh[q];
-      pb[warp][c] = g[q];
+    s1 = warp_sum(s1) * invd;
+    s2 = warp_sum(s2) * invd;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c4 = lane + 32 * j;
+      if (c4 < d4) {
+        float4 v = make_float4(r * (g[j].x * gm[j].x - s1 - xh[j].x * s2), r * (g[j].y * gm[j].y - s1 - xh[j].y * s2),
+                               r * (g[j].z * gm[j].z - s1 - xh[j].z * s2), r * (g[j].w * gm[j].w - s1 - xh[j].w * s2));
+        float4* o = reinterpret_cast<float4*>(dx + (size_t)t * d) + c4;
+        if (accumulate) {
+          const float4 p = *o;
+          v.x += p.x; v.y += p.y; v.z += p.z; v.w += p.w;
+        }
+        *o = v;
+        ag[j].x += g[j].x * xh[j].x; ag[j].y += g[j].y * xh[j].y; ag[j].z += g[j].z * xh[j].z; ag[j].w += g[j].w * xh[j].w;
+        ab[j].x += g[j].x; ab[j].y += g[j].y; ab[j].z += g[j].z; ab[j].w += g[j].w;
+      }
     }
-  } else {
-    for (int q = 0; q < per; ++q) { pg[warp][lane + 32 * q] = 0.f; pb[warp][lane + 32 * q] = 0.f; }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    pg[warp][lane + 32 * j] = ag[j];
+    pb[warp][lane + 32 * j] = ab[j];
   }
   __syncthreads();
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     float sg = 0.f, sbb = 0.f;
-    for (int q = 0; q < 8; ++q) { sg += pg[q][c]; sbb += pb[q][c]; }
+    for (int q = 0; q < 8; ++q) {
+      sg += reinterpret_cast<const float*>(&pg[q][0])[c];
+      sbb += reinterpret_cast<const float*>(&pb[q][0])[c];
+    }
     gpart[(size_t)blockIdx.x * 2 * d + c] = sg;
     gpart[(size_t)blockIdx.x * 2 * d + d + c] = sbb;
   }
