@@ -534,26 +534,39 @@ __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ 
   __shared__ float red[4][64];
   const int t0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
   if (vec) {
-    for (int q = threadIdx.x; q < 64 * 16; q += blockDim.x) {
+    // all of a thread's loads are issued before any is used (256 threads: 4 float4 each)
+    float4 v[4];
+    uint2 pr[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = threadIdx.x + 256 * i;
+      const int t = t0 + (q >> 4), n = n0 + 4 * (q & 15);
+      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      pr[i] = make_uint2(0u, 0u);
+      if (t < T && n < N) {
+        v[i] = *reinterpret_cast<const float4*>(dy + (size_t)t * ldy + n);
+        if (pre) pr[i] = *reinterpret_cast<const uint2*>(pre + (size_t)t * N + n);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = threadIdx.x + 256 * i;
       const int tt = q >> 4, nn = 4 * (q & 15);
       const int t = t0 + tt, n = n0 + nn;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (t < T && n < N) {
-        v = *reinterpret_cast<const float4*>(dy + (size_t)t * ldy + n);
         if (pre) {
-          const uint2 pr = *reinterpret_cast<const uint2*>(pre + (size_t)t * N + n);
-          const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&pr.x);
-          const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&pr.y);
-          v.x *= gelu_grad(__low2float(p01)); v.y *= gelu_grad(__high2float(p01));
-          v.z *= gelu_grad(__low2float(p23)); v.w *= gelu_grad(__high2float(p23));
+          const __nv_bfloat162 p01 = *reinterpret_cast<const __nv_bfloat162*>(&pr[i].x);
+          const __nv_bfloat162 p23 = *reinterpret_cast<const __nv_bfloat162*>(&pr[i].y);
+          v[i].x *= gelu_grad(__low2float(p01)); v[i].y *= gelu_grad(__high2float(p01));
+          v[i].z *= gelu_grad(__low2float(p23)); v[i].w *= gelu_grad(__high2float(p23));
         }
         if (d16) {
-          const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+          const __nv_bfloat162 a = __floats2bfloat162_rn(v[i].x, v[i].y), b = __floats2bfloat162_rn(v[i].z, v[i].w);
           *reinterpret_cast<uint2*>(d16 + (size_t)t * N + n) =
               make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
         }
       }
-      *reinterpret_cast<float4*>(&tile[tt][nn]) = v;
+      *reinterpret_cast<float4*>(&tile[tt][nn]) = v[i];
     }
   } else {
     for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
@@ -606,12 +619,18 @@ __global__ void __launch_bounds__(256) transpose_bf16_kernel(const bf16* __restr
   __shared__ __align__(16) bf16 tile[64][72];
   const int t0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
   if (vec) {
-    for (int q = threadIdx.x; q < 64 * 8; q += blockDim.x) {
-      const int tt = q >> 3, kk = 8 * (q & 7);
-      const int t = t0 + tt, k = k0 + kk;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (t < T && k < K) v = *reinterpret_cast<const uint4*>(x + (size_t)t * ld + k);
-      *reinterpret_cast<uint4*>(&tile[tt][kk]) = v;
+    uint4 v[2];   // 256 threads: two 16-byte loads each, both issued before either is stored
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = threadIdx.x + 256 * i;
+      const int t = t0 + (q >> 3), k = k0 + 8 * (q & 7);
+      v[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (t < T && k < K) v[i] = *reinterpret_cast<const uint4*>(x + (size_t)t * ld + k);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = threadIdx.x + 256 * i;
+      *reinterpret_cast<uint4*>(&tile[q >> 3][8 * (q & 7)]) = v[i];
     }
     __syncthreads();
     const bool v8 = (T % 8) == 0;
