@@ -309,23 +309,6 @@ int make_batch(const hmpcg_config& cf, const hmpcg_system* systems, int nsys, Sy
 }
 
 // ============================================================================ forward
-// Launch with programmatic stream serialisation: the forward kernels start with pdl_entry(),
-// so each may be scheduled while its predecessor in the stream finishes.
-template <class... KArgs, class... Args>
-static void pdl_launch(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... a) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = g;
-  cfg.blockDim = b;
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(a)...);
-}
-
 // Window attention launch: W tokens per window, head dim hd.
 static int launch_attention(int W, int hd, int T, int d, int h, const bf16* qkv, const float* bias, bf16* o, float* lse,
                             cudaStream_t s) {

@@ -3,6 +3,7 @@
 #pragma once
 #include <string>
 #include <vector>
+#include <utility>
 #include "ctx.cuh"
 
 namespace hm {
@@ -208,6 +209,23 @@ __device__ __forceinline__ void leaf_levels(const SysBatch& sb, int b, int k, Le
     rows += lgch >= lgL ? 1 : (sb.L >> lgch);
   }
   g.row0[sb.levels] = rows;
+}
+// Launch with programmatic stream serialisation: a kernel launched this way must start with
+// pdl_entry(), so that it may be scheduled while its predecessor in the stream finishes and still
+// reads that predecessor's results only after it has completed.
+template <class... KArgs, class... Args>
+inline void pdl_launch(void (*k)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st, Args&&... a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(a)...);
 }
 // staged row of level index q (0-based) for the leaf's node kk
 __device__ __forceinline__ int leaf_level_row(const LeafLevels& g, int q, int kk) {

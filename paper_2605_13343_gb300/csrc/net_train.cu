@@ -120,13 +120,13 @@ static void reduce_parts(Train* T, const float* part, int nparts, int64_t n, flo
   const int grid = (int)((n + 255) / 256);
   int G = 64;
   if (nparts <= G) {
-    reduce_parts_kernel<<<grid, 256, 0, st>>>(part, nparts, n, out, acc);
+    pdl_launch(reduce_parts_kernel, dim3(grid), dim3(256), 0, st, part, nparts, n, out, acc);
     return;
   }
   while ((int64_t)((nparts + G - 1) / G) * n > T->part2_cap) G *= 2;
   const int groups = (nparts + G - 1) / G;
-  reduce_parts_group_kernel<<<dim3(grid, groups), 256, 0, st>>>(part, nparts, G, n, T->part2);
-  reduce_parts_kernel<<<grid, 256, 0, st>>>(T->part2, groups, n, out, acc);
+  pdl_launch(reduce_parts_group_kernel, dim3(grid, groups), dim3(256), 0, st, part, nparts, G, n, T->part2);
+  pdl_launch(reduce_parts_kernel, dim3(grid), dim3(256), 0, st, (const float*)T->part2, groups, n, out, acc);
 }
 
 // Backward of y = x W^T + b for x: BF16 [T][Kin] (row stride ldx), dY: FP32 [T][Nout].
@@ -138,11 +138,11 @@ static int linear_bwd(Net* N, const float* dY, int ldy, const bf16* X, int ldx, 
   Train* T = N->tr;
   const int tb = (Tn + 63) / 64;
   const int vdy = ((uintptr_t)dY % 16 == 0 && ldy % 4 == 0 && Nout % 4 == 0 && (uintptr_t)gelu_pre % 8 == 0) ? 1 : 0;
-  prep_dy_kernel<<<dim3(tb, (Nout + 63) / 64), 256, 0, st>>>(dY, ldy, Tn, Nout, gelu_pre, T->d16, T->d16t,
-                                                             T->colpart, vdy);
+  pdl_launch(prep_dy_kernel, dim3(tb, (Nout + 63) / 64), dim3(256), 0, st, dY, ldy, Tn, Nout, gelu_pre, T->d16,
+             T->d16t, T->colpart, vdy);
   if (boff >= 0) reduce_parts(T, T->colpart, tb, Nout, N->grad + boff, 0, st);
   const int vx = ((uintptr_t)X % 16 == 0 && ldx % 8 == 0 && Kin % 8 == 0) ? 1 : 0;
-  transpose_bf16_kernel<<<dim3(tb, (Kin + 63) / 64), 256, 0, st>>>(X, ldx, Tn, Kin, T->xt, vx);
+  pdl_launch(transpose_bf16_kernel, dim3(tb, (Kin + 63) / 64), dim3(256), 0, st, X, ldx, Tn, Kin, T->xt, vx);
   {
     GemmArgs g;
     g.A = T->d16t; g.lda = Tn; g.B = T->xt; g.ldb = Tn;
@@ -176,7 +176,8 @@ static int ln_bwd(Net* N, const float* dy, int ldy, const float* x, const float*
   auto al16 = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
   if (d % 4 || d > 256 || ldy % 4 || !al16(dy) || !al16(x) || !al16(dx)) return HMPCG_E_SHAPE;
   const int nb = (Tn + kLnTok - 1) / kLnTok;
-  layernorm_bwd_kernel<<<nb, 256, 0, st>>>(dy, ldy, x, mu, rs, N->w32 + goff, Tn, d, dx, acc, T->lnpart);
+  pdl_launch(layernorm_bwd_kernel, dim3(nb), dim3(256), 0, st, dy, ldy, x, mu, rs, (const float*)(N->w32 + goff), Tn, d,
+             dx, acc, T->lnpart);
   // lnpart rows are [dgamma (d) | dbeta (d)]; gamma and beta are adjacent in the blob
   (void)boff;
   reduce_parts(T, T->lnpart, nb, 2 * d, N->grad + goff, 0, st);

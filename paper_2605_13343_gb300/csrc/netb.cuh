@@ -530,6 +530,7 @@ __global__ void pack_bwd_tiles_kernel(const SysBatch sb, const float* __restrict
 __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int N,
                                                       const bf16* __restrict__ pre, bf16* __restrict__ d16,
                                                       bf16* __restrict__ d16t, float* __restrict__ colpart, int vec) {
+  pdl_entry();
   __shared__ __align__(16) float tile[64][68];
   __shared__ float red[4][64];
   const int t0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
@@ -616,6 +617,7 @@ __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ 
 // 8 consecutive tokens.  Otherwise BF16 pairs (T, K and ld even).
 __global__ void __launch_bounds__(256) transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K,
                                                              bf16* __restrict__ xt, int vec) {
+  pdl_entry();
   __shared__ __align__(16) bf16 tile[64][72];
   const int t0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
   if (vec) {
@@ -690,6 +692,7 @@ HM_INLINE float sum_parts(const float* __restrict__ part, int p0, int p1, int64_
 }
 __global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int64_t n, float* __restrict__ out,
                                     int accumulate) {
+  pdl_entry();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   const float s = sum_parts(part, 0, nparts, n, j);
@@ -698,6 +701,7 @@ __global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, 
 // First stage of a two-stage column sum: CTA row blockIdx.y sums parts [y G, (y + 1) G).
 __global__ void reduce_parts_group_kernel(const float* __restrict__ part, int nparts, int G, int64_t n,
                                           float* __restrict__ out) {
+  pdl_entry();
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int p0 = blockIdx.y * G, p1 = min(nparts, p0 + G);
@@ -720,6 +724,7 @@ __global__ void __launch_bounds__(256) layernorm_bwd_kernel(const float* __restr
                                                             const float* __restrict__ rs, const float* __restrict__ gam,
                                                             int T, int d, float* __restrict__ dx, int accumulate,
                                                             float* __restrict__ gpart) {
+  pdl_entry();
   __shared__ float4 pg[8][64], pb[8][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d4 = d >> 2;
