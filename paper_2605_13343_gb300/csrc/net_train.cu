@@ -138,11 +138,11 @@ static int linear_bwd(Net* N, const float* dY, int ldy, const bf16* X, int ldx, 
   Train* T = N->tr;
   const int tb = (Tn + 63) / 64;
   const int vdy = ((uintptr_t)dY % 16 == 0 && ldy % 4 == 0 && Nout % 4 == 0 && (uintptr_t)gelu_pre % 8 == 0) ? 1 : 0;
-  pdl_launch(prep_dy_kernel, dim3(tb, (Nout + 63) / 64), dim3(256), 0, st, dY, ldy, Tn, Nout, gelu_pre, T->d16,
+  pdl_launch(prep_dy_kernel, dim3(tb, (Nout + 63) / 64), dim3(kTileThreads), 0, st, dY, ldy, Tn, Nout, gelu_pre, T->d16,
              T->d16t, T->colpart, vdy);
   if (boff >= 0) reduce_parts(T, T->colpart, tb, Nout, N->grad + boff, 0, st);
   const int vx = ((uintptr_t)X % 16 == 0 && ldx % 8 == 0 && Kin % 8 == 0) ? 1 : 0;
-  pdl_launch(transpose_bf16_kernel, dim3(tb, (Kin + 63) / 64), dim3(256), 0, st, X, ldx, Tn, Kin, T->xt, vx);
+  pdl_launch(transpose_bf16_kernel, dim3(tb, (Kin + 63) / 64), dim3(kTileThreads), 0, st, X, ldx, Tn, Kin, T->xt, vx);
   {
     GemmArgs g;
     g.A = T->d16t; g.lda = Tn; g.B = T->xt; g.ldb = Tn;

@@ -521,13 +521,14 @@ __global__ void pack_bwd_tiles_kernel(const SysBatch sb, const float* __restrict
 }
 
 // ------------------------------------------------------------------ generic helpers
+constexpr int kTileThreads = 256;   // threads of the 64 x 64 tile kernels below (their index maps assume it)
 // dY (FP32, T x N, row stride ldy) -> BF16 copy (T x N), BF16 transpose (N x T), and
 // per-64-token column sums (bias gradient partials, four 16-row sums added pairwise).  With pre
 // (BF16 T x N, the pre-activation of a GELU whose output the layer read) dY is first multiplied
 // by GELU'(pre) in FP32: the activation's backward folded into this pass.  A 64 x 64 tile per
 // CTA.  vec (dy 16-byte aligned, ldy and N multiples of 4): float4 loads and 8-byte BF16
 // stores; T a multiple of 8 as well: the transpose is stored 8 tokens (16 bytes) at a time.
-__global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int N,
+__global__ void __launch_bounds__(kTileThreads) prep_dy_kernel(const float* __restrict__ dy, int ldy, int T, int N,
                                                       const bf16* __restrict__ pre, bf16* __restrict__ d16,
                                                       bf16* __restrict__ d16t, float* __restrict__ colpart, int vec) {
   pdl_entry();
@@ -535,12 +536,12 @@ __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ 
   __shared__ float red[4][64];
   const int t0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
   if (vec) {
-    // all of a thread's loads are issued before any is used (256 threads: 4 float4 each)
+    // all of a thread's loads are issued before any is used (4 float4 each)
     float4 v[4];
     uint2 pr[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int q = threadIdx.x + 256 * i;
+      const int q = threadIdx.x + kTileThreads * i;
       const int t = t0 + (q >> 4), n = n0 + 4 * (q & 15);
       v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       pr[i] = make_uint2(0u, 0u);
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ 
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int q = threadIdx.x + 256 * i;
+      const int q = threadIdx.x + kTileThreads * i;
       const int tt = q >> 4, nn = 4 * (q & 15);
       const int t = t0 + tt, n = n0 + nn;
       if (t < T && n < N) {
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ 
   }
   if (colpart) {
     {
-      const int nn = threadIdx.x & 63, gq = threadIdx.x >> 6;   // 256 threads: 64 columns x 4 row groups
+      const int nn = threadIdx.x & 63, gq = threadIdx.x >> 6;   // 64 columns x 4 row groups
       float s = 0.f;
       for (int tt = 16 * gq; tt < 16 * gq + 16; ++tt) s += tile[tt][nn];
       red[gq][nn] = s;
@@ -615,23 +616,23 @@ __global__ void __launch_bounds__(256) prep_dy_kernel(const float* __restrict__ 
 // BF16 (T x K, row stride ld) -> BF16 transpose (K x T), a 64 x 64 tile per CTA.  vec (x 16-byte
 // aligned, ld and K multiples of 8): 16-byte loads; T a multiple of 8 as well: 16-byte stores of
 // 8 consecutive tokens.  Otherwise BF16 pairs (T, K and ld even).
-__global__ void __launch_bounds__(256) transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K,
+__global__ void __launch_bounds__(kTileThreads) transpose_bf16_kernel(const bf16* __restrict__ x, int ld, int T, int K,
                                                              bf16* __restrict__ xt, int vec) {
   pdl_entry();
   __shared__ __align__(16) bf16 tile[64][72];
   const int t0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
   if (vec) {
-    uint4 v[2];   // 256 threads: two 16-byte loads each, both issued before either is stored
+    uint4 v[2];   // two 16-byte loads each, both issued before either is stored
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int q = threadIdx.x + 256 * i;
+      const int q = threadIdx.x + kTileThreads * i;
       const int t = t0 + (q >> 3), k = k0 + 8 * (q & 7);
       v[i] = make_uint4(0u, 0u, 0u, 0u);
       if (t < T && k < K) v[i] = *reinterpret_cast<const uint4*>(x + (size_t)t * ld + k);
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-      const int q = threadIdx.x + 256 * i;
+      const int q = threadIdx.x + kTileThreads * i;
       *reinterpret_cast<uint4*>(&tile[q >> 3][8 * (q & 7)]) = v[i];
     }
     __syncthreads();
