@@ -284,7 +284,8 @@ int hmpcg_set_highways(void* ctx, int32_t on);
  * threads) race on it and must be serialised by the caller. */
 int hmpcg_apply_noalloc(const hmpcg_factors* f, const float* r, float* z, void* stream);
 
-/* The tensor-core GEMM the network runs on (tcgen05, TMA, TMEM accumulator):
+/* The tensor-core GEMM the network runs on (tcgen05 and TMA; persistent, one CTA per SM, two
+ * TMEM accumulators so that one output tile's epilogue overlaps the next tile's MMAs):
  * C[M x N] = A[M x K] B[N x K]^T (+ bias[N]) (GELU if act == 1), A and B
  * row-major BF16 with K contiguous (K % 64 == 0, N % 16 == 0, 16-byte aligned
  * rows), C row-major FP32.  Exposed for kernel-level tests and measurement. */
